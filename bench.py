@@ -1,0 +1,395 @@
+"""Benchmark of the differentiable MLS-MPM hot path (forward + reverse tape) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cube3d|robots3d|...]
+    python bench.py --impl reference ...     # the FP64 CPU oracle, timed on host cores
+
+One bench step = one pass of the whole hot path on one batch: set the initial state,
+forward T MLS-MPM steps with checkpoints, centre-of-mass loss, backward through the
+tape (segment re-simulation, per-step grid recompute, adjoint kernels), gradients out.
+The metric is particle-steps per second of forward+backward (N particles x T steps per
+bench step).  `value` is measured with the inputs already on the device; `e2e` times
+the same step through the public API from pinned host buffers, the host<->device copies
+inside the timed region.  Prints one JSON line (rank 0).
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload (independent
+scenes; no collective on the data path) -- weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s fwd+bwd (3D MLS-MPM, FP32 bulk, FP64 polar)"
+UNIT = "particle-steps/s"
+
+# algorithmic bytes per unit of each kernel category (3D, FP32 state rows):
+#   particle passes: per particle; node passes: per node of the touched box.
+# x, v: 12 B each; C, F: 36 B each; mu, la: 8 B; full state 96 B.
+ALG_BYTES_3D = {
+    "p2g": 96 + 8,                       # read x, v, C, F, mu, la
+    "g2p_p2g": 48 + 8 + 48,              # read x, F, mu, la; write x, F
+    "g2p_p2g_full": 48 + 8 + 96,         # read x, F, mu, la; write x, v, C, F
+    "g2p": 48 + 96,                      # read x, F; write the full state
+    "adj_g2p": 96 + 48 + 48 + 48,        # read adj, C', x, F; write adj x, F
+    "adj_fused": 96 + 48 + 48 + 8 + 16 + 48,  # state s+1, x F of state s, adj x F, mu la,
+                                              # mubar labar (rw), write adj x F
+    "adj_p2g": 96 + 48 + 8 + 16 + 96,
+    "grid_update": 16 + 16 + 16,         # read (m, p), write (u, m), clear (m, p)
+    "grid_adj": 16 + 16 + 16 + 16,       # read ubar, (u, m); write (pbar, mbar), clear ubar
+}
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name):
+    from paper_1910_00935_gb300 import scenes
+    scene = scenes.make(name)
+    d = scene["desc"]
+    N = sum(d["n_particles"])
+    descr = {
+        "cube3d": "3D elastic cube: 262,144 particles (64^3 lattice, 2/cell/axis), 128^3 grid, "
+                  "neo-Hookean E=5e3 nu=0.3, dt=1e-4, T=1024, checkpoint every 64, COM loss",
+        "robots3d": "16 batched 3D actuated robots x 65,536 particles, 64^3 grids, "
+                    "fixed-corotated (FP64 polar), 8 groups x 4 sine terms, T=2048, ckpt 64",
+        "rects2d": "64 batched 2D rectangles (1k-16k particles), 128^2 grids, T=512",
+        "square2d_grad": "2D square 4,096 particles, 128^2 grid, T=512, ckpt 32",
+    }.get(name, name)
+    return scene, N, d["steps"], descr
+
+
+def cpu_baseline(name, seconds_hint=20.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the full
+    particle set for a few steps of forward + reverse (1 host thread)."""
+    import oracle
+    from paper_1910_00935_gb300 import scenes
+    scene, N, T, _ = make_workload(name)
+    sample_T = {"cube3d": 2, "robots3d": 1, "rects2d": 4, "square2d_grad": 32}.get(name, 2)
+    if name == "robots3d":  # one of the 16 independent scenes
+        from paper_1910_00935_gb300.scenes import actuated_robots_3d
+        scene = actuated_robots_3d(n_scenes=1)
+        N = sum(scene["desc"]["n_particles"])
+    t0 = time.perf_counter()
+    oracle.loss_and_grad(scenes.oracle_view(scene), sample_T)
+    dt = time.perf_counter() - t0
+    return {"value": N * sample_T / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{N} particles x {sample_T} steps forward+backward of {name}",
+            "seconds": round(dt, 3), "units": N * sample_T}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    name = args.workload
+    _, N, T, descr = make_workload(name)
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(name)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+            cb = r
+    ms = 1e3 * sum(times) / len(times)
+    value = cb["units"] / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": descr, "particles": N, "T": T},
+            "cpu_baseline": {**cb, "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube3d")
+    ap.add_argument("--T", type=int, default=0, help="override the workload's step count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1910_00935_gb300 import build as mbuild
+    if rank == 0 or world == 1:
+        mbuild.build()
+    if world > 1:
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+        torch.cuda.set_device(local_rank)
+        dist.barrier()
+        mbuild.build()
+    else:
+        torch.cuda.set_device(0)
+    from paper_1910_00935_gb300 import mpm
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    scene, N, T, descr = make_workload(args.workload)
+    if args.T:
+        T = args.T
+    desc = scene["desc"]
+    a = scene["arrays"]
+    G = desc.get("n_groups", 0)
+    sim = mpm.Simulator(desc, T, device=dev)
+    names = ["x0", "v0", "C0", "F0", "E", "nu"]
+    host = {k: torch.as_tensor(a[k]).pin_memory() for k in names + ["target"]}
+    if G:
+        host["group"] = torch.as_tensor(a["group"]).pin_memory()
+        host["w"] = torch.as_tensor(a["w"]).pin_memory()
+    devin = {k: v.to(dev) for k, v in host.items()}
+    stream = torch.cuda.current_stream()
+
+    def device_step():
+        mpm.mpm_set_initial(sim.h, devin["x0"], devin["v0"], devin["C0"], devin["F0"], devin["E"],
+                            devin["nu"], devin.get("group"), devin.get("w"))
+        mpm.mpm_forward(sim.h, T)
+        mpm.mpm_loss(sim.h, desc["loss_kind"], devin["target"], bufs["loss"], bufs["gT"], bufs["g0"])
+        mpm.mpm_backward(sim.h, bufs["gT"], None, None, None, bufs["gx0"], bufs["gv0"], None, None,
+                         bufs["gE"], bufs["gnu"], bufs["gw"] if G else None)
+
+    d = desc["dim"]
+    S = len(desc["n_particles"])
+    bufs = {k: torch.empty(*shape, device=dev) for k, shape in
+            (("loss", (S,)), ("gT", (d, N)), ("g0", (d, N)), ("gx0", (d, N)), ("gv0", (d, N)),
+             ("gE", (N,)), ("gnu", (N,)), ("gw", (S, max(G, 1), max(desc.get("n_basis", 0), 1))))}
+
+    # L2 flush buffer (larger than the 129 MB L2), written between timed iterations
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        device_step()
+    torch.cuda.synchronize()
+    rc = mpm.mpm_sync_status(sim.h)
+    if rc != mpm.MPM_OK:
+        raise RuntimeError(f"device error during warm-up: {mpm.mpm_last_error(sim.h)}")
+
+    # ---- timed region: device-resident inputs ----
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    launches0 = sim.info(mpm.MPM_INFO_KERNEL_LAUNCHES)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        flush.fill_(1)
+        e0.record(stream)
+        device_step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = sim.info(mpm.MPM_INFO_KERNEL_LAUNCHES) - launches0
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / args.steps
+    clk = clocks.stop() if clocks else None
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * T / (ms / 1e3)
+
+    # ---- forward-only throughput (same inputs, same stream) ----
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    mpm.mpm_set_initial(sim.h, devin["x0"], devin["v0"], devin["C0"], devin["F0"], devin["E"],
+                        devin["nu"], devin.get("group"), devin.get("w"))
+    f0.record(stream)
+    mpm.mpm_forward(sim.h, T)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1)
+
+    # ---- e2e: host buffers through the public API, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        out_host = {k: torch.empty_like(bufs[k], device="cpu").pin_memory()
+                    for k in ("loss", "gv0", "gx0", "gE", "gnu", "gw")}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = sum(v.numel() * v.element_size() for k, v in out_host.items() if G or k != "gw")
+
+        def e2e_step():
+            for k, v in host.items():
+                devin[k].copy_(v, non_blocking=True)
+            device_step()
+            for k, v in out_host.items():
+                if G or k != "gw":
+                    v.copy_(bufs[k], non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        times = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            times.append(time.perf_counter() - t0)
+        e_ms = 1e3 * sum(times) / len(times)
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * N * T / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- live per-kernel timing: CUDA events around every launch on its stream ----
+    sim.set_option(mpm.MPM_OPT_PROFILE, 1)
+    flush.fill_(1)
+    device_step()
+    torch.cuda.synchronize()
+    prof = sim.profile()
+    sim.set_option(mpm.MPM_OPT_PROFILE, 0)
+    rc = mpm.mpm_sync_status(sim.h)
+    if rc != mpm.MPM_OK:
+        raise RuntimeError(f"device error: {mpm.mpm_last_error(sim.h)}")
+    total_prof = sum(ms_ for _, ms_ in prof.values()) or 1.0
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_launch, dom_ms = prof[dom]
+    hbm, peak_src = measured_peaks()
+    alg = ALG_BYTES_3D if desc["dim"] == 3 else None
+    per_unit = alg.get(dom) if alg else None
+    units = N  # particle passes process every particle once
+    roof = None
+    if per_unit and n_launch:
+        avg_ms = dom_ms / n_launch
+        achieved = per_unit * units / (avg_ms / 1e3) / 1e9
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", f"traffic_{args.workload}_{dom}.json")
+        if os.path.exists(tpath):
+            try:
+                traffic = json.load(open(tpath)).get("bytes_per_launch")
+            except Exception:
+                traffic = None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
+                "alg_bytes_per_launch": per_unit * units, "avg_launch_ms": avg_ms,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                else "fallback 6.8 TB/s",
+                "share_of_step": dom_ms / total_prof}
+
+    if rank != 0:
+        return
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cb = cpu_baseline(args.workload)
+        except Exception as e:  # the oracle needs gcc; report, never fake
+            cb = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": str(e)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": descr, "particles": N, "scenes": S, "T": T,
+                   "ckpt_every": desc["ckpt_every"], "grid": f"{desc['n_grid']}^{desc['dim']}",
+                   "l2": "flushed between timed iterations (512 MiB write)",
+                   "precision": "FP32 state/grid, FP64 polar decomposition",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "forward": {"value": N * T / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernel_times_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
+        "cpu_baseline": cb,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * mpm.h -- C ABI of libmpm.so, the GB300 (sm_103a) differentiable MLS-MPM
+ * elastic-object simulator: the hot path of DiffTaichi's diffmpm (Section 4.1 and
+ * Appendix D of "DiffTaichi: Differentiable Programming for Physical Simulation").
+ *
+ * What the library computes
+ *   One time step (Appendix D, "advance"): clear the grid, P2G scatter of mass and
+ *   APIC/MLS momentum with quadratic B-spline weights and the Kirchhoff stress
+ *   folded into the affine matrix, grid update (momentum/mass + dt g, sticky walls),
+ *   G2P gather of velocity and affine matrix C, x' = x + dt v', F' = (I + dt C') F.
+ *   The reverse pass is the light-weight tape of Section 3.2: the forward stores
+ *   the full particle state every ckpt_every steps (Appendix D.2); mpm_backward
+ *   re-simulates each segment and replays the step adjoints in reverse order,
+ *   recomputing each step's grid (Appendix D.1, "advance_grad").
+ *   Materials: fixed-corotated (polar factor and its adjoint in FP64) or
+ *   neo-Hookean; optional actuation stress a_g(t) (F e)(F e)^T with
+ *   a_g(t) = sum_k w_gk sin(2 pi k t / act_period + act_phase), k = 1..n_basis.
+ *
+ * Conventions (every entry point)
+ *   - Returns an int status (MPM_OK = 0 or an MPM_ERR_* code); no exception
+ *     crosses the ABI.  mpm_last_error() gives a message for the last failure.
+ *   - Pointers named "device" are CUDA device pointers; "host" are host pointers.
+ *   - Per-particle arrays are float32, component-major: a[c * N + p] with N the
+ *     total particle count; scenes are concatenated in particle order.  Vectors
+ *     have dim components, matrices dim*dim (row-major within a particle: C[i][j]
+ *     is component i*dim + j).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     asynchronous on that stream; device-side errors (a particle's stencil
+ *     leaving the grid, non-finite values, det F <= 0, a bounded wait running out)
+ *     are sticky in the handle and reported by mpm_sync_status().
+ *   - Ownership: the library allocates no device memory.  The caller provides one
+ *     device workspace (size from mpm_workspace_bytes) at create time and owns it;
+ *     it must outlive the handle.  Inputs are copied into the workspace; outputs
+ *     go to caller-allocated buffers.  The handle itself is a small host object.
+ */
+#ifndef MPM_H_
+#define MPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MPM_OK 0
+#define MPM_ERR_ARG 1        /* invalid argument (NULL handle, bad size, ...) */
+#define MPM_ERR_CUDA 2       /* a CUDA runtime call failed */
+#define MPM_ERR_OOB 3        /* a particle's 3^dim stencil left [0, n_grid-1] */
+#define MPM_ERR_NONFINITE 4  /* non-finite state or det F <= 0 */
+#define MPM_ERR_TIMEOUT 5    /* a bounded device-side wait gave up */
+#define MPM_ERR_STATE 6      /* call out of order (backward before forward, T > max) */
+#define MPM_ERR_WORKSPACE 7  /* workspace NULL, misaligned or too small */
+
+/* materials */
+#define MPM_FIXED_COROTATED 0
+#define MPM_NEO_HOOKEAN 1
+
+/* losses computed by mpm_loss (the compute_loss pattern of Section 3.2) */
+#define MPM_LOSS_COM_TARGET 0 /* L_s = |COM_s(x_T) - target_s|^2 */
+#define MPM_LOSS_COM_X_DISP 1 /* L_s = -(COM_s,x(x_T) - COM_s,x(x_0)) */
+
+/* options for mpm_set_option (tuning knobs; defaults in brackets) */
+#define MPM_OPT_USE_GRAPHS 1      /* capture forward/backward into CUDA graphs [1] */
+#define MPM_OPT_SMEM_TILE 2       /* P2G scatters through shared-memory grid tiles [1] */
+#define MPM_OPT_TILE_CAPACITY 3   /* max nodes of one CTA's shared tile [1024] */
+#define MPM_OPT_PROFILE 4         /* 1: time every kernel launch with CUDA events on its
+                                     stream (launches go unbatched, no graphs) [0];
+                                     setting it clears the collected timings */
+
+/* kernel categories for mpm_get_profile */
+#define MPM_KERNEL_P2G 1          /* P2G from a full state (segment starts, grid recompute) */
+#define MPM_KERNEL_G2P_P2G 2      /* fused G2P of step t-1 + P2G of step t, x and F written */
+#define MPM_KERNEL_G2P_P2G_FULL 3 /* same, full state written (checkpoints, re-simulation) */
+#define MPM_KERNEL_G2P 4          /* last G2P of a run or segment, full state written */
+#define MPM_KERNEL_GRID_UPDATE 5  /* grid_op over each scene's touched box */
+#define MPM_KERNEL_ADJ_G2P 6      /* G2P adjoint from the seeds (step T-1) */
+#define MPM_KERNEL_ADJ_FUSED 7    /* P2G adjoint of step s+1 + G2P adjoint of step s */
+#define MPM_KERNEL_ADJ_P2G 8      /* P2G adjoint of step 0 */
+#define MPM_KERNEL_GRID_ADJ 9     /* grid_op adjoint over each scene's touched box */
+
+/* queries for mpm_get_info */
+#define MPM_INFO_KERNEL_LAUNCHES 1 /* kernels launched by this handle so far */
+#define MPM_INFO_N_TOTAL 2         /* total particles N */
+#define MPM_INFO_STEPS_RECORDED 3  /* T of the last mpm_forward (0 = none) */
+
+typedef struct mpm_handle mpm_handle;
+
+/* Scene description, copied at create.  Every scene of a batch shares these
+ * scalars; each has its own dense n_grid^dim grid on [0,1]^dim. */
+typedef struct mpm_scene_desc {
+  int32_t dim;                 /* 2 or 3 */
+  int32_t n_grid;              /* grid nodes per axis, 8..1024; dx = 1/n_grid */
+  int32_t n_scenes;            /* >= 1 independent scenes */
+  const int64_t* n_particles;  /* host [n_scenes], each >= 1 */
+  float dt;                    /* time step */
+  float gravity[3];            /* added as dt*g in the grid update */
+  int32_t wall_cells;          /* sticky walls: node i with any i_k < wall or i_k >= n-wall gets v = 0 */
+  int32_t material;            /* MPM_FIXED_COROTATED or MPM_NEO_HOOKEAN */
+  float rho;                   /* density; particle volume (dx/2)^dim, mass rho*volume */
+  int32_t ckpt_every;          /* k: full state stored every k steps (Appendix D.2), >= 1 */
+  int32_t n_groups;            /* actuator groups, 0..8 (0 = no actuation) */
+  int32_t n_basis;             /* sine terms per group, 0..8 */
+  float act_period;            /* P of sin(2 pi k t / P + phase), t = step index */
+  float act_phase;
+  int32_t deterministic_p2g;   /* reserved: must be 0 */
+} mpm_scene_desc;
+
+/* Device bytes the workspace needs for this description and at most max_steps
+ * steps per forward (checkpoints, one segment buffer, adjoints, four grids per
+ * scene, sort scratch).  out_bytes: host. */
+int mpm_workspace_bytes(const mpm_scene_desc* desc, int32_t max_steps, size_t* out_bytes);
+
+/* Create a handle.  workspace: device, >= mpm_workspace_bytes bytes, 256-byte
+ * aligned, owned by the caller.  out: host, receives the handle. */
+int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_bytes,
+               int32_t max_steps, mpm_handle** out);
+
+/* Copy the initial state in (device pointers, component-major, N particles).
+ * C0 may be NULL (zero), F0 NULL (identity).  E, nu: Young's modulus and Poisson
+ * ratio per particle.  group: int32 [N] actuator group in [0, n_groups) (NULL if
+ * n_groups == 0); w: float [n_scenes][n_groups][n_basis] actuation weights.
+ * Particles are reordered internally by a spatial (Morton) key per scene so that
+ * P2G tiles are compact; all outputs come back in the caller's order.
+ * Invalidates any recorded forward. */
+int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float* C0,
+                    const float* F0, const float* E, const float* nu, const int32_t* group,
+                    const float* w, void* stream);
+
+/* Run T steps (1 <= T <= max_steps) from the initial state and record the tape.
+ * Stores the full state at steps 0, k, 2k, ... (k = ckpt_every). */
+int mpm_forward(mpm_handle* h, int32_t T, void* stream);
+
+/* Copy the state at step T of the last forward to caller buffers (device,
+ * component-major, caller order).  Any pointer may be NULL. */
+int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* stream);
+
+/* Centre-of-mass loss of every scene on the state at step T (FP64 accumulation).
+ * target: device float [n_scenes][dim] (MPM_LOSS_COM_TARGET; else may be NULL).
+ * loss: device float [n_scenes].  dL_dxT: device float [dim][N], the seed of
+ * dL/dx_T.  dL_dx0: device float [dim][N] or NULL, the direct dependence of the
+ * loss on x_0 (nonzero only for MPM_LOSS_COM_X_DISP; add it to mpm_backward's gx0). */
+int mpm_loss(mpm_handle* h, int32_t kind, const float* target, float* loss, float* dL_dxT,
+             float* dL_dx0, void* stream);
+
+/* Reverse pass of the last forward (the tape is replayed in reverse, Section 3.2):
+ * given dL/dstate_T (device, caller order; any of the four may be NULL = zero),
+ * write dL/dstate_0 (gx0, gv0, gC0, gF0: device [dim|dim*dim][N]), dL/dE and dL/dnu
+ * (device [N]) and dL/dw (device [n_scenes][n_groups][n_basis]).  Any output may be
+ * NULL.  May be called more than once per forward. */
+int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const float* dL_dC,
+                 const float* dL_dF, float* gx0, float* gv0, float* gC0, float* gF0,
+                 float* gE, float* gnu, float* gw, void* stream);
+
+/* Wait for the handle's last stream and return the first sticky device error
+ * (MPM_OK, MPM_ERR_OOB, MPM_ERR_NONFINITE, MPM_ERR_TIMEOUT) or MPM_ERR_CUDA;
+ * clears the device error word. */
+int mpm_sync_status(mpm_handle* h);
+
+/* Set a tuning knob (MPM_OPT_*); drops any cached CUDA graphs. */
+int mpm_set_option(mpm_handle* h, int32_t key, int64_t value);
+
+/* Read a counter (MPM_INFO_*). value: host. */
+int mpm_get_info(mpm_handle* h, int32_t key, int64_t* value);
+
+/* Timings collected while MPM_OPT_PROFILE is on: launches of kernel category
+ * `kind` (MPM_KERNEL_*) and their summed device time in milliseconds.  Waits for the
+ * recorded events.  launches, total_ms: host. */
+int mpm_get_profile(mpm_handle* h, int32_t kind, int64_t* launches, double* total_ms);
+
+/* Message of the last failure on this handle (static storage if h is NULL). */
+const char* mpm_last_error(mpm_handle* h);
+
+/* Destroy the handle (host objects and CUDA graphs; the workspace stays the caller's). */
+void mpm_destroy(mpm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPM_H_ */

@@ -1,0 +1,726 @@
+// mpm_api.cu -- the C ABI of libmpm.so (declared in include/mpm.h): workspace
+// layout, handle, and the light-weight tape of Section 3.2 with the checkpointing
+// of Appendix D.
+//
+// Tape.  The forward of T steps only records T (and therefore the actuation time
+// of every step); the particle state itself is stored every k = ckpt_every steps
+// (Appendix D.2, segment-wise recomputation).  The backward walks s = T-1 .. 0;
+// entering a segment it re-simulates the segment from its checkpoint into one
+// segment buffer, then for each step recomputes that step's grid (Appendix D.1)
+// and runs the fused adjoint pass [P2G-adjoint of step s+1 | G2P-adjoint of step
+// s] followed by the grid adjoint of step s.
+//
+// Launch sequences are captured into CUDA graphs (one per forward length T and one
+// per backward length), cached on the handle and replayed on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "mpm_internal.h"
+#include "mpm_kernels.cuh"
+
+using namespace mpm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t perm, keys0, keys1, idx0, sort_tmp, sort_tmp_bytes;
+  size_t tiles, scene_off;
+  size_t mu, la, E, nu, group, wact, wbar, mubar, labar;
+  size_t fin, cur, ckpt, seg, adj;
+  size_t PM, U, UB, PBM;
+  size_t bbox, bbox_u, done, err, com;
+  size_t total;
+};
+
+struct Dims {
+  int D, Q, S, K, n_ckpt, n_tiles, n_grid;
+  int64_t N, nnodes;
+};
+
+bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
+  auto fail = [&](const char* m) {
+    if (why) *why = m;
+    return false;
+  };
+  if (!d) return fail("desc is NULL");
+  if (d->dim != 2 && d->dim != 3) return fail("dim must be 2 or 3");
+  if (d->n_grid < 8 || d->n_grid > 1024) return fail("n_grid must be in [8, 1024]");
+  if (d->n_scenes < 1 || d->n_scenes > 65535) return fail("n_scenes must be in [1, 65535]");
+  if (!d->n_particles) return fail("n_particles is NULL");
+  int64_t N = 0;
+  for (int s = 0; s < d->n_scenes; ++s) {
+    if (d->n_particles[s] < 1) return fail("every scene needs >= 1 particle");
+    N += d->n_particles[s];
+  }
+  if (N > (int64_t)INT32_MAX / 32) return fail("too many particles");
+  if (!(d->dt > 0.0f) || !std::isfinite(d->dt)) return fail("dt must be > 0");
+  if (d->wall_cells < 0 || 2 * d->wall_cells >= d->n_grid) return fail("bad wall_cells");
+  if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN)
+    return fail("unknown material");
+  if (!(d->rho > 0.0f)) return fail("rho must be > 0");
+  if (d->ckpt_every < 1) return fail("ckpt_every must be >= 1");
+  if (d->n_groups < 0 || d->n_groups > kMaxGroups) return fail("n_groups must be in [0, 8]");
+  if (d->n_basis < 0 || d->n_basis > kMaxBasis) return fail("n_basis must be in [0, 8]");
+  if (d->n_groups > 0 && (d->n_basis < 1 || !(d->act_period != 0.0f)))
+    return fail("actuation needs n_basis >= 1 and act_period != 0");
+  if (d->deterministic_p2g != 0) return fail("deterministic_p2g is reserved (must be 0)");
+  if (max_steps < 1) return fail("max_steps must be >= 1");
+  if (max_steps > (1 << 24)) return fail("max_steps too large");
+  return true;
+}
+
+Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
+  Dims m;
+  m.D = d->dim;
+  m.Q = 2 * m.D + 2 * m.D * m.D;
+  m.S = d->n_scenes;
+  m.K = d->ckpt_every < max_steps ? d->ckpt_every : max_steps;
+  m.n_ckpt = (max_steps - 1) / m.K + 1;  // states 0, K, 2K, ... < max_steps
+  m.n_grid = d->n_grid;
+  m.nnodes = 1;
+  for (int a = 0; a < m.D; ++a) m.nnodes *= d->n_grid;
+  m.N = 0;
+  m.n_tiles = 0;
+  for (int s = 0; s < m.S; ++s) {
+    m.N += d->n_particles[s];
+    m.n_tiles += (int)((d->n_particles[s] + kTile - 1) / kTile);
+  }
+  return m;
+}
+
+Layout make_layout(const Dims& m) {
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + (bytes ? bytes : 1));
+    return at;
+  };
+  const size_t N = (size_t)m.N, Q = (size_t)m.Q, S = (size_t)m.S;
+  L.perm = take(N * 4);
+  L.keys0 = take(N * 8);
+  L.keys1 = take(N * 8);
+  L.idx0 = take(N * 4);
+  L.sort_tmp_bytes = sort_temp_bytes(m.N);
+  L.sort_tmp = take(L.sort_tmp_bytes);
+  L.tiles = take((size_t)m.n_tiles * sizeof(int4));
+  L.scene_off = take((S + 1) * 8);
+  L.mu = take(N * 4);
+  L.la = take(N * 4);
+  L.E = take(N * 4);
+  L.nu = take(N * 4);
+  L.group = take(N * 4);
+  L.wact = take(S * kMaxGroups * kMaxBasis * 4);
+  L.wbar = take(S * kMaxGroups * kMaxBasis * 4);
+  L.mubar = take(N * 4);
+  L.labar = take(N * 4);
+  L.fin = take(Q * N * 4);
+  L.cur = take(Q * N * 4);
+  L.ckpt = take((size_t)m.n_ckpt * Q * N * 4);
+  L.seg = take((size_t)(m.K + 1) * Q * N * 4);
+  L.adj = take(Q * N * 4);
+  const size_t grid = S * (size_t)m.nnodes * sizeof(float4);
+  L.PM = take(grid);
+  L.U = take(grid);
+  L.UB = take(grid);
+  L.PBM = take(grid);
+  L.bbox = take(S * 8 * 4);
+  L.bbox_u = take(S * 8 * 4);
+  L.done = take(4);
+  L.err = take(4);
+  L.com = take(S * 6 * 8);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+struct mpm_handle {
+  mpm_scene_desc desc;
+  std::vector<int64_t> n_particles;
+  int32_t max_steps = 0;
+  Dims m;
+  Layout L;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool initialized = false;
+  int32_t T_recorded = 0;
+  // options
+  bool use_graphs = true;
+  bool smem_tile = true;
+  int tile_capacity = 1024;
+  // graphs
+  cudaStream_t cap_stream = nullptr;
+  std::map<int64_t, std::pair<cudaGraphExec_t, int64_t>> graphs;  // key -> (exec, launches)
+  int64_t launches = 0;
+  // live per-launch timing (MPM_OPT_PROFILE)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_records;
+  std::string last_error;
+  cudaStream_t last_stream = nullptr;
+
+  template <typename T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(ws + off);
+  }
+  float* state(size_t base, int slot) const {
+    return at<float>(base) + (size_t)slot * m.Q * m.N;
+  }
+};
+
+namespace {
+
+thread_local std::string g_static_error;
+
+int fail(mpm_handle* h, int code, const std::string& msg) {
+  if (h) h->last_error = msg; else g_static_error = msg;
+  return code;
+}
+
+int cuda_fail(mpm_handle* h, cudaError_t e, const char* where) {
+  return fail(h, MPM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #expr); \
+  } while (0)
+
+SimParams params_for(const mpm_handle* h, int t) {
+  const mpm_scene_desc& d = h->desc;
+  SimParams P;
+  memset(&P, 0, sizeof(P));
+  P.n_grid = d.n_grid;
+  P.nnodes = (int)h->m.nnodes;
+  P.dx = 1.0f / (float)d.n_grid;
+  P.inv_dx = (float)d.n_grid;
+  P.dt = d.dt;
+  for (int a = 0; a < 3; ++a) P.gravity[a] = d.gravity[a];
+  P.wall = d.wall_cells;
+  const double dx = 1.0 / d.n_grid;
+  const double vol = std::pow(0.5 * dx, (double)d.dim);
+  P.p_mass = (float)(d.rho * vol);
+  P.kappa = (float)(-(double)d.dt * vol * 4.0 / (dx * dx));
+  P.n_groups = d.n_groups;
+  P.n_basis = d.n_basis;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int k = 1; k <= d.n_basis; ++k)
+    P.basis[k - 1] =
+        (float)std::sin(two_pi * k * (double)t / (double)d.act_period + (double)d.act_phase);
+  P.tile_capacity = h->smem_tile ? h->tile_capacity : 0;
+  return P;
+}
+
+int grid_blocks_per_scene(const mpm_handle* h) {
+  // enough CTAs to cover a typical active box; the kernels stride over the rest
+  int64_t per_scene = 304 / h->m.S;
+  if (per_scene < 2) per_scene = 2;
+  if (per_scene > 256) per_scene = 256;
+  return (int)per_scene;
+}
+
+// ------------------------------ launch helpers ------------------------------
+
+struct Launcher {
+  mpm_handle* h;
+  cudaStream_t s;
+  int64_t count = 0;
+
+  // bracket one launch with events when profiling (category = MPM_KERNEL_*)
+  template <typename Fn>
+  cudaError_t timed(int category, Fn&& launch) {
+    if (!h->profile) return launch();
+    size_t used = h->ev_records.size() * 2;
+    while (h->ev_pool.size() < used + 2) {
+      cudaEvent_t e;
+      cudaError_t ce = cudaEventCreate(&e);
+      if (ce != cudaSuccess) return ce;
+      h->ev_pool.push_back(e);
+    }
+    cudaEvent_t a = h->ev_pool[used], b = h->ev_pool[used + 1];
+    cudaError_t e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) h->ev_records.push_back({category, {a, b}});
+    return e;
+  }
+
+  cudaError_t step(int mode, int t, const float* in, float* out) {
+    const Dims& m = h->m;
+    SimParams P = params_for(h, t);
+    StepArgs A;
+    A.tiles = h->at<int4>(h->L.tiles);
+    A.N = (int)m.N;
+    A.in = in;
+    A.out = out;
+    A.mu = h->at<float>(h->L.mu);
+    A.la = h->at<float>(h->L.la);
+    A.group = h->at<int>(h->L.group);
+    A.wact = h->at<float>(h->L.wact);
+    A.U = h->at<float4>(h->L.U);
+    A.PM = h->at<float4>(h->L.PM);
+    A.bbox = h->at<int>(h->L.bbox);
+    A.err = h->at<unsigned>(h->L.err);
+    ++count;
+    const int cat = mode == kP2GOnly ? MPM_KERNEL_P2G
+                    : mode == kG2PP2G ? MPM_KERNEL_G2P_P2G
+                    : mode == kG2PP2GFull ? MPM_KERNEL_G2P_P2G_FULL : MPM_KERNEL_G2P;
+    return timed(cat, [&] {
+      return m.D == 2 ? launch_step<2>(h->desc.material, mode, P, A, m.n_tiles, s)
+                      : launch_step<3>(h->desc.material, mode, P, A, m.n_tiles, s);
+    });
+  }
+  cudaError_t grid_update() {
+    SimParams P = params_for(h, 0);
+    ++count;
+    float4* PM = h->at<float4>(h->L.PM);
+    float4* U = h->at<float4>(h->L.U);
+    int* bb = h->at<int>(h->L.bbox);
+    int* bbu = h->at<int>(h->L.bbox_u);
+    unsigned* done = h->at<unsigned>(h->L.done);
+    int bps = grid_blocks_per_scene(h);
+    return timed(MPM_KERNEL_GRID_UPDATE, [&] {
+      return h->m.D == 2 ? launch_grid_update<2>(P, PM, U, bb, bbu, done, h->m.S, bps, s)
+                         : launch_grid_update<3>(P, PM, U, bb, bbu, done, h->m.S, bps, s);
+    });
+  }
+  cudaError_t adjoint(int mode, int t_p2g, const float* st1, const float* st0) {
+    const Dims& m = h->m;
+    SimParams P = params_for(h, t_p2g);
+    AdjArgs A;
+    A.tiles = h->at<int4>(h->L.tiles);
+    A.N = (int)m.N;
+    A.st1 = st1;
+    A.st0 = st0;
+    A.adj = h->at<float>(h->L.adj);
+    A.mu = h->at<float>(h->L.mu);
+    A.la = h->at<float>(h->L.la);
+    A.mubar = h->at<float>(h->L.mubar);
+    A.labar = h->at<float>(h->L.labar);
+    A.group = h->at<int>(h->L.group);
+    A.wact = h->at<float>(h->L.wact);
+    A.wbar = h->at<float>(h->L.wbar);
+    A.PBM = h->at<float4>(h->L.PBM);
+    A.U = h->at<float4>(h->L.U);
+    A.UB = h->at<float4>(h->L.UB);
+    A.err = h->at<unsigned>(h->L.err);
+    ++count;
+    const int cat = mode == kAdjG2P ? MPM_KERNEL_ADJ_G2P
+                    : mode == kAdjFused ? MPM_KERNEL_ADJ_FUSED : MPM_KERNEL_ADJ_P2G;
+    return timed(cat, [&] {
+      return m.D == 2 ? launch_adjoint<2>(h->desc.material, mode, P, A, m.n_tiles, s)
+                      : launch_adjoint<3>(h->desc.material, mode, P, A, m.n_tiles, s);
+    });
+  }
+  cudaError_t grid_adjoint() {
+    SimParams P = params_for(h, 0);
+    ++count;
+    int bps = grid_blocks_per_scene(h);
+    float4* UB = h->at<float4>(h->L.UB);
+    const float4* U = h->at<float4>(h->L.U);
+    float4* PBM = h->at<float4>(h->L.PBM);
+    const int* bbu = h->at<int>(h->L.bbox_u);
+    return timed(MPM_KERNEL_GRID_ADJ, [&] {
+      return h->m.D == 2 ? launch_grid_adjoint<2>(P, UB, U, PBM, bbu, h->m.S, bps, s)
+                         : launch_grid_adjoint<3>(P, UB, U, PBM, bbu, h->m.S, bps, s);
+    });
+  }
+};
+
+#define LK(expr)                                        \
+  do {                                                  \
+    cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #expr); \
+  } while (0)
+
+// forward: states 0..T; full state stored at multiples of K and at T (fin)
+int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
+  const int K = h->m.K;
+  const float* src = h->state(h->L.ckpt, 0);
+  float* cur = h->at<float>(h->L.cur);
+  LK(Lc.step(kP2GOnly, 0, src, nullptr));
+  LK(Lc.grid_update());
+  for (int t = 1; t < T; ++t) {
+    float* dst;
+    int mode;
+    if (t % K == 0) {
+      dst = h->state(h->L.ckpt, t / K);
+      mode = kG2PP2GFull;
+    } else {
+      dst = cur;
+      mode = kG2PP2G;
+    }
+    LK(Lc.step(mode, t, src, dst));
+    LK(Lc.grid_update());
+    src = dst;
+  }
+  LK(Lc.step(kG2POnlyFull, T, src, h->at<float>(h->L.fin)));
+  return MPM_OK;
+}
+
+// re-simulate segment [s0, top): seg slot i <- state s0 + i (i = 1..top-s0)
+int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top) {
+  const float* ck = h->state(h->L.ckpt, s0 / h->m.K);
+  LK(Lc.step(kP2GOnly, s0, ck, nullptr));
+  LK(Lc.grid_update());
+  const float* prev = ck;
+  for (int t = s0 + 1; t < top; ++t) {
+    float* dst = h->state(h->L.seg, t - s0);
+    LK(Lc.step(kG2PP2GFull, t, prev, dst));
+    LK(Lc.grid_update());
+    prev = dst;
+  }
+  LK(Lc.step(kG2POnlyFull, top, prev, h->state(h->L.seg, top - s0)));
+  return MPM_OK;
+}
+
+int issue_backward(mpm_handle* h, Launcher& Lc, int T) {
+  const int K = h->m.K;
+  for (int s = T - 1; s >= 0; --s) {
+    const int j = s / K, s0 = j * K;
+    const int top = (s0 + K < T) ? s0 + K : T;
+    bool fresh_grid = false;
+    if (s == top - 1) {
+      int rc = issue_resim(h, Lc, s0, top);
+      if (rc) return rc;
+      fresh_grid = true;  // the re-simulation's last grid is step s's grid
+    }
+    const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
+    const float* st_s1 = h->state(h->L.seg, s + 1 - s0);
+    if (!fresh_grid) {
+      LK(Lc.step(kP2GOnly, s, st_s, nullptr));  // recompute this step's grid (Appendix D.1)
+      LK(Lc.grid_update());
+    }
+    if (s == T - 1)
+      LK(Lc.adjoint(kAdjG2P, s + 1, st_s1, st_s));
+    else
+      LK(Lc.adjoint(kAdjFused, s + 1, st_s1, st_s));
+    LK(Lc.grid_adjoint());
+  }
+  const float* st0 = h->state(h->L.ckpt, 0);
+  LK(Lc.adjoint(kAdjP2G, 0, st0, st0));
+  return MPM_OK;
+}
+
+void drop_graphs(mpm_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.first);
+  h->graphs.clear();
+}
+
+// Run a launch sequence on `stream`, through a cached CUDA graph when enabled.
+template <typename Fn>
+int run_sequence(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
+  if (!h->use_graphs || h->profile) {
+    Launcher Lc{h, stream};
+    int rc = issue(Lc);
+    h->launches += Lc.count;
+    return rc;
+  }
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    Launcher Lc{h, h->cap_stream};
+    int rc = issue(Lc);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    it = h->graphs.emplace(key, std::make_pair(ex, Lc.count)).first;
+  }
+  CK(cudaGraphLaunch(it->second.first, stream));
+  h->launches += it->second.second;
+  return MPM_OK;
+}
+
+}  // namespace
+
+// =============================== C ABI ======================================
+
+extern "C" {
+
+int mpm_workspace_bytes(const mpm_scene_desc* desc, int32_t max_steps, size_t* out_bytes) {
+  std::string why;
+  if (!out_bytes) return fail(nullptr, MPM_ERR_ARG, "out_bytes is NULL");
+  if (!valid_desc(desc, max_steps, &why)) return fail(nullptr, MPM_ERR_ARG, why);
+  Dims m = make_dims(desc, max_steps);
+  *out_bytes = make_layout(m).total;
+  return MPM_OK;
+}
+
+int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_bytes,
+               int32_t max_steps, mpm_handle** out) {
+  std::string why;
+  if (!out) return fail(nullptr, MPM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!valid_desc(desc, max_steps, &why)) return fail(nullptr, MPM_ERR_ARG, why);
+  Dims m = make_dims(desc, max_steps);
+  Layout L = make_layout(m);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+    return fail(nullptr, MPM_ERR_WORKSPACE, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < L.total)
+    return fail(nullptr, MPM_ERR_WORKSPACE, "workspace smaller than mpm_workspace_bytes");
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(nullptr, MPM_ERR_WORKSPACE, "workspace is not device memory");
+  }
+  mpm_handle* h = new mpm_handle();
+  h->desc = *desc;
+  h->n_particles.assign(desc->n_particles, desc->n_particles + desc->n_scenes);
+  h->desc.n_particles = h->n_particles.data();
+  h->max_steps = max_steps;
+  h->m = m;
+  h->L = L;
+  h->ws = static_cast<char*>(workspace);
+  h->ws_bytes = workspace_bytes;
+  // tile table and scene offsets (host -> device once)
+  std::vector<int4> tiles;
+  std::vector<int64_t> off(m.S + 1, 0);
+  for (int s = 0; s < m.S; ++s) {
+    off[s + 1] = off[s] + h->n_particles[s];
+    for (int64_t b = off[s]; b < off[s + 1]; b += kTile) {
+      int cnt = (int)((off[s + 1] - b) < kTile ? (off[s + 1] - b) : kTile);
+      tiles.push_back(make_int4(s, (int)b, cnt, 0));
+    }
+  }
+  cudaError_t e = cudaMemcpy(h->at<int4>(L.tiles), tiles.data(), tiles.size() * sizeof(int4),
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->at<int64_t>(L.scene_off), off.data(), off.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->at<char>(L.err), 0, 4);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, MPM_ERR_CUDA, std::string("mpm_create: ") + cudaGetErrorString(e));
+  }
+  *out = h;
+  return MPM_OK;
+}
+
+int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float* C0,
+                    const float* F0, const float* E, const float* nu, const int32_t* group,
+                    const float* w, void* stream) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  if (!x0 || !v0 || !E || !nu) return fail(h, MPM_ERR_ARG, "x0, v0, E and nu are required");
+  if (h->desc.n_groups > 0 && (!group || !w))
+    return fail(h, MPM_ERR_ARG, "group and w are required when n_groups > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  const Dims& m = h->m;
+  const Layout& L = h->L;
+  int end_bit = 32;
+  while ((1ll << (end_bit - 32)) < m.S) ++end_bit;
+  CK(launch_sort_keys(m.D, m.n_grid, m.S, h->at<int64_t>(L.scene_off), m.N, x0,
+                      h->at<uint64_t>(L.keys0), h->at<int>(L.idx0), s));
+  CK(launch_sort(h->at<void>(L.sort_tmp), L.sort_tmp_bytes, h->at<uint64_t>(L.keys0),
+                 h->at<uint64_t>(L.keys1), h->at<int>(L.idx0), h->at<int>(L.perm), m.N, end_bit, s));
+  CK(launch_gather_initial(m.D, m.N, h->at<int>(L.perm), x0, v0, C0, F0, E, nu, group,
+                           h->state(L.ckpt, 0), h->at<float>(L.mu), h->at<float>(L.la),
+                           h->at<float>(L.E), h->at<float>(L.nu), h->at<int>(L.group), s));
+  const size_t wbytes = (size_t)m.S * h->desc.n_groups * h->desc.n_basis * sizeof(float);
+  if (wbytes) CK(cudaMemcpyAsync(h->at<float>(L.wact), w, wbytes, cudaMemcpyDeviceToDevice, s));
+  const size_t grid = (size_t)m.S * m.nnodes * sizeof(float4);
+  CK(cudaMemsetAsync(h->at<char>(L.PM), 0, grid, s));
+  CK(cudaMemsetAsync(h->at<char>(L.UB), 0, grid, s));
+  CK(launch_reset_boxes(h->at<int>(L.bbox), h->at<int>(L.bbox_u), h->at<unsigned>(L.done), m.S, s));
+  h->launches += 4;
+  h->initialized = true;
+  h->T_recorded = 0;
+  return MPM_OK;
+}
+
+int mpm_forward(mpm_handle* h, int32_t T, void* stream) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  if (!h->initialized) return fail(h, MPM_ERR_STATE, "mpm_set_initial has not been called");
+  if (T < 1 || T > h->max_steps) return fail(h, MPM_ERR_STATE, "T must be in [1, max_steps]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  int rc = run_sequence(h, (int64_t)T * 2, s, [&](Launcher& Lc) { return issue_forward(h, Lc, T); });
+  if (rc) return rc;
+  h->T_recorded = T;
+  return MPM_OK;
+}
+
+int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* stream) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  if (!h->T_recorded) return fail(h, MPM_ERR_STATE, "no forward recorded");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  const Dims& m = h->m;
+  const float* fin = h->at<float>(h->L.fin);
+  const int* perm = h->at<int>(h->L.perm);
+  const int D = m.D;
+  float* outs[4] = {x, v, C, F};
+  const int rows[4] = {D, D, D * D, D * D};
+  int r0 = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (outs[k]) {
+      CK(launch_scatter_rows(rows[k], m.N, perm, fin + (size_t)r0 * m.N, outs[k], s));
+      ++h->launches;
+    }
+    r0 += rows[k];
+  }
+  return MPM_OK;
+}
+
+int mpm_loss(mpm_handle* h, int32_t kind, const float* target, float* loss, float* dL_dxT,
+             float* dL_dx0, void* stream) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  if (!h->T_recorded) return fail(h, MPM_ERR_STATE, "no forward recorded");
+  if (kind != MPM_LOSS_COM_TARGET && kind != MPM_LOSS_COM_X_DISP)
+    return fail(h, MPM_ERR_ARG, "unknown loss kind");
+  if (kind == MPM_LOSS_COM_TARGET && !target) return fail(h, MPM_ERR_ARG, "target is NULL");
+  if (!dL_dxT) return fail(h, MPM_ERR_ARG, "dL_dxT is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  const Dims& m = h->m;
+  double* com = h->at<double>(h->L.com);
+  CK(cudaMemsetAsync(com, 0, (size_t)m.S * 6 * sizeof(double), s));
+  CK(launch_com(m.D, m.N, m.S, h->at<int64_t>(h->L.scene_off), h->at<int>(h->L.perm),
+                h->at<float>(h->L.fin), h->state(h->L.ckpt, 0), com, s));
+  CK(launch_loss_seed(m.D, kind, m.N, m.S, h->at<int64_t>(h->L.scene_off), h->at<int>(h->L.perm),
+                      com, target, loss, dL_dxT, dL_dx0, s));
+  h->launches += 2;
+  return MPM_OK;
+}
+
+int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const float* dL_dC,
+                 const float* dL_dF, float* gx0, float* gv0, float* gC0, float* gF0, float* gE,
+                 float* gnu, float* gw, void* stream) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  if (!h->T_recorded) return fail(h, MPM_ERR_STATE, "backward needs a recorded forward");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  const Dims& m = h->m;
+  const Layout& L = h->L;
+  const int D = m.D;
+  const int* perm = h->at<int>(L.perm);
+  float* adj = h->at<float>(L.adj);
+  const float* seeds[4] = {dL_dx, dL_dv, dL_dC, dL_dF};
+  const int rows[4] = {D, D, D * D, D * D};
+  int r0 = 0;
+  for (int k = 0; k < 4; ++k) {
+    CK(launch_gather_rows(rows[k], m.N, perm, seeds[k], adj + (size_t)r0 * m.N, s));
+    r0 += rows[k];
+  }
+  CK(cudaMemsetAsync(h->at<float>(L.mubar), 0, (size_t)m.N * 4, s));
+  CK(cudaMemsetAsync(h->at<float>(L.labar), 0, (size_t)m.N * 4, s));
+  CK(cudaMemsetAsync(h->at<float>(L.wbar), 0, (size_t)m.S * kMaxGroups * kMaxBasis * 4, s));
+  h->launches += 4;
+  const int T = h->T_recorded;
+  int rc = run_sequence(h, (int64_t)T * 2 + 1, s, [&](Launcher& Lc) { return issue_backward(h, Lc, T); });
+  if (rc) return rc;
+  float* outs[4] = {gx0, gv0, gC0, gF0};
+  r0 = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (outs[k]) {
+      CK(launch_scatter_rows(rows[k], m.N, perm, adj + (size_t)r0 * m.N, outs[k], s));
+      ++h->launches;
+    }
+    r0 += rows[k];
+  }
+  if (gE || gnu) {
+    CK(launch_material_grad(m.N, perm, h->at<float>(L.E), h->at<float>(L.nu), h->at<float>(L.mubar),
+                            h->at<float>(L.labar), gE, gnu, s));
+    ++h->launches;
+  }
+  const size_t wbytes = (size_t)m.S * h->desc.n_groups * h->desc.n_basis * sizeof(float);
+  if (gw && wbytes) CK(cudaMemcpyAsync(gw, h->at<float>(L.wbar), wbytes, cudaMemcpyDeviceToDevice, s));
+  return MPM_OK;
+}
+
+int mpm_sync_status(mpm_handle* h) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+  unsigned err = 0;
+  e = cudaMemcpy(&err, h->at<unsigned>(h->L.err), 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "read error word");
+  if (err) {
+    cudaMemset(h->at<unsigned>(h->L.err), 0, 4);
+    if (err & kErrOOB) return fail(h, MPM_ERR_OOB, "a particle's stencil left the grid");
+    if (err & kErrNonFinite) return fail(h, MPM_ERR_NONFINITE, "non-finite value or det F <= 0");
+    if (err & kErrTimeout) return fail(h, MPM_ERR_TIMEOUT, "a bounded device wait gave up");
+  }
+  return MPM_OK;
+}
+
+int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  switch (key) {
+    case MPM_OPT_USE_GRAPHS: h->use_graphs = value != 0; break;
+    case MPM_OPT_SMEM_TILE: h->smem_tile = value != 0; break;
+    case MPM_OPT_PROFILE:
+      h->profile = value != 0;
+      h->ev_records.clear();
+      break;
+    case MPM_OPT_TILE_CAPACITY:
+      if (value < 27 || value > 12288) return fail(h, MPM_ERR_ARG, "tile capacity must be in [27, 12288]");
+      h->tile_capacity = (int)value;
+      break;
+    default: return fail(h, MPM_ERR_ARG, "unknown option");
+  }
+  drop_graphs(h);
+  return MPM_OK;
+}
+
+int mpm_get_info(mpm_handle* h, int32_t key, int64_t* value) {
+  if (!h || !value) return fail(h, MPM_ERR_ARG, "NULL argument");
+  switch (key) {
+    case MPM_INFO_KERNEL_LAUNCHES: *value = h->launches; return MPM_OK;
+    case MPM_INFO_N_TOTAL: *value = h->m.N; return MPM_OK;
+    case MPM_INFO_STEPS_RECORDED: *value = h->T_recorded; return MPM_OK;
+  }
+  return fail(h, MPM_ERR_ARG, "unknown info key");
+}
+
+int mpm_get_profile(mpm_handle* h, int32_t kind, int64_t* launches, double* total_ms) {
+  if (!h || !launches || !total_ms) return fail(h, MPM_ERR_ARG, "NULL argument");
+  int64_t n = 0;
+  double ms = 0.0;
+  for (auto& r : h->ev_records) {
+    if (r.first != kind) continue;
+    cudaError_t e = cudaEventSynchronize(r.second.second);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, r.second.first, r.second.second);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventElapsedTime");
+    ++n;
+    ms += t;
+  }
+  *launches = n;
+  *total_ms = ms;
+  return MPM_OK;
+}
+
+const char* mpm_last_error(mpm_handle* h) {
+  return h ? h->last_error.c_str() : g_static_error.c_str();
+}
+
+void mpm_destroy(mpm_handle* h) {
+  if (!h) return;
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,439 @@
+// mpm_common.cuh -- per-particle device math of the MLS-MPM step and its adjoint.
+//
+// Quadratic B-spline stencil, Kirchhoff stress (fixed-corotated / neo-Hookean,
+// plus the actuation fibre stress of diffmpm's open-loop controller, Section 4.1),
+// the stress adjoint, and the FP64 polar decomposition with its adjoint (the
+// hand-written SVD/polar gradient of Appendix C).  Bulk arithmetic is FP32; the
+// polar factor R, F - R, S = R^T F and the polar adjoint are FP64.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpm {
+
+constexpr int kTile = 256;        // particles (= threads) per CTA in particle passes
+constexpr int kMaxBasis = 8;
+constexpr int kMaxGroups = 8;
+
+// device error bits (sticky, OR-ed into the handle's error word)
+constexpr unsigned kErrOOB = 1u;
+constexpr unsigned kErrNonFinite = 2u;
+constexpr unsigned kErrTimeout = 4u;
+
+enum Material : int { kFixedCorotated = 0, kNeoHookean = 1 };
+
+// Scalars every kernel of one launch needs (passed by value).
+struct SimParams {
+  int n_grid;
+  int nnodes;        // n_grid^dim, nodes per scene grid
+  float dx, inv_dx, dt;
+  float gravity[3];
+  int wall;
+  float p_mass;      // rho * (dx/2)^dim
+  float kappa;       // -dt * V0 * 4 / dx^2 (stress term of the affine matrix)
+  int n_groups, n_basis;
+  float basis[kMaxBasis];  // sin(2 pi k t / P + phi), k = 1..n_basis, at this pass's step
+  int tile_capacity;       // max nodes of a CTA's shared grid tile (0 = global atomics)
+};
+
+// ---------------------------------------------------------------------------
+// quadratic B-spline stencil (MLS-MPM, Hu et al. 2018)
+// ---------------------------------------------------------------------------
+template <int D>
+struct Stencil {
+  int base[D];
+  float f[D];      // x/dx - base in [0.5, 1.5)
+  float w[D][3];
+  float dw[D][3];  // dw/df
+};
+
+// Returns false (and leaves a harmless in-range base) when the stencil would leave
+// [0, n-1] or x is not finite; such a particle must not touch the grid.
+template <int D>
+__device__ __forceinline__ bool make_stencil(const float* x, const SimParams& P, Stencil<D>& s) {
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float X = x[a] * P.inv_dx;
+    float b = floorf(X - 0.5f);
+    bool good = (X == X) && b >= 0.0f && b <= (float)(P.n_grid - 3);
+    ok = ok && good;
+    b = good ? b : 0.0f;
+    float f = good ? X - b : 1.0f;
+    s.base[a] = (int)b;
+    s.f[a] = f;
+    float r0 = 1.5f - f, r1 = f - 1.0f, r2 = f - 0.5f;
+    s.w[a][0] = 0.5f * r0 * r0;
+    s.w[a][1] = 0.75f - r1 * r1;
+    s.w[a][2] = 0.5f * r2 * r2;
+    s.dw[a][0] = -r0;
+    s.dw[a][1] = -2.0f * r1;
+    s.dw[a][2] = r2;
+  }
+  return ok;
+}
+
+template <int D>
+__device__ __forceinline__ void offsets(int o, int off[D]) {
+  if (D == 2) {
+    off[0] = o / 3;
+    off[1] = o % 3;
+  } else {
+    off[0] = o / 9;
+    off[1] = (o / 3) % 3;
+    off[D - 1] = o % 3;
+  }
+}
+
+// weight, dW/dx and dpos = x_i - x_p for one stencil offset
+template <int D>
+__device__ __forceinline__ void node_terms(const Stencil<D>& s, const int off[D], const SimParams& P,
+                                           float& W, float gW[D], float dpos[D]) {
+  float wa[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) wa[a] = s.w[a][off[a]];
+  W = wa[0];
+#pragma unroll
+  for (int a = 1; a < D; ++a) W *= wa[a];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float g = s.dw[a][off[a]] * P.inv_dx;
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+      if (b != a) g *= wa[b];
+    gW[a] = g;
+    dpos[a] = ((float)off[a] - s.f[a]) * P.dx;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small matrix helpers (row-major D x D)
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void cofactor(const float A[D][D], float c[D][D]) {
+  if (D == 2) {
+    c[0][0] = A[1][1];
+    c[0][1] = -A[1][0];
+    c[1][0] = -A[0][1];
+    c[1][1] = A[0][0];
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        c[i][j] = A[i1][j1] * A[i2][j2] - A[i1][j2] * A[i2][j1];
+      }
+  }
+}
+
+// J - 1 for F = I + E, summed by invariants so that it keeps its relative accuracy
+// when F is close to the identity (E is exact in FP32 for F_ii in [0.5, 2]).
+template <int D>
+__device__ __forceinline__ float det_minus_one(const float F[D][D]) {
+  if (D == 2) {
+    float e00 = F[0][0] - 1.0f, e11 = F[1][1] - 1.0f;
+    return e00 + e11 + (e00 * e11 - F[0][1] * F[1][0]);
+  } else {
+    float e00 = F[0][0] - 1.0f, e11 = F[1][1] - 1.0f, e22 = F[2][2] - 1.0f;
+    float m2 = (e00 * e11 - F[0][1] * F[1][0]) + (e00 * e22 - F[0][2] * F[2][0]) +
+               (e11 * e22 - F[1][2] * F[2][1]);
+    float d3 = e00 * (e11 * e22 - F[1][2] * F[2][1]) - F[0][1] * (F[1][0] * e22 - F[1][2] * F[2][0]) +
+               F[0][2] * (F[1][0] * F[2][1] - e11 * F[2][0]);
+    return (e00 + e11 + e22) + m2 + d3;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 polar decomposition F = R S (R in SO(d), S symmetric positive definite)
+// ---------------------------------------------------------------------------
+template <int D>
+struct Polar {
+  double R[D][D];
+  float Rf[D][D];   // R rounded to FP32
+  float Df[D][D];   // F - R computed in FP64, rounded once
+};
+
+// 2D: R is the rotation by atan2(F10 - F01, F00 + F11), formed without a
+// transcendental as (c, s) / |(c, s)|.  3D: Newton's iteration X <- (X + X^-T)/2
+// from X = F, which converges quadratically to the orthogonal polar factor and keeps
+// det X > 0 (Higham 1986).  Returns false for det F <= 0 or non-finite input.
+template <int D>
+__device__ __forceinline__ bool polar_f64(const float F[D][D], Polar<D>& p) {
+  if (D == 2) {
+    double c = (double)F[0][0] + (double)F[1][1];
+    double s = (double)F[1][0] - (double)F[0][1];
+    double r = sqrt(c * c + s * s);
+    double det = (double)F[0][0] * F[1][1] - (double)F[0][1] * F[1][0];
+    if (!(det > 0.0) || !(r > 0.0)) {
+      c = 1.0; s = 0.0; r = 1.0;
+    }
+    double ir = 1.0 / r;
+    p.R[0][0] = c * ir;
+    p.R[0][1] = -s * ir;
+    p.R[1][0] = s * ir;
+    p.R[1][1] = c * ir;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        p.Rf[i][j] = (float)p.R[i][j];
+        p.Df[i][j] = (float)((double)F[i][j] - p.R[i][j]);
+      }
+    return det > 0.0 && r > 0.0;
+  } else {
+    double X[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) X[i][j] = (double)F[i][j];
+    bool ok = true;
+    for (int it = 0; it < 24; ++it) {
+      double c[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+          c[i][j] = X[i1][j1] * X[i2][j2] - X[i1][j2] * X[i2][j1];
+        }
+      double det = X[0][0] * c[0][0] + X[0][1] * c[0][1] + X[0][2] * c[0][2];
+      if (!(det > 0.0) || !(det < 1e300)) {
+        ok = false;
+        break;
+      }
+      double hid = 0.5 / det, diff = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          double xn = 0.5 * X[i][j] + c[i][j] * hid;
+          double dd = xn - X[i][j];
+          diff += dd * dd;
+          X[i][j] = xn;
+        }
+      if (diff < 1e-20) break;  // the next update would be below FP64 resolution
+    }
+    if (!ok) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) X[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        p.R[i][j] = X[i][j];
+        p.Rf[i][j] = (float)X[i][j];
+        p.Df[i][j] = (float)((double)F[i][j] - X[i][j]);
+      }
+    return ok;
+  }
+}
+
+// Fbar += dR/dF^T [Rbar] in FP64.  With F = R S, dR = R W (W antisymmetric) and
+// W S + S W = R^T dF - dF^T R; the adjoint is Fbar += 2 R Y where Y is the
+// antisymmetric solution of Y S + S Y = skew(R^T Rbar).  In 3D that equation is
+// (tr(S) I - S) y = b on axial vectors (eigenvalues sigma_i + sigma_j > 0), in 2D
+// y = b / tr(S); no singular-value differences appear.
+template <int D>
+__device__ __forceinline__ void polar_adjoint_f64(const float F[D][D], const Polar<D>& p,
+                                                  const float Rbar[D][D], float Fbar[D][D]) {
+  double M[D][D], S[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double m = 0.0, s = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        m += p.R[k][i] * (double)Rbar[k][j];
+        s += p.R[k][i] * (double)F[k][j];
+      }
+      M[i][j] = m;
+      S[i][j] = s;
+    }
+  if (D == 2) {
+    double b = 0.5 * (M[1][0] - M[0][1]);
+    double tr = S[0][0] + S[1][1];
+    double y = b / fmax(tr, 1e-6);
+    // 2 R Y, Y = [[0, -y], [y, 0]]
+    Fbar[0][0] += (float)(2.0 * p.R[0][1] * y);
+    Fbar[0][1] += (float)(-2.0 * p.R[0][0] * y);
+    Fbar[1][0] += (float)(2.0 * p.R[1][1] * y);
+    Fbar[1][1] += (float)(-2.0 * p.R[1][0] * y);
+  } else {
+    double b0 = 0.5 * (M[2][1] - M[1][2]);
+    double b1 = 0.5 * (M[0][2] - M[2][0]);
+    double b2 = 0.5 * (M[1][0] - M[0][1]);
+    double tr = S[0][0] + S[1][1] + S[2][2];
+    // G = tr(S) I - sym(S)
+    double g00 = tr - S[0][0], g11 = tr - S[1][1], g22 = tr - S[2][2];
+    double g01 = -0.5 * (S[0][1] + S[1][0]);
+    double g02 = -0.5 * (S[0][2] + S[2][0]);
+    double g12 = -0.5 * (S[1][2] + S[2][1]);
+    double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+    double c11 = g00 * g22 - g02 * g02, c12 = g01 * g02 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+    double det = g00 * c00 + g01 * c01 + g02 * c02;
+    double id = 1.0 / fmax(det, 1e-18);
+    double y0 = (c00 * b0 + c01 * b1 + c02 * b2) * id;
+    double y1 = (c01 * b0 + c11 * b1 + c12 * b2) * id;
+    double y2 = (c02 * b0 + c12 * b1 + c22 * b2) * id;
+    const double Y[3][3] = {{0.0, -y2, y1}, {y2, 0.0, -y0}, {-y1, y0, 0.0}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s += p.R[i][k] * Y[k][j];
+        Fbar[i][j] += (float)(2.0 * s);
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kirchhoff stress tau(F) and its adjoint
+// ---------------------------------------------------------------------------
+template <int D>
+struct StressCache {
+  float J, Jm1;
+  Polar<D> pol;  // fixed-corotated only
+};
+
+// tau = 2 mu (F - R) F^T + la (J - 1) J I        (fixed-corotated)
+// tau = mu (F F^T - I) + la ln(J) I               (neo-Hookean)
+// tau += act (F e)(F e)^T, e = unit vector of `axis` (actuation fibre)
+template <int D, int MAT>
+__device__ __forceinline__ bool kirchhoff(const float F[D][D], float mu, float la, float act, int axis,
+                                          float tau[D][D], StressCache<D>& sc) {
+  bool ok = true;
+  sc.Jm1 = det_minus_one<D>(F);
+  sc.J = 1.0f + sc.Jm1;
+  if (MAT == kFixedCorotated) {
+    ok = polar_f64<D>(F, sc.pol);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += sc.pol.Df[i][k] * F[j][k];
+        tau[i][j] = 2.0f * mu * s;
+      }
+    float vol = la * sc.Jm1 * sc.J;
+#pragma unroll
+    for (int i = 0; i < D; ++i) tau[i][i] += vol;
+  } else {
+    ok = sc.J > 0.0f;
+    // F F^T - I = E + E^T + E E^T with E = F - I
+    float E[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) E[i][j] = F[i][j] - (i == j ? 1.0f : 0.0f);
+    float lnJ = log1pf(sc.Jm1);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float s = E[i][j] + E[j][i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += E[i][k] * E[j][k];
+        tau[i][j] = mu * s + (i == j ? la * lnJ : 0.0f);
+      }
+  }
+  if (act != 0.0f) {
+    float fe[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) fe[i] = F[i][axis];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) tau[i][j] += act * fe[i] * fe[j];
+  }
+  return ok && (sc.J == sc.J);
+}
+
+// Given taubar = dL/dtau, accumulate Fbar, mubar, labar and return abar = dL/dact.
+template <int D, int MAT>
+__device__ __forceinline__ float kirchhoff_adjoint(const float F[D][D], float mu, float la, float act,
+                                                   int axis, const StressCache<D>& sc,
+                                                   const float tb[D][D], float Fbar[D][D],
+                                                   float& mubar, float& labar) {
+  float trtb = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) trtb += tb[i][i];
+  float cof[D][D];
+  cofactor<D>(F, cof);
+  if (MAT == kFixedCorotated) {
+    // d/dF [2 mu (F F^T - R F^T)] at fixed R: 2 mu (tb F + tb^T (F - R));  Rbar = -2 mu tb F
+    float Rbar[D][D];
+    float mub = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float tF = 0.0f, tD = 0.0f, DFt = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          tF += tb[i][k] * F[k][j];
+          tD += tb[k][i] * sc.pol.Df[k][j];
+          DFt += sc.pol.Df[i][k] * F[j][k];
+        }
+        Fbar[i][j] += 2.0f * mu * (tF + tD);
+        Rbar[i][j] = -2.0f * mu * tF;
+        mub += tb[i][j] * DFt;
+      }
+    polar_adjoint_f64<D>(F, sc.pol, Rbar, Fbar);
+    float c = la * (2.0f * sc.J - 1.0f) * trtb;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) Fbar[i][j] += c * cof[i][j];
+    mubar += 2.0f * mub;
+    labar += trtb * sc.Jm1 * sc.J;
+  } else {
+    float iJ = 1.0f / sc.J;
+    float c = la * trtb * iJ;
+    float mub = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += (tb[i][k] + tb[k][i]) * F[k][j];
+        Fbar[i][j] += mu * s + c * cof[i][j];
+        float e = F[i][j] - (i == j ? 1.0f : 0.0f);
+        float et = F[j][i] - (i == j ? 1.0f : 0.0f);
+        float g = e + et;
+#pragma unroll
+        for (int k = 0; k < D; ++k) g += (F[i][k] - (i == k ? 1.0f : 0.0f)) * (F[j][k] - (j == k ? 1.0f : 0.0f));
+        mub += tb[i][j] * g;
+      }
+    mubar += mub;
+    labar += trtb * log1pf(sc.Jm1);
+  }
+  // actuation: abar = (F e)^T tb (F e);  Fbar[:, axis] += act (tb + tb^T) F e
+  float fe[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) fe[i] = F[i][axis];
+  float abar = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float s = 0.0f, r = 0.0f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      r += tb[i][j] * fe[j];
+      s += (tb[i][j] + tb[j][i]) * fe[j];
+    }
+    abar += fe[i] * r;
+    Fbar[i][axis] += act * s;
+  }
+  return abar;
+}
+
+}  // namespace mpm

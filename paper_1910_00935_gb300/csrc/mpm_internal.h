@@ -1,0 +1,56 @@
+// mpm_internal.h -- host-side declarations shared by the C-ABI and the kernel
+// translation units (launch wrappers; no device code).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mpm_common.cuh"
+
+namespace mpm {
+
+struct StepArgs;
+struct AdjArgs;
+
+// kernels_2d.cu / kernels_3d.cu (templated on dimension)
+template <int D>
+cudaError_t launch_step(int material, int mode, const SimParams& P, const StepArgs& A, int n_tiles,
+                        cudaStream_t s);
+template <int D>
+cudaError_t launch_adjoint(int material, int mode, const SimParams& P, const AdjArgs& A, int n_tiles,
+                           cudaStream_t s);
+template <int D>
+cudaError_t launch_grid_update(const SimParams& P, float4* PM, float4* U, int* bbox, int* bbox_u,
+                               unsigned* done, int n_scenes, int blocks_per_scene, cudaStream_t s);
+template <int D>
+cudaError_t launch_grid_adjoint(const SimParams& P, float4* UB, const float4* U, float4* PBM,
+                                const int* bbox_u, int n_scenes, int blocks_per_scene,
+                                cudaStream_t s);
+
+// setup.cu
+size_t sort_temp_bytes(int64_t n);
+cudaError_t launch_sort_keys(int dim, int n_grid, int n_scenes, const int64_t* scene_off, int64_t N,
+                             const float* x0, uint64_t* keys, int* idx, cudaStream_t s);
+cudaError_t launch_sort(void* tmp, size_t tmp_bytes, const uint64_t* keys_in, uint64_t* keys_out,
+                        const int* idx_in, int* idx_out, int64_t N, int end_bit, cudaStream_t s);
+cudaError_t launch_gather_initial(int dim, int64_t N, const int* perm, const float* x0,
+                                  const float* v0, const float* C0, const float* F0, const float* E,
+                                  const float* nu, const int* group_in, float* state, float* mu,
+                                  float* la, float* Eo, float* nuo, int* group_out, cudaStream_t s);
+cudaError_t launch_reset_boxes(int* bbox, int* bbox_u, unsigned* done, int n_scenes,
+                               cudaStream_t s);
+cudaError_t launch_gather_rows(int rows, int64_t N, const int* perm, const float* src_caller,
+                               float* dst_internal, cudaStream_t s);
+cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const float* src_internal,
+                                float* dst_caller, cudaStream_t s);
+cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, const float* nu,
+                                 const float* mubar, const float* labar, float* gE, float* gnu,
+                                 cudaStream_t s);
+cudaError_t launch_com(int dim, int64_t N, int n_scenes, const int64_t* scene_off, const int* perm,
+                       const float* xT, const float* x0, double* com, cudaStream_t s);
+cudaError_t launch_loss_seed(int dim, int kind, int64_t N, int n_scenes, const int64_t* scene_off,
+                             const int* perm, const double* com, const float* target, float* loss,
+                             float* dL_dxT, float* dL_dx0, cudaStream_t s);
+
+}  // namespace mpm

@@ -1,0 +1,251 @@
+// setup.cu -- one-time set-up, permutation, loss and output kernels.
+//
+// Particles are reordered once per mpm_set_initial by (scene, Morton code of the
+// initial cell) so that every P2G tile covers a compact block of cells; an elastic
+// body keeps its neighbours, so the order stays coherent for the whole run and the
+// tape never has to record a permutation.  Every input is gathered into that order
+// and every output scattered back to the caller's.
+#include <climits>
+#include <cub/device/device_radix_sort.cuh>
+
+#include "mpm_internal.h"
+
+namespace mpm {
+
+namespace {
+
+__device__ __forceinline__ uint32_t spread2(uint32_t v) {  // 16 bits -> every 2nd bit
+  v &= 0xFFFFu;
+  v = (v | (v << 8)) & 0x00FF00FFu;
+  v = (v | (v << 4)) & 0x0F0F0F0Fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 10 bits -> every 3rd bit
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__device__ __forceinline__ int scene_of(const int64_t* off, int n_scenes, int64_t p) {
+  int lo = 0, hi = n_scenes - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void sort_keys_kernel(int dim, int n_grid, int n_scenes, const int64_t* off, int64_t N,
+                                 const float* x0, uint64_t* keys, int* idx) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+      float X = x0[a * N + p] * (float)n_grid;
+      int ci = (X == X) ? (int)fminf(fmaxf(floorf(X), 0.0f), (float)(n_grid - 1)) : 0;
+      c[a] = (uint32_t)ci;
+    }
+    uint32_t m = dim == 2 ? (spread2(c[1]) | (spread2(c[0]) << 1))
+                          : (spread3(c[2]) | (spread3(c[1]) << 1) | (spread3(c[0]) << 2));
+    keys[p] = ((uint64_t)scene_of(off, n_scenes, p) << 32) | m;
+    idx[p] = (int)p;
+  }
+}
+
+__global__ void gather_initial_kernel(int dim, int64_t N, const int* perm, const float* x0,
+                                      const float* v0, const float* C0, const float* F0,
+                                      const float* E, const float* nu, const int* group_in,
+                                      float* st, float* mu, float* la, float* Eo, float* nuo,
+                                      int* group_out) {
+  const int dd = dim * dim;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = perm[i];
+    for (int a = 0; a < dim; ++a) {
+      st[a * N + i] = x0[a * N + e];
+      st[(dim + a) * N + i] = v0[a * N + e];
+    }
+    for (int k = 0; k < dd; ++k) {
+      st[(2 * dim + k) * N + i] = C0 ? C0[k * N + e] : 0.0f;
+      st[(2 * dim + dd + k) * N + i] = F0 ? F0[k * N + e] : ((k / dim == k % dim) ? 1.0f : 0.0f);
+    }
+    float Ee = E[e], ne = nu[e];
+    Eo[i] = Ee;
+    nuo[i] = ne;
+    // Lame parameters of Young's modulus and Poisson ratio
+    mu[i] = Ee / (2.0f * (1.0f + ne));
+    la[i] = Ee * ne / ((1.0f + ne) * (1.0f - 2.0f * ne));
+    group_out[i] = group_in ? group_in[e] : 0;
+  }
+}
+
+__global__ void reset_boxes_kernel(int* bbox, int* bbox_u, unsigned* done, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * 8; i += gridDim.x * blockDim.x) {
+    bbox[i] = (i % 8) < 4 ? INT_MAX : INT_MIN;
+    bbox_u[i] = (i % 8) < 4 ? INT_MAX : INT_MIN;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0u;
+}
+
+__global__ void gather_rows_kernel(int rows, int64_t N, const int* perm, const float* src,
+                                   float* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = perm[i];
+    for (int r = 0; r < rows; ++r) dst[r * N + i] = src ? src[r * N + e] : 0.0f;
+  }
+}
+
+__global__ void scatter_rows_kernel(int rows, int64_t N, const int* perm, const float* src,
+                                    float* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = perm[i];
+    for (int r = 0; r < rows; ++r) dst[r * N + e] = src[r * N + i];
+  }
+}
+
+// chain rule of the Lame parameters: (mubar, labar) -> (Ebar, nubar)
+__global__ void material_grad_kernel(int64_t N, const int* perm, const float* E, const float* nu,
+                                     const float* mubar, const float* labar, float* gE,
+                                     float* gnu) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = perm[i];
+    float Ee = E[i], v = nu[i];
+    float q = (1.0f + v) * (1.0f - 2.0f * v);
+    float mb = mubar[i], lb = labar[i];
+    if (gE) gE[e] = mb / (2.0f * (1.0f + v)) + lb * v / q;
+    if (gnu) gnu[e] = -mb * Ee / (2.0f * (1.0f + v) * (1.0f + v)) + lb * Ee * (1.0f + 2.0f * v * v) / (q * q);
+  }
+}
+
+// per-scene sums of x_T and x_0 (FP64), com[scene][6]
+__global__ void com_kernel(int dim, int64_t N, int n_scenes, const int64_t* off, const float* xT,
+                           const float* x0, double* com) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int s = scene_of(off, n_scenes, i);
+    for (int a = 0; a < dim; ++a) {
+      atomicAdd(&com[s * 6 + a], (double)xT[a * N + i]);
+      atomicAdd(&com[s * 6 + 3 + a], (double)x0[a * N + i]);
+    }
+  }
+}
+
+__global__ void loss_seed_kernel(int dim, int kind, int64_t N, int n_scenes, const int64_t* off,
+                                 const int* perm, const double* com, const float* target,
+                                 float* loss, float* gT, float* g0) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = scene_of(off, n_scenes, i);
+    const double n_s = (double)(off[s + 1] - off[s]);
+    const int64_t e = perm[i];
+    double L = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      double c = com[s * 6 + a] / n_s, c0 = com[s * 6 + 3 + a] / n_s;
+      double seedT = 0.0, seed0 = 0.0;
+      if (kind == 0) {
+        double r = c - (double)target[s * dim + a];
+        L += r * r;
+        seedT = 2.0 * r / n_s;
+      } else if (a == 0) {
+        L = -(c - c0);
+        seedT = -1.0 / n_s;
+        seed0 = 1.0 / n_s;
+      }
+      gT[a * N + e] = (float)seedT;
+      if (g0) g0[a * N + e] = (float)seed0;
+    }
+    if (i == off[s] && loss) loss[s] = (float)L;
+  }
+}
+
+inline int grid_for(int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
+}
+
+}  // namespace
+
+size_t sort_temp_bytes(int64_t n) {
+  size_t bytes = 0;
+  cudaError_t e = cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const uint64_t*)nullptr,
+                                                  (uint64_t*)nullptr, (const int*)nullptr,
+                                                  (int*)nullptr, (int)n, 0, 64, (cudaStream_t)0);
+  if (e != cudaSuccess) {
+    // no device to query (size-only call on a host without a GPU): a safe upper bound
+    cudaGetLastError();
+    bytes = (size_t)32 * 1024 * 1024 + (size_t)n * 16;
+  }
+  return bytes;
+}
+
+cudaError_t launch_sort_keys(int dim, int n_grid, int n_scenes, const int64_t* scene_off, int64_t N,
+                             const float* x0, uint64_t* keys, int* idx, cudaStream_t s) {
+  sort_keys_kernel<<<grid_for(N), 256, 0, s>>>(dim, n_grid, n_scenes, scene_off, N, x0, keys, idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort(void* tmp, size_t tmp_bytes, const uint64_t* keys_in, uint64_t* keys_out,
+                        const int* idx_in, int* idx_out, int64_t N, int end_bit, cudaStream_t s) {
+  return cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, keys_out, idx_in, idx_out, (int)N,
+                                         0, end_bit, s);
+}
+
+cudaError_t launch_gather_initial(int dim, int64_t N, const int* perm, const float* x0,
+                                  const float* v0, const float* C0, const float* F0, const float* E,
+                                  const float* nu, const int* group_in, float* state, float* mu,
+                                  float* la, float* Eo, float* nuo, int* group_out, cudaStream_t s) {
+  gather_initial_kernel<<<grid_for(N), 256, 0, s>>>(dim, N, perm, x0, v0, C0, F0, E, nu, group_in,
+                                                    state, mu, la, Eo, nuo, group_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_boxes(int* bbox, int* bbox_u, unsigned* done, int n_scenes,
+                               cudaStream_t s) {
+  reset_boxes_kernel<<<grid_for(n_scenes * 8), 256, 0, s>>>(bbox, bbox_u, done, n_scenes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(int rows, int64_t N, const int* perm, const float* src_caller,
+                               float* dst_internal, cudaStream_t s) {
+  gather_rows_kernel<<<grid_for(N), 256, 0, s>>>(rows, N, perm, src_caller, dst_internal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const float* src_internal,
+                                float* dst_caller, cudaStream_t s) {
+  scatter_rows_kernel<<<grid_for(N), 256, 0, s>>>(rows, N, perm, src_internal, dst_caller);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, const float* nu,
+                                 const float* mubar, const float* labar, float* gE, float* gnu,
+                                 cudaStream_t s) {
+  material_grad_kernel<<<grid_for(N), 256, 0, s>>>(N, perm, E, nu, mubar, labar, gE, gnu);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_com(int dim, int64_t N, int n_scenes, const int64_t* scene_off, const int* perm,
+                       const float* xT, const float* x0, double* com, cudaStream_t s) {
+  (void)perm;
+  com_kernel<<<grid_for(N), 256, 0, s>>>(dim, N, n_scenes, scene_off, xT, x0, com);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_seed(int dim, int kind, int64_t N, int n_scenes, const int64_t* scene_off,
+                             const int* perm, const double* com, const float* target, float* loss,
+                             float* dL_dxT, float* dL_dx0, cudaStream_t s) {
+  loss_seed_kernel<<<grid_for(N), 256, 0, s>>>(dim, kind, N, n_scenes, scene_off, perm, com, target,
+                                               loss, dL_dxT, dL_dx0);
+  return cudaGetLastError();
+}
+
+}  // namespace mpm

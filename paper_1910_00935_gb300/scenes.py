@@ -155,14 +155,14 @@ def batched_rects_2d(seed=0, n_scenes=64, steps=512, n_min=1024, n_max=16384, ck
 
 
 def actuated_robots_3d(seed=0, n_scenes=16, steps=2048, dims=(64, 32, 32), n_grid=64,
-                       ckpt_every=64, n_basis=4):
+                       ckpt_every=64, n_basis=4, bottom_dx=4.0):
     """n_scenes 3D box robots of dims[0]*dims[1]*dims[2] particles at spacing dx/2,
-    bottom at y = 4 dx, x from 0.1, centred in z; 8 actuator groups (octants: bit0
+    bottom at y = bottom_dx * dx (4 dx), x from 0.1, centred in z; 8 actuator groups (octants: bit0
     x-half, bit1 y-half, bit2 z-half; fibre axis g mod 3); w ~ U(-50, 50) per scene;
     fixed-corotated E=5e3, nu=0.3; v0 = U(+-0.05); loss -(COM_x(T) - COM_x(0))."""
     dx = 1.0 / n_grid
     h = 0.5 * dx
-    corner = (0.1, 4 * dx, 0.5 - dims[2] * h / 2)
+    corner = (0.1, bottom_dx * dx, 0.5 - dims[2] * h / 2)
     parts = []
     for s in range(n_scenes):
         x0, idx = lattice(3, dims, corner, h)

@@ -1,0 +1,332 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element on the
+same seeded FP32 inputs.
+
+Bars: positions (and the rest of the state) within 1e-4 relative L2 after the
+workload's steps; gradients within 1e-3 relative L2 per block; one-step results
+within 1e-5 (FP32 rounding of one step).  Sizes span many 256-particle tiles with a
+ragged last tile; the full-size workloads are checked on reduced step counts and, for
+the 16-scene robot batch, on sampled scenes the oracle computes one by one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from mpm_testlib import rel_l2, scene_slice, subset_scenes, to_np
+from paper_1910_00935_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+POS_TOL, GRAD_TOL, STEP_TOL = 1e-4, 1e-3, 1e-5
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    from paper_1910_00935_gb300 import build, mpm as m
+    build.build()
+    return m
+
+
+def _run_gpu(mpm, scene, T, seeds=None, loss=True, options=None, max_steps=None):
+    sim = mpm.from_scene(scene, max_steps=max_steps or T)
+    for k, v in (options or {}).items():
+        sim.set_option(k, v)
+    sim.forward(T)
+    out = {"state": [to_np(t) for t in sim.state()]}
+    if loss:
+        L, gT, g0 = sim.loss(scene["desc"]["loss_kind"], torch.as_tensor(scene["arrays"]["target"]))
+        out["loss"], out["seedT"], out["seed0"] = to_np(L), gT, g0
+        if seeds is None:
+            seeds = dict(dL_dx=gT)
+    if seeds is not None:
+        g = sim.backward(**{k: (torch.as_tensor(v) if isinstance(v, np.ndarray) else v)
+                            for k, v in seeds.items()})
+        out["grad"] = {k: to_np(v) for k, v in g.items()}
+        if loss and "seed0" in out and seeds.get("dL_dx") is out.get("seedT"):
+            out["grad"]["gx0"] = out["grad"]["gx0"] + to_np(out["seed0"])
+    rc = mpm.mpm_sync_status(sim.h)
+    assert rc == mpm.MPM_OK, mpm.mpm_last_error(sim.h)
+    out["launches"] = sim.info(mpm.MPM_INFO_KERNEL_LAUNCHES)
+    sim.close()
+    return out
+
+
+def _oracle_states(scene, T):
+    return oracle.simulate(scenes.oracle_view(scene), T)
+
+
+def _compare_states(gpu_state, orc_blocks, scene, tol):
+    d = scene["desc"]["dim"]
+    for si, blk in enumerate(orc_blocks):
+        sl = scene_slice(scene, si)
+        n = sl.stop - sl.start
+        ox, ov, oC, oF = oracle.unpack_state(blk, d, n)
+        gx, gv, gC, gF = [a[:, sl] for a in gpu_state]
+        assert rel_l2(gx, ox) <= tol, ("x", si, rel_l2(gx, ox))
+        assert rel_l2(gF, oF) <= tol, ("F", si, rel_l2(gF, oF))
+        # velocities/affine fields are differences of positions: looser by dt-scaling,
+        # still checked at 10x the position bar
+        assert rel_l2(gv, ov) <= 10 * tol, ("v", si, rel_l2(gv, ov))
+        assert rel_l2(gC, oC) <= 100 * tol, ("C", si, rel_l2(gC, oC))
+
+
+def _random_seeds(scene, rng, scale=1.0):
+    d = scene["desc"]["dim"]
+    N = sum(scene["desc"]["n_particles"])
+    f = lambda r: (scale * rng.standard_normal((r, N))).astype(np.float32)
+    return dict(dL_dx=f(d), dL_dv=f(d), dL_dC=f(d * d) * 1e-3, dL_dF=f(d * d))
+
+
+def _oracle_grad_linear(scene, T, seeds):
+    """Oracle gradient of L = <seeds, state_T> (per scene)."""
+    desc = scene["desc"]
+    p = oracle.params_from_desc(desc)
+    d = desc["dim"]
+    a = scene["arrays"]
+    res = {k: [] for k in ("gx0", "gv0", "gC0", "gF0", "gE", "gnu", "gw")}
+    for si in range(len(desc["n_particles"])):
+        sl = scene_slice(scene, si)
+        mu, la = oracle.lame(a["E"][sl], a["nu"][sl])
+        grp = a["group"][sl] if desc["n_groups"] else None
+        w = a["w"][si] if desc["n_groups"] else None
+        states = oracle.run(p, T, a["x0"][:, sl], a["v0"][:, sl], a["C0"][:, sl], a["F0"][:, sl],
+                            mu, la, grp, w)
+        adjT = oracle.pack_state(*[seeds[k][:, sl] for k in ("dL_dx", "dL_dv", "dL_dC", "dL_dF")])
+        adj0, mub, lab, wb = oracle.grad(p, T, states, adjT, mu, la, grp, w)
+        gx, gv, gC, gF = oracle.unpack_state(adj0, d, sl.stop - sl.start)
+        eb, nb = oracle.lame_adjoint(a["E"][sl], a["nu"][sl], mub, lab)
+        for k, v in (("gx0", gx), ("gv0", gv), ("gC0", gC), ("gF0", gF), ("gE", eb), ("gnu", nb),
+                     ("gw", wb)):
+            res[k].append(v)
+    cat = {k: np.concatenate(v, axis=-1) for k, v in res.items() if k != "gw"}
+    cat["gw"] = np.stack(res["gw"]) if desc["n_groups"] else None
+    return cat
+
+
+def _compare_grads(gpu, orc, keys, tol=GRAD_TOL):
+    for k in keys:
+        r = rel_l2(gpu[k], orc[k])
+        assert r <= tol, (k, r)
+
+
+# ---------------------------------------------------------------------------
+# one step: grid-level and state-level parity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,kw", [("square2d", {}), ("cube3d", dict(n_side=24, n_grid=64)),
+                                     ("robots3d", dict(n_scenes=2, dims=(20, 10, 12)))])
+def test_one_step_matches_oracle(mpm, name, kw):
+    scene = scenes.make(name, **kw)
+    g = _run_gpu(mpm, scene, 1, loss=False)
+    _compare_states(g["state"], _oracle_states(scene, 1), scene, STEP_TOL)
+
+
+# ---------------------------------------------------------------------------
+# the workloads' forward passes
+# ---------------------------------------------------------------------------
+
+def test_square2d_forward_128_steps(mpm):
+    scene = scenes.make("square2d")  # 4096 particles, 16 tiles, fixed-corotated, T = 128
+    g = _run_gpu(mpm, scene, 128)
+    orc = _oracle_states(scene, 128)
+    _compare_states(g["state"], orc, scene, POS_TOL)
+    assert g["launches"] > 0
+
+
+def test_ragged_tiles_and_uneven_batch(mpm):
+    # 3 scenes of log-uniform sizes (none a multiple of the 256-particle tile)
+    base = scenes.make("rects2d", n_scenes=6)
+    scene = subset_scenes(base, [0, 3, 5])
+    T = 24
+    g = _run_gpu(mpm, scene, T)
+    _compare_states(g["state"], _oracle_states(scene, T), scene, POS_TOL)
+
+
+def test_rects2d_batch_forward(mpm):
+    scene = scenes.make("rects2d")  # 64 scenes, log-uniform sizes
+    T = 32
+    g = _run_gpu(mpm, scene, T)
+    _compare_states(g["state"], _oracle_states(scene, T), scene, POS_TOL)
+
+
+def test_cube3d_full_size_short_run(mpm):
+    scene = scenes.make("cube3d")  # 262,144 particles, 128^3 grid, neo-Hookean
+    T = 6
+    g = _run_gpu(mpm, scene, T)
+    _compare_states(g["state"], _oracle_states(scene, T), scene, POS_TOL)
+
+
+def test_robots3d_full_batch_sampled_scenes(mpm):
+    scene = scenes.make("robots3d")  # 16 x 65,536 particles, actuation, fixed-corotated
+    T = 8
+    g = _run_gpu(mpm, scene, T)
+    sampled = [0, 11]
+    sub = subset_scenes(scene, sampled)
+    orc = _oracle_states(sub, T)
+    state_sub = [np.concatenate([a[:, scene_slice(scene, i)] for i in sampled], axis=1)
+                 for a in g["state"]]
+    _compare_states(state_sub, orc, sub, POS_TOL)
+
+
+# ---------------------------------------------------------------------------
+# gradients
+# ---------------------------------------------------------------------------
+
+def test_square2d_grad_full_run(mpm):
+    """The differentiable run: T = 512, checkpoint every 32, COM loss."""
+    scene = scenes.make("square2d_grad")
+    T = 512
+    g = _run_gpu(mpm, scene, T, max_steps=T)
+    o = oracle.loss_and_grad(scenes.oracle_view(scene), T)
+    assert abs(g["loss"][0] - o["loss"]) <= 1e-4 * abs(o["loss"])
+    _compare_grads(g["grad"], o, ["gv0", "gx0"])
+    # gradient w.r.t. the 2-vector initial-velocity bias = sum over particles of dL/dv0
+    bias_g, bias_o = g["grad"]["gv0"].sum(1), o["gv0"].sum(1)
+    assert rel_l2(bias_g, bias_o) <= GRAD_TOL
+    # internal forces conserve momentum and the body never meets a wall, so dL/dE
+    # vanishes identically: both sides must be ~0 on the scale of the loss
+    E = scene["arrays"]["E"].astype(np.float64)
+    assert np.sum(np.abs(o["gE"]) * E) <= 1e-9 * o["loss"]
+    assert np.sum(np.abs(g["grad"]["gE"]) * E) <= 1e-3 * o["loss"]
+
+
+@pytest.mark.parametrize("name,kw,T,k", [
+    ("square2d", dict(n_side=40), 64, 8),
+    ("cube3d", dict(n_side=20, n_grid=64), 24, 8),
+    ("robots3d", dict(n_scenes=2, dims=(16, 8, 8)), 40, 16),
+])
+def test_gradients_of_random_functional(mpm, name, kw, T, k):
+    """dL/d(x0, v0, C0, F0, E, nu, w) of L = <c, state_T> for random c: exercises every
+    adjoint term (the COM loss alone leaves most of them untouched)."""
+    scene = scenes.make(name, **kw)
+    scene["desc"]["ckpt_every"] = k
+    seeds = _random_seeds(scene, np.random.default_rng(5))
+    g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    o = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
+    keys = ["gx0", "gv0", "gC0", "gF0", "gE", "gnu"] + (["gw"] if scene["desc"]["n_groups"] else [])
+    _compare_grads(g["grad"], o, keys)
+
+
+def test_cube3d_full_size_gradient(mpm):
+    scene = scenes.make("cube3d")
+    T = 4
+    scene["desc"]["ckpt_every"] = 2
+    seeds = _random_seeds(scene, np.random.default_rng(9))
+    g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    o = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
+    _compare_grads(g["grad"], o, ["gx0", "gv0", "gC0", "gF0", "gE", "gnu"])
+
+
+def test_robots3d_displacement_loss_gradient(mpm):
+    """Robots standing on the sticky floor (lowest stencils reach the wall nodes), so
+    the actuation moves the centre of mass and dL/dw is not identically zero."""
+    scene = scenes.make("robots3d", n_scenes=2, dims=(16, 8, 8), bottom_dx=3.0)
+    T = 64
+    g = _run_gpu(mpm, scene, T)
+    o = oracle.loss_and_grad(scenes.oracle_view(scene), T)
+    assert rel_l2(g["loss"], o["losses"]) <= 1e-3
+    _compare_grads(g["grad"], o, ["gw", "gx0", "gv0"])
+
+
+# ---------------------------------------------------------------------------
+# tape and launch-form invariances
+# ---------------------------------------------------------------------------
+
+def test_checkpoint_interval_invariance(mpm):
+    """Appendix D.2: segment-wise recomputation gives the same gradient for every
+    segment length (here against the oracle, which stores every state, and against
+    each other; the GPU re-simulation differs from the forward only by FP32
+    atomic-order rounding)."""
+    scene = scenes.make("square2d", n_side=32)
+    T = 48
+    seeds = _random_seeds(scene, np.random.default_rng(1))
+    o = _oracle_grad_linear(scene, T, {k: v.astype(np.float64) for k, v in seeds.items()})
+    grads = []
+    for k in (1, 7, 16, 48):
+        scene["desc"]["ckpt_every"] = k
+        grads.append(_run_gpu(mpm, scene, T, seeds=seeds, loss=False)["grad"])
+    for g in grads:
+        _compare_grads(g, o, ["gx0", "gv0", "gF0", "gE"])
+    for g in grads[1:]:
+        for key in ("gx0", "gv0", "gF0", "gE"):
+            assert rel_l2(g[key], grads[0][key]) <= GRAD_TOL, key
+
+
+def test_graphs_and_tiles_do_not_change_results(mpm):
+    scene = scenes.make("cube3d", n_side=16, n_grid=64)
+    T = 12
+    seeds = _random_seeds(scene, np.random.default_rng(2))
+    ref = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    for opts in ({mpm.MPM_OPT_USE_GRAPHS: 0}, {mpm.MPM_OPT_SMEM_TILE: 0},
+                 {mpm.MPM_OPT_TILE_CAPACITY: 64}):
+        g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False, options=opts)
+        assert rel_l2(g["state"][0], ref["state"][0]) <= 1e-6
+        for key in ("gx0", "gv0", "gF0"):
+            assert rel_l2(g["grad"][key], ref["grad"][key]) <= 1e-4, (opts, key)
+
+
+def test_batched_equals_unbatched(mpm):
+    base = scenes.make("rects2d", n_scenes=5)
+    T = 20
+    seeds = _random_seeds(base, np.random.default_rng(3))
+    batched = _run_gpu(mpm, base, T, seeds=seeds, loss=False)
+    for i in (1, 4):
+        single = subset_scenes(base, [i])
+        sl = scene_slice(base, i)
+        s_seeds = {k: np.ascontiguousarray(v[:, sl]) for k, v in seeds.items()}
+        g = _run_gpu(mpm, single, T, seeds=s_seeds, loss=False)
+        assert rel_l2(batched["state"][0][:, sl], g["state"][0]) <= 1e-6
+        assert rel_l2(batched["grad"]["gv0"][:, sl], g["grad"]["gv0"]) <= 1e-4
+
+
+def test_autograd_function_matches_backward(mpm):
+    scene = scenes.make("square2d", n_side=24)
+    T = 16
+    sim = mpm.from_scene(scene, max_steps=T)
+    a = {k: torch.as_tensor(v).cuda() for k, v in scene["arrays"].items()}
+    v0 = a["v0"].clone().requires_grad_(True)
+    E = a["E"].clone().requires_grad_(True)
+    xT, vT, CT, FT = mpm.simulate(sim, T, a["x0"], v0, a["C0"], a["F0"], E, a["nu"])
+    loss = ((xT.mean(1) - torch.tensor([0.7, 0.5], device="cuda")) ** 2).sum() + (vT ** 2).sum()
+    gv, gE = torch.autograd.grad(loss, [v0, E])
+    seeds = dict(dL_dx=to_np(2 * (xT.mean(1, keepdim=True) - torch.tensor([[0.7], [0.5]], device="cuda"))
+                             / xT.shape[1] * torch.ones_like(xT)).astype(np.float32),
+                 dL_dv=to_np(2 * vT).astype(np.float32),
+                 dL_dC=np.zeros((4, xT.shape[1]), np.float32),
+                 dL_dF=np.zeros((4, xT.shape[1]), np.float32))
+    orc = _oracle_grad_linear(scene, T, {k: v.astype(np.float64) for k, v in seeds.items()})
+    assert rel_l2(to_np(gv), orc["gv0"]) <= GRAD_TOL
+    assert rel_l2(to_np(gE), orc["gE"]) <= GRAD_TOL
+    sim.close()
+
+
+# ---------------------------------------------------------------------------
+# error behaviour (host-made failures only; nothing here can fault the GPU)
+# ---------------------------------------------------------------------------
+
+def test_out_of_grid_particle_reports_oob(mpm):
+    scene = scenes.make("square2d", n_side=16)
+    scene["arrays"]["x0"][0, 5] = 0.001  # x/dx = 0.128 < 0.5: stencil base -1
+    sim = mpm.from_scene(scene, max_steps=4)
+    sim.forward(2)
+    assert mpm.mpm_sync_status(sim.h) == mpm.MPM_ERR_OOB
+    assert "grid" in mpm.mpm_last_error(sim.h)
+    assert mpm.mpm_sync_status(sim.h) == mpm.MPM_OK  # the error word was cleared
+    sim.close()
+
+
+def test_state_errors(mpm):
+    scene = scenes.make("square2d", n_side=8)
+    sim = mpm.Simulator(scene["desc"], 8)
+    with pytest.raises(mpm.MPMError) as e:
+        sim.forward(4)  # before set_initial
+    assert e.value.code == mpm.MPM_ERR_STATE
+    sim.close()
+    sim = mpm.from_scene(scene, max_steps=8)
+    with pytest.raises(mpm.MPMError) as e:
+        sim.backward()
+    assert e.value.code == mpm.MPM_ERR_STATE
+    with pytest.raises(mpm.MPMError) as e:
+        sim.forward(9)
+    assert e.value.code == mpm.MPM_ERR_STATE
+    sim.close()
