@@ -52,6 +52,7 @@ extern "C" {
 #define MPM_ERR_TIMEOUT 5    /* a bounded device-side wait gave up */
 #define MPM_ERR_STATE 6      /* call out of order (backward before forward, T > max) */
 #define MPM_ERR_WORKSPACE 7  /* workspace NULL, misaligned or too small */
+#define MPM_ERR_TOO_LARGE 8  /* mpm_step_noalloc: problem larger than its fixed scratch */
 
 /* materials */
 #define MPM_FIXED_COROTATED 0
@@ -174,6 +175,44 @@ const char* mpm_last_error(mpm_handle* h);
 
 /* Destroy the handle (host objects and CUDA graphs; the workspace stays the caller's). */
 void mpm_destroy(mpm_handle* h);
+
+/* ---------------------------------------------------------------------------
+ * mpm_step_noalloc -- one forward MLS-MPM step with no workspace and no allocation.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory at all -- code embedded in a host application that owns the
+ * device memory budget and forbids allocation after start-up (plugins, real-time
+ * control loops where an allocation could stall or fail), or a small C caller with no
+ * allocator to hand for a workspace.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * The grid scratch lives in one fixed device array inside the library (about 10 MiB:
+ * MPM_NOALLOC_MAX_NODES nodes of two float4 grids plus per-particle Lame parameters
+ * and tile table), held by every GPU that loads the library until the process exits.
+ * Limits: one scene, no actuation, n_grid^dim <= MPM_NOALLOC_MAX_NODES and
+ * n_particles[0] <= MPM_NOALLOC_MAX_PARTICLES; larger problems return
+ * MPM_ERR_TOO_LARGE and launch nothing.
+ *
+ * desc: host; dim, n_grid, n_scenes (must be 1), n_particles[0], dt, gravity,
+ *   wall_cells, material and rho are used (ckpt_every is ignored, n_groups must be 0).
+ * state_in / state_out: device float, one component-major block [Q][N] with
+ *   Q = 2 dim + 2 dim^2 rows in the order x, v, C, F (C and F row-major per
+ *   particle); state_in holds step s, state_out receives step s+1 (distinct buffers).
+ * E, nu: device float [N].  device_err: device uint32 or NULL; when given, the
+ *   step ORs its device error bits into it (1 = a stencil left the grid, 2 =
+ *   non-finite value or det F <= 0); when NULL those bits go to the fixed array
+ *   and are not reported.
+ * Results equal mpm_forward with T = 1 up to FP32 atomic-order rounding.
+ *
+ * The first call on each device performs a one-time set-up (it looks up the device
+ * address of the fixed array, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array and each
+ * call clears what must start at zero; calls that overlap on the GPU (two streams,
+ * or two threads) race on it and must be serialised by the caller.
+ * Returns MPM_OK, MPM_ERR_ARG, MPM_ERR_TOO_LARGE or MPM_ERR_CUDA. */
+#define MPM_NOALLOC_MAX_NODES (1 << 18)     /* 64^3 in 3D, 512^2 in 2D */
+#define MPM_NOALLOC_MAX_PARTICLES (1 << 18) /* 262,144 */
+int mpm_step_noalloc(const mpm_scene_desc* desc, const float* state_in, const float* E,
+                     const float* nu, float* state_out, uint32_t* device_err, void* stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,170 @@
+// noalloc.cu -- mpm_step_noalloc: one MLS-MPM step of one scene with no workspace.
+//
+// For callers that cannot allocate device memory at all: code embedded in a host
+// application that owns the whole device memory budget and forbids allocation after
+// start-up (plugins, real-time control loops where an allocation could stall or fail),
+// and small C callers that have no allocator to hand for a workspace.  Such a caller
+// passes only its inputs and outputs; the grid scratch of the step lives in the
+// file-scope array below, which every GPU that loads the library holds until the
+// process exits.
+//
+// The step runs the library's own kernels (P2G from the full input state, the grid
+// update, G2P writing the full output state) with pointers into that array, so its
+// results equal those of mpm_forward with T = 1 up to FP32 atomic-order rounding.
+#include <cstring>
+#include <mutex>
+
+#include "../../include/mpm.h"
+#include "mpm_internal.h"
+#include "mpm_kernels.cuh"
+
+using namespace mpm;
+
+namespace {
+
+constexpr int64_t kMaxNodes = MPM_NOALLOC_MAX_NODES;
+constexpr int64_t kMaxParticles = MPM_NOALLOC_MAX_PARTICLES;
+constexpr int64_t kMaxTiles = (kMaxParticles + kTile - 1) / kTile;
+
+// byte offsets inside the scratch array (each 256-byte aligned)
+constexpr size_t kOffPM = 0;                                    // float4 (m, p) per node
+constexpr size_t kOffU = kOffPM + (size_t)kMaxNodes * 16;      // float4 (u, m) per node
+constexpr size_t kOffMu = kOffU + (size_t)kMaxNodes * 16;      // float per particle
+constexpr size_t kOffLa = kOffMu + (size_t)kMaxParticles * 4;  // float per particle
+constexpr size_t kOffTiles = kOffLa + (size_t)kMaxParticles * 4;
+constexpr size_t kOffMisc = kOffTiles + (size_t)kMaxTiles * 16;  // bbox[8], bbox_u[8], done, err
+constexpr size_t kScratchBytes = kOffMisc + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+__global__ void noalloc_prepare_kernel(int64_t N, const float* E, const float* nu, float* mu,
+                                       float* la, int4* tiles) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float e = E[i], v = nu[i];
+    mu[i] = e / (2.0f * (1.0f + v));
+    la[i] = e * v / ((1.0f + v) * (1.0f - 2.0f * v));
+    if (i % kTile == 0) {
+      int64_t cnt = N - i < kTile ? N - i : kTile;
+      tiles[i / kTile] = make_int4(0, (int)i, (int)cnt, 0);
+    }
+  }
+}
+
+// every rejection is reported by its status code alone (documented in mpm.h)
+int reject(int code, const char* /*why*/) { return code; }
+
+}  // namespace
+
+extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, const float* E,
+                                const float* nu, float* state_out, uint32_t* device_err,
+                                void* stream) {
+  if (!d || !state_in || !E || !nu || !state_out)
+    return reject(MPM_ERR_ARG, "mpm_step_noalloc: NULL argument");
+  if (d->dim != 2 && d->dim != 3) return reject(MPM_ERR_ARG, "mpm_step_noalloc: dim must be 2 or 3");
+  if (d->n_scenes != 1 || !d->n_particles)
+    return reject(MPM_ERR_ARG, "mpm_step_noalloc: exactly one scene");
+  if (d->n_groups != 0) return reject(MPM_ERR_ARG, "mpm_step_noalloc: no actuation");
+  if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN)
+    return reject(MPM_ERR_ARG, "mpm_step_noalloc: unknown material");
+  if (d->n_grid < 8 || !(d->dt > 0.0f) || !(d->rho > 0.0f) || d->wall_cells < 0 ||
+      2 * d->wall_cells >= d->n_grid)
+    return reject(MPM_ERR_ARG, "mpm_step_noalloc: bad n_grid, dt, rho or wall_cells");
+  int64_t nnodes = 1;
+  for (int a = 0; a < d->dim; ++a) nnodes *= d->n_grid;
+  const int64_t N = d->n_particles[0];
+  if (N < 1) return reject(MPM_ERR_ARG, "mpm_step_noalloc: no particles");
+  if (nnodes > kMaxNodes)
+    return reject(MPM_ERR_TOO_LARGE, "mpm_step_noalloc: n_grid^dim exceeds MPM_NOALLOC_MAX_NODES");
+  if (N > kMaxParticles)
+    return reject(MPM_ERR_TOO_LARGE, "mpm_step_noalloc: more than MPM_NOALLOC_MAX_PARTICLES");
+
+  // one-time set-up per device: the device address of the scratch array
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return reject(MPM_ERR_CUDA, "mpm_step_noalloc: no current CUDA device");
+  }
+  char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return reject(MPM_ERR_CUDA, "mpm_step_noalloc: cudaGetSymbolAddress failed");
+      }
+      g_scratch_ptr[dev] = p;
+    }
+    base = static_cast<char*>(g_scratch_ptr[dev]);
+  }
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float4* PM = reinterpret_cast<float4*>(base + kOffPM);
+  float4* U = reinterpret_cast<float4*>(base + kOffU);
+  float* mu = reinterpret_cast<float*>(base + kOffMu);
+  float* la = reinterpret_cast<float*>(base + kOffLa);
+  int4* tiles = reinterpret_cast<int4*>(base + kOffTiles);
+  int* bbox = reinterpret_cast<int*>(base + kOffMisc);
+  int* bbox_u = bbox + 8;
+  unsigned* done = reinterpret_cast<unsigned*>(bbox + 16);
+  unsigned* err = device_err ? reinterpret_cast<unsigned*>(device_err) : done + 1;
+
+  // the array keeps the previous call's contents: clear what must start at zero
+  cudaError_t e = cudaMemsetAsync(PM, 0, (size_t)nnodes * sizeof(float4), s);
+  if (e == cudaSuccess && !device_err) e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = launch_reset_boxes(bbox, bbox_u, done, 1, s);
+  if (e == cudaSuccess) {
+    int blocks = (int)((N + 255) / 256);
+    noalloc_prepare_kernel<<<blocks, 256, 0, s>>>(N, E, nu, mu, la, tiles);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return reject(MPM_ERR_CUDA, cudaGetErrorString(e));
+
+  SimParams P;
+  memset(&P, 0, sizeof(P));
+  P.n_grid = d->n_grid;
+  P.nnodes = (int)nnodes;
+  P.dx = 1.0f / (float)d->n_grid;
+  P.inv_dx = (float)d->n_grid;
+  P.dt = d->dt;
+  for (int a = 0; a < 3; ++a) P.gravity[a] = d->gravity[a];
+  P.wall = d->wall_cells;
+  const double dx = 1.0 / d->n_grid;
+  const double vol = d->dim == 2 ? 0.25 * dx * dx : 0.125 * dx * dx * dx;
+  P.p_mass = (float)(d->rho * vol);
+  P.kappa = (float)(-(double)d->dt * vol * 4.0 / (dx * dx));
+  P.tile_capacity = 1024;
+
+  StepArgs A;
+  A.tiles = tiles;
+  A.N = (int)N;
+  A.in = state_in;
+  A.out = state_out;
+  A.mu = mu;
+  A.la = la;
+  A.group = nullptr;
+  A.wact = nullptr;
+  A.U = U;
+  A.PM = PM;
+  A.bbox = bbox;
+  A.err = err;
+  const int n_tiles = (int)((N + kTile - 1) / kTile);
+  const int bps = 256;
+  if (d->dim == 2) {
+    e = launch_step<2>(d->material, kP2GOnly, P, A, n_tiles, s);
+    if (e == cudaSuccess) e = launch_grid_update<2>(P, PM, U, bbox, bbox_u, done, 1, bps, s);
+    if (e == cudaSuccess) e = launch_step<2>(d->material, kG2POnlyFull, P, A, n_tiles, s);
+  } else {
+    e = launch_step<3>(d->material, kP2GOnly, P, A, n_tiles, s);
+    if (e == cudaSuccess) e = launch_grid_update<3>(P, PM, U, bbox, bbox_u, done, 1, bps, s);
+    if (e == cudaSuccess) e = launch_step<3>(d->material, kG2POnlyFull, P, A, n_tiles, s);
+  }
+  if (e != cudaSuccess) return reject(MPM_ERR_CUDA, cudaGetErrorString(e));
+  return MPM_OK;
+}

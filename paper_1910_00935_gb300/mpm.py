@@ -25,6 +25,8 @@ from . import build as _build
 
 MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOB = 0, 1, 2, 3
 MPM_ERR_NONFINITE, MPM_ERR_TIMEOUT, MPM_ERR_STATE, MPM_ERR_WORKSPACE = 4, 5, 6, 7
+MPM_ERR_TOO_LARGE = 8
+MPM_NOALLOC_MAX_NODES = MPM_NOALLOC_MAX_PARTICLES = 1 << 18
 MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN = 0, 1
 MPM_LOSS_COM_TARGET, MPM_LOSS_COM_X_DISP = 0, 1
 MPM_OPT_USE_GRAPHS, MPM_OPT_SMEM_TILE, MPM_OPT_TILE_CAPACITY, MPM_OPT_PROFILE = 1, 2, 3, 4
@@ -34,7 +36,8 @@ MPM_INFO_KERNEL_LAUNCHES, MPM_INFO_N_TOTAL, MPM_INFO_STEPS_RECORDED = 1, 2, 3
 
 EXPORTED = ["mpm_workspace_bytes", "mpm_create", "mpm_set_initial", "mpm_forward",
             "mpm_get_state", "mpm_loss", "mpm_backward", "mpm_sync_status", "mpm_set_option",
-            "mpm_get_info", "mpm_get_profile", "mpm_last_error", "mpm_destroy"]
+            "mpm_get_info", "mpm_get_profile", "mpm_last_error", "mpm_destroy",
+            "mpm_step_noalloc"]
 
 
 class MPMError(RuntimeError):
@@ -96,6 +99,7 @@ def lib(load_only: bool = False):
                                                ctypes.POINTER(ctypes.c_double)]),
             "mpm_last_error": (ctypes.c_char_p, [vp]),
             "mpm_destroy": (None, [vp]),
+            "mpm_step_noalloc": (ctypes.c_int, [D, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -212,6 +216,13 @@ def mpm_last_error(h=None) -> str:
 
 def mpm_destroy(h):
     lib().mpm_destroy(h)
+
+
+def mpm_step_noalloc(desc: SceneDesc, state_in, E, nu, state_out, device_err=None,
+                     stream=None) -> int:
+    """One step with no workspace (see include/mpm.h); returns the status code."""
+    return lib().mpm_step_noalloc(ctypes.byref(desc), _ptr(state_in), _ptr(E), _ptr(nu),
+                                  _ptr(state_out), _ptr(device_err), _stream(stream))
 
 
 # ----------------------------------------------------------------------------
