@@ -219,6 +219,7 @@ SimParams params_for(const mpm_handle* h, int t) {
     P.basis[k - 1] =
         (float)std::sin(two_pi * k * (double)t / (double)d.act_period + (double)d.act_phase);
   P.tile_capacity = h->smem_tile ? h->tile_capacity : 0;
+  P.f_diag = 0.0f;  // the workspace holds E = F - I
   return P;
 }
 
@@ -573,7 +574,8 @@ int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* s
   int r0 = 0;
   for (int k = 0; k < 4; ++k) {
     if (outs[k]) {
-      CK(launch_scatter_rows(rows[k], m.N, perm, fin + (size_t)r0 * m.N, outs[k], s));
+      // the workspace holds E = F - I; the caller gets F
+      CK(launch_scatter_rows(rows[k], m.N, perm, fin + (size_t)r0 * m.N, outs[k], k == 3 ? D : 0, s));
       ++h->launches;
     }
     r0 += rows[k];
@@ -632,7 +634,7 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   r0 = 0;
   for (int k = 0; k < 4; ++k) {
     if (outs[k]) {
-      CK(launch_scatter_rows(rows[k], m.N, perm, adj + (size_t)r0 * m.N, outs[k], s));
+      CK(launch_scatter_rows(rows[k], m.N, perm, adj + (size_t)r0 * m.N, outs[k], 0, s));
       ++h->launches;
     }
     r0 += rows[k];

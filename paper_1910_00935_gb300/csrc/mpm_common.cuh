@@ -5,6 +5,9 @@
 // the stress adjoint, and the FP64 polar decomposition with its adjoint (the
 // hand-written SVD/polar gradient of Appendix C).  Bulk arithmetic is FP32; the
 // polar factor R, F - R, S = R^T F and the polar adjoint are FP64.
+//
+// The deformation gradient is carried as E = F - I: an FP32 F close to a rotation-free
+// identity keeps only ~1e-7/|strain| relative precision on the strain, E keeps 1e-7.
 #pragma once
 
 #include <cstdint>
@@ -35,23 +38,26 @@ struct SimParams {
   int n_groups, n_basis;
   float basis[kMaxBasis];  // sin(2 pi k t / P + phi), k = 1..n_basis, at this pass's step
   int tile_capacity;       // max nodes of a CTA's shared grid tile (0 = global atomics)
+  float f_diag;            // the F rows of the state hold F - f_diag I (0: E = F - I, 1: F)
 };
 
 // ---------------------------------------------------------------------------
-// quadratic B-spline stencil (MLS-MPM, Hu et al. 2018)
+// quadratic B-spline stencil (MLS-MPM, Hu et al. 2018), kept per axis: the weight of
+// node base + (i, j, k) is w[0][i] w[1][j] w[2][k] and dpos = (dp[0][i], dp[1][j], dp[2][k])
 // ---------------------------------------------------------------------------
 template <int D>
-struct Stencil {
+struct Axes {
   int base[D];
   float f[D];      // x/dx - base in [0.5, 1.5)
   float w[D][3];
   float dw[D][3];  // dw/df
+  float dp[D][3];  // (o - f) dx
 };
 
 // Returns false (and leaves a harmless in-range base) when the stencil would leave
 // [0, n-1] or x is not finite; such a particle must not touch the grid.
 template <int D>
-__device__ __forceinline__ bool make_stencil(const float* x, const SimParams& P, Stencil<D>& s) {
+__device__ __forceinline__ bool make_axes(const float* x, const SimParams& P, Axes<D>& s) {
   bool ok = true;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -70,40 +76,26 @@ __device__ __forceinline__ bool make_stencil(const float* x, const SimParams& P,
     s.dw[a][0] = -r0;
     s.dw[a][1] = -2.0f * r1;
     s.dw[a][2] = r2;
+    s.dp[a][0] = -f * P.dx;
+    s.dp[a][1] = (1.0f - f) * P.dx;
+    s.dp[a][2] = (2.0f - f) * P.dx;
   }
   return ok;
 }
 
+// weights only, from f (used by scatters that receive f from another thread)
 template <int D>
-__device__ __forceinline__ void offsets(int o, int off[D]) {
-  if (D == 2) {
-    off[0] = o / 3;
-    off[1] = o % 3;
-  } else {
-    off[0] = o / 9;
-    off[1] = (o / 3) % 3;
-    off[D - 1] = o % 3;
-  }
-}
-
-// weight, dW/dx and dpos = x_i - x_p for one stencil offset
-template <int D>
-__device__ __forceinline__ void node_terms(const Stencil<D>& s, const int off[D], const SimParams& P,
-                                           float& W, float gW[D], float dpos[D]) {
-  float wa[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) wa[a] = s.w[a][off[a]];
-  W = wa[0];
-#pragma unroll
-  for (int a = 1; a < D; ++a) W *= wa[a];
+__device__ __forceinline__ void axes_from_f(const float f[D], const SimParams& P, float w[D][3],
+                                            float dp[D][3]) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    float g = s.dw[a][off[a]] * P.inv_dx;
-#pragma unroll
-    for (int b = 0; b < D; ++b)
-      if (b != a) g *= wa[b];
-    gW[a] = g;
-    dpos[a] = ((float)off[a] - s.f[a]) * P.dx;
+    float r0 = 1.5f - f[a], r1 = f[a] - 1.0f, r2 = f[a] - 0.5f;
+    w[a][0] = 0.5f * r0 * r0;
+    w[a][1] = 0.75f - r1 * r1;
+    w[a][2] = 0.5f * r2 * r2;
+    dp[a][0] = -f[a] * P.dx;
+    dp[a][1] = (1.0f - f[a]) * P.dx;
+    dp[a][2] = (2.0f - f[a]) * P.dx;
   }
 }
 
@@ -128,21 +120,28 @@ __device__ __forceinline__ void cofactor(const float A[D][D], float c[D][D]) {
   }
 }
 
-// J - 1 for F = I + E, summed by invariants so that it keeps its relative accuracy
-// when F is close to the identity (E is exact in FP32 for F_ii in [0.5, 2]).
+// J - 1 for F = I + E, summed by invariants (trace, principal minors, det E) so that it
+// keeps its relative accuracy when F is close to the identity.
 template <int D>
-__device__ __forceinline__ float det_minus_one(const float F[D][D]) {
+__device__ __forceinline__ float det_minus_one(const float E[D][D]) {
   if (D == 2) {
-    float e00 = F[0][0] - 1.0f, e11 = F[1][1] - 1.0f;
-    return e00 + e11 + (e00 * e11 - F[0][1] * F[1][0]);
+    return E[0][0] + E[1][1] + (E[0][0] * E[1][1] - E[0][1] * E[1][0]);
   } else {
-    float e00 = F[0][0] - 1.0f, e11 = F[1][1] - 1.0f, e22 = F[2][2] - 1.0f;
-    float m2 = (e00 * e11 - F[0][1] * F[1][0]) + (e00 * e22 - F[0][2] * F[2][0]) +
-               (e11 * e22 - F[1][2] * F[2][1]);
-    float d3 = e00 * (e11 * e22 - F[1][2] * F[2][1]) - F[0][1] * (F[1][0] * e22 - F[1][2] * F[2][0]) +
-               F[0][2] * (F[1][0] * F[2][1] - e11 * F[2][0]);
-    return (e00 + e11 + e22) + m2 + d3;
+    float m2 = (E[0][0] * E[1][1] - E[0][1] * E[1][0]) + (E[0][0] * E[2][2] - E[0][2] * E[2][0]) +
+               (E[1][1] * E[2][2] - E[1][2] * E[2][1]);
+    float d3 = E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1]) -
+               E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0]) +
+               E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]);
+    return (E[0][0] + E[1][1] + E[2][2]) + m2 + d3;
   }
+}
+
+template <int D>
+__device__ __forceinline__ void plus_identity(const float E[D][D], float F[D][D]) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) F[i][j] = E[i][j] + (i == j ? 1.0f : 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -160,12 +159,17 @@ struct Polar {
 // from X = F, which converges quadratically to the orthogonal polar factor and keeps
 // det X > 0 (Higham 1986).  Returns false for det F <= 0 or non-finite input.
 template <int D>
-__device__ __forceinline__ bool polar_f64(const float F[D][D], Polar<D>& p) {
+__device__ __forceinline__ bool polar_f64(const float E[D][D], Polar<D>& p) {
+  double Fd[D][D];  // F = I + E, exact in FP64
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) Fd[i][j] = (double)E[i][j] + (i == j ? 1.0 : 0.0);
   if (D == 2) {
-    double c = (double)F[0][0] + (double)F[1][1];
-    double s = (double)F[1][0] - (double)F[0][1];
+    double c = Fd[0][0] + Fd[1][1];
+    double s = Fd[1][0] - Fd[0][1];
     double r = sqrt(c * c + s * s);
-    double det = (double)F[0][0] * F[1][1] - (double)F[0][1] * F[1][0];
+    double det = Fd[0][0] * Fd[1][1] - Fd[0][1] * Fd[1][0];
     if (!(det > 0.0) || !(r > 0.0)) {
       c = 1.0; s = 0.0; r = 1.0;
     }
@@ -179,7 +183,7 @@ __device__ __forceinline__ bool polar_f64(const float F[D][D], Polar<D>& p) {
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         p.Rf[i][j] = (float)p.R[i][j];
-        p.Df[i][j] = (float)((double)F[i][j] - p.R[i][j]);
+        p.Df[i][j] = (float)(Fd[i][j] - p.R[i][j]);
       }
     return det > 0.0 && r > 0.0;
   } else {
@@ -187,7 +191,7 @@ __device__ __forceinline__ bool polar_f64(const float F[D][D], Polar<D>& p) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) X[i][j] = (double)F[i][j];
+      for (int j = 0; j < 3; ++j) X[i][j] = Fd[i][j];
     bool ok = true;
     for (int it = 0; it < 24; ++it) {
       double c[3][3];
@@ -227,7 +231,7 @@ __device__ __forceinline__ bool polar_f64(const float F[D][D], Polar<D>& p) {
       for (int j = 0; j < 3; ++j) {
         p.R[i][j] = X[i][j];
         p.Rf[i][j] = (float)X[i][j];
-        p.Df[i][j] = (float)((double)F[i][j] - X[i][j]);
+        p.Df[i][j] = (float)(Fd[i][j] - X[i][j]);
       }
     return ok;
   }
@@ -239,7 +243,7 @@ __device__ __forceinline__ bool polar_f64(const float F[D][D], Polar<D>& p) {
 // (tr(S) I - S) y = b on axial vectors (eigenvalues sigma_i + sigma_j > 0), in 2D
 // y = b / tr(S); no singular-value differences appear.
 template <int D>
-__device__ __forceinline__ void polar_adjoint_f64(const float F[D][D], const Polar<D>& p,
+__device__ __forceinline__ void polar_adjoint_f64(const float E[D][D], const Polar<D>& p,
                                                   const float Rbar[D][D], float Fbar[D][D]) {
   double M[D][D], S[D][D];
 #pragma unroll
@@ -250,7 +254,7 @@ __device__ __forceinline__ void polar_adjoint_f64(const float F[D][D], const Pol
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         m += p.R[k][i] * (double)Rbar[k][j];
-        s += p.R[k][i] * (double)F[k][j];
+        s += p.R[k][i] * ((double)E[k][j] + (k == j ? 1.0 : 0.0));
       }
       M[i][j] = m;
       S[i][j] = s;
@@ -306,21 +310,24 @@ struct StressCache {
 // tau = 2 mu (F - R) F^T + la (J - 1) J I        (fixed-corotated)
 // tau = mu (F F^T - I) + la ln(J) I               (neo-Hookean)
 // tau += act (F e)(F e)^T, e = unit vector of `axis` (actuation fibre)
+// with F = I + E; every product is formed on E (or on F - R) so small strains keep
+// their relative precision.
 template <int D, int MAT>
-__device__ __forceinline__ bool kirchhoff(const float F[D][D], float mu, float la, float act, int axis,
+__device__ __forceinline__ bool kirchhoff(const float E[D][D], float mu, float la, float act, int axis,
                                           float tau[D][D], StressCache<D>& sc) {
   bool ok = true;
-  sc.Jm1 = det_minus_one<D>(F);
+  sc.Jm1 = det_minus_one<D>(E);
   sc.J = 1.0f + sc.Jm1;
   if (MAT == kFixedCorotated) {
-    ok = polar_f64<D>(F, sc.pol);
+    ok = polar_f64<D>(E, sc.pol);
+    // (F - R) F^T = Df + Df E^T
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        float s = 0.0f;
+        float s = sc.pol.Df[i][j];
 #pragma unroll
-        for (int k = 0; k < D; ++k) s += sc.pol.Df[i][k] * F[j][k];
+        for (int k = 0; k < D; ++k) s += sc.pol.Df[i][k] * E[j][k];
         tau[i][j] = 2.0f * mu * s;
       }
     float vol = la * sc.Jm1 * sc.J;
@@ -328,12 +335,7 @@ __device__ __forceinline__ bool kirchhoff(const float F[D][D], float mu, float l
     for (int i = 0; i < D; ++i) tau[i][i] += vol;
   } else {
     ok = sc.J > 0.0f;
-    // F F^T - I = E + E^T + E E^T with E = F - I
-    float E[D][D];
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int j = 0; j < D; ++j) E[i][j] = F[i][j] - (i == j ? 1.0f : 0.0f);
+    // F F^T - I = E + E^T + E E^T
     float lnJ = log1pf(sc.Jm1);
 #pragma unroll
     for (int i = 0; i < D; ++i)
@@ -348,7 +350,7 @@ __device__ __forceinline__ bool kirchhoff(const float F[D][D], float mu, float l
   if (act != 0.0f) {
     float fe[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) fe[i] = F[i][axis];
+    for (int i = 0; i < D; ++i) fe[i] = E[i][axis] + (i == axis ? 1.0f : 0.0f);
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -357,16 +359,17 @@ __device__ __forceinline__ bool kirchhoff(const float F[D][D], float mu, float l
   return ok && (sc.J == sc.J);
 }
 
-// Given taubar = dL/dtau, accumulate Fbar, mubar, labar and return abar = dL/dact.
+// Given taubar = dL/dtau, accumulate Fbar (= dL/dE), mubar, labar and return abar = dL/dact.
 template <int D, int MAT>
-__device__ __forceinline__ float kirchhoff_adjoint(const float F[D][D], float mu, float la, float act,
+__device__ __forceinline__ float kirchhoff_adjoint(const float E[D][D], float mu, float la, float act,
                                                    int axis, const StressCache<D>& sc,
                                                    const float tb[D][D], float Fbar[D][D],
                                                    float& mubar, float& labar) {
   float trtb = 0.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i) trtb += tb[i][i];
-  float cof[D][D];
+  float F[D][D], cof[D][D];
+  plus_identity<D>(E, F);
   cofactor<D>(F, cof);
   if (MAT == kFixedCorotated) {
     // d/dF [2 mu (F F^T - R F^T)] at fixed R: 2 mu (tb F + tb^T (F - R));  Rbar = -2 mu tb F
@@ -376,18 +379,18 @@ __device__ __forceinline__ float kirchhoff_adjoint(const float F[D][D], float mu
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        float tF = 0.0f, tD = 0.0f, DFt = 0.0f;
+        float tF = tb[i][j], tD = 0.0f, DFt = sc.pol.Df[i][j];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          tF += tb[i][k] * F[k][j];
+          tF += tb[i][k] * E[k][j];
           tD += tb[k][i] * sc.pol.Df[k][j];
-          DFt += sc.pol.Df[i][k] * F[j][k];
+          DFt += sc.pol.Df[i][k] * E[j][k];
         }
         Fbar[i][j] += 2.0f * mu * (tF + tD);
         Rbar[i][j] = -2.0f * mu * tF;
         mub += tb[i][j] * DFt;
       }
-    polar_adjoint_f64<D>(F, sc.pol, Rbar, Fbar);
+    polar_adjoint_f64<D>(E, sc.pol, Rbar, Fbar);
     float c = la * (2.0f * sc.J - 1.0f) * trtb;
 #pragma unroll
     for (int i = 0; i < D; ++i)
@@ -403,15 +406,13 @@ __device__ __forceinline__ float kirchhoff_adjoint(const float F[D][D], float mu
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        float s = 0.0f;
+        float s = tb[i][j] + tb[j][i];  // (tb + tb^T) F = (tb + tb^T) + (tb + tb^T) E
 #pragma unroll
-        for (int k = 0; k < D; ++k) s += (tb[i][k] + tb[k][i]) * F[k][j];
+        for (int k = 0; k < D; ++k) s += (tb[i][k] + tb[k][i]) * E[k][j];
         Fbar[i][j] += mu * s + c * cof[i][j];
-        float e = F[i][j] - (i == j ? 1.0f : 0.0f);
-        float et = F[j][i] - (i == j ? 1.0f : 0.0f);
-        float g = e + et;
+        float g = E[i][j] + E[j][i];
 #pragma unroll
-        for (int k = 0; k < D; ++k) g += (F[i][k] - (i == k ? 1.0f : 0.0f)) * (F[j][k] - (j == k ? 1.0f : 0.0f));
+        for (int k = 0; k < D; ++k) g += E[i][k] * E[j][k];
         mub += tb[i][j] * g;
       }
     mubar += mub;

@@ -42,8 +42,9 @@ cudaError_t launch_reset_boxes(int* bbox, int* bbox_u, unsigned* done, int n_sce
                                cudaStream_t s);
 cudaError_t launch_gather_rows(int rows, int64_t N, const int* perm, const float* src_caller,
                                float* dst_internal, cudaStream_t s);
+// identity_dim > 0: rows are a dim x dim matrix per particle and I is added on the way out
 cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const float* src_internal,
-                                float* dst_caller, cudaStream_t s);
+                                float* dst_caller, int identity_dim, cudaStream_t s);
 cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, const float* nu,
                                  const float* mubar, const float* labar, float* gE, float* gnu,
                                  cudaStream_t s);

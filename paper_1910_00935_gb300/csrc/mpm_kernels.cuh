@@ -2,12 +2,22 @@
 // adjoint (Appendix D: p2g, grid_op, g2p and their .grad counterparts).
 //
 // Particle passes run one CTA per tile of up to kTile particles of one scene
-// (particles are Morton-sorted per scene at set-up, so a tile covers a compact
-// block of cells).  Scatters (P2G mass/momentum, G2P-adjoint grid-velocity
-// adjoint) accumulate into a shared-memory copy of the tile's node box and flush
-// it with one float4 atomic per non-empty node; a tile whose box exceeds the
-// shared capacity scatters with global float4 atomics instead.  Node passes sweep
-// the bounding box of the nodes touched in each scene.
+// (particles are Morton-sorted per scene at set-up, so a tile covers a compact block
+// of cells, ~8 particles per cell in 3D).  Each pass works in two orders:
+//   - gathers, stress and state I/O run in tile order (thread t = particle t), so the
+//     state rows are read and written coalesced;
+//   - scatters run in an interleaved order (warp w takes particles w, w+8, w+16, ...),
+//     so that the 32 lanes of a warp sit in 32 different cells and never hit the same
+//     node in the same instruction.  The per-particle scatter record (stencil base, f,
+//     and the affine pair a + B dpos) moves between the two orders through shared
+//     memory.
+// Scatters accumulate into a shared-memory copy of the tile's node box and flush it
+// with one float4 atomic per non-empty node; a tile whose box exceeds the shared
+// capacity scatters with global float4 atomics instead.  Node passes sweep the bounding
+// box of the nodes touched in each scene.
+//
+// Stencil loops are separable: the weight of node (i, j, k) is w0[i] w1[j] w2[k] and
+// dpos = (dp0[i], dp1[j], dp2[k]), so partial products over (i) and (i, j) are hoisted.
 #pragma once
 
 #include <climits>
@@ -32,7 +42,7 @@ enum AdjMode : int {
 struct StepArgs {
   const int4* tiles;  // {scene, first particle, count, 0}
   int N;              // row stride (total particles)
-  const float* in;    // state rows x, v, C, F (component-major)
+  const float* in;    // state rows x, v, C, F - f_diag I (component-major)
   float* out;
   const float* mu;
   const float* la;
@@ -68,25 +78,73 @@ struct Rows {
   static constexpr int X = 0, V = D, C = 2 * D, F = 2 * D + D * D, Q = 2 * D + 2 * D * D;
 };
 
+// scatter records: packed base, f[D], a[D], B[D][D]
 template <int D>
-__device__ __forceinline__ int64_t node_flat(const int idx[D], int n) {
-  int64_t r = idx[0];
+struct Xch {
+  static constexpr int kWidth = 1 + 2 * D + D * D;
+  static constexpr int kStride = kTile + kTile / 8;  // padded: conflict-free in both orders
+};
+
+__device__ __forceinline__ int scatter_slot(int t) { return (t & 31) * (kTile / 32) + (t >> 5); }
+__device__ __forceinline__ int xidx(int j) { return j + (j >> 3); }
+
+// dynamic shared memory of a particle pass: node box (4 * cap floats) + scatter records
+template <int D>
+inline size_t pass_smem_bytes(int cap) {
+  return sizeof(float) * ((size_t)4 * (cap > 0 ? cap : 1) + (size_t)Xch<D>::kWidth * Xch<D>::kStride);
+}
+
+template <int D>
+__device__ __forceinline__ int pack_base(const int b[D]) {
+  return D == 2 ? (b[0] << 16) | b[D - 1] : (b[0] << 20) | (b[1] << 10) | b[D - 1];
+}
+template <int D>
+__device__ __forceinline__ void unpack_base(int v, int b[D]) {
+  if (D == 2) {
+    b[0] = v >> 16;
+    b[D - 1] = v & 0xFFFF;
+  } else {
+    b[0] = v >> 20;
+    b[1] = (v >> 10) & 0x3FF;
+    b[D - 1] = v & 0x3FF;
+  }
+}
+
+// flat node index inside one scene grid
+template <int D>
+__device__ __forceinline__ int node_flat(const int idx[D], int n) {
+  int r = idx[0];
 #pragma unroll
   for (int a = 1; a < D; ++a) r = r * n + idx[a];
   return r;
 }
 
-// flat index of the stencil's centre node base + (1, ..., 1)
+// flat offset of stencil node (i, j, k) from the stencil base
 template <int D>
-__device__ __forceinline__ int64_t centre_flat(const int base[D], int n) {
-  int idx[D];
+__device__ __forceinline__ int stencil_off(int i, int j, int k, int n) {
+  return D == 2 ? i * n + j : (i * n + j) * n + k;
+}
+
+// Calls fn(i, j, k, W) for the 3^D stencil nodes (k = 0 in 2D); indices are
+// compile-time after unrolling.
+template <int D, typename Fn>
+__device__ __forceinline__ void for_nodes(const float w[D][3], Fn&& fn) {
 #pragma unroll
-  for (int a = 0; a < D; ++a) idx[a] = base[a] + 1;
-  return node_flat<D>(idx, n);
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float wij = w[0][i] * w[1][j];
+      if (D == 2) {
+        fn(i, j, 0, wij);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) fn(i, j, k, wij * w[D - 1][k]);
+      }
+    }
 }
 
 // ---------------------------------------------------------------------------
-// CTA-cooperative scatter into a shared-memory node box
+// CTA-cooperative node box in shared memory
 // ---------------------------------------------------------------------------
 template <int D>
 struct BoxInfo {
@@ -143,33 +201,8 @@ __device__ __forceinline__ BoxInfo<D> box_begin(bool valid, const int base[D], i
 }
 
 template <int D>
-__device__ __forceinline__ int box_local(const BoxInfo<D>& b, const int idx[D]) {
-  int l = idx[0] - b.lo[0];
-#pragma unroll
-  for (int a = 1; a < D; ++a) l = l * b.dim[a] + (idx[a] - b.lo[a]);
-  return l;
-}
-
-// add (c0..c3) at node idx (NC of them meaningful): into the shared box, or straight
-// to global memory
-template <int D, int NC>
-__device__ __forceinline__ void box_add(const BoxInfo<D>& b, float* sm, int cap, float4* g,
-                                        int64_t scene_off, int n, const int idx[D], float c0, float c1,
-                                        float c2, float c3) {
-  if (b.use_tile) {
-    int l = box_local<D>(b, idx);
-    atomicAdd(&sm[l], c0);
-    atomicAdd(&sm[cap + l], c1);
-    if (NC > 2) atomicAdd(&sm[2 * cap + l], c2);
-    if (NC > 3) atomicAdd(&sm[3 * cap + l], c3);
-  } else {
-    atomicAdd(g + scene_off + node_flat<D>(idx, n), make_float4(c0, c1, c2, c3));
-  }
-}
-
-template <int D>
 __device__ __forceinline__ void box_flush(const BoxInfo<D>& b, const float* sm, int cap, float4* g,
-                                          int64_t scene_off, int n) {
+                                          int n) {
   __syncthreads();
   if (!b.use_tile) return;
   for (int l = threadIdx.x; l < b.vol; l += blockDim.x) {
@@ -181,8 +214,115 @@ __device__ __forceinline__ void box_flush(const BoxInfo<D>& b, const float* sm, 
         idx[a] = b.lo[a] + r % b.dim[a];
         r /= b.dim[a];
       }
-      atomicAdd(g + scene_off + node_flat<D>(idx, n), v);
+      atomicAdd(g + node_flat<D>(idx, n), v);
     }
+  }
+}
+
+// Write this thread's scatter record (tile order).  A negative base marks "no scatter".
+template <int D>
+__device__ __forceinline__ void put_record(float* xr, bool valid, const int base[D], const float f[D],
+                                           const float a[D], const float B[D][D]) {
+  constexpr int S = Xch<D>::kStride;
+  const int i = xidx(threadIdx.x);
+  xr[i] = __int_as_float(valid ? pack_base<D>(base) : -1);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    xr[(1 + c) * S + i] = f[c];
+    xr[(1 + D + c) * S + i] = a[c];
+  }
+#pragma unroll
+  for (int c = 0; c < D * D; ++c) xr[(1 + 2 * D + c) * S + i] = B[c / D][c % D];
+}
+
+// Interleaved scatter of the records: node (i, j, k) receives
+//   mass  W * mass_c                      (when WITH_MASS)
+//   vec   W * (a + B dpos)
+// into the shared box (or global memory g when the box did not fit).
+template <int D, bool WITH_MASS>
+__device__ __forceinline__ void scatter_records(const float* xr, int count, const BoxInfo<D>& bx,
+                                                float* sm, int cap, float4* g, int n,
+                                                const SimParams& P, float mass_c) {
+  constexpr int S = Xch<D>::kStride;
+  const int j = scatter_slot(threadIdx.x);
+  if (j >= count) return;
+  const int xi = xidx(j);
+  const int packed = __float_as_int(xr[xi]);
+  if (packed < 0) return;
+  int base[D];
+  unpack_base<D>(packed, base);
+  float f[D], a[D], B[D][D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    f[c] = xr[(1 + c) * S + xi];
+    a[c] = xr[(1 + D + c) * S + xi];
+  }
+#pragma unroll
+  for (int c = 0; c < D * D; ++c) B[c / D][c % D] = xr[(1 + 2 * D + c) * S + xi];
+  float w[D][3], dp[D][3];
+  axes_from_f<D>(f, P, w, dp);
+  if (bx.use_tile) {
+    int lb = base[0] - bx.lo[0];
+#pragma unroll
+    for (int c = 1; c < D; ++c) lb = lb * bx.dim[c] + (base[c] - bx.lo[c]);
+    const int s1 = D == 2 ? 1 : bx.dim[D - 1];
+    const int s0 = bx.dim[1] * s1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float qi[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) qi[c] = a[c] + B[c][0] * dp[0][i];
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
+        const float wij = w[0][i] * w[1][jj];
+        float qij[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) qij[c] = qi[c] + B[c][1] * dp[1][jj];
+        if (D == 2) {
+          const int l = lb + i * s0 + jj;
+          if (WITH_MASS) {
+            atomicAdd(&sm[l], wij * mass_c);
+            atomicAdd(&sm[cap + l], wij * qij[0]);
+            atomicAdd(&sm[2 * cap + l], wij * qij[1]);
+          } else {
+            atomicAdd(&sm[l], wij * qij[0]);
+            atomicAdd(&sm[cap + l], wij * qij[1]);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float W = wij * w[D - 1][k];
+            const int l = lb + i * s0 + jj * s1 + k;
+            float q[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) q[c] = qij[c] + B[c][D - 1] * dp[D - 1][k];
+            if (WITH_MASS) {
+              atomicAdd(&sm[l], W * mass_c);
+              atomicAdd(&sm[cap + l], W * q[0]);
+              atomicAdd(&sm[2 * cap + l], W * q[1]);
+              atomicAdd(&sm[3 * cap + l], W * q[D - 1]);
+            } else {
+              atomicAdd(&sm[l], W * q[0]);
+              atomicAdd(&sm[cap + l], W * q[1]);
+              atomicAdd(&sm[2 * cap + l], W * q[D - 1]);
+            }
+          }
+        }
+      }
+    }
+  } else {
+    float4* gb = g + node_flat<D>(base, n);
+    for_nodes<D>(w, [&](int i, int jj, int k, float W) {
+      float q[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        q[c] = a[c] + B[c][0] * dp[0][i] + B[c][1] * dp[1][jj];
+        if (D == 3) q[c] += B[c][D - 1] * dp[D - 1][k];
+      }
+      float4 v = WITH_MASS ? make_float4(W * mass_c, W * q[0], W * q[1], D == 3 ? W * q[2] : 0.0f)
+                           : make_float4(W * q[0], W * q[1], D == 3 ? W * q[2] : 0.0f, 0.0f);
+      atomicAdd(gb + stencil_off<D>(i, jj, k, n), v);
+    });
   }
 }
 
@@ -201,24 +341,34 @@ __device__ __forceinline__ float particle_act(const SimParams& P, const int* gro
   return a;
 }
 
+template <int D>
+__device__ __forceinline__ void load_E(const float* rows, int64_t N, int64_t p, float f_diag,
+                                       float E[D][D]) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+      E[i][j] = rows[(Rows<D>::F + i * D + j) * N + p] - (i == j ? f_diag : 0.0f);
+}
+
 // ---------------------------------------------------------------------------
 // forward particle pass
 // ---------------------------------------------------------------------------
 template <int D, int MAT, int MODE>
-__global__ void __launch_bounds__(kTile) step_kernel(SimParams P, StepArgs A) {
+__global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P, StepArgs A) {
   using R = Rows<D>;
   extern __shared__ float sm[];
   __shared__ int s_box[8];
+  float* xr = sm + 4 * (P.tile_capacity > 0 ? P.tile_capacity : 1);
   const int4 tile = A.tiles[blockIdx.x];
   const int scene = tile.x;
   const bool active = (int)threadIdx.x < tile.z;
   const int64_t p = (int64_t)tile.y + (active ? threadIdx.x : 0);
   const int64_t N = A.N;
-  const int64_t soff = (int64_t)scene * P.nnodes;
   const int n = P.n_grid;
   unsigned err = 0;
 
-  float x[D], v[D], C[D][D], F[D][D];
+  float x[D], v[D], C[D][D], E[D][D];
   if (MODE == kP2GOnly) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -226,23 +376,17 @@ __global__ void __launch_bounds__(kTile) step_kernel(SimParams P, StepArgs A) {
       v[a] = A.in[(R::V + a) * N + p];
     }
 #pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        C[i][j] = A.in[(R::C + i * D + j) * N + p];
-        F[i][j] = A.in[(R::F + i * D + j) * N + p];
-      }
+    for (int i = 0; i < D * D; ++i) C[i / D][i % D] = A.in[(R::C + i) * N + p];
+    load_E<D>(A.in, N, p, P.f_diag, E);
   } else {
-    // ---- G2P: gather u, build v' and C', advect, update F ----
-    float xo[D], Fo[D][D];
+    // ---- G2P: v' = sum W u, C' = 4/dx^2 sum W (u - u_c) dpos^T, x' = x + dt v',
+    //      E' = E + dt C' (I + E)
+    float xo[D], Eo[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a) xo[a] = A.in[(R::X + a) * N + p];
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int j = 0; j < D; ++j) Fo[i][j] = A.in[(R::F + i * D + j) * N + p];
-    Stencil<D> s;
-    bool ok = make_stencil<D>(xo, P, s) && active;
+    load_E<D>(A.in, N, p, P.f_diag, Eo);
+    Axes<D> s;
+    const bool ok = make_axes<D>(xo, P, s) && active;
     if (active && !ok) err |= kErrOOB;
     float B[D][D];
 #pragma unroll
@@ -252,30 +396,23 @@ __global__ void __launch_bounds__(kTile) step_kernel(SimParams P, StepArgs A) {
       for (int b = 0; b < D; ++b) B[a][b] = 0.0f;
     }
     if (ok) {
-      // sum W u dpos^T is accumulated on u - u_c (u_c: the stencil's centre node); the
-      // two are equal because sum W dpos = 0, and the centred form keeps FP32 accuracy
-      // when u is nearly uniform over the stencil
-      const float4 uc4 = __ldg(A.U + soff + centre_flat<D>(s.base, n));
+      // centred on the stencil's centre node: equal because sum W dpos = 0, and
+      // accurate in FP32 when u is nearly uniform over the stencil
+      const float4* Ug = A.U + (int64_t)scene * P.nnodes + node_flat<D>(s.base, n);
+      const float4 uc4 = __ldg(Ug + stencil_off<D>(1, 1, 1, n));
       const float uc[3] = {uc4.x, uc4.y, uc4.z};
-      constexpr int NS = D == 2 ? 9 : 27;
-#pragma unroll
-      for (int o = 0; o < NS; ++o) {
-        int off[D], idx[D];
-        offsets<D>(o, off);
-        float W, gW[D], dpos[D];
-        node_terms<D>(s, off, P, W, gW, dpos);
-#pragma unroll
-        for (int a = 0; a < D; ++a) idx[a] = s.base[a] + off[a];
-        float4 u = __ldg(A.U + soff + node_flat<D>(idx, n));
-        const float uu[3] = {u.x, u.y, u.z};
+      for_nodes<D>(s.w, [&](int i, int j, int k, float W) {
+        const float4 u4 = __ldg(Ug + stencil_off<D>(i, j, k, n));
+        const float u[3] = {u4.x, u4.y, u4.z};
+        const float dpos[3] = {s.dp[0][i], s.dp[1][j], D == 3 ? s.dp[D - 1][k] : 0.0f};
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          v[a] += W * uu[a];
-          float wd = W * (uu[a] - uc[a]);
+          v[a] += W * u[a];
+          const float wd = W * (u[a] - uc[a]);
 #pragma unroll
           for (int b = 0; b < D; ++b) B[a][b] += wd * dpos[b];
         }
-      }
+      });
     }
     const float c4 = 4.0f * P.inv_dx * P.inv_dx;
 #pragma unroll
@@ -288,16 +425,17 @@ __global__ void __launch_bounds__(kTile) step_kernel(SimParams P, StepArgs A) {
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        float s2 = Fo[i][j];
+        float g = P.dt * C[i][j];  // dt C' (I + E)
 #pragma unroll
-        for (int k = 0; k < D; ++k) s2 += P.dt * C[i][k] * Fo[k][j];
-        F[i][j] = s2;
+        for (int k = 0; k < D; ++k) g += P.dt * C[i][k] * Eo[k][j];
+        E[i][j] = Eo[i][j] + g;
       }
     if (active) {
 #pragma unroll
       for (int a = 0; a < D; ++a) A.out[(R::X + a) * N + p] = x[a];
 #pragma unroll
-      for (int i = 0; i < D * D; ++i) A.out[(R::F + i) * N + p] = F[i / D][i % D];
+      for (int i = 0; i < D * D; ++i)
+        A.out[(R::F + i) * N + p] = E[i / D][i % D] + (i / D == i % D ? P.f_diag : 0.0f);
       if (MODE == kG2PP2GFull || MODE == kG2POnlyFull) {
 #pragma unroll
         for (int a = 0; a < D; ++a) A.out[(R::V + a) * N + p] = v[a];
@@ -308,18 +446,23 @@ __global__ void __launch_bounds__(kTile) step_kernel(SimParams P, StepArgs A) {
   }
 
   if (MODE != kG2POnlyFull) {
-    // ---- P2G: stress, affine matrix, scatter (m, m v + A dpos) ----
-    Stencil<D> s;
-    bool ok = make_stencil<D>(x, P, s) && active;
+    // ---- P2G: stress, affine matrix A = kappa tau + m C; scatter (m, m v + A dpos) ----
+    Axes<D> s;
+    bool ok = make_axes<D>(x, P, s) && active;
     if (active && !ok) err |= kErrOOB;
     float Am[D][D], mv[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      mv[i] = 0.0f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) Am[i][j] = 0.0f;
+    }
     if (ok) {
       int axis;
-      float act = particle_act(P, A.group, A.wact, scene, p, D, axis);
+      const float act = particle_act(P, A.group, A.wact, scene, p, D, axis);
       float tau[D][D];
       StressCache<D> sc;
-      bool sok = kirchhoff<D, MAT>(F, A.mu[p], A.la[p], act, axis, tau, sc);
-      if (!sok) {
+      if (!kirchhoff<D, MAT>(E, A.mu[p], A.la[p], act, axis, tau, sc)) {
         err |= kErrNonFinite;
         ok = false;
       }
@@ -330,30 +473,11 @@ __global__ void __launch_bounds__(kTile) step_kernel(SimParams P, StepArgs A) {
         for (int j = 0; j < D; ++j) Am[i][j] = P.kappa * tau[i][j] + P.p_mass * C[i][j];
       }
     }
+    put_record<D>(xr, ok, s.base, s.f, mv, Am);
     BoxInfo<D> bx = box_begin<D>(ok, s.base, P.tile_capacity, sm, s_box);
-    if (ok) {
-      constexpr int NS = D == 2 ? 9 : 27;
-#pragma unroll
-      for (int o = 0; o < NS; ++o) {
-        int off[D], idx[D];
-        offsets<D>(o, off);
-        float W, gW[D], dpos[D];
-        node_terms<D>(s, off, P, W, gW, dpos);
-#pragma unroll
-        for (int a = 0; a < D; ++a) idx[a] = s.base[a] + off[a];
-        float c[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          float q = mv[a];
-#pragma unroll
-          for (int b = 0; b < D; ++b) q += Am[a][b] * dpos[b];
-          c[a] = W * q;
-        }
-        box_add<D, D + 1>(bx, sm, P.tile_capacity, A.PM, soff, n, idx, W * P.p_mass, c[0], c[1],
-                              c[2]);
-      }
-    }
-    box_flush<D>(bx, sm, P.tile_capacity, A.PM, soff, n);
+    float4* PMs = A.PM + (int64_t)scene * P.nnodes;
+    scatter_records<D, true>(xr, tile.z, bx, sm, P.tile_capacity, PMs, n, P, P.p_mass);
+    box_flush<D>(bx, sm, P.tile_capacity, PMs, n);
     if (threadIdx.x == 0 && bx.vol > 0) {
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -369,22 +493,22 @@ __global__ void __launch_bounds__(kTile) step_kernel(SimParams P, StepArgs A) {
 // adjoint particle pass
 // ---------------------------------------------------------------------------
 template <int D, int MAT, int MODE>
-__global__ void __launch_bounds__(kTile) adjoint_kernel(SimParams P, AdjArgs A) {
+__global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs A) {
   using R = Rows<D>;
   extern __shared__ float sm[];
   __shared__ int s_box[8];
   __shared__ float s_wbar[kMaxGroups * kMaxBasis];
+  float* xr = sm + 4 * (P.tile_capacity > 0 ? P.tile_capacity : 1);
   const int4 tile = A.tiles[blockIdx.x];
   const int scene = tile.x;
   const bool active = (int)threadIdx.x < tile.z;
   const int64_t p = (int64_t)tile.y + (active ? threadIdx.x : 0);
   const int64_t N = A.N;
-  const int64_t soff = (int64_t)scene * P.nnodes;
   const int n = P.n_grid;
   const float c4 = 4.0f * P.inv_dx * P.inv_dx;
   unsigned err = 0;
 
-  // adjoint of state s+1: xb, vb, Cb, Fb
+  // adjoint of state s+1: xb, vb, Cb, Fb (Fb = dL/dE = dL/dF)
   float xb[D], vb[D], Cb[D][D], Fb[D][D];
   float C1[D][D];  // C of state s+1
 #pragma unroll
@@ -403,78 +527,102 @@ __global__ void __launch_bounds__(kTile) adjoint_kernel(SimParams P, AdjArgs A) 
 #pragma unroll
     for (int i = 0; i < D * D; ++i) Cb[i / D][i % D] = A.adj[(R::C + i) * N + p];
   } else {
-    // ---- P2G adjoint of step s+1 (gather pbar, mbar) ----
+    // ---- P2G adjoint of step s+1: gather (pbar, mbar) ----
     if (threadIdx.x < kMaxGroups * kMaxBasis) s_wbar[threadIdx.x] = 0.0f;
-    float x[D], v[D], F[D][D], Am[D][D];
+    float x[D], v[D], E[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       x[a] = A.st1[(R::X + a) * N + p];
       v[a] = A.st1[(R::V + a) * N + p];
     }
-#pragma unroll
-    for (int i = 0; i < D * D; ++i) F[i / D][i % D] = A.st1[(R::F + i) * N + p];
-    Stencil<D> s;
-    bool ok = make_stencil<D>(x, P, s) && active;
+    load_E<D>(A.st1, N, p, P.f_diag, E);
+    Axes<D> s;
+    bool ok = make_axes<D>(x, P, s) && active;
     if (active && !ok) err |= kErrOOB;
     int axis;
-    float act = particle_act(P, A.group, A.wact, scene, p, D, axis);
-    float mu = A.mu[p], la = A.la[p];
+    const float act = particle_act(P, A.group, A.wact, scene, p, D, axis);
+    const float mu = A.mu[p], la = A.la[p];
     float tau[D][D];
     StressCache<D> sc;
-    if (!kirchhoff<D, MAT>(F, mu, la, act, axis, tau, sc) && ok) {
+    if (!kirchhoff<D, MAT>(E, mu, la, act, axis, tau, sc) && ok) {
       err |= kErrNonFinite;
       ok = false;
     }
+    float Am[D][D], mv[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i)
+    for (int i = 0; i < D; ++i) {
+      mv[i] = P.p_mass * v[i];
 #pragma unroll
       for (int j = 0; j < D; ++j) Am[i][j] = P.kappa * tau[i][j] + P.p_mass * C1[i][j];
-    float Ab[D][D];
+    }
+    float Ab[D][D], xg[D], sw[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       vb[a] = 0.0f;
+      xg[a] = 0.0f;
+      sw[a] = 0.0f;
 #pragma unroll
       for (int b = 0; b < D; ++b) Ab[a][b] = 0.0f;
     }
     if (ok) {
-      // Abar and the x-adjoint use pbar - pbar_c and mbar - mbar_c (centre node): equal
-      // to the plain sums because sum W dpos = 0, sum grad W = 0 and
-      // sum grad W dpos^T = I, and free of the FP32 cancellation of a smooth pbar field
-      const float4 gc = __ldg(A.PBM + soff + centre_flat<D>(s.base, n));
+      // pbar - pbar_c and mbar - mbar_c (centre node) in the moment and weight-gradient
+      // terms: equal to the plain sums because sum W dpos = 0, sum grad W = 0 and
+      // sum grad W dpos^T = I, without the FP32 cancellation of a smooth pbar field
+      const float4* Gg = A.PBM + (int64_t)scene * P.nnodes + node_flat<D>(s.base, n);
+      const float4 gc = __ldg(Gg + stencil_off<D>(1, 1, 1, n));
       const float pc[3] = {gc.x, gc.y, gc.z};
-      constexpr int NS = D == 2 ? 9 : 27;
 #pragma unroll
-      for (int o = 0; o < NS; ++o) {
-        int off[D], idx[D];
-        offsets<D>(o, off);
-        float W, gW[D], dpos[D];
-        node_terms<D>(s, off, P, W, gW, dpos);
+      for (int i = 0; i < 3; ++i) {
+        float qi[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) idx[a] = s.base[a] + off[a];
-        float4 g = __ldg(A.PBM + soff + node_flat<D>(idx, n));
-        const float pb[3] = {g.x, g.y, g.z};
-        float dp[D];
+        for (int c = 0; c < D; ++c) qi[c] = mv[c] + Am[c][0] * s.dp[0][i];
 #pragma unroll
-        for (int a = 0; a < D; ++a) dp[a] = pb[a] - pc[a];
-        float Wbar = P.p_mass * (g.w - gc.w);
+        for (int j = 0; j < 3; ++j) {
+          const float wij = s.w[0][i] * s.w[1][j];
+          const float dwij0 = s.dw[0][i] * s.w[1][j];
+          const float dwij1 = s.w[0][i] * s.dw[1][j];
+          float qij[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          float q = P.p_mass * v[a];
+          for (int c = 0; c < D; ++c) qij[c] = qi[c] + Am[c][1] * s.dp[1][j];
 #pragma unroll
-          for (int b = 0; b < D; ++b) q += Am[a][b] * dpos[b];
-          Wbar += dp[a] * q;
-          vb[a] += W * P.p_mass * pb[a];
+          for (int k = 0; k < (D == 3 ? 3 : 1); ++k) {
+            const float wk = D == 3 ? s.w[D - 1][k] : 1.0f;
+            const float W = wij * wk;
+            float gW[D];
+            gW[0] = dwij0 * wk;
+            gW[1] = dwij1 * wk;
+            if (D == 3) gW[D - 1] = wij * s.dw[D - 1][k];
+            float q[D];
 #pragma unroll
-          for (int b = 0; b < D; ++b) Ab[a][b] += W * dp[a] * dpos[b];
-        }
+            for (int c = 0; c < D; ++c)
+              q[c] = D == 3 ? qij[c] + Am[c][D - 1] * s.dp[D - 1][k] : qij[c];
+            const float dpos[3] = {s.dp[0][i], s.dp[1][j], D == 3 ? s.dp[D - 1][k] : 0.0f};
+            const float4 g4 = __ldg(Gg + stencil_off<D>(i, j, k, n));
+            const float pb[3] = {g4.x, g4.y, g4.z};
+            float Wbar = P.p_mass * (g4.w - gc.w);
 #pragma unroll
-        for (int b = 0; b < D; ++b) {
-          float atp = 0.0f;
+            for (int c = 0; c < D; ++c) {
+              const float dpb = pb[c] - pc[c];
+              Wbar += dpb * q[c];
+              vb[c] += W * pb[c];
+              sw[c] += W * dpb;
 #pragma unroll
-          for (int a = 0; a < D; ++a) atp += Am[a][b] * dp[a];
-          xb[b] += Wbar * gW[b] - W * atp;
+              for (int b = 0; b < D; ++b) Ab[c][b] += W * dpb * dpos[b];
+            }
+#pragma unroll
+            for (int b = 0; b < D; ++b) xg[b] += Wbar * gW[b];
+          }
         }
       }
+    }
+    // x += inv_dx sum Wbar gradW - A^T sum W dpbar
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      float atw = 0.0f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) atw += Am[a][b] * sw[a];
+      xb[b] += P.inv_dx * xg[b] - atw;
+      vb[b] *= P.p_mass;
     }
     float tb[D][D];
 #pragma unroll
@@ -485,24 +633,26 @@ __global__ void __launch_bounds__(kTile) adjoint_kernel(SimParams P, AdjArgs A) 
         tb[i][j] = P.kappa * Ab[i][j];
       }
     float mub = 0.0f, lab = 0.0f, abar = 0.0f;
-    if (ok) abar = kirchhoff_adjoint<D, MAT>(F, mu, la, act, axis, sc, tb, Fb, mub, lab);
+    if (ok) abar = kirchhoff_adjoint<D, MAT>(E, mu, la, act, axis, sc, tb, Fb, mub, lab);
     if (active) {
       A.mubar[p] += mub;
       A.labar[p] += lab;
     }
-    __syncthreads();  // s_wbar zeroed
-    if (P.n_groups > 0 && ok) {
-      int g = A.group[p];
-      if (g >= 0 && g < P.n_groups) {
+    if (P.n_groups > 0) {
+      __syncthreads();  // s_wbar zeroed
+      if (ok) {
+        int g = A.group[p];
+        if (g >= 0 && g < P.n_groups) {
 #pragma unroll
-        for (int k = 0; k < kMaxBasis; ++k)
-          if (k < P.n_basis) atomicAdd(&s_wbar[g * P.n_basis + k], abar * P.basis[k]);
+          for (int k = 0; k < kMaxBasis; ++k)
+            if (k < P.n_basis) atomicAdd(&s_wbar[g * P.n_basis + k], abar * P.basis[k]);
+        }
       }
-    }
-    __syncthreads();
-    if (P.n_groups > 0 && (int)threadIdx.x < P.n_groups * P.n_basis) {
-      float wv = s_wbar[threadIdx.x];
-      if (wv != 0.0f) atomicAdd(&A.wbar[(int64_t)scene * P.n_groups * P.n_basis + threadIdx.x], wv);
+      __syncthreads();
+      if ((int)threadIdx.x < P.n_groups * P.n_basis) {
+        float wv = s_wbar[threadIdx.x];
+        if (wv != 0.0f) atomicAdd(&A.wbar[(int64_t)scene * P.n_groups * P.n_basis + threadIdx.x], wv);
+      }
     }
     if (MODE == kAdjP2G) {
       if (active) {
@@ -522,13 +672,12 @@ __global__ void __launch_bounds__(kTile) adjoint_kernel(SimParams P, AdjArgs A) 
     }
   }
 
-  // ---- G2P adjoint of step s: x' = x + dt v', F' = (I + dt C') F ----
+  // ---- G2P adjoint of step s: x' = x + dt v', E' = E + dt C' (I + E) ----
   {
-    float x0[D], F0[D][D];
+    float x0[D], E0[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a) x0[a] = A.st0[(R::X + a) * N + p];
-#pragma unroll
-    for (int i = 0; i < D * D; ++i) F0[i / D][i % D] = A.st0[(R::F + i) * N + p];
+    load_E<D>(A.st0, N, p, P.f_diag, E0);
     float vt[D], Ct[D][D], Fb0[D][D], xb0[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -539,61 +688,86 @@ __global__ void __launch_bounds__(kTile) adjoint_kernel(SimParams P, AdjArgs A) 
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        float g = Fb[i][j], h = Cb[i][j];
+        float g = Fb[i][j], h = Cb[i][j] + P.dt * Fb[i][j];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           g += P.dt * C1[k][i] * Fb[k][j];  // (I + dt C')^T Fbar'
-          h += P.dt * Fb[i][k] * F0[j][k];  // Cbar' + dt Fbar' F^T
+          h += P.dt * Fb[i][k] * E0[j][k];  // Cbar' + dt Fbar' (I + E)^T
         }
         Fb0[i][j] = g;
         Ct[i][j] = h;
       }
-    Stencil<D> s;
-    bool ok = make_stencil<D>(x0, P, s) && active;
+    Axes<D> s;
+    const bool ok = make_axes<D>(x0, P, s) && active;
     if (active && !ok) err |= kErrOOB;
-    BoxInfo<D> bx = box_begin<D>(ok, s.base, P.tile_capacity, sm, s_box);
     if (ok) {
-      // x-adjoint terms on u - u_c (centre node): equal to the plain sums by the same
-      // B-spline identities, without the FP32 cancellation of a smooth u field
-      const float4 uc4 = __ldg(A.U + soff + centre_flat<D>(s.base, n));
+      // x-adjoint terms on u - u_c (centre node), by the same B-spline identities
+      const float4* Ug = A.U + (int64_t)scene * P.nnodes + node_flat<D>(s.base, n);
+      const float4 uc4 = __ldg(Ug + stencil_off<D>(1, 1, 1, n));
       const float uc[3] = {uc4.x, uc4.y, uc4.z};
-      constexpr int NS = D == 2 ? 9 : 27;
+      float xg[D], sw[D];
 #pragma unroll
-      for (int o = 0; o < NS; ++o) {
-        int off[D], idx[D];
-        offsets<D>(o, off);
-        float W, gW[D], dpos[D];
-        node_terms<D>(s, off, P, W, gW, dpos);
+      for (int a = 0; a < D; ++a) xg[a] = sw[a] = 0.0f;
 #pragma unroll
-        for (int a = 0; a < D; ++a) idx[a] = s.base[a] + off[a];
-        float4 u4 = __ldg(A.U + soff + node_flat<D>(idx, n));
-        const float u[3] = {u4.x - uc[0], u4.y - uc[1], u4.z - uc[2]};
-        float Wbar = 0.0f, ub[3] = {0.0f, 0.0f, 0.0f};
+      for (int i = 0; i < 3; ++i) {
+        float qi[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          float cd = 0.0f;
+        for (int c = 0; c < D; ++c) qi[c] = vt[c] + c4 * Ct[c][0] * s.dp[0][i];
 #pragma unroll
-          for (int b = 0; b < D; ++b) cd += Ct[a][b] * dpos[b];
-          ub[a] = W * (vt[a] + c4 * cd);
-          Wbar += u[a] * (vt[a] + c4 * cd);
+        for (int j = 0; j < 3; ++j) {
+          const float wij = s.w[0][i] * s.w[1][j];
+          const float dwij0 = s.dw[0][i] * s.w[1][j];
+          const float dwij1 = s.w[0][i] * s.dw[1][j];
+          float qij[D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) qij[c] = qi[c] + c4 * Ct[c][1] * s.dp[1][j];
+#pragma unroll
+          for (int k = 0; k < (D == 3 ? 3 : 1); ++k) {
+            const float wk = D == 3 ? s.w[D - 1][k] : 1.0f;
+            const float W = wij * wk;
+            float gW[D];
+            gW[0] = dwij0 * wk;
+            gW[1] = dwij1 * wk;
+            if (D == 3) gW[D - 1] = wij * s.dw[D - 1][k];
+            const float4 u4 = __ldg(Ug + stencil_off<D>(i, j, k, n));
+            const float du[3] = {u4.x - uc[0], u4.y - uc[1], u4.z - uc[2]};
+            float Wbar = 0.0f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+              const float q = D == 3 ? qij[c] + c4 * Ct[c][D - 1] * s.dp[D - 1][k] : qij[c];
+              Wbar += du[c] * q;
+              sw[c] += W * du[c];
+            }
+#pragma unroll
+            for (int b = 0; b < D; ++b) xg[b] += Wbar * gW[b];
+          }
         }
+      }
 #pragma unroll
-        for (int b = 0; b < D; ++b) {
-          float ctu = 0.0f;
+      for (int b = 0; b < D; ++b) {
+        float ctu = 0.0f;
 #pragma unroll
-          for (int a = 0; a < D; ++a) ctu += Ct[a][b] * u[a];
-          xb0[b] += Wbar * gW[b] - c4 * W * ctu;
-        }
-        box_add<D, D>(bx, sm, P.tile_capacity, A.UB, soff, n, idx, ub[0], ub[1], ub[2], 0.0f);
+        for (int a = 0; a < D; ++a) ctu += Ct[a][b] * sw[a];
+        xb0[b] += P.inv_dx * xg[b] - c4 * ctu;
       }
     }
-    box_flush<D>(bx, sm, P.tile_capacity, A.UB, soff, n);
     if (active) {
 #pragma unroll
       for (int a = 0; a < D; ++a) A.adj[(R::X + a) * N + p] = xb0[a];
 #pragma unroll
       for (int i = 0; i < D * D; ++i) A.adj[(R::F + i) * N + p] = Fb0[i / D][i % D];
     }
+    // ---- scatter ubar_i += W (vt + c4 Ct dpos) ----
+    float Bs[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) Bs[i][j] = c4 * Ct[i][j];
+    put_record<D>(xr, ok, s.base, s.f, vt, Bs);
+    BoxInfo<D> bx = box_begin<D>(ok, s.base, P.tile_capacity, sm, s_box);
+    float4* UBs = A.UB + (int64_t)scene * P.nnodes;
+    scatter_records<D, false>(xr, tile.z, bx, sm, P.tile_capacity, UBs, n, P, 0.0f);
+    box_flush<D>(bx, sm, P.tile_capacity, UBs, n);
   }
   if (err) atomicOr(A.err, err);
 }
@@ -602,7 +776,7 @@ __global__ void __launch_bounds__(kTile) adjoint_kernel(SimParams P, AdjArgs A) 
 // node passes over each scene's touched box (blockIdx.y = scene)
 // ---------------------------------------------------------------------------
 template <int D>
-__device__ __forceinline__ bool box_node(const int* bb, int l, int idx[D]) {
+__device__ __forceinline__ void box_node(const int* bb, int l, int idx[D]) {
   int r = l;
 #pragma unroll
   for (int a = D - 1; a >= 0; --a) {
@@ -610,7 +784,6 @@ __device__ __forceinline__ bool box_node(const int* bb, int l, int idx[D]) {
     idx[a] = bb[a] + r % ext;
     r /= ext;
   }
-  return true;
 }
 
 template <int D>

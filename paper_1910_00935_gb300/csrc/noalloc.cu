@@ -140,6 +140,7 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
   P.p_mass = (float)(d->rho * vol);
   P.kappa = (float)(-(double)d->dt * vol * 4.0 / (dx * dx));
   P.tile_capacity = 1024;
+  P.f_diag = 1.0f;  // the caller's state rows hold F itself
 
   StepArgs A;
   A.tiles = tiles;

@@ -72,8 +72,10 @@ __global__ void gather_initial_kernel(int dim, int64_t N, const int* perm, const
       st[(dim + a) * N + i] = v0[a * N + e];
     }
     for (int k = 0; k < dd; ++k) {
+      // the deformation gradient is stored as E = F - I
+      const float id = (k / dim == k % dim) ? 1.0f : 0.0f;
       st[(2 * dim + k) * N + i] = C0 ? C0[k * N + e] : 0.0f;
-      st[(2 * dim + dd + k) * N + i] = F0 ? F0[k * N + e] : ((k / dim == k % dim) ? 1.0f : 0.0f);
+      st[(2 * dim + dd + k) * N + i] = F0 ? F0[k * N + e] - id : 0.0f;
     }
     float Ee = E[e], ne = nu[e];
     Eo[i] = Ee;
@@ -103,11 +105,14 @@ __global__ void gather_rows_kernel(int rows, int64_t N, const int* perm, const f
 }
 
 __global__ void scatter_rows_kernel(int rows, int64_t N, const int* perm, const float* src,
-                                    float* dst) {
+                                    float* dst, int identity_dim) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = perm[i];
-    for (int r = 0; r < rows; ++r) dst[r * N + e] = src[r * N + i];
+    for (int r = 0; r < rows; ++r) {
+      float add = (identity_dim > 0 && r / identity_dim == r % identity_dim) ? 1.0f : 0.0f;
+      dst[r * N + e] = src[r * N + i] + add;
+    }
   }
 }
 
@@ -126,16 +131,31 @@ __global__ void material_grad_kernel(int64_t N, const int* perm, const float* E,
   }
 }
 
-// per-scene sums of x_T and x_0 (FP64), com[scene][6]
-__global__ void com_kernel(int dim, int64_t N, int n_scenes, const int64_t* off, const float* xT,
+// per-scene sums of x_T and x_0 (FP64), com[scene][6]: one CTA per (scene, chunk),
+// CTA-reduced in shared memory, one FP64 atomic per CTA and component
+__global__ void com_kernel(int dim, int n_scenes, const int64_t* off, int64_t N, const float* xT,
                            const float* x0, double* com) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int s = scene_of(off, n_scenes, i);
+  __shared__ double red[6][256 / 32];
+  const int s = blockIdx.y;
+  const int64_t b = off[s], e = off[s + 1];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e;
+       i += (int64_t)gridDim.x * blockDim.x)
     for (int a = 0; a < dim; ++a) {
-      atomicAdd(&com[s * 6 + a], (double)xT[a * N + i]);
-      atomicAdd(&com[s * 6 + 3 + a], (double)x0[a * N + i]);
+      acc[a] += (double)xT[a * N + i];
+      acc[3 + a] += (double)x0[a * N + i];
     }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = 0; c < 6; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[c][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+    if (v != 0.0) atomicAdd(&com[s * 6 + threadIdx.x], v);
   }
 }
 
@@ -221,8 +241,9 @@ cudaError_t launch_gather_rows(int rows, int64_t N, const int* perm, const float
 }
 
 cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const float* src_internal,
-                                float* dst_caller, cudaStream_t s) {
-  scatter_rows_kernel<<<grid_for(N), 256, 0, s>>>(rows, N, perm, src_internal, dst_caller);
+                                float* dst_caller, int identity_dim, cudaStream_t s) {
+  scatter_rows_kernel<<<grid_for(N), 256, 0, s>>>(rows, N, perm, src_internal, dst_caller,
+                                                  identity_dim);
   return cudaGetLastError();
 }
 
@@ -236,7 +257,7 @@ cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, con
 cudaError_t launch_com(int dim, int64_t N, int n_scenes, const int64_t* scene_off, const int* perm,
                        const float* xT, const float* x0, double* com, cudaStream_t s) {
   (void)perm;
-  com_kernel<<<grid_for(N), 256, 0, s>>>(dim, N, n_scenes, scene_off, xT, x0, com);
+  com_kernel<<<dim3(64, n_scenes), 256, 0, s>>>(dim, n_scenes, scene_off, N, xT, x0, com);
   return cudaGetLastError();
 }
 
