@@ -123,9 +123,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(name):
+def make_workload(name, seed=0):
     from paper_1910_00935_gb300 import scenes
-    scene = scenes.make(name)
+    scene = scenes.make(name, seed=seed)
     d = scene["desc"]
     N = sum(d["n_particles"])
     descr = {
@@ -193,6 +193,8 @@ def main():
     ap.add_argument("--T", type=int, default=0, help="override the workload's step count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-per-scene", action="store_true",
+                    help="also time the same batch one scene per launch sequence")
     args = ap.parse_args()
 
     world = _env_int("WORLD_SIZE", 1)
@@ -218,7 +220,8 @@ def main():
     from paper_1910_00935_gb300 import mpm
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    scene, N, T, descr = make_workload(args.workload)
+    # every rank simulates its own independent replica of the workload (seeded by rank)
+    scene, N, T, descr = make_workload(args.workload, seed=rank)
     if args.T:
         T = args.T
     desc = scene["desc"]
@@ -363,6 +366,36 @@ def main():
                 else "fallback 6.8 TB/s",
                 "share_of_step": dom_ms / total_prof}
 
+    per_scene = None
+    if args.compare_per_scene and len(desc["n_particles"]) > 1:
+        from paper_1910_00935_gb300.sharding import subset
+        sims = []
+        for i in range(len(desc["n_particles"])):
+            sub = subset(scene, [i])
+            si = mpm.from_scene(sub, max_steps=T, device=dev)
+            si._tgt = torch.as_tensor(sub["arrays"]["target"]).to(dev)
+            sims.append(si)
+
+        def per_scene_step():
+            for si in sims:
+                si.forward(T)
+                L_, gT_, g0_ = si.loss(desc["loss_kind"], si._tgt)
+                si.backward(dL_dx=gT_)
+
+        per_scene_step()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        p0.record(stream)
+        per_scene_step()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1)
+        per_scene = {"value": N * T / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                     "form": "one scene per launch sequence, scenes run back to back"}
+        for si in sims:
+            si.close()
+
     if rank != 0:
         return
     cb = None
@@ -381,6 +414,7 @@ def main():
                    "precision": "FP32 state/grid, FP64 polar decomposition",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "forward": {"value": N * T / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms},
+        "one_scene_per_launch": per_scene,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roof,

@@ -153,11 +153,12 @@ struct BoxInfo {
   bool use_tile;
 };
 
-// Every thread of the CTA must call this (it synchronises).  valid: this thread's
-// particle scatters; base: its stencil base.  Zeroes the box when it fits.
+// Extent of the node box covering the stencils of the CTA's valid particles.  Every
+// thread of the CTA must call this; it synchronises before touching s_box (so it may
+// follow any earlier use of s_box or of the shared box) and after computing it.
 template <int D>
-__device__ __forceinline__ BoxInfo<D> box_begin(bool valid, const int base[D], int cap, float* sm,
-                                                int* s_box) {
+__device__ __forceinline__ BoxInfo<D> box_extent(bool valid, const int base[D], int cap, int* s_box) {
+  __syncthreads();
   if (threadIdx.x < D) {
     s_box[threadIdx.x] = INT_MAX;
     s_box[4 + threadIdx.x] = INT_MIN;
@@ -189,6 +190,13 @@ __device__ __forceinline__ BoxInfo<D> box_begin(bool valid, const int base[D], i
   }
   b.vol = any ? vol : 0;
   b.use_tile = any && vol <= cap;
+  return b;
+}
+
+// Zero the SoA accumulation box (4 arrays of cap floats).  Synchronises on both sides.
+template <int D>
+__device__ __forceinline__ void box_zero(const BoxInfo<D>& b, float* sm, int cap) {
+  __syncthreads();
   if (b.use_tile)
     for (int l = threadIdx.x; l < b.vol; l += blockDim.x) {
       sm[l] = 0.0f;
@@ -197,7 +205,45 @@ __device__ __forceinline__ BoxInfo<D> box_begin(bool valid, const int base[D], i
       sm[3 * cap + l] = 0.0f;
     }
   __syncthreads();
-  return b;
+}
+
+// Copy the box of a scene grid g (float4 per node) into shared memory (float4 per node,
+// box-local order), one coalesced load per node.  Synchronises on both sides.
+template <int D>
+__device__ __forceinline__ void box_load(const BoxInfo<D>& b, float4* sm4, const float4* g, int n) {
+  __syncthreads();
+  if (b.use_tile)
+    for (int l = threadIdx.x; l < b.vol; l += blockDim.x) {
+      int idx[D], r = l;
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+        idx[a] = b.lo[a] + r % b.dim[a];
+        r /= b.dim[a];
+      }
+      sm4[l] = __ldg(g + node_flat<D>(idx, n));
+    }
+  __syncthreads();
+}
+
+// Run body(load) with load(i, j, k) returning the float4 of stencil node base + (i, j, k):
+// from the shared box when it holds the CTA's stencils, else from global memory.
+template <int D, typename Body>
+__device__ __forceinline__ void with_nodes(const BoxInfo<D>& b, const float4* sm4, const float4* g,
+                                           const int base[D], int n, Body&& body) {
+  if (b.use_tile) {
+    int lb = base[0] - b.lo[0];
+#pragma unroll
+    for (int c = 1; c < D; ++c) lb = lb * b.dim[c] + (base[c] - b.lo[c]);
+    const int s1 = D == 2 ? 1 : b.dim[D - 1];
+    const int s0 = b.dim[1] * s1;
+    const float4* p = sm4 + lb;
+    body([&](int i, int j, int k) { return p[i * s0 + j * s1 + k]; });
+  } else {
+    const float4* p = g + node_flat<D>(base, n);
+    const int s1 = D == 2 ? 1 : n;
+    const int s0 = D == 2 ? n : n * n;
+    body([&](int i, int j, int k) { return __ldg(p + i * s0 + j * s1 + k); });
+  }
 }
 
 template <int D>
@@ -357,7 +403,7 @@ __device__ __forceinline__ void load_E(const float* rows, int64_t N, int64_t p, 
 template <int D, int MAT, int MODE>
 __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P, StepArgs A) {
   using R = Rows<D>;
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8];
   float* xr = sm + 4 * (P.tile_capacity > 0 ? P.tile_capacity : 1);
   const int4 tile = A.tiles[blockIdx.x];
@@ -395,23 +441,27 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
 #pragma unroll
       for (int b = 0; b < D; ++b) B[a][b] = 0.0f;
     }
+    const float4* Ug = A.U + (int64_t)scene * P.nnodes;
+    const BoxInfo<D> gbx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
+    box_load<D>(gbx, reinterpret_cast<float4*>(sm), Ug, n);
     if (ok) {
       // centred on the stencil's centre node: equal because sum W dpos = 0, and
       // accurate in FP32 when u is nearly uniform over the stencil
-      const float4* Ug = A.U + (int64_t)scene * P.nnodes + node_flat<D>(s.base, n);
-      const float4 uc4 = __ldg(Ug + stencil_off<D>(1, 1, 1, n));
-      const float uc[3] = {uc4.x, uc4.y, uc4.z};
-      for_nodes<D>(s.w, [&](int i, int j, int k, float W) {
-        const float4 u4 = __ldg(Ug + stencil_off<D>(i, j, k, n));
-        const float u[3] = {u4.x, u4.y, u4.z};
-        const float dpos[3] = {s.dp[0][i], s.dp[1][j], D == 3 ? s.dp[D - 1][k] : 0.0f};
+      with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), Ug, s.base, n, [&](auto load) {
+        const float4 uc4 = load(1, 1, D == 3 ? 1 : 0);
+        const float uc[3] = {uc4.x, uc4.y, uc4.z};
+        for_nodes<D>(s.w, [&](int i, int j, int k, float W) {
+          const float4 u4 = load(i, j, k);
+          const float u[3] = {u4.x, u4.y, u4.z};
+          const float dpos[3] = {s.dp[0][i], s.dp[1][j], D == 3 ? s.dp[D - 1][k] : 0.0f};
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          v[a] += W * u[a];
-          const float wd = W * (u[a] - uc[a]);
+          for (int a = 0; a < D; ++a) {
+            v[a] += W * u[a];
+            const float wd = W * (u[a] - uc[a]);
 #pragma unroll
-          for (int b = 0; b < D; ++b) B[a][b] += wd * dpos[b];
-        }
+            for (int b = 0; b < D; ++b) B[a][b] += wd * dpos[b];
+          }
+        });
       });
     }
     const float c4 = 4.0f * P.inv_dx * P.inv_dx;
@@ -474,7 +524,8 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
       }
     }
     put_record<D>(xr, ok, s.base, s.f, mv, Am);
-    BoxInfo<D> bx = box_begin<D>(ok, s.base, P.tile_capacity, sm, s_box);
+    const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
+    box_zero<D>(bx, sm, P.tile_capacity);
     float4* PMs = A.PM + (int64_t)scene * P.nnodes;
     scatter_records<D, true>(xr, tile.z, bx, sm, P.tile_capacity, PMs, n, P, P.p_mass);
     box_flush<D>(bx, sm, P.tile_capacity, PMs, n);
@@ -495,7 +546,7 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
 template <int D, int MAT, int MODE>
 __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs A) {
   using R = Rows<D>;
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8];
   __shared__ float s_wbar[kMaxGroups * kMaxBasis];
   float* xr = sm + 4 * (P.tile_capacity > 0 ? P.tile_capacity : 1);
@@ -564,12 +615,14 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
 #pragma unroll
       for (int b = 0; b < D; ++b) Ab[a][b] = 0.0f;
     }
-    if (ok) {
+    const float4* PBMs = A.PBM + (int64_t)scene * P.nnodes;
+    const BoxInfo<D> gbx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
+    box_load<D>(gbx, reinterpret_cast<float4*>(sm), PBMs, n);
+    if (ok) with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), PBMs, s.base, n, [&](auto load) {
       // pbar - pbar_c and mbar - mbar_c (centre node) in the moment and weight-gradient
       // terms: equal to the plain sums because sum W dpos = 0, sum grad W = 0 and
       // sum grad W dpos^T = I, without the FP32 cancellation of a smooth pbar field
-      const float4* Gg = A.PBM + (int64_t)scene * P.nnodes + node_flat<D>(s.base, n);
-      const float4 gc = __ldg(Gg + stencil_off<D>(1, 1, 1, n));
+      const float4 gc = load(1, 1, D == 3 ? 1 : 0);
       const float pc[3] = {gc.x, gc.y, gc.z};
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -597,7 +650,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
             for (int c = 0; c < D; ++c)
               q[c] = D == 3 ? qij[c] + Am[c][D - 1] * s.dp[D - 1][k] : qij[c];
             const float dpos[3] = {s.dp[0][i], s.dp[1][j], D == 3 ? s.dp[D - 1][k] : 0.0f};
-            const float4 g4 = __ldg(Gg + stencil_off<D>(i, j, k, n));
+            const float4 g4 = load(i, j, k);
             const float pb[3] = {g4.x, g4.y, g4.z};
             float Wbar = P.p_mass * (g4.w - gc.w);
 #pragma unroll
@@ -614,7 +667,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
           }
         }
       }
-    }
+    });
     // x += inv_dx sum Wbar gradW - A^T sum W dpbar
 #pragma unroll
     for (int b = 0; b < D; ++b) {
@@ -700,10 +753,12 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     Axes<D> s;
     const bool ok = make_axes<D>(x0, P, s) && active;
     if (active && !ok) err |= kErrOOB;
-    if (ok) {
+    const float4* Ug = A.U + (int64_t)scene * P.nnodes;
+    const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
+    box_load<D>(bx, reinterpret_cast<float4*>(sm), Ug, n);
+    if (ok) with_nodes<D>(bx, reinterpret_cast<const float4*>(sm), Ug, s.base, n, [&](auto load) {
       // x-adjoint terms on u - u_c (centre node), by the same B-spline identities
-      const float4* Ug = A.U + (int64_t)scene * P.nnodes + node_flat<D>(s.base, n);
-      const float4 uc4 = __ldg(Ug + stencil_off<D>(1, 1, 1, n));
+      const float4 uc4 = load(1, 1, D == 3 ? 1 : 0);
       const float uc[3] = {uc4.x, uc4.y, uc4.z};
       float xg[D], sw[D];
 #pragma unroll
@@ -729,7 +784,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
             gW[0] = dwij0 * wk;
             gW[1] = dwij1 * wk;
             if (D == 3) gW[D - 1] = wij * s.dw[D - 1][k];
-            const float4 u4 = __ldg(Ug + stencil_off<D>(i, j, k, n));
+            const float4 u4 = load(i, j, k);
             const float du[3] = {u4.x - uc[0], u4.y - uc[1], u4.z - uc[2]};
             float Wbar = 0.0f;
 #pragma unroll
@@ -750,7 +805,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
         for (int a = 0; a < D; ++a) ctu += Ct[a][b] * sw[a];
         xb0[b] += P.inv_dx * xg[b] - c4 * ctu;
       }
-    }
+    });
     if (active) {
 #pragma unroll
       for (int a = 0; a < D; ++a) A.adj[(R::X + a) * N + p] = xb0[a];
@@ -764,7 +819,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
 #pragma unroll
       for (int j = 0; j < D; ++j) Bs[i][j] = c4 * Ct[i][j];
     put_record<D>(xr, ok, s.base, s.f, vt, Bs);
-    BoxInfo<D> bx = box_begin<D>(ok, s.base, P.tile_capacity, sm, s_box);
+    box_zero<D>(bx, sm, P.tile_capacity);  // same extent as the gather box
     float4* UBs = A.UB + (int64_t)scene * P.nnodes;
     scatter_records<D, false>(xr, tile.z, bx, sm, P.tile_capacity, UBs, n, P, 0.0f);
     box_flush<D>(bx, sm, P.tile_capacity, UBs, n);

@@ -20,16 +20,5 @@ def scene_slice(scene, i):
 
 def subset_scenes(scene, idx):
     """A batch made of some scenes of another batch (arrays sliced, desc updated)."""
-    desc = dict(scene["desc"])
-    a = scene["arrays"]
-    sl = [scene_slice(scene, i) for i in idx]
-    cat = lambda k, ax=1: np.ascontiguousarray(np.concatenate([a[k][..., s] for s in sl], axis=ax))
-    arr = {k: cat(k) for k in ("x0", "v0", "C0", "F0")}
-    arr["E"] = np.ascontiguousarray(np.concatenate([a["E"][s] for s in sl]))
-    arr["nu"] = np.ascontiguousarray(np.concatenate([a["nu"][s] for s in sl]))
-    arr["group"] = np.ascontiguousarray(np.concatenate([a["group"][s] for s in sl]))
-    arr["w"] = np.ascontiguousarray(a["w"][list(idx)])
-    arr["target"] = np.ascontiguousarray(a["target"][list(idx)])
-    desc["n_particles"] = [int(scene["desc"]["n_particles"][i]) for i in idx]
-    desc["n_scenes"] = len(idx)
-    return {"desc": desc, "arrays": arr}
+    from paper_1910_00935_gb300.sharding import subset
+    return subset(scene, idx)

@@ -1,0 +1,73 @@
+"""Multi-rank host logic on CPU (world size 2, gloo): scenes sharded across ranks with no
+data-path collective give exactly the single-process results, and the benchmark's
+max-over-ranks timing reduction works.  The per-rank work is the FP64 oracle (no GPU)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import oracle
+from paper_1910_00935_gb300 import scenes
+from paper_1910_00935_gb300.sharding import shard_scenes, subset
+
+
+def test_shards_partition_and_balance():
+    counts = [5000, 100, 2000, 2000, 7000, 300, 300, 4000]
+    for world in (1, 2, 3, 4):
+        shards = [shard_scenes(counts, world, r) for r in range(world)]
+        flat = sorted(i for s in shards for i in s)
+        assert flat == list(range(len(counts)))          # a partition
+        loads = [sum(counts[i] for i in s) for s in shards]
+        assert max(loads) - min(loads) <= max(counts)     # greedy balance bound
+        assert shards == [shard_scenes(counts, world, r) for r in range(world)]  # deterministic
+    with pytest.raises(ValueError):
+        shard_scenes(counts, 2, 2)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, T, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    base = scenes.make("rects2d", n_scenes=5, n_min=200, n_max=600)
+    mine = shard_scenes(base["desc"]["n_particles"], world, rank)
+    res = oracle.simulate(scenes.oracle_view(subset(base, mine)), T)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, {i: r for i, r in zip(mine, res)})
+    t = torch.tensor([float(rank + 1)])
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    if rank == 0:
+        merged = {}
+        for g in gathered:
+            merged.update(g)
+        q.put((merged, float(t.item())))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharded_run_equals_single_process():
+    T = 6
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, T, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    merged, tmax = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert tmax == 2.0  # max over ranks
+    base = scenes.make("rects2d", n_scenes=5, n_min=200, n_max=600)
+    single = oracle.simulate(scenes.oracle_view(base), T)
+    assert sorted(merged) == list(range(5))
+    for i in range(5):
+        np.testing.assert_array_equal(merged[i], single[i])  # bitwise
