@@ -64,7 +64,9 @@ extern "C" {
 
 /* options for mpm_set_option (tuning knobs; defaults in brackets) */
 #define MPM_OPT_USE_GRAPHS 1      /* capture forward/backward into CUDA graphs [1] */
-#define MPM_OPT_SMEM_TILE 2       /* P2G scatters through shared-memory grid tiles [1] */
+#define MPM_OPT_SMEM_TILE 2       /* 1: scatters accumulate in a shared-memory node box and
+                                     flush once per node; 0: float4 reductions straight to
+                                     the L2-resident grid [0, faster on GB300] */
 #define MPM_OPT_TILE_CAPACITY 3   /* max nodes of one CTA's shared tile [1024] */
 #define MPM_OPT_PROFILE 4         /* 1: time every kernel launch with CUDA events on its
                                      stream (launches go unbatched, no graphs) [0];

@@ -156,7 +156,7 @@ struct mpm_handle {
   int32_t T_recorded = 0;
   // options
   bool use_graphs = true;
-  bool smem_tile = true;
+  bool smem_tile = false;  // measured on GB300: global float4 reductions beat shared FP32 atomics
   int tile_capacity = 1024;
   // graphs
   cudaStream_t cap_stream = nullptr;

@@ -257,8 +257,8 @@ def test_graphs_and_tiles_do_not_change_results(mpm):
     T = 12
     seeds = _random_seeds(scene, np.random.default_rng(2))
     ref = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
-    for opts in ({mpm.MPM_OPT_USE_GRAPHS: 0}, {mpm.MPM_OPT_SMEM_TILE: 0},
-                 {mpm.MPM_OPT_TILE_CAPACITY: 64}):
+    for opts in ({mpm.MPM_OPT_USE_GRAPHS: 0}, {mpm.MPM_OPT_SMEM_TILE: 1},
+                 {mpm.MPM_OPT_SMEM_TILE: 1, mpm.MPM_OPT_TILE_CAPACITY: 64}):
         g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False, options=opts)
         assert rel_l2(g["state"][0], ref["state"][0]) <= 1e-6
         for key in ("gx0", "gv0", "gF0"):
