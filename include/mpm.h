@@ -72,6 +72,10 @@ extern "C" {
                                      stream (launches go unbatched, no graphs) [0];
                                      setting it clears the collected timings */
 
+#define MPM_OPT_GATHER_CAPACITY 5 /* max nodes of a CTA's shared gather box; 0 = gathers
+                                     read the grid through L1 [1024] */
+#define MPM_OPT_GRID_BLOCKS 6     /* CTAs per scene of the node passes; 0 = automatic [0] */
+
 /* kernel categories for mpm_get_profile */
 #define MPM_KERNEL_P2G 1          /* P2G from a full state (segment starts, grid recompute) */
 #define MPM_KERNEL_G2P_P2G 2      /* fused G2P of step t-1 + P2G of step t, x and F written */

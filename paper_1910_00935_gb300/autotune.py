@@ -1,0 +1,123 @@
+"""Autotuner for the launch knobs of libmpm (measurement-based, cached).
+
+The knobs are the library's runtime options: the capacity of the shared gather box
+(MPM_OPT_GATHER_CAPACITY), the scatter path (MPM_OPT_SMEM_TILE: shared node box vs. float4
+reductions straight to the grid), the shared box capacity (MPM_OPT_TILE_CAPACITY) and the
+CTA count of the node passes (MPM_OPT_GRID_BLOCKS).  `tune` times a short forward+backward
+of the caller's own simulator for each candidate, one knob at a time (coordinate descent
+from the defaults), keeps the fastest, and caches the result in a JSON file keyed by the
+workload's shape class and the device name.  Results never change numerics beyond FP32
+atomic-order rounding (the GPU tests check every knob setting against the oracle).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+SPACE = {
+    "gather_capacity": [1024, 0, 512, 2048],
+    "smem_tile": [0, 1],
+    "tile_capacity": [1024, 2048],
+    "grid_blocks": [0, 32, 64, 128],
+}
+DEFAULTS = {"gather_capacity": 1024, "smem_tile": 0, "tile_capacity": 1024, "grid_blocks": 0}
+
+_OPTION_IDS = {"gather_capacity": 5, "smem_tile": 2, "tile_capacity": 3, "grid_blocks": 6}
+
+
+def default_cache_path() -> str:
+    return os.environ.get("MPM_TUNE_CACHE",
+                          os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
+                                       "autotune.json"))
+
+
+def shape_key(desc: dict, device_name: str = "") -> str:
+    """Workloads of the same dimension, material, grid, scene count and particle count
+    (to within a factor of 2) share tuned knobs."""
+    N = int(sum(desc["n_particles"]))
+    return "|".join(str(v) for v in (
+        device_name, desc["dim"], desc["material"], desc["n_grid"], len(desc["n_particles"]),
+        int(math.log2(max(N, 1))), 1 if desc.get("n_groups", 0) else 0))
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or default_cache_path()
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str | None = None) -> None:
+    path = path or default_cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def coordinate_descent(measure, space=SPACE, start=DEFAULTS, rounds: int = 1):
+    """Minimise measure(config) -> seconds one knob at a time.  Returns (best config,
+    best time, list of (config, time) evaluated)."""
+    best = dict(start)
+    best_t = measure(best)
+    log = [(dict(best), best_t)]
+    for _ in range(rounds):
+        improved = False
+        for knob, values in space.items():
+            for v in values:
+                if v == best[knob]:
+                    continue
+                cand = dict(best, **{knob: v})
+                t = measure(cand)
+                log.append((dict(cand), t))
+                if t < best_t:
+                    best, best_t, improved = cand, t, True
+        if not improved:
+            break
+    return best, best_t, log
+
+
+def apply(sim, config: dict) -> None:
+    """Set the knobs of `config` on a Simulator."""
+    for knob, value in config.items():
+        sim.set_option(_OPTION_IDS[knob], int(value))
+
+
+def tune(sim, T: int = 32, repeats: int = 2, cache_path: str | None = None, force: bool = False):
+    """Tune the knobs for `sim` (a Simulator with its initial state set) and apply them.
+    Returns the chosen configuration."""
+    import torch
+
+    key = shape_key(sim.desc, torch.cuda.get_device_name(sim.device))
+    cache = load_cache(cache_path)
+    if not force and key in cache:
+        apply(sim, cache[key]["config"])
+        return cache[key]["config"]
+    T = min(T, sim.max_steps)
+    target = torch.zeros(sim.n_scenes, sim.dim, device=sim.device)
+
+    def measure(config):
+        apply(sim, config)
+        best = float("inf")
+        for _ in range(repeats + 1):  # the first run captures the graphs
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sim.forward(T)
+            _, gT, _ = sim.loss(0, target)
+            sim.backward(dL_dx=gT)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        sim.check()
+        return best
+
+    config, t, log = coordinate_descent(measure)
+    apply(sim, config)
+    cache[key] = {"config": config, "seconds_per_probe": t, "T_probe": T,
+                  "evaluated": [[c, s] for c, s in log]}
+    save_cache(cache, cache_path)
+    return config

@@ -8,7 +8,7 @@ namespace mpm {
 namespace {
 template <int MAT, int MODE>
 cudaError_t step_one(const SimParams& P, const StepArgs& A, int n_tiles, cudaStream_t s) {
-  const size_t smem = pass_smem_bytes<3>(P.tile_capacity);
+  const size_t smem = pass_smem_bytes<3>(P.tile_capacity, P.gather_capacity);
   auto k = step_kernel<3, MAT, MODE>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -20,7 +20,7 @@ cudaError_t step_one(const SimParams& P, const StepArgs& A, int n_tiles, cudaStr
 
 template <int MAT, int MODE>
 cudaError_t adj_one(const SimParams& P, const AdjArgs& A, int n_tiles, cudaStream_t s) {
-  const size_t smem = pass_smem_bytes<3>(P.tile_capacity);
+  const size_t smem = pass_smem_bytes<3>(P.tile_capacity, P.gather_capacity);
   auto k = adjoint_kernel<3, MAT, MODE>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

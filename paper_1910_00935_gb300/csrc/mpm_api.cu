@@ -158,6 +158,8 @@ struct mpm_handle {
   bool use_graphs = true;
   bool smem_tile = false;  // measured on GB300: global float4 reductions beat shared FP32 atomics
   int tile_capacity = 1024;
+  int gather_capacity = 1024;
+  int grid_blocks = 0;  // CTAs per scene of the node passes (0 = automatic)
   // graphs
   cudaStream_t cap_stream = nullptr;
   std::map<int64_t, std::pair<cudaGraphExec_t, int64_t>> graphs;  // key -> (exec, launches)
@@ -219,11 +221,13 @@ SimParams params_for(const mpm_handle* h, int t) {
     P.basis[k - 1] =
         (float)std::sin(two_pi * k * (double)t / (double)d.act_period + (double)d.act_phase);
   P.tile_capacity = h->smem_tile ? h->tile_capacity : 0;
+  P.gather_capacity = h->gather_capacity;
   P.f_diag = 0.0f;  // the workspace holds E = F - I
   return P;
 }
 
 int grid_blocks_per_scene(const mpm_handle* h) {
+  if (h->grid_blocks > 0) return h->grid_blocks;
   // enough CTAs to cover a typical active box; the kernels stride over the rest
   int64_t per_scene = 304 / h->m.S;
   if (per_scene < 2) per_scene = 2;
@@ -670,6 +674,15 @@ int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
   switch (key) {
     case MPM_OPT_USE_GRAPHS: h->use_graphs = value != 0; break;
     case MPM_OPT_SMEM_TILE: h->smem_tile = value != 0; break;
+    case MPM_OPT_GATHER_CAPACITY:
+      if (value != 0 && (value < 27 || value > 12288))
+        return fail(h, MPM_ERR_ARG, "gather capacity must be 0 or in [27, 12288]");
+      h->gather_capacity = (int)value;
+      break;
+    case MPM_OPT_GRID_BLOCKS:
+      if (value < 0 || value > 65535) return fail(h, MPM_ERR_ARG, "grid blocks must be in [0, 65535]");
+      h->grid_blocks = (int)value;
+      break;
     case MPM_OPT_PROFILE:
       h->profile = value != 0;
       h->ev_records.clear();

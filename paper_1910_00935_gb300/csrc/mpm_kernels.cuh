@@ -88,10 +88,47 @@ struct Xch {
 __device__ __forceinline__ int scatter_slot(int t) { return (t & 31) * (kTile / 32) + (t >> 5); }
 __device__ __forceinline__ int xidx(int j) { return j + (j >> 3); }
 
-// dynamic shared memory of a particle pass: node box (4 * cap floats) + scatter records
+// dynamic shared memory of a particle pass: node box (4 floats per node, shared by the
+// gather box and the scatter box) + scatter records
+__host__ __device__ inline int box_floats(int scatter_cap, int gather_cap) {
+  int c = scatter_cap > gather_cap ? scatter_cap : gather_cap;
+  return 4 * (c > 0 ? c : 1);
+}
 template <int D>
-inline size_t pass_smem_bytes(int cap) {
-  return sizeof(float) * ((size_t)4 * (cap > 0 ? cap : 1) + (size_t)Xch<D>::kWidth * Xch<D>::kStride);
+inline size_t pass_smem_bytes(int scatter_cap, int gather_cap) {
+  return sizeof(float) * ((size_t)box_floats(scatter_cap, gather_cap) +
+                          (size_t)Xch<D>::kWidth * Xch<D>::kStride);
+}
+
+// Scene bounding box of the nodes a scatter touches: each warp reduces its valid lanes
+// into s_bbox (shared int atomics, native); after the CTA's next barrier thread 0 folds
+// s_bbox into the scene box with one set of global atomics (cta_bbox_flush).
+// s_bbox must have been reset (cta_bbox_reset) before a barrier preceding this call.
+__device__ __forceinline__ void cta_bbox_reset(int* s_bbox) {
+  if (threadIdx.x < 8) s_bbox[threadIdx.x] = (threadIdx.x & 4) ? INT_MIN : INT_MAX;
+}
+template <int D>
+__device__ __forceinline__ void warp_bbox(bool valid, const int base[D], int* s_bbox) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    int lo = __reduce_min_sync(0xffffffffu, valid ? base[a] : INT_MAX);
+    int hi = __reduce_max_sync(0xffffffffu, valid ? base[a] + 2 : INT_MIN);
+    if (lane == 0 && hi >= lo) {
+      atomicMin(&s_bbox[a], lo);
+      atomicMax(&s_bbox[4 + a], hi);
+    }
+  }
+}
+template <int D>
+__device__ __forceinline__ void cta_bbox_flush(const int* s_bbox, int* bbox_scene) {
+  if (threadIdx.x == 0 && s_bbox[4] >= s_bbox[0]) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      atomicMin(&bbox_scene[a], s_bbox[a]);
+      atomicMax(&bbox_scene[4 + a], s_bbox[4 + a]);
+    }
+  }
 }
 
 template <int D>
@@ -405,7 +442,9 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
   using R = Rows<D>;
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8];
-  float* xr = sm + 4 * (P.tile_capacity > 0 ? P.tile_capacity : 1);
+  __shared__ int s_bbox[8];
+  cta_bbox_reset(s_bbox);
+  float* xr = sm + box_floats(P.tile_capacity, P.gather_capacity);
   const int4 tile = A.tiles[blockIdx.x];
   const int scene = tile.x;
   const bool active = (int)threadIdx.x < tile.z;
@@ -442,8 +481,12 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
       for (int b = 0; b < D; ++b) B[a][b] = 0.0f;
     }
     const float4* Ug = A.U + (int64_t)scene * P.nnodes;
-    const BoxInfo<D> gbx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
-    box_load<D>(gbx, reinterpret_cast<float4*>(sm), Ug, n);
+    BoxInfo<D> gbx;
+    gbx.use_tile = false;
+    if (P.gather_capacity > 0) {
+      gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);
+      box_load<D>(gbx, reinterpret_cast<float4*>(sm), Ug, n);
+    }
     if (ok) {
       // centred on the stencil's centre node: equal because sum W dpos = 0, and
       // accurate in FP32 when u is nearly uniform over the stencil
@@ -523,18 +566,30 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
         for (int j = 0; j < D; ++j) Am[i][j] = P.kappa * tau[i][j] + P.p_mass * C[i][j];
       }
     }
-    put_record<D>(xr, ok, s.base, s.f, mv, Am);
-    const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
-    box_zero<D>(bx, sm, P.tile_capacity);
     float4* PMs = A.PM + (int64_t)scene * P.nnodes;
-    scatter_records<D, true>(xr, tile.z, bx, sm, P.tile_capacity, PMs, n, P, P.p_mass);
-    box_flush<D>(bx, sm, P.tile_capacity, PMs, n);
-    if (threadIdx.x == 0 && bx.vol > 0) {
+    if (P.tile_capacity > 0) {
+      put_record<D>(xr, ok, s.base, s.f, mv, Am);
+      const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
+      box_zero<D>(bx, sm, P.tile_capacity);
+      scatter_records<D, true>(xr, tile.z, bx, sm, P.tile_capacity, PMs, n, P, P.p_mass);
+      box_flush<D>(bx, sm, P.tile_capacity, PMs, n);
+      if (threadIdx.x == 0 && bx.vol > 0) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        atomicMin(&A.bbox[scene * 8 + a], bx.lo[a]);
-        atomicMax(&A.bbox[scene * 8 + 4 + a], bx.lo[a] + bx.dim[a] - 1);
+        for (int a = 0; a < D; ++a) {
+          atomicMin(&A.bbox[scene * 8 + a], bx.lo[a]);
+          atomicMax(&A.bbox[scene * 8 + 4 + a], bx.lo[a] + bx.dim[a] - 1);
+        }
       }
+    } else {
+      // float4 reductions straight to the grid, in the interleaved lane order
+      if (MODE == kP2GOnly || P.gather_capacity <= 0) __syncthreads();  // s_bbox reset visible
+      put_record<D>(xr, ok, s.base, s.f, mv, Am);
+      warp_bbox<D>(ok, s.base, s_bbox);
+      __syncthreads();
+      cta_bbox_flush<D>(s_bbox, A.bbox + scene * 8);
+      BoxInfo<D> none;
+      none.use_tile = false;
+      scatter_records<D, true>(xr, tile.z, none, sm, 0, PMs, n, P, P.p_mass);
     }
   }
   if (err) atomicOr(A.err, err);
@@ -549,7 +604,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8];
   __shared__ float s_wbar[kMaxGroups * kMaxBasis];
-  float* xr = sm + 4 * (P.tile_capacity > 0 ? P.tile_capacity : 1);
+  float* xr = sm + box_floats(P.tile_capacity, P.gather_capacity);
   const int4 tile = A.tiles[blockIdx.x];
   const int scene = tile.x;
   const bool active = (int)threadIdx.x < tile.z;
@@ -616,8 +671,12 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
       for (int b = 0; b < D; ++b) Ab[a][b] = 0.0f;
     }
     const float4* PBMs = A.PBM + (int64_t)scene * P.nnodes;
-    const BoxInfo<D> gbx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
-    box_load<D>(gbx, reinterpret_cast<float4*>(sm), PBMs, n);
+    BoxInfo<D> gbx;
+    gbx.use_tile = false;
+    if (P.gather_capacity > 0) {
+      gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);
+      box_load<D>(gbx, reinterpret_cast<float4*>(sm), PBMs, n);
+    }
     if (ok) with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), PBMs, s.base, n, [&](auto load) {
       // pbar - pbar_c and mbar - mbar_c (centre node) in the moment and weight-gradient
       // terms: equal to the plain sums because sum W dpos = 0, sum grad W = 0 and
@@ -754,9 +813,15 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     const bool ok = make_axes<D>(x0, P, s) && active;
     if (active && !ok) err |= kErrOOB;
     const float4* Ug = A.U + (int64_t)scene * P.nnodes;
-    const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
-    box_load<D>(bx, reinterpret_cast<float4*>(sm), Ug, n);
-    if (ok) with_nodes<D>(bx, reinterpret_cast<const float4*>(sm), Ug, s.base, n, [&](auto load) {
+    // one extent serves the gather box and the scatter box (same stencils)
+    const int cap_box = P.tile_capacity > P.gather_capacity ? P.tile_capacity : P.gather_capacity;
+    BoxInfo<D> bx;
+    bx.use_tile = false;
+    if (cap_box > 0) bx = box_extent<D>(ok, s.base, cap_box, s_box);
+    BoxInfo<D> gbx = bx;
+    gbx.use_tile = bx.use_tile && P.gather_capacity > 0 && bx.vol <= P.gather_capacity;
+    if (P.gather_capacity > 0) box_load<D>(gbx, reinterpret_cast<float4*>(sm), Ug, n);
+    if (ok) with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), Ug, s.base, n, [&](auto load) {
       // x-adjoint terms on u - u_c (centre node), by the same B-spline identities
       const float4 uc4 = load(1, 1, D == 3 ? 1 : 0);
       const float uc[3] = {uc4.x, uc4.y, uc4.z};
@@ -818,11 +883,17 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) Bs[i][j] = c4 * Ct[i][j];
-    put_record<D>(xr, ok, s.base, s.f, vt, Bs);
-    box_zero<D>(bx, sm, P.tile_capacity);  // same extent as the gather box
     float4* UBs = A.UB + (int64_t)scene * P.nnodes;
-    scatter_records<D, false>(xr, tile.z, bx, sm, P.tile_capacity, UBs, n, P, 0.0f);
-    box_flush<D>(bx, sm, P.tile_capacity, UBs, n);
+    BoxInfo<D> sbx = bx;
+    sbx.use_tile = bx.use_tile && P.tile_capacity > 0 && bx.vol <= P.tile_capacity;
+    put_record<D>(xr, ok, s.base, s.f, vt, Bs);
+    if (P.tile_capacity > 0) {
+      box_zero<D>(sbx, sm, P.tile_capacity);  // same extent as the gather box
+    } else {
+      __syncthreads();
+    }
+    scatter_records<D, false>(xr, tile.z, sbx, sm, P.tile_capacity, UBs, n, P, 0.0f);
+    if (P.tile_capacity > 0) box_flush<D>(sbx, sm, P.tile_capacity, UBs, n);
   }
   if (err) atomicOr(A.err, err);
 }

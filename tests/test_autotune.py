@@ -1,0 +1,52 @@
+"""Autotuner logic on the host (no GPU): coordinate descent finds the minimum of a known
+cost over the knob space, the cache round-trips, and shape keys group workloads."""
+import pytest
+
+from paper_1910_00935_gb300 import autotune
+
+torch = pytest.importorskip("torch")
+
+
+def test_coordinate_descent_finds_separable_minimum():
+    target = {"gather_capacity": 512, "smem_tile": 1, "tile_capacity": 2048, "grid_blocks": 64}
+    cost = lambda c: sum((0 if c[k] == target[k] else 1.0 + i) for i, k in enumerate(c))
+    best, t, log = autotune.coordinate_descent(cost, rounds=3)
+    assert best == target and t == 0
+    assert all(set(c) == set(autotune.SPACE) for c, _ in log)
+
+
+def test_cache_round_trip(tmp_path):
+    path = str(tmp_path / "t.json")
+    assert autotune.load_cache(path) == {}
+    autotune.save_cache({"k": {"config": autotune.DEFAULTS}}, path)
+    assert autotune.load_cache(path)["k"]["config"] == autotune.DEFAULTS
+
+
+def test_shape_key_groups_by_size_class():
+    d = dict(dim=3, material=1, n_grid=128, n_particles=[262144])
+    assert autotune.shape_key(d, "gpu") == autotune.shape_key(dict(d, n_particles=[300000]), "gpu")
+    assert autotune.shape_key(d, "gpu") != autotune.shape_key(dict(d, n_particles=[600000]), "gpu")
+    assert autotune.shape_key(d, "gpu") != autotune.shape_key(dict(d, dim=2), "gpu")
+
+
+@pytest.mark.gpu
+def test_tune_on_gpu_keeps_results(tmp_path):
+    import numpy as np
+    from paper_1910_00935_gb300 import build, mpm, scenes
+    build.build()
+    sc = scenes.make("cube3d", n_side=16, n_grid=64)
+    T = 8
+    ref = mpm.from_scene(sc, max_steps=T)
+    ref.forward(T)
+    x_ref = ref.state()[0].cpu().numpy()
+    ref.close()
+    sim = mpm.from_scene(sc, max_steps=T)
+    cfg = autotune.tune(sim, T=T, repeats=1, cache_path=str(tmp_path / "c.json"))
+    assert set(cfg) == set(autotune.SPACE)
+    sim.forward(T)
+    x = sim.state()[0].cpu().numpy()
+    sim.check()
+    assert np.linalg.norm(x - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
+    # second call hits the cache
+    assert autotune.tune(sim, T=T, cache_path=str(tmp_path / "c.json")) == cfg
+    sim.close()
