@@ -41,11 +41,9 @@ ALG_BYTES_3D = {
     "g2p_p2g_full": 48 + 8 + 96,         # read x, F, mu, la; write x, v, C, F
     "g2p": 48 + 96,                      # read x, F; write the full state
     "adj_g2p": 96 + 48 + 48 + 48,        # read adj, C', x, F; write adj x, F
-    "adj_fused": 96 + 48 + 48 + 8 + 16 + 48,  # state s+1, x F of state s, adj x F, mu la,
-                                              # mubar labar (rw), write adj x F
+    "adj_fused": 96 + 48 + 48 + 8 + 16 + 48 + 96,  # state s+1, x F of state s, adj x F (rw),
+                                                   # mu la, mubar labar (rw), state s-1 (P2G)
     "adj_p2g": 96 + 48 + 8 + 16 + 96,
-    "grid_update": 16 + 16 + 16,         # read (m, p), write (u, m), clear (m, p)
-    "grid_adj": 16 + 16 + 16 + 16,       # read ubar, (u, m); write (pbar, mbar), clear ubar
 }
 
 

@@ -74,18 +74,19 @@ extern "C" {
 
 #define MPM_OPT_GATHER_CAPACITY 5 /* max nodes of a CTA's shared gather box; 0 = gathers
                                      read the grid through L1 [1024] */
-#define MPM_OPT_GRID_BLOCKS 6     /* CTAs per scene of the node passes; 0 = automatic [0] */
+#define MPM_OPT_GRID_BLOCKS 6     /* CTAs per scene of the end-of-sequence grid clear; 0 = automatic [0] */
 
 /* kernel categories for mpm_get_profile */
 #define MPM_KERNEL_P2G 1          /* P2G from a full state (segment starts, grid recompute) */
 #define MPM_KERNEL_G2P_P2G 2      /* fused G2P of step t-1 + P2G of step t, x and F written */
 #define MPM_KERNEL_G2P_P2G_FULL 3 /* same, full state written (checkpoints, re-simulation) */
 #define MPM_KERNEL_G2P 4          /* last G2P of a run or segment, full state written */
-#define MPM_KERNEL_GRID_UPDATE 5  /* grid_op over each scene's touched box */
+#define MPM_KERNEL_GRID_CLEAR 5   /* zeroing of grid buffers at the end of a launch sequence */
 #define MPM_KERNEL_ADJ_G2P 6      /* G2P adjoint from the seeds (step T-1) */
-#define MPM_KERNEL_ADJ_FUSED 7    /* P2G adjoint of step s+1 + G2P adjoint of step s */
+#define MPM_KERNEL_ADJ_FUSED 7    /* P2G adjoint of step s+1 + G2P adjoint of step s +
+                                     recomputed P2G of step s-1 */
 #define MPM_KERNEL_ADJ_P2G 8      /* P2G adjoint of step 0 */
-#define MPM_KERNEL_GRID_ADJ 9     /* grid_op adjoint over each scene's touched box */
+
 
 /* queries for mpm_get_info */
 #define MPM_INFO_KERNEL_LAUNCHES 1 /* kernels launched by this handle so far */
@@ -191,9 +192,9 @@ void mpm_destroy(mpm_handle* h);
  * allocator to hand for a workspace.  It calls no cudaMalloc, cudaFree or allocating
  * library routine.
  *
- * The grid scratch lives in one fixed device array inside the library (about 10 MiB:
- * MPM_NOALLOC_MAX_NODES nodes of two float4 grids plus per-particle Lame parameters
- * and tile table), held by every GPU that loads the library until the process exits.
+ * The grid scratch lives in one fixed device array inside the library (about 6 MiB:
+ * one float4 grid of MPM_NOALLOC_MAX_NODES nodes plus per-particle Lame parameters and
+ * the tile table), held by every GPU that loads the library until the process exits.
  * Limits: one scene, no actuation, n_grid^dim <= MPM_NOALLOC_MAX_NODES and
  * n_particles[0] <= MPM_NOALLOC_MAX_PARTICLES; larger problems return
  * MPM_ERR_TOO_LARGE and launch nothing.

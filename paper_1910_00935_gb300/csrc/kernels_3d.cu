@@ -1,4 +1,4 @@
-// kernels_3d.cu -- 3D instantiations of the particle and grid passes and their
+// kernels_3d.cu -- 3D instantiations of the particle passes and the grid clear and their
 // launch wrappers (material and mode are compile-time, dispatched here).
 #include "mpm_internal.h"
 #include "mpm_kernels.cuh"
@@ -67,19 +67,9 @@ cudaError_t launch_adjoint<3>(int material, int mode, const SimParams& P, const 
 }
 
 template <>
-cudaError_t launch_grid_update<3>(const SimParams& P, float4* PM, float4* U, int* bbox,
-                                    int* bbox_u, unsigned* done, int n_scenes, int blocks_per_scene,
-                                    cudaStream_t s) {
-  grid_update_kernel<3><<<dim3(blocks_per_scene, n_scenes), 256, 0, s>>>(P, PM, U, bbox, bbox_u,
-                                                                         done);
-  return cudaGetLastError();
-}
-
-template <>
-cudaError_t launch_grid_adjoint<3>(const SimParams& P, float4* UB, const float4* U, float4* PBM,
-                                     const int* bbox_u, int n_scenes, int blocks_per_scene,
-                                     cudaStream_t s) {
-  grid_adjoint_kernel<3><<<dim3(blocks_per_scene, n_scenes), 256, 0, s>>>(P, UB, U, PBM, bbox_u);
+cudaError_t launch_clear<3>(const Clears& C, int nnodes, int n_grid, int n_scenes, int blocks_per_scene,
+                          cudaStream_t s) {
+  clear_kernel<3><<<dim3(blocks_per_scene, n_scenes), 256, 0, s>>>(C, nnodes, n_grid);
   return cudaGetLastError();
 }
 

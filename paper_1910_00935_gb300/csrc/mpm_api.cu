@@ -6,9 +6,16 @@
 // of every step); the particle state itself is stored every k = ckpt_every steps
 // (Appendix D.2, segment-wise recomputation).  The backward walks s = T-1 .. 0;
 // entering a segment it re-simulates the segment from its checkpoint into one
-// segment buffer, then for each step recomputes that step's grid (Appendix D.1)
-// and runs the fused adjoint pass [P2G-adjoint of step s+1 | G2P-adjoint of step
-// s] followed by the grid adjoint of step s.
+// segment buffer; then each adjoint pass runs [P2G-adjoint of step s+1 | G2P-adjoint
+// of step s | recomputed P2G of step s-1] -- the grid of each step is recomputed once,
+// one pass before it is needed (Appendix D.1).  One particle pass per step in every
+// phase; grid_op and its adjoint are applied by the consuming pass.
+//
+// Grids.  The per-step grids are accumulation buffers from two rings (mass/momentum,
+// velocity adjoint) managed on the host: a pass scatters into a free clean buffer, the
+// buffer stays live until its last reader, and the next pass zeroes its recorded box.
+// Each buffer has two parity boxes so that resetting a box never races with a reader.
+// Every launch sequence starts and ends with all buffers clean.
 //
 // Launch sequences are captured into CUDA graphs (one per forward length T and one
 // per backward length), cached on the handle and replayed on the caller's stream.
@@ -31,13 +38,17 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+constexpr int kPMSlots = 6;  // mass/momentum grids in flight (measured need: 4)
+constexpr int kUBSlots = 4;  // velocity-adjoint grids in flight (need: 3)
+
 struct Layout {
   size_t perm, keys0, keys1, idx0, sort_tmp, sort_tmp_bytes;
-  size_t tiles, scene_off;
+  size_t tiles, scene_off, scene_tiles;
   size_t mu, la, E, nu, group, wact, wbar, mubar, labar;
   size_t fin, cur, ckpt, seg, adj;
-  size_t PM, U, UB, PBM;
-  size_t bbox, bbox_u, done, err, com;
+  size_t grids;  // kPMSlots + kUBSlots dense grids
+  size_t boxes;  // (kPMSlots + kUBSlots) x 2 parities x [scene][8]
+  size_t err, com;
   size_t total;
 };
 
@@ -114,6 +125,7 @@ Layout make_layout(const Dims& m) {
   L.sort_tmp = take(L.sort_tmp_bytes);
   L.tiles = take((size_t)m.n_tiles * sizeof(int4));
   L.scene_off = take((S + 1) * 8);
+  L.scene_tiles = take(S * 4);
   L.mu = take(N * 4);
   L.la = take(N * 4);
   L.E = take(N * 4);
@@ -129,13 +141,8 @@ Layout make_layout(const Dims& m) {
   L.seg = take((size_t)(m.K + 1) * Q * N * 4);
   L.adj = take(Q * N * 4);
   const size_t grid = S * (size_t)m.nnodes * sizeof(float4);
-  L.PM = take(grid);
-  L.U = take(grid);
-  L.UB = take(grid);
-  L.PBM = take(grid);
-  L.bbox = take(S * 8 * 4);
-  L.bbox_u = take(S * 8 * 4);
-  L.done = take(4);
+  L.grids = take(grid * (kPMSlots + kUBSlots));
+  L.boxes = take((size_t)(kPMSlots + kUBSlots) * 2 * S * 8 * 4);
   L.err = take(4);
   L.com = take(S * 6 * 8);
   L.total = o;
@@ -164,6 +171,13 @@ struct mpm_handle {
   cudaStream_t cap_stream = nullptr;
   std::map<int64_t, std::pair<cudaGraphExec_t, int64_t>> graphs;  // key -> (exec, launches)
   int64_t launches = 0;
+  // grid rings (host bookkeeping of the launch sequence being issued)
+  struct Ring {
+    int first;               // index of the ring's first buffer among all grid buffers
+    int n;
+    std::vector<int> use;    // writes so far (box parity)
+    std::vector<int> state;  // 0 free, 1 live, 2 pending clear, 3 clearing in this launch
+  } pm{0, kPMSlots, {}, {}}, ub{kPMSlots, kUBSlots, {}, {}};
   // live per-launch timing (MPM_OPT_PROFILE)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -235,6 +249,73 @@ int grid_blocks_per_scene(const mpm_handle* h) {
   return (int)per_scene;
 }
 
+// ------------------------------ grid rings ---------------------------------
+
+using Ring = mpm_handle::Ring;
+
+void ring_reset(Ring& r) {
+  r.use.assign(r.n, 0);
+  r.state.assign(r.n, 0);
+}
+
+float4* ring_grid(const mpm_handle* h, const Ring& r, int id) {
+  return h->at<float4>(h->L.grids) + (size_t)(r.first + id) * h->m.S * h->m.nnodes;
+}
+
+int* ring_box(const mpm_handle* h, const Ring& r, int id, int parity) {
+  return h->at<int>(h->L.boxes) + ((size_t)(r.first + id) * 2 + (parity & 1)) * h->m.S * 8;
+}
+
+// A buffer to scatter into: its box for this use and the other parity box to reset.
+struct WriteSlot {
+  int id = -1;
+  float4* grid = nullptr;
+  int* box = nullptr;
+  int* box_reset = nullptr;
+};
+
+bool ring_alloc(mpm_handle* h, Ring& r, WriteSlot& w) {
+  for (int i = 0; i < r.n; ++i)
+    if (r.state[i] == 0) {
+      r.state[i] = 1;
+      w.id = i;
+      w.grid = ring_grid(h, r, i);
+      w.box = ring_box(h, r, i, r.use[i]);
+      w.box_reset = ring_box(h, r, i, r.use[i] + 1);
+      return true;
+    }
+  return false;
+}
+
+void ring_release(Ring& r, int id) {
+  if (id >= 0 && r.state[id] == 1) r.state[id] = 2;
+}
+
+// Hand up to kMaxClears pending buffers to the next launch.
+Clears take_clears(mpm_handle* h) {
+  Clears C;
+  memset(&C, 0, sizeof(C));
+  for (Ring* r : {&h->pm, &h->ub})
+    for (int i = 0; i < r->n && C.n < kMaxClears; ++i)
+      if (r->state[i] == 2) {
+        C.job[C.n].grid = ring_grid(h, *r, i);
+        C.job[C.n].box = ring_box(h, *r, i, r->use[i]);
+        ++C.n;
+        r->state[i] = 3;
+      }
+  return C;
+}
+
+// After a launch: buffers cleared by it are clean and free again.
+void after_launch(mpm_handle* h) {
+  for (Ring* r : {&h->pm, &h->ub})
+    for (int i = 0; i < r->n; ++i)
+      if (r->state[i] == 3) {
+        r->state[i] = 0;
+        r->use[i] += 1;
+      }
+}
+
 // ------------------------------ launch helpers ------------------------------
 
 struct Launcher {
@@ -261,11 +342,15 @@ struct Launcher {
     return e;
   }
 
-  cudaError_t step(int mode, int t, const float* in, float* out) {
+  // one forward particle pass: G2P of step t-1 from grid `read` (-1: none), P2G of step
+  // t into a new grid (returned in *written, -1 for G2P only)
+  cudaError_t step(int mode, int t, const float* in, float* out, int read, int* written) {
     const Dims& m = h->m;
     SimParams P = params_for(h, t);
     StepArgs A;
+    memset(&A, 0, sizeof(A));
     A.tiles = h->at<int4>(h->L.tiles);
+    A.scene_tiles = h->at<int>(h->L.scene_tiles);
     A.N = (int)m.N;
     A.in = in;
     A.out = out;
@@ -273,41 +358,46 @@ struct Launcher {
     A.la = h->at<float>(h->L.la);
     A.group = h->at<int>(h->L.group);
     A.wact = h->at<float>(h->L.wact);
-    A.U = h->at<float4>(h->L.U);
-    A.PM = h->at<float4>(h->L.PM);
-    A.bbox = h->at<int>(h->L.bbox);
     A.err = h->at<unsigned>(h->L.err);
+    if (read >= 0) A.PMr = ring_grid(h, h->pm, read);
+    if (written) {
+      WriteSlot w;
+      if (!ring_alloc(h, h->pm, w)) return cudaErrorMemoryAllocation;
+      A.PMw = w.grid;
+      A.box_w = w.box;
+      A.box_reset = w.box_reset;
+      *written = w.id;
+    }
+    A.clears = take_clears(h);
     ++count;
     const int cat = mode == kP2GOnly ? MPM_KERNEL_P2G
                     : mode == kG2PP2G ? MPM_KERNEL_G2P_P2G
                     : mode == kG2PP2GFull ? MPM_KERNEL_G2P_P2G_FULL : MPM_KERNEL_G2P;
-    return timed(cat, [&] {
+    cudaError_t e = timed(cat, [&] {
       return m.D == 2 ? launch_step<2>(h->desc.material, mode, P, A, m.n_tiles, s)
                       : launch_step<3>(h->desc.material, mode, P, A, m.n_tiles, s);
     });
+    after_launch(h);
+    return e;
   }
-  cudaError_t grid_update() {
-    SimParams P = params_for(h, 0);
-    ++count;
-    float4* PM = h->at<float4>(h->L.PM);
-    float4* U = h->at<float4>(h->L.U);
-    int* bb = h->at<int>(h->L.bbox);
-    int* bbu = h->at<int>(h->L.bbox_u);
-    unsigned* done = h->at<unsigned>(h->L.done);
-    int bps = grid_blocks_per_scene(h);
-    return timed(MPM_KERNEL_GRID_UPDATE, [&] {
-      return h->m.D == 2 ? launch_grid_update<2>(P, PM, U, bb, bbu, done, h->m.S, bps, s)
-                         : launch_grid_update<3>(P, PM, U, bb, bbu, done, h->m.S, bps, s);
-    });
-  }
-  cudaError_t adjoint(int mode, int t_p2g, const float* st1, const float* st0) {
+
+  // one adjoint pass (see the file comment); pm1/ub1: grids of step s+1 (-1 in kAdjG2P
+  // mode), pm0: grid of step s; writes the velocity adjoint of step s (*ub_written) and,
+  // when stm != null, the recomputed grid of step s-1 (*pm_written)
+  cudaError_t adjoint(int mode, int s_step, const float* st1, const float* st0, const float* stm,
+                      int pm1, int ub1, int pm0, int* ub_written, int* pm_written) {
     const Dims& m = h->m;
-    SimParams P = params_for(h, t_p2g);
+    SimParams P = params_for(h, s_step + 1);
+    SimParams P2 = params_for(h, s_step - 1 >= 0 ? s_step - 1 : 0);
+    memcpy(P.basis2, P2.basis, sizeof(P.basis2));
     AdjArgs A;
+    memset(&A, 0, sizeof(A));
     A.tiles = h->at<int4>(h->L.tiles);
+    A.scene_tiles = h->at<int>(h->L.scene_tiles);
     A.N = (int)m.N;
     A.st1 = st1;
     A.st0 = st0;
+    A.stm = stm;
     A.adj = h->at<float>(h->L.adj);
     A.mu = h->at<float>(h->L.mu);
     A.la = h->at<float>(h->L.la);
@@ -316,30 +406,62 @@ struct Launcher {
     A.group = h->at<int>(h->L.group);
     A.wact = h->at<float>(h->L.wact);
     A.wbar = h->at<float>(h->L.wbar);
-    A.PBM = h->at<float4>(h->L.PBM);
-    A.U = h->at<float4>(h->L.U);
-    A.UB = h->at<float4>(h->L.UB);
     A.err = h->at<unsigned>(h->L.err);
+    if (pm1 >= 0) A.PM1 = ring_grid(h, h->pm, pm1);
+    if (ub1 >= 0) A.UB1 = ring_grid(h, h->ub, ub1);
+    if (pm0 >= 0) A.PM0 = ring_grid(h, h->pm, pm0);
+    if (ub_written) {
+      WriteSlot w;
+      if (!ring_alloc(h, h->ub, w)) return cudaErrorMemoryAllocation;
+      A.UB0 = w.grid;
+      A.box_ub = w.box;
+      A.box_ub_reset = w.box_reset;
+      *ub_written = w.id;
+    }
+    if (stm && pm_written) {
+      WriteSlot w;
+      if (!ring_alloc(h, h->pm, w)) return cudaErrorMemoryAllocation;
+      A.PMm = w.grid;
+      A.box_m = w.box;
+      A.box_m_reset = w.box_reset;
+      *pm_written = w.id;
+    } else {
+      A.stm = nullptr;
+    }
+    A.clears = take_clears(h);
     ++count;
     const int cat = mode == kAdjG2P ? MPM_KERNEL_ADJ_G2P
                     : mode == kAdjFused ? MPM_KERNEL_ADJ_FUSED : MPM_KERNEL_ADJ_P2G;
-    return timed(cat, [&] {
+    cudaError_t e = timed(cat, [&] {
       return m.D == 2 ? launch_adjoint<2>(h->desc.material, mode, P, A, m.n_tiles, s)
                       : launch_adjoint<3>(h->desc.material, mode, P, A, m.n_tiles, s);
     });
+    after_launch(h);
+    return e;
   }
-  cudaError_t grid_adjoint() {
-    SimParams P = params_for(h, 0);
+
+  // End of a launch sequence: zero every dirty buffer, reset every box.
+  cudaError_t finish() {
+    for (Ring* r : {&h->pm, &h->ub})
+      for (int i = 0; i < r->n; ++i)
+        if (r->state[i] == 1) r->state[i] = 2;
+    cudaError_t e = cudaSuccess;
+    for (;;) {
+      Clears C = take_clears(h);
+      if (C.n == 0) break;
+      ++count;
+      e = timed(MPM_KERNEL_GRID_CLEAR, [&] {
+        return h->m.D == 2 ? launch_clear<2>(C, (int)h->m.nnodes, h->m.n_grid, h->m.S, grid_blocks_per_scene(h), s)
+                           : launch_clear<3>(C, (int)h->m.nnodes, h->m.n_grid, h->m.S, grid_blocks_per_scene(h), s);
+      });
+      after_launch(h);
+      if (e != cudaSuccess) return e;
+    }
     ++count;
-    int bps = grid_blocks_per_scene(h);
-    float4* UB = h->at<float4>(h->L.UB);
-    const float4* U = h->at<float4>(h->L.U);
-    float4* PBM = h->at<float4>(h->L.PBM);
-    const int* bbu = h->at<int>(h->L.bbox_u);
-    return timed(MPM_KERNEL_GRID_ADJ, [&] {
-      return h->m.D == 2 ? launch_grid_adjoint<2>(P, UB, U, PBM, bbu, h->m.S, bps, s)
-                         : launch_grid_adjoint<3>(P, UB, U, PBM, bbu, h->m.S, bps, s);
-    });
+    e = launch_reset_boxes(h->at<int>(h->L.boxes), (int64_t)(kPMSlots + kUBSlots) * 2 * h->m.S, s);
+    ring_reset(h->pm);
+    ring_reset(h->ub);
+    return e;
   }
 };
 
@@ -352,10 +474,12 @@ struct Launcher {
 // forward: states 0..T; full state stored at multiples of K and at T (fin)
 int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
   const int K = h->m.K;
+  ring_reset(h->pm);
+  ring_reset(h->ub);
   const float* src = h->state(h->L.ckpt, 0);
   float* cur = h->at<float>(h->L.cur);
-  LK(Lc.step(kP2GOnly, 0, src, nullptr));
-  LK(Lc.grid_update());
+  int g = -1;
+  LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g));
   for (int t = 1; t < T; ++t) {
     float* dst;
     int mode;
@@ -366,55 +490,70 @@ int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
       dst = cur;
       mode = kG2PP2G;
     }
-    LK(Lc.step(mode, t, src, dst));
-    LK(Lc.grid_update());
+    int g_next = -1;
+    LK(Lc.step(mode, t, src, dst, g, &g_next));
+    ring_release(h->pm, g);
+    g = g_next;
     src = dst;
   }
-  LK(Lc.step(kG2POnlyFull, T, src, h->at<float>(h->L.fin)));
+  LK(Lc.step(kG2POnlyFull, T, src, h->at<float>(h->L.fin), g, nullptr));
+  ring_release(h->pm, g);
+  LK(Lc.finish());
   return MPM_OK;
 }
 
-// re-simulate segment [s0, top): seg slot i <- state s0 + i (i = 1..top-s0)
-int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top) {
+// re-simulate segment [s0, top): seg slot i <- state s0 + i (i = 1..top-s0); returns the
+// grid of step top-1 (kept live for the adjoint passes)
+int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top, int* grid_top_minus_1) {
   const float* ck = h->state(h->L.ckpt, s0 / h->m.K);
-  LK(Lc.step(kP2GOnly, s0, ck, nullptr));
-  LK(Lc.grid_update());
+  int g = -1;
+  LK(Lc.step(kP2GOnly, s0, ck, nullptr, -1, &g));
   const float* prev = ck;
   for (int t = s0 + 1; t < top; ++t) {
     float* dst = h->state(h->L.seg, t - s0);
-    LK(Lc.step(kG2PP2GFull, t, prev, dst));
-    LK(Lc.grid_update());
+    int g_next = -1;
+    LK(Lc.step(kG2PP2GFull, t, prev, dst, g, &g_next));
+    ring_release(h->pm, g);
+    g = g_next;
     prev = dst;
   }
-  LK(Lc.step(kG2POnlyFull, top, prev, h->state(h->L.seg, top - s0)));
+  LK(Lc.step(kG2POnlyFull, top, prev, h->state(h->L.seg, top - s0), g, nullptr));
+  *grid_top_minus_1 = g;
   return MPM_OK;
 }
 
 int issue_backward(mpm_handle* h, Launcher& Lc, int T) {
   const int K = h->m.K;
+  ring_reset(h->pm);
+  ring_reset(h->ub);
+  // live grids: PM of steps s+1 and s, UB of step s+1
+  int pm_s1 = -1, pm_s = -1, ub_s1 = -1;
   for (int s = T - 1; s >= 0; --s) {
     const int j = s / K, s0 = j * K;
     const int top = (s0 + K < T) ? s0 + K : T;
-    bool fresh_grid = false;
     if (s == top - 1) {
-      int rc = issue_resim(h, Lc, s0, top);
+      int rc = issue_resim(h, Lc, s0, top, &pm_s);
       if (rc) return rc;
-      fresh_grid = true;  // the re-simulation's last grid is step s's grid
     }
     const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
     const float* st_s1 = h->state(h->L.seg, s + 1 - s0);
-    if (!fresh_grid) {
-      LK(Lc.step(kP2GOnly, s, st_s, nullptr));  // recompute this step's grid (Appendix D.1)
-      LK(Lc.grid_update());
-    }
-    if (s == T - 1)
-      LK(Lc.adjoint(kAdjG2P, s + 1, st_s1, st_s));
-    else
-      LK(Lc.adjoint(kAdjFused, s + 1, st_s1, st_s));
-    LK(Lc.grid_adjoint());
+    const float* st_sm = (s - 1 >= s0) ? ((s - 1 == s0) ? h->state(h->L.ckpt, j)
+                                                          : h->state(h->L.seg, s - 1 - s0))
+                                        : nullptr;
+    int ub_s = -1, pm_sm = -1;
+    LK(Lc.adjoint(s == T - 1 ? kAdjG2P : kAdjFused, s, st_s1, st_s, st_sm,
+                  s == T - 1 ? -1 : pm_s1, s == T - 1 ? -1 : ub_s1, pm_s, &ub_s, &pm_sm));
+    ring_release(h->pm, pm_s1);
+    ring_release(h->ub, ub_s1);
+    pm_s1 = pm_s;
+    ub_s1 = ub_s;
+    pm_s = pm_sm;  // -1 at a segment start: the next segment's re-simulation provides it
   }
   const float* st0 = h->state(h->L.ckpt, 0);
-  LK(Lc.adjoint(kAdjP2G, 0, st0, st0));
+  LK(Lc.adjoint(kAdjP2G, -1, st0, st0, nullptr, pm_s1, ub_s1, -1, nullptr, nullptr));
+  ring_release(h->pm, pm_s1);
+  ring_release(h->ub, ub_s1);
+  LK(Lc.finish());
   return MPM_OK;
 }
 
@@ -425,7 +564,7 @@ void drop_graphs(mpm_handle* h) {
 
 // Run a launch sequence on `stream`, through a cached CUDA graph when enabled.
 template <typename Fn>
-int run_sequence(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
+int run_sequence_impl(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
   if (!h->use_graphs || h->profile) {
     Launcher Lc{h, stream};
     int rc = issue(Lc);
@@ -454,6 +593,18 @@ int run_sequence(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
   CK(cudaGraphLaunch(it->second.first, stream));
   h->launches += it->second.second;
   return MPM_OK;
+}
+
+// A failed sequence may leave grid buffers dirty: the handle then needs mpm_set_initial
+// (which clears every buffer) before the next forward.
+template <typename Fn>
+int run_sequence(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
+  int rc = run_sequence_impl(h, key, stream, issue);
+  if (rc != MPM_OK) {
+    h->initialized = false;
+    h->T_recorded = 0;
+  }
+  return rc;
 }
 
 }  // namespace
@@ -500,17 +651,21 @@ int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_byt
   // tile table and scene offsets (host -> device once)
   std::vector<int4> tiles;
   std::vector<int64_t> off(m.S + 1, 0);
+  std::vector<int> scene_tiles(m.S, 0);
   for (int s = 0; s < m.S; ++s) {
     off[s + 1] = off[s] + h->n_particles[s];
     for (int64_t b = off[s]; b < off[s + 1]; b += kTile) {
       int cnt = (int)((off[s + 1] - b) < kTile ? (off[s + 1] - b) : kTile);
-      tiles.push_back(make_int4(s, (int)b, cnt, 0));
+      tiles.push_back(make_int4(s, (int)b, cnt, scene_tiles[s]++));
     }
   }
   cudaError_t e = cudaMemcpy(h->at<int4>(L.tiles), tiles.data(), tiles.size() * sizeof(int4),
                              cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(h->at<int64_t>(L.scene_off), off.data(), off.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->at<int>(L.scene_tiles), scene_tiles.data(), scene_tiles.size() * 4,
+                   cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->at<char>(L.err), 0, 4);
   if (e != cudaSuccess) {
     delete h;
@@ -543,10 +698,11 @@ int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float
   const size_t wbytes = (size_t)m.S * h->desc.n_groups * h->desc.n_basis * sizeof(float);
   if (wbytes) CK(cudaMemcpyAsync(h->at<float>(L.wact), w, wbytes, cudaMemcpyDeviceToDevice, s));
   const size_t grid = (size_t)m.S * m.nnodes * sizeof(float4);
-  CK(cudaMemsetAsync(h->at<char>(L.PM), 0, grid, s));
-  CK(cudaMemsetAsync(h->at<char>(L.UB), 0, grid, s));
-  CK(launch_reset_boxes(h->at<int>(L.bbox), h->at<int>(L.bbox_u), h->at<unsigned>(L.done), m.S, s));
-  h->launches += 4;
+  CK(cudaMemsetAsync(h->at<char>(L.grids), 0, grid * (kPMSlots + kUBSlots), s));
+  CK(launch_reset_boxes(h->at<int>(L.boxes), (int64_t)(kPMSlots + kUBSlots) * 2 * m.S, s));
+  ring_reset(h->pm);
+  ring_reset(h->ub);
+  h->launches += 3;
   h->initialized = true;
   h->T_recorded = 0;
   return MPM_OK;

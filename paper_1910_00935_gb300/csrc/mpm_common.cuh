@@ -37,6 +37,7 @@ struct SimParams {
   float kappa;       // -dt * V0 * 4 / dx^2 (stress term of the affine matrix)
   int n_groups, n_basis;
   float basis[kMaxBasis];  // sin(2 pi k t / P + phi), k = 1..n_basis, at this pass's step
+  float basis2[kMaxBasis]; // same at the step of an adjoint pass's recomputed P2G
   int tile_capacity;       // max nodes of a CTA's shared scatter box (0 = global reductions)
   int gather_capacity;     // max nodes of a CTA's shared gather box (0 = gathers through L1)
   float f_diag;            // the F rows of the state hold F - f_diag I (0: E = F - I, 1: F)

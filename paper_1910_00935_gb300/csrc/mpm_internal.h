@@ -12,6 +12,7 @@ namespace mpm {
 
 struct StepArgs;
 struct AdjArgs;
+struct Clears;
 
 // kernels_2d.cu / kernels_3d.cu (templated on dimension)
 template <int D>
@@ -21,12 +22,8 @@ template <int D>
 cudaError_t launch_adjoint(int material, int mode, const SimParams& P, const AdjArgs& A, int n_tiles,
                            cudaStream_t s);
 template <int D>
-cudaError_t launch_grid_update(const SimParams& P, float4* PM, float4* U, int* bbox, int* bbox_u,
-                               unsigned* done, int n_scenes, int blocks_per_scene, cudaStream_t s);
-template <int D>
-cudaError_t launch_grid_adjoint(const SimParams& P, float4* UB, const float4* U, float4* PBM,
-                                const int* bbox_u, int n_scenes, int blocks_per_scene,
-                                cudaStream_t s);
+cudaError_t launch_clear(const Clears& C, int nnodes, int n_grid, int n_scenes, int blocks_per_scene,
+                         cudaStream_t s);
 
 // setup.cu
 size_t sort_temp_bytes(int64_t n);
@@ -38,8 +35,8 @@ cudaError_t launch_gather_initial(int dim, int64_t N, const int* perm, const flo
                                   const float* v0, const float* C0, const float* F0, const float* E,
                                   const float* nu, const int* group_in, float* state, float* mu,
                                   float* la, float* Eo, float* nuo, int* group_out, cudaStream_t s);
-cudaError_t launch_reset_boxes(int* bbox, int* bbox_u, unsigned* done, int n_scenes,
-                               cudaStream_t s);
+// reset n_boxes consecutive [8]-int boxes to empty (lo = INT_MAX, hi = INT_MIN)
+cudaError_t launch_reset_boxes(int* boxes, int64_t n_boxes, cudaStream_t s);
 cudaError_t launch_gather_rows(int rows, int64_t N, const int* perm, const float* src_caller,
                                float* dst_internal, cudaStream_t s);
 // identity_dim > 0: rows are a dim x dim matrix per particle and I is added on the way out

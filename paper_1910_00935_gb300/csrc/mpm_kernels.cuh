@@ -1,5 +1,13 @@
-// mpm_kernels.cuh -- the particle and grid passes of one MLS-MPM step and of its
-// adjoint (Appendix D: p2g, grid_op, g2p and their .grad counterparts).
+// mpm_kernels.cuh -- the particle passes of one MLS-MPM step and of its adjoint
+// (Appendix D: p2g, grid_op, g2p and their .grad counterparts).
+//
+// There are no separate grid passes.  grid_op (v = p/m + dt g, sticky walls) and its
+// adjoint (pbar = ubar/m, mbar = -ubar.p/m^2) are node-local, so the particle pass that
+// consumes a grid applies them to every node it gathers.  Grids are accumulation
+// buffers handed out by the host's ring allocator: a pass scatters into a clean buffer,
+// records the touched box per scene, and a later pass zeroes that box once the buffer's
+// last reader has finished (each buffer keeps two parity copies of its box so that a box
+// is never reset while another CTA may still read it).
 //
 // Particle passes run one CTA per tile of up to kTile particles of one scene
 // (particles are Morton-sorted per scene at set-up, so a tile covers a compact block
@@ -11,10 +19,9 @@
 //     node in the same instruction.  The per-particle scatter record (stencil base, f,
 //     and the affine pair a + B dpos) moves between the two orders through shared
 //     memory.
-// Scatters accumulate into a shared-memory copy of the tile's node box and flush it
-// with one float4 atomic per non-empty node; a tile whose box exceeds the shared
-// capacity scatters with global float4 atomics instead.  Node passes sweep the bounding
-// box of the nodes touched in each scene.
+// Scatters go to the grid with float4 reductions (default), or accumulate in a shared
+// node box flushed once per node (MPM_OPT_SMEM_TILE).  Gathers read a shared gather box
+// filled once per CTA (grid functions applied while filling), or the grid directly.
 //
 // Stencil loops are separable: the weight of node (i, j, k) is w0[i] w1[j] w2[k] and
 // dpos = (dp0[i], dp1[j], dp2[k]), so partial products over (i) and (i, j) are hoisted.
@@ -39,27 +46,43 @@ enum AdjMode : int {
   kAdjP2G = 2,    // P2G-adjoint of step s+1 only (s+1 = 0), writes the full adjoint
 };
 
+// a dirty grid buffer to zero over its recorded per-scene boxes
+struct ClearJob {
+  float4* grid;     // scene-major dense grids
+  const int* box;   // [scene][8]: lo[3], hi[3]
+};
+constexpr int kMaxClears = 3;
+struct Clears {
+  ClearJob job[kMaxClears];
+  int n;
+};
+
 struct StepArgs {
-  const int4* tiles;  // {scene, first particle, count, 0}
-  int N;              // row stride (total particles)
-  const float* in;    // state rows x, v, C, F - f_diag I (component-major)
+  const int4* tiles;       // {scene, first particle, count, rank of the tile in its scene}
+  const int* scene_tiles;  // tiles per scene
+  int N;                   // row stride (total particles)
+  const float* in;         // state rows x, v, C, F - f_diag I (component-major)
   float* out;
   const float* mu;
   const float* la;
   const int* group;
-  const float* wact;  // [scene][group][basis]
-  const float4* U;    // (u, m) per node, scene-major
-  float4* PM;         // (m, p) accumulation per node
-  int* bbox;          // [scene][8]: lo[3], hi[3] of touched nodes
+  const float* wact;       // [scene][group][basis]
+  const float4* PMr;       // grid (m, p) of step t-1, read by G2P (null: P2G only)
+  float4* PMw;             // grid of step t, accumulated by P2G (null: G2P only)
+  int* box_w;              // [scene][8] box of PMw for this use
+  int* box_reset;          // [scene][8] the other parity box of PMw, reset here (or null)
+  Clears clears;
   unsigned* err;
 };
 
 struct AdjArgs {
   const int4* tiles;
+  const int* scene_tiles;
   int N;
-  const float* st1;  // state s+1 (full)
-  const float* st0;  // state s (x and F rows)
-  float* adj;        // adjoint rows x, v, C, F
+  const float* st1;   // state s+1 (full)
+  const float* st0;   // state s (x and F rows)
+  const float* stm;   // state s-1 (full) for the recomputed P2G of step s-1, or null
+  float* adj;         // adjoint rows x, v, C, F
   const float* mu;
   const float* la;
   float* mubar;
@@ -67,9 +90,16 @@ struct AdjArgs {
   const int* group;
   const float* wact;
   float* wbar;        // [scene][group][basis]
-  const float4* PBM;  // (pbar, mbar) of step s+1
-  const float4* U;    // (u, m) of step s
-  float4* UB;         // grid-velocity adjoint of step s (accumulated)
+  const float4* PM1;  // grid (m, p) of step s+1 (P2G-adjoint)
+  const float4* UB1;  // grid-velocity adjoint of step s+1
+  const float4* PM0;  // grid of step s (G2P-adjoint)
+  float4* UB0;        // grid-velocity adjoint of step s (accumulated)
+  int* box_ub;
+  int* box_ub_reset;
+  float4* PMm;        // grid of step s-1 (recomputed P2G) or null
+  int* box_m;
+  int* box_m_reset;
+  Clears clears;
   unsigned* err;
 };
 
@@ -244,10 +274,10 @@ __device__ __forceinline__ void box_zero(const BoxInfo<D>& b, float* sm, int cap
   __syncthreads();
 }
 
-// Copy the box of a scene grid g (float4 per node) into shared memory (float4 per node,
-// box-local order), one coalesced load per node.  Synchronises on both sides.
-template <int D>
-__device__ __forceinline__ void box_load(const BoxInfo<D>& b, float4* sm4, const float4* g, int n) {
+// Fill the shared gather box (float4 per node, box-local order) with value(idx) for every
+// node idx of the box, one node per thread.  Synchronises on both sides.
+template <int D, typename Value>
+__device__ __forceinline__ void box_load(const BoxInfo<D>& b, float4* sm4, Value&& value) {
   __syncthreads();
   if (b.use_tile)
     for (int l = threadIdx.x; l < b.vol; l += blockDim.x) {
@@ -257,16 +287,16 @@ __device__ __forceinline__ void box_load(const BoxInfo<D>& b, float4* sm4, const
         idx[a] = b.lo[a] + r % b.dim[a];
         r /= b.dim[a];
       }
-      sm4[l] = __ldg(g + node_flat<D>(idx, n));
+      sm4[l] = value(idx);
     }
   __syncthreads();
 }
 
-// Run body(load) with load(i, j, k) returning the float4 of stencil node base + (i, j, k):
-// from the shared box when it holds the CTA's stencils, else from global memory.
-template <int D, typename Body>
-__device__ __forceinline__ void with_nodes(const BoxInfo<D>& b, const float4* sm4, const float4* g,
-                                           const int base[D], int n, Body&& body) {
+// Run body(load) with load(i, j, k) returning value(base + (i, j, k)): from the shared
+// gather box when it holds the CTA's stencils, else computed from global memory.
+template <int D, typename Value, typename Body>
+__device__ __forceinline__ void with_nodes(const BoxInfo<D>& b, const float4* sm4, const int base[D],
+                                           Value&& value, Body&& body) {
   if (b.use_tile) {
     int lb = base[0] - b.lo[0];
 #pragma unroll
@@ -276,10 +306,13 @@ __device__ __forceinline__ void with_nodes(const BoxInfo<D>& b, const float4* sm
     const float4* p = sm4 + lb;
     body([&](int i, int j, int k) { return p[i * s0 + j * s1 + k]; });
   } else {
-    const float4* p = g + node_flat<D>(base, n);
-    const int s1 = D == 2 ? 1 : n;
-    const int s0 = D == 2 ? n : n * n;
-    body([&](int i, int j, int k) { return __ldg(p + i * s0 + j * s1 + k); });
+    body([&](int i, int j, int k) {
+      int idx[D];
+      idx[0] = base[0] + i;
+      idx[1] = base[1] + j;
+      if (D == 3) idx[D - 1] = base[D - 1] + k;
+      return value(idx);
+    });
   }
 }
 
@@ -409,8 +442,9 @@ __device__ __forceinline__ void scatter_records(const float* xr, int count, cons
   }
 }
 
-__device__ __forceinline__ float particle_act(const SimParams& P, const int* group, const float* wact,
-                                              int scene, int64_t p, int dim, int& axis) {
+__device__ __forceinline__ float particle_act(const SimParams& P, const float* basis, const int* group,
+                                              const float* wact, int scene, int64_t p, int dim,
+                                              int& axis) {
   axis = 0;
   if (P.n_groups <= 0) return 0.0f;
   int g = group[p];
@@ -420,7 +454,7 @@ __device__ __forceinline__ float particle_act(const SimParams& P, const int* gro
   float a = 0.0f;
 #pragma unroll
   for (int k = 0; k < kMaxBasis; ++k)
-    if (k < P.n_basis) a += w[k] * P.basis[k];
+    if (k < P.n_basis) a += w[k] * basis[k];
   return a;
 }
 
@@ -435,7 +469,144 @@ __device__ __forceinline__ void load_E(const float* rows, int64_t N, int64_t p, 
 }
 
 // ---------------------------------------------------------------------------
-// forward particle pass
+// grid functions applied at gather time
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ bool is_wall(const int idx[D], const SimParams& P) {
+  bool wall = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a) wall = wall || idx[a] < P.wall || idx[a] >= P.n_grid - P.wall;
+  return wall;
+}
+
+// grid_op: v = p/m + dt g for m > 0 off the sticky walls, else 0 (w keeps m)
+template <int D>
+__device__ __forceinline__ float4 node_velocity(float4 pm, const int idx[D], const SimParams& P) {
+  float4 u = make_float4(0.0f, 0.0f, 0.0f, pm.x);
+  if (pm.x > 0.0f && !is_wall<D>(idx, P)) {
+    const float im = 1.0f / pm.x;
+    u.x = pm.y * im + P.dt * P.gravity[0];
+    u.y = pm.z * im + P.dt * P.gravity[1];
+    if (D == 3) u.z = pm.w * im + P.dt * P.gravity[2];
+  }
+  return u;
+}
+
+// grid_op.grad: pbar = ubar / m and mbar = -ubar . (p / m) / m for m > 0 off the walls
+template <int D>
+__device__ __forceinline__ float4 node_adjoint(float4 ub, float4 pm, const int idx[D],
+                                               const SimParams& P) {
+  float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (pm.x > 0.0f && !is_wall<D>(idx, P)) {
+    const float im = 1.0f / pm.x;
+    r.x = ub.x * im;
+    r.y = ub.y * im;
+    float dot = ub.x * pm.y + ub.y * pm.z;
+    if (D == 3) {
+      r.z = ub.z * im;
+      dot += ub.z * pm.w;
+    }
+    r.w = -dot * im * im;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// clears and box resets (each CTA takes its share of its own scene)
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void run_clears(const Clears& C, int scene, int rank, int nranks,
+                                           int nnodes, int n) {
+  for (int c = 0; c < C.n; ++c) {
+    const int* bb = C.job[c].box + scene * 8;
+    int lo[D], ext[D], vol = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      lo[a] = bb[a];
+      ext[a] = bb[4 + a] - bb[a] + 1;
+      vol = ext[a] > 0 ? vol * ext[a] : 0;
+    }
+    float4* g = C.job[c].grid + (int64_t)scene * nnodes;
+    for (int l = rank * blockDim.x + threadIdx.x; l < vol; l += nranks * blockDim.x) {
+      int idx[D], r = l;
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+        idx[a] = lo[a] + r % ext[a];
+        r /= ext[a];
+      }
+      g[node_flat<D>(idx, n)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  }
+}
+
+__device__ __forceinline__ void reset_box(int* box, int scene) {
+  if (box && threadIdx.x < 8) box[scene * 8 + threadIdx.x] = (threadIdx.x & 4) ? INT_MIN : INT_MAX;
+}
+
+// ---------------------------------------------------------------------------
+// P2G of the CTA's particles: stress, affine matrix A = kappa tau + m C, scatter
+// (m, m v + A dpos) into the scene grid g, fold the touched box into box_scene.
+// Every thread calls it; s_bbox must have been reset before an earlier barrier.
+// ---------------------------------------------------------------------------
+template <int D, int MAT>
+__device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis, bool active, int scene,
+                                         int64_t p, int count, const float x[D], const float v[D],
+                                         const float C[D][D], const float E[D][D], const float* mu,
+                                         const float* la, const int* group, const float* wact,
+                                         float4* g, int* box_scene, float* sm, float* xr,
+                                         int* s_box, int* s_bbox, unsigned& err) {
+  Axes<D> s;
+  bool ok = make_axes<D>(x, P, s) && active;
+  if (active && !ok) err |= kErrOOB;
+  float Am[D][D], mv[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    mv[i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) Am[i][j] = 0.0f;
+  }
+  if (ok) {
+    int axis;
+    const float act = particle_act(P, basis, group, wact, scene, p, D, axis);
+    float tau[D][D];
+    StressCache<D> sc;
+    if (!kirchhoff<D, MAT>(E, mu[p], la[p], act, axis, tau, sc)) {
+      err |= kErrNonFinite;
+      ok = false;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      mv[i] = P.p_mass * v[i];
+#pragma unroll
+      for (int j = 0; j < D; ++j) Am[i][j] = P.kappa * tau[i][j] + P.p_mass * C[i][j];
+    }
+  }
+  __syncthreads();  // the record area may still be read by an earlier scatter
+  put_record<D>(xr, ok, s.base, s.f, mv, Am);
+  if (P.tile_capacity > 0) {
+    const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
+    box_zero<D>(bx, sm, P.tile_capacity);
+    scatter_records<D, true>(xr, count, bx, sm, P.tile_capacity, g, P.n_grid, P, P.p_mass);
+    box_flush<D>(bx, sm, P.tile_capacity, g, P.n_grid);
+    if (threadIdx.x == 0 && bx.vol > 0) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        atomicMin(&box_scene[a], bx.lo[a]);
+        atomicMax(&box_scene[4 + a], bx.lo[a] + bx.dim[a] - 1);
+      }
+    }
+  } else {
+    warp_bbox<D>(ok, s.base, s_bbox);
+    __syncthreads();
+    cta_bbox_flush<D>(s_bbox, box_scene);
+    BoxInfo<D> none;
+    none.use_tile = false;
+    scatter_records<D, true>(xr, count, none, sm, 0, g, P.n_grid, P, P.p_mass);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forward particle pass: [G2P of step t-1] then [P2G of step t]
 // ---------------------------------------------------------------------------
 template <int D, int MAT, int MODE>
 __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P, StepArgs A) {
@@ -452,6 +623,9 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
   const int64_t N = A.N;
   const int n = P.n_grid;
   unsigned err = 0;
+  run_clears<D>(A.clears, scene, tile.w, A.scene_tiles[scene], P.nnodes, n);
+  if (tile.w == 0) reset_box(A.box_reset, scene);
+  __syncthreads();  // s_bbox reset
 
   float x[D], v[D], C[D][D], E[D][D];
   if (MODE == kP2GOnly) {
@@ -465,7 +639,7 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
     load_E<D>(A.in, N, p, P.f_diag, E);
   } else {
     // ---- G2P: v' = sum W u, C' = 4/dx^2 sum W (u - u_c) dpos^T, x' = x + dt v',
-    //      E' = E + dt C' (I + E)
+    //      E' = E + dt C' (I + E), with u = grid_op(PM of step t-1) at each node
     float xo[D], Eo[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a) xo[a] = A.in[(R::X + a) * N + p];
@@ -480,17 +654,18 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
 #pragma unroll
       for (int b = 0; b < D; ++b) B[a][b] = 0.0f;
     }
-    const float4* Ug = A.U + (int64_t)scene * P.nnodes;
+    const float4* PMg = A.PMr + (int64_t)scene * P.nnodes;
+    auto velocity = [&](const int idx[D]) { return node_velocity<D>(__ldg(PMg + node_flat<D>(idx, n)), idx, P); };
     BoxInfo<D> gbx;
     gbx.use_tile = false;
     if (P.gather_capacity > 0) {
       gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);
-      box_load<D>(gbx, reinterpret_cast<float4*>(sm), Ug, n);
+      box_load<D>(gbx, reinterpret_cast<float4*>(sm), velocity);
     }
     if (ok) {
       // centred on the stencil's centre node: equal because sum W dpos = 0, and
       // accurate in FP32 when u is nearly uniform over the stencil
-      with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), Ug, s.base, n, [&](auto load) {
+      with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), s.base, velocity, [&](auto load) {
         const float4 uc4 = load(1, 1, D == 3 ? 1 : 0);
         const float uc[3] = {uc4.x, uc4.y, uc4.z};
         for_nodes<D>(s.w, [&](int i, int j, int k, float W) {
@@ -538,72 +713,28 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
     }
   }
 
-  if (MODE != kG2POnlyFull) {
-    // ---- P2G: stress, affine matrix A = kappa tau + m C; scatter (m, m v + A dpos) ----
-    Axes<D> s;
-    bool ok = make_axes<D>(x, P, s) && active;
-    if (active && !ok) err |= kErrOOB;
-    float Am[D][D], mv[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      mv[i] = 0.0f;
-#pragma unroll
-      for (int j = 0; j < D; ++j) Am[i][j] = 0.0f;
-    }
-    if (ok) {
-      int axis;
-      const float act = particle_act(P, A.group, A.wact, scene, p, D, axis);
-      float tau[D][D];
-      StressCache<D> sc;
-      if (!kirchhoff<D, MAT>(E, A.mu[p], A.la[p], act, axis, tau, sc)) {
-        err |= kErrNonFinite;
-        ok = false;
-      }
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        mv[i] = P.p_mass * v[i];
-#pragma unroll
-        for (int j = 0; j < D; ++j) Am[i][j] = P.kappa * tau[i][j] + P.p_mass * C[i][j];
-      }
-    }
-    float4* PMs = A.PM + (int64_t)scene * P.nnodes;
-    if (P.tile_capacity > 0) {
-      put_record<D>(xr, ok, s.base, s.f, mv, Am);
-      const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
-      box_zero<D>(bx, sm, P.tile_capacity);
-      scatter_records<D, true>(xr, tile.z, bx, sm, P.tile_capacity, PMs, n, P, P.p_mass);
-      box_flush<D>(bx, sm, P.tile_capacity, PMs, n);
-      if (threadIdx.x == 0 && bx.vol > 0) {
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          atomicMin(&A.bbox[scene * 8 + a], bx.lo[a]);
-          atomicMax(&A.bbox[scene * 8 + 4 + a], bx.lo[a] + bx.dim[a] - 1);
-        }
-      }
-    } else {
-      // float4 reductions straight to the grid, in the interleaved lane order
-      if (MODE == kP2GOnly || P.gather_capacity <= 0) __syncthreads();  // s_bbox reset visible
-      put_record<D>(xr, ok, s.base, s.f, mv, Am);
-      warp_bbox<D>(ok, s.base, s_bbox);
-      __syncthreads();
-      cta_bbox_flush<D>(s_bbox, A.bbox + scene * 8);
-      BoxInfo<D> none;
-      none.use_tile = false;
-      scatter_records<D, true>(xr, tile.z, none, sm, 0, PMs, n, P, P.p_mass);
-    }
-  }
+  if (MODE != kG2POnlyFull)
+    p2g_pass<D, MAT>(P, P.basis, active, scene, p, tile.z, x, v, C, E, A.mu, A.la, A.group, A.wact,
+                     A.PMw + (int64_t)scene * P.nnodes, A.box_w + scene * 8, sm, xr, s_box, s_bbox,
+                     err);
   if (err) atomicOr(A.err, err);
 }
 
 // ---------------------------------------------------------------------------
-// adjoint particle pass
+// adjoint particle pass: [P2G-adjoint of step s+1] [G2P-adjoint of step s]
+// [recomputed P2G of step s-1, the grid the next adjoint pass needs (Appendix D.1)]
 // ---------------------------------------------------------------------------
 template <int D, int MAT, int MODE>
 __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs A) {
   using R = Rows<D>;
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8];
+  __shared__ int s_bbox_ub[8];
+  __shared__ int s_bbox_pm[8];
   __shared__ float s_wbar[kMaxGroups * kMaxBasis];
+  cta_bbox_reset(s_bbox_ub);
+  cta_bbox_reset(s_bbox_pm);
+  if (threadIdx.x < kMaxGroups * kMaxBasis) s_wbar[threadIdx.x] = 0.0f;
   float* xr = sm + box_floats(P.tile_capacity, P.gather_capacity);
   const int4 tile = A.tiles[blockIdx.x];
   const int scene = tile.x;
@@ -613,6 +744,12 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
   const int n = P.n_grid;
   const float c4 = 4.0f * P.inv_dx * P.inv_dx;
   unsigned err = 0;
+  run_clears<D>(A.clears, scene, tile.w, A.scene_tiles[scene], P.nnodes, n);
+  if (tile.w == 0) {
+    reset_box(A.box_ub_reset, scene);
+    reset_box(A.box_m_reset, scene);
+  }
+  __syncthreads();  // shared boxes and s_wbar reset
 
   // adjoint of state s+1: xb, vb, Cb, Fb (Fb = dL/dE = dL/dF)
   float xb[D], vb[D], Cb[D][D], Fb[D][D];
@@ -633,8 +770,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
 #pragma unroll
     for (int i = 0; i < D * D; ++i) Cb[i / D][i % D] = A.adj[(R::C + i) * N + p];
   } else {
-    // ---- P2G adjoint of step s+1: gather (pbar, mbar) ----
-    if (threadIdx.x < kMaxGroups * kMaxBasis) s_wbar[threadIdx.x] = 0.0f;
+    // ---- P2G adjoint of step s+1: gather (pbar, mbar) = grid_op.grad(ubar, (m, p)) ----
     float x[D], v[D], E[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -646,7 +782,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     bool ok = make_axes<D>(x, P, s) && active;
     if (active && !ok) err |= kErrOOB;
     int axis;
-    const float act = particle_act(P, A.group, A.wact, scene, p, D, axis);
+    const float act = particle_act(P, P.basis, A.group, A.wact, scene, p, D, axis);
     const float mu = A.mu[p], la = A.la[p];
     float tau[D][D];
     StressCache<D> sc;
@@ -670,14 +806,19 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
 #pragma unroll
       for (int b = 0; b < D; ++b) Ab[a][b] = 0.0f;
     }
-    const float4* PBMs = A.PBM + (int64_t)scene * P.nnodes;
+    const float4* UBg = A.UB1 + (int64_t)scene * P.nnodes;
+    const float4* PMg = A.PM1 + (int64_t)scene * P.nnodes;
+    auto pbar = [&](const int idx[D]) {
+      const int f = node_flat<D>(idx, n);
+      return node_adjoint<D>(__ldg(UBg + f), __ldg(PMg + f), idx, P);
+    };
     BoxInfo<D> gbx;
     gbx.use_tile = false;
     if (P.gather_capacity > 0) {
       gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);
-      box_load<D>(gbx, reinterpret_cast<float4*>(sm), PBMs, n);
+      box_load<D>(gbx, reinterpret_cast<float4*>(sm), pbar);
     }
-    if (ok) with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), PBMs, s.base, n, [&](auto load) {
+    if (ok) with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), s.base, pbar, [&](auto load) {
       // pbar - pbar_c and mbar - mbar_c (centre node) in the moment and weight-gradient
       // terms: equal to the plain sums because sum W dpos = 0, sum grad W = 0 and
       // sum grad W dpos^T = I, without the FP32 cancellation of a smooth pbar field
@@ -751,7 +892,6 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
       A.labar[p] += lab;
     }
     if (P.n_groups > 0) {
-      __syncthreads();  // s_wbar zeroed
       if (ok) {
         int g = A.group[p];
         if (g >= 0 && g < P.n_groups) {
@@ -812,16 +952,16 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     Axes<D> s;
     const bool ok = make_axes<D>(x0, P, s) && active;
     if (active && !ok) err |= kErrOOB;
-    const float4* Ug = A.U + (int64_t)scene * P.nnodes;
-    // one extent serves the gather box and the scatter box (same stencils)
+    const float4* PMg = A.PM0 + (int64_t)scene * P.nnodes;
+    auto velocity = [&](const int idx[D]) { return node_velocity<D>(__ldg(PMg + node_flat<D>(idx, n)), idx, P); };
     const int cap_box = P.tile_capacity > P.gather_capacity ? P.tile_capacity : P.gather_capacity;
     BoxInfo<D> bx;
     bx.use_tile = false;
     if (cap_box > 0) bx = box_extent<D>(ok, s.base, cap_box, s_box);
     BoxInfo<D> gbx = bx;
     gbx.use_tile = bx.use_tile && P.gather_capacity > 0 && bx.vol <= P.gather_capacity;
-    if (P.gather_capacity > 0) box_load<D>(gbx, reinterpret_cast<float4*>(sm), Ug, n);
-    if (ok) with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), Ug, s.base, n, [&](auto load) {
+    if (P.gather_capacity > 0) box_load<D>(gbx, reinterpret_cast<float4*>(sm), velocity);
+    if (ok) with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), s.base, velocity, [&](auto load) {
       // x-adjoint terms on u - u_c (centre node), by the same B-spline identities
       const float4 uc4 = load(1, 1, D == 3 ? 1 : 0);
       const float uc[3] = {uc4.x, uc4.y, uc4.z};
@@ -883,133 +1023,53 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) Bs[i][j] = c4 * Ct[i][j];
-    float4* UBs = A.UB + (int64_t)scene * P.nnodes;
-    BoxInfo<D> sbx = bx;
-    sbx.use_tile = bx.use_tile && P.tile_capacity > 0 && bx.vol <= P.tile_capacity;
+    float4* UBs = A.UB0 + (int64_t)scene * P.nnodes;
     put_record<D>(xr, ok, s.base, s.f, vt, Bs);
     if (P.tile_capacity > 0) {
+      BoxInfo<D> sbx = bx;
+      sbx.use_tile = bx.use_tile && bx.vol <= P.tile_capacity;
       box_zero<D>(sbx, sm, P.tile_capacity);  // same extent as the gather box
+      scatter_records<D, false>(xr, tile.z, sbx, sm, P.tile_capacity, UBs, n, P, 0.0f);
+      box_flush<D>(sbx, sm, P.tile_capacity, UBs, n);
+      if (threadIdx.x == 0 && sbx.vol > 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          atomicMin(&A.box_ub[scene * 8 + a], sbx.lo[a]);
+          atomicMax(&A.box_ub[scene * 8 + 4 + a], sbx.lo[a] + sbx.dim[a] - 1);
+        }
+      }
     } else {
+      warp_bbox<D>(ok, s.base, s_bbox_ub);
       __syncthreads();
+      cta_bbox_flush<D>(s_bbox_ub, A.box_ub + scene * 8);
+      BoxInfo<D> none;
+      none.use_tile = false;
+      scatter_records<D, false>(xr, tile.z, none, sm, 0, UBs, n, P, 0.0f);
     }
-    scatter_records<D, false>(xr, tile.z, sbx, sm, P.tile_capacity, UBs, n, P, 0.0f);
-    if (P.tile_capacity > 0) box_flush<D>(sbx, sm, P.tile_capacity, UBs, n);
+  }
+
+  // ---- recomputed P2G of step s-1 (the grid of the next adjoint pass) ----
+  if (A.stm) {
+    float x[D], v[D], C[D][D], E[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      x[a] = A.stm[(R::X + a) * N + p];
+      v[a] = A.stm[(R::V + a) * N + p];
+    }
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) C[i / D][i % D] = A.stm[(R::C + i) * N + p];
+    load_E<D>(A.stm, N, p, P.f_diag, E);
+    p2g_pass<D, MAT>(P, P.basis2, active, scene, p, tile.z, x, v, C, E, A.mu, A.la, A.group, A.wact,
+                     A.PMm + (int64_t)scene * P.nnodes, A.box_m + scene * 8, sm, xr, s_box, s_bbox_pm,
+                     err);
   }
   if (err) atomicOr(A.err, err);
 }
 
-// ---------------------------------------------------------------------------
-// node passes over each scene's touched box (blockIdx.y = scene)
-// ---------------------------------------------------------------------------
+// Zero the dirty boxes of the clear jobs (end of a launch sequence); blockIdx.y = scene.
 template <int D>
-__device__ __forceinline__ void box_node(const int* bb, int l, int idx[D]) {
-  int r = l;
-#pragma unroll
-  for (int a = D - 1; a >= 0; --a) {
-    int ext = bb[4 + a] - bb[a] + 1;
-    idx[a] = bb[a] + r % ext;
-    r /= ext;
-  }
-}
-
-template <int D>
-__device__ __forceinline__ int box_volume(const int* bb) {
-  int vol = 1;
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if (bb[4 + a] < bb[a]) return 0;  // reset box (lo = INT_MAX, hi = INT_MIN)
-    vol *= bb[4 + a] - bb[a] + 1;
-  }
-  return vol;
-}
-
-// grid_op: u = p/m + dt g for m > 0 off the walls, else 0; store (u, m); clear PM.
-// The last CTA to finish copies the box to bbox_u (used by the grid adjoint of this
-// step) and resets the accumulation box for the next P2G.
-template <int D>
-__global__ void grid_update_kernel(SimParams P, float4* PM, float4* U, int* bbox, int* bbox_u,
-                                   unsigned* done) {
-  __shared__ int bb[8];
-  __shared__ bool last;
-  const int scene = blockIdx.y;
-  if (threadIdx.x < 8) bb[threadIdx.x] = bbox[scene * 8 + threadIdx.x];
-  __syncthreads();
-  const int vol = box_volume<D>(bb);
-  const int64_t soff = (int64_t)scene * P.nnodes;
-  const int n = P.n_grid;
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < vol; l += gridDim.x * blockDim.x) {
-    int idx[D];
-    box_node<D>(bb, l, idx);
-    const int64_t g = soff + node_flat<D>(idx, n);
-    float4 pm = PM[g];
-    bool wall = false;
-#pragma unroll
-    for (int a = 0; a < D; ++a) wall = wall || idx[a] < P.wall || idx[a] >= n - P.wall;
-    float4 u = make_float4(0.0f, 0.0f, 0.0f, pm.x);
-    if (pm.x > 0.0f && !wall) {
-      float im = 1.0f / pm.x;
-      u.x = pm.y * im + P.dt * P.gravity[0];
-      u.y = pm.z * im + P.dt * P.gravity[1];
-      if (D == 3) u.z = pm.w * im + P.dt * P.gravity[2];
-    }
-    U[g] = u;
-    PM[g] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  }
-  // last-CTA hand-off of the box (threadfence-reduction pattern)
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned total = gridDim.x * gridDim.y;
-    last = atomicAdd(done, 1u) == total - 1;
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    for (int i = threadIdx.x; i < (int)gridDim.y * 8; i += blockDim.x) {
-      int v = bbox[i];
-      bbox_u[i] = v;
-      bbox[i] = (i % 8) < 4 ? INT_MAX : INT_MIN;
-    }
-    if (threadIdx.x == 0) *done = 0u;
-  }
-}
-
-// grid_op.grad: pbar = ubar / m, mbar = -ubar . (u - dt g) / m on non-wall nodes with
-// m > 0, else 0; clear the accumulated ubar.
-template <int D>
-__global__ void grid_adjoint_kernel(SimParams P, float4* UB, const float4* U, float4* PBM,
-                                    const int* bbox_u) {
-  __shared__ int bb[8];
-  const int scene = blockIdx.y;
-  if (threadIdx.x < 8) bb[threadIdx.x] = bbox_u[scene * 8 + threadIdx.x];
-  __syncthreads();
-  const int vol = box_volume<D>(bb);
-  const int64_t soff = (int64_t)scene * P.nnodes;
-  const int n = P.n_grid;
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < vol; l += gridDim.x * blockDim.x) {
-    int idx[D];
-    box_node<D>(bb, l, idx);
-    const int64_t g = soff + node_flat<D>(idx, n);
-    float4 ub = UB[g];
-    float4 u = U[g];
-    bool wall = false;
-#pragma unroll
-    for (int a = 0; a < D; ++a) wall = wall || idx[a] < P.wall || idx[a] >= n - P.wall;
-    float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (u.w > 0.0f && !wall) {
-      float im = 1.0f / u.w;
-      r.x = ub.x * im;
-      r.y = ub.y * im;
-      float dot = ub.x * (u.x - P.dt * P.gravity[0]) + ub.y * (u.y - P.dt * P.gravity[1]);
-      if (D == 3) {
-        r.z = ub.z * im;
-        dot += ub.z * (u.z - P.dt * P.gravity[2]);
-      }
-      r.w = -dot * im;
-    }
-    PBM[g] = r;
-    UB[g] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  }
+__global__ void clear_kernel(Clears C, int nnodes, int n) {
+  run_clears<D>(C, blockIdx.y, blockIdx.x, gridDim.x, nnodes, n);
 }
 
 }  // namespace mpm

@@ -8,9 +8,11 @@
 // file-scope array below, which every GPU that loads the library holds until the
 // process exits.
 //
-// The step runs the library's own kernels (P2G from the full input state, the grid
-// update, G2P writing the full output state) with pointers into that array, so its
-// results equal those of mpm_forward with T = 1 up to FP32 atomic-order rounding.
+// The step runs the library's own kernels (P2G from the full input state, then G2P
+// writing the full output state, grid_op applied as it gathers) with pointers into that
+// array, so its results equal those of mpm_forward with T = 1 up to FP32 atomic-order
+// rounding.
+#include <climits>
 #include <cstring>
 #include <mutex>
 
@@ -28,11 +30,10 @@ constexpr int64_t kMaxTiles = (kMaxParticles + kTile - 1) / kTile;
 
 // byte offsets inside the scratch array (each 256-byte aligned)
 constexpr size_t kOffPM = 0;                                    // float4 (m, p) per node
-constexpr size_t kOffU = kOffPM + (size_t)kMaxNodes * 16;      // float4 (u, m) per node
-constexpr size_t kOffMu = kOffU + (size_t)kMaxNodes * 16;      // float per particle
+constexpr size_t kOffMu = kOffPM + (size_t)kMaxNodes * 16;     // float per particle
 constexpr size_t kOffLa = kOffMu + (size_t)kMaxParticles * 4;  // float per particle
 constexpr size_t kOffTiles = kOffLa + (size_t)kMaxParticles * 4;
-constexpr size_t kOffMisc = kOffTiles + (size_t)kMaxTiles * 16;  // bbox[8], bbox_u[8], done, err
+constexpr size_t kOffMisc = kOffTiles + (size_t)kMaxTiles * 16;  // box[8], tile count, err
 constexpr size_t kScratchBytes = kOffMisc + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -42,7 +43,7 @@ std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 __global__ void noalloc_prepare_kernel(int64_t N, const float* E, const float* nu, float* mu,
-                                       float* la, int4* tiles) {
+                                       float* la, int4* tiles, int* n_tiles, int* box) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     float e = E[i], v = nu[i];
@@ -50,8 +51,12 @@ __global__ void noalloc_prepare_kernel(int64_t N, const float* E, const float* n
     la[i] = e * v / ((1.0f + v) * (1.0f - 2.0f * v));
     if (i % kTile == 0) {
       int64_t cnt = N - i < kTile ? N - i : kTile;
-      tiles[i / kTile] = make_int4(0, (int)i, (int)cnt, 0);
+      tiles[i / kTile] = make_int4(0, (int)i, (int)cnt, (int)(i / kTile));
     }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 8) {
+    box[threadIdx.x] = (threadIdx.x & 4) ? INT_MIN : INT_MAX;
+    if (threadIdx.x == 0) *n_tiles = (int)((N + kTile - 1) / kTile);
   }
 }
 
@@ -106,22 +111,21 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float4* PM = reinterpret_cast<float4*>(base + kOffPM);
-  float4* U = reinterpret_cast<float4*>(base + kOffU);
   float* mu = reinterpret_cast<float*>(base + kOffMu);
   float* la = reinterpret_cast<float*>(base + kOffLa);
   int4* tiles = reinterpret_cast<int4*>(base + kOffTiles);
-  int* bbox = reinterpret_cast<int*>(base + kOffMisc);
-  int* bbox_u = bbox + 8;
-  unsigned* done = reinterpret_cast<unsigned*>(bbox + 16);
-  unsigned* err = device_err ? reinterpret_cast<unsigned*>(device_err) : done + 1;
+  int* box = reinterpret_cast<int*>(base + kOffMisc);
+  int* n_tiles_dev = box + 8;
+  unsigned* err = device_err ? reinterpret_cast<unsigned*>(device_err)
+                             : reinterpret_cast<unsigned*>(box + 9);
 
-  // the array keeps the previous call's contents: clear what must start at zero
+  // the array keeps the previous call's contents: clear what must start at zero (the
+  // mass/momentum grid; the prepare kernel rewrites the box, tiles and Lame parameters)
   cudaError_t e = cudaMemsetAsync(PM, 0, (size_t)nnodes * sizeof(float4), s);
   if (e == cudaSuccess && !device_err) e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) e = launch_reset_boxes(bbox, bbox_u, done, 1, s);
   if (e == cudaSuccess) {
     int blocks = (int)((N + 255) / 256);
-    noalloc_prepare_kernel<<<blocks, 256, 0, s>>>(N, E, nu, mu, la, tiles);
+    noalloc_prepare_kernel<<<blocks, 256, 0, s>>>(N, E, nu, mu, la, tiles, n_tiles_dev, box);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return reject(MPM_ERR_CUDA, cudaGetErrorString(e));
@@ -143,28 +147,28 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
   P.f_diag = 1.0f;  // the caller's state rows hold F itself
 
   StepArgs A;
+  memset(&A, 0, sizeof(A));
   A.tiles = tiles;
+  A.scene_tiles = n_tiles_dev;
   A.N = (int)N;
   A.in = state_in;
   A.out = state_out;
   A.mu = mu;
   A.la = la;
-  A.group = nullptr;
-  A.wact = nullptr;
-  A.U = U;
-  A.PM = PM;
-  A.bbox = bbox;
+  A.PMw = PM;  // P2G pass
+  A.box_w = box;
   A.err = err;
   const int n_tiles = (int)((N + kTile - 1) / kTile);
-  const int bps = 256;
+  StepArgs G = A;  // G2P pass reads the same grid
+  G.PMr = PM;
+  G.PMw = nullptr;
+  G.box_w = nullptr;
   if (d->dim == 2) {
     e = launch_step<2>(d->material, kP2GOnly, P, A, n_tiles, s);
-    if (e == cudaSuccess) e = launch_grid_update<2>(P, PM, U, bbox, bbox_u, done, 1, bps, s);
-    if (e == cudaSuccess) e = launch_step<2>(d->material, kG2POnlyFull, P, A, n_tiles, s);
+    if (e == cudaSuccess) e = launch_step<2>(d->material, kG2POnlyFull, P, G, n_tiles, s);
   } else {
     e = launch_step<3>(d->material, kP2GOnly, P, A, n_tiles, s);
-    if (e == cudaSuccess) e = launch_grid_update<3>(P, PM, U, bbox, bbox_u, done, 1, bps, s);
-    if (e == cudaSuccess) e = launch_step<3>(d->material, kG2POnlyFull, P, A, n_tiles, s);
+    if (e == cudaSuccess) e = launch_step<3>(d->material, kG2POnlyFull, P, G, n_tiles, s);
   }
   if (e != cudaSuccess) return reject(MPM_ERR_CUDA, cudaGetErrorString(e));
   return MPM_OK;

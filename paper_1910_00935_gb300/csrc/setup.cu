@@ -87,12 +87,10 @@ __global__ void gather_initial_kernel(int dim, int64_t N, const int* perm, const
   }
 }
 
-__global__ void reset_boxes_kernel(int* bbox, int* bbox_u, unsigned* done, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * 8; i += gridDim.x * blockDim.x) {
-    bbox[i] = (i % 8) < 4 ? INT_MAX : INT_MIN;
-    bbox_u[i] = (i % 8) < 4 ? INT_MAX : INT_MIN;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0u;
+__global__ void reset_boxes_kernel(int* boxes, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * 8;
+       i += (int64_t)gridDim.x * blockDim.x)
+    boxes[i] = (i % 8) < 4 ? INT_MAX : INT_MIN;
 }
 
 __global__ void gather_rows_kernel(int rows, int64_t N, const int* perm, const float* src,
@@ -228,9 +226,8 @@ cudaError_t launch_gather_initial(int dim, int64_t N, const int* perm, const flo
   return cudaGetLastError();
 }
 
-cudaError_t launch_reset_boxes(int* bbox, int* bbox_u, unsigned* done, int n_scenes,
-                               cudaStream_t s) {
-  reset_boxes_kernel<<<grid_for(n_scenes * 8), 256, 0, s>>>(bbox, bbox_u, done, n_scenes);
+cudaError_t launch_reset_boxes(int* boxes, int64_t n_boxes, cudaStream_t s) {
+  reset_boxes_kernel<<<grid_for(n_boxes * 8), 256, 0, s>>>(boxes, n_boxes);
   return cudaGetLastError();
 }
 
