@@ -74,6 +74,9 @@ extern "C" {
 
 #define MPM_OPT_GATHER_CAPACITY 5 /* max nodes of a CTA's shared gather box; 0 = gathers
                                      read the grid through L1 [1024] */
+#define MPM_OPT_POLAR_CACHE 7     /* 3D fixed-corotated: the re-simulation stores each state's
+                                     FP64 polar factor for the two backward passes that need it
+                                     instead of recomputing it [1] */
 #define MPM_OPT_GRID_BLOCKS 6     /* CTAs per scene of the end-of-sequence grid clear; 0 = automatic [0] */
 
 /* kernel categories for mpm_get_profile */

@@ -46,6 +46,7 @@ struct Layout {
   size_t tiles, scene_off, scene_tiles;
   size_t mu, la, E, nu, group, wact, wbar, mubar, labar;
   size_t fin, cur, ckpt, seg, adj;
+  size_t rcache;  // (K+1) x [9][N] FP64 polar factors of a re-simulated segment (3D FCR)
   size_t grids;  // kPMSlots + kUBSlots dense grids
   size_t boxes;  // (kPMSlots + kUBSlots) x 2 parities x [scene][8]
   size_t err, com;
@@ -55,6 +56,7 @@ struct Layout {
 struct Dims {
   int D, Q, S, K, n_ckpt, n_tiles, n_grid;
   int64_t N, nnodes;
+  bool polar_cache;  // 3D fixed-corotated: FP64 polar factors are cached per segment
 };
 
 bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
@@ -97,6 +99,7 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
   m.K = d->ckpt_every < max_steps ? d->ckpt_every : max_steps;
   m.n_ckpt = (max_steps - 1) / m.K + 1;  // states 0, K, 2K, ... < max_steps
   m.n_grid = d->n_grid;
+  m.polar_cache = d->dim == 3 && d->material == MPM_FIXED_COROTATED;
   m.nnodes = 1;
   for (int a = 0; a < m.D; ++a) m.nnodes *= d->n_grid;
   m.N = 0;
@@ -140,6 +143,7 @@ Layout make_layout(const Dims& m) {
   L.ckpt = take((size_t)m.n_ckpt * Q * N * 4);
   L.seg = take((size_t)(m.K + 1) * Q * N * 4);
   L.adj = take(Q * N * 4);
+  L.rcache = m.polar_cache ? take((size_t)(m.K + 1) * 9 * N * 8) : take(0);
   const size_t grid = S * (size_t)m.nnodes * sizeof(float4);
   L.grids = take(grid * (kPMSlots + kUBSlots));
   L.boxes = take((size_t)(kPMSlots + kUBSlots) * 2 * S * 8 * 4);
@@ -166,7 +170,8 @@ struct mpm_handle {
   bool smem_tile = false;  // measured on GB300: global float4 reductions beat shared FP32 atomics
   int tile_capacity = 1024;
   int gather_capacity = 1024;
-  int grid_blocks = 0;  // CTAs per scene of the node passes (0 = automatic)
+  int grid_blocks = 0;  // CTAs per scene of the end-of-sequence grid clear (0 = automatic)
+  bool use_polar_cache = true;
   // graphs
   cudaStream_t cap_stream = nullptr;
   std::map<int64_t, std::pair<cudaGraphExec_t, int64_t>> graphs;  // key -> (exec, launches)
@@ -191,6 +196,9 @@ struct mpm_handle {
   }
   float* state(size_t base, int slot) const {
     return at<float>(base) + (size_t)slot * m.Q * m.N;
+  }
+  double* rslot(int slot) const {
+    return m.polar_cache && use_polar_cache ? at<double>(L.rcache) + (size_t)slot * 9 * m.N : nullptr;
   }
 };
 
@@ -344,7 +352,8 @@ struct Launcher {
 
   // one forward particle pass: G2P of step t-1 from grid `read` (-1: none), P2G of step
   // t into a new grid (returned in *written, -1 for G2P only)
-  cudaError_t step(int mode, int t, const float* in, float* out, int read, int* written) {
+  cudaError_t step(int mode, int t, const float* in, float* out, int read, int* written,
+                   double* R_out = nullptr) {
     const Dims& m = h->m;
     SimParams P = params_for(h, t);
     StepArgs A;
@@ -360,6 +369,7 @@ struct Launcher {
     A.wact = h->at<float>(h->L.wact);
     A.err = h->at<unsigned>(h->L.err);
     if (read >= 0) A.PMr = ring_grid(h, h->pm, read);
+    A.Rw = R_out;
     if (written) {
       WriteSlot w;
       if (!ring_alloc(h, h->pm, w)) return cudaErrorMemoryAllocation;
@@ -385,7 +395,8 @@ struct Launcher {
   // mode), pm0: grid of step s; writes the velocity adjoint of step s (*ub_written) and,
   // when stm != null, the recomputed grid of step s-1 (*pm_written)
   cudaError_t adjoint(int mode, int s_step, const float* st1, const float* st0, const float* stm,
-                      int pm1, int ub1, int pm0, int* ub_written, int* pm_written) {
+                      int pm1, int ub1, int pm0, int* ub_written, int* pm_written,
+                      const double* R1 = nullptr, const double* Rm = nullptr) {
     const Dims& m = h->m;
     SimParams P = params_for(h, s_step + 1);
     SimParams P2 = params_for(h, s_step - 1 >= 0 ? s_step - 1 : 0);
@@ -407,6 +418,8 @@ struct Launcher {
     A.wact = h->at<float>(h->L.wact);
     A.wbar = h->at<float>(h->L.wbar);
     A.err = h->at<unsigned>(h->L.err);
+    A.R1 = R1;
+    A.Rm = Rm;
     if (pm1 >= 0) A.PM1 = ring_grid(h, h->pm, pm1);
     if (ub1 >= 0) A.UB1 = ring_grid(h, h->ub, ub1);
     if (pm0 >= 0) A.PM0 = ring_grid(h, h->pm, pm0);
@@ -507,12 +520,12 @@ int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
 int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top, int* grid_top_minus_1) {
   const float* ck = h->state(h->L.ckpt, s0 / h->m.K);
   int g = -1;
-  LK(Lc.step(kP2GOnly, s0, ck, nullptr, -1, &g));
+  LK(Lc.step(kP2GOnly, s0, ck, nullptr, -1, &g, h->rslot(0)));
   const float* prev = ck;
   for (int t = s0 + 1; t < top; ++t) {
     float* dst = h->state(h->L.seg, t - s0);
     int g_next = -1;
-    LK(Lc.step(kG2PP2GFull, t, prev, dst, g, &g_next));
+    LK(Lc.step(kG2PP2GFull, t, prev, dst, g, &g_next, h->rslot(t - s0)));
     ring_release(h->pm, g);
     g = g_next;
     prev = dst;
@@ -541,8 +554,12 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T) {
                                                           : h->state(h->L.seg, s - 1 - s0))
                                         : nullptr;
     int ub_s = -1, pm_sm = -1;
+    // cached polar factors: state s+1 only inside this segment (the segment's top state
+    // was never the P2G input of this re-simulation), state s-1 always when present
+    const double* R1 = (s + 1 < top) ? h->rslot(s + 1 - s0) : nullptr;
+    const double* Rm = (s - 1 >= s0) ? h->rslot(s - 1 - s0) : nullptr;
     LK(Lc.adjoint(s == T - 1 ? kAdjG2P : kAdjFused, s, st_s1, st_s, st_sm,
-                  s == T - 1 ? -1 : pm_s1, s == T - 1 ? -1 : ub_s1, pm_s, &ub_s, &pm_sm));
+                  s == T - 1 ? -1 : pm_s1, s == T - 1 ? -1 : ub_s1, pm_s, &ub_s, &pm_sm, R1, Rm));
     ring_release(h->pm, pm_s1);
     ring_release(h->ub, ub_s1);
     pm_s1 = pm_s;
@@ -839,6 +856,7 @@ int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
       if (value < 0 || value > 65535) return fail(h, MPM_ERR_ARG, "grid blocks must be in [0, 65535]");
       h->grid_blocks = (int)value;
       break;
+    case MPM_OPT_POLAR_CACHE: h->use_polar_cache = value != 0; break;
     case MPM_OPT_PROFILE:
       h->profile = value != 0;
       h->ev_records.clear();

@@ -239,6 +239,30 @@ __device__ __forceinline__ bool polar_f64(const float E[D][D], Polar<D>& p) {
   }
 }
 
+// The polar factor of F = I + E from a cached FP64 R ([9][N] rows, row-major per particle):
+// F - R is formed in FP64 as in polar_f64.
+template <int D>
+__device__ __forceinline__ void polar_from_cache(const double* Rc, int64_t N, int64_t p,
+                                                 const float E[D][D], Polar<D>& pol) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const double r = Rc[(int64_t)(i * D + j) * N + p];
+      pol.R[i][j] = r;
+      pol.Rf[i][j] = (float)r;
+      pol.Df[i][j] = (float)((double)E[i][j] + (i == j ? 1.0 : 0.0) - r);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void polar_to_cache(double* Rc, int64_t N, int64_t p, const Polar<D>& pol) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) Rc[(int64_t)(i * D + j) * N + p] = pol.R[i][j];
+}
+
 // Fbar += dR/dF^T [Rbar] in FP64.  With F = R S, dR = R W (W antisymmetric) and
 // W S + S W = R^T dF - dF^T R; the adjoint is Fbar += 2 R Y where Y is the
 // antisymmetric solution of Y S + S Y = skew(R^T Rbar).  In 3D that equation is
@@ -314,14 +338,22 @@ struct StressCache {
 // tau += act (F e)(F e)^T, e = unit vector of `axis` (actuation fibre)
 // with F = I + E; every product is formed on E (or on F - R) so small strains keep
 // their relative precision.
+// Rc (fixed-corotated only, may be null): the cached FP64 polar factor of this particle
+// ([9][N] rows, particle p), used instead of recomputing it.
 template <int D, int MAT>
 __device__ __forceinline__ bool kirchhoff(const float E[D][D], float mu, float la, float act, int axis,
-                                          float tau[D][D], StressCache<D>& sc) {
+                                          float tau[D][D], StressCache<D>& sc,
+                                          const double* Rc = nullptr, int64_t N = 0, int64_t p = 0) {
   bool ok = true;
   sc.Jm1 = det_minus_one<D>(E);
   sc.J = 1.0f + sc.Jm1;
   if (MAT == kFixedCorotated) {
-    ok = polar_f64<D>(E, sc.pol);
+    if (Rc) {
+      polar_from_cache<D>(Rc, N, p, E, sc.pol);
+      ok = sc.J > 0.0f;
+    } else {
+      ok = polar_f64<D>(E, sc.pol);
+    }
     // (F - R) F^T = Df + Df E^T
 #pragma unroll
     for (int i = 0; i < D; ++i)

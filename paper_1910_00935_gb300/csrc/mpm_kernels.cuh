@@ -69,6 +69,7 @@ struct StepArgs {
   const float* wact;       // [scene][group][basis]
   const float4* PMr;       // grid (m, p) of step t-1, read by G2P (null: P2G only)
   float4* PMw;             // grid of step t, accumulated by P2G (null: G2P only)
+  double* Rw;              // [9][N] FP64 polar factors of the P2G's states, written (or null)
   int* box_w;              // [scene][8] box of PMw for this use
   int* box_reset;          // [scene][8] the other parity box of PMw, reset here (or null)
   Clears clears;
@@ -97,6 +98,8 @@ struct AdjArgs {
   int* box_ub;
   int* box_ub_reset;
   float4* PMm;        // grid of step s-1 (recomputed P2G) or null
+  const double* R1;   // [9][N] cached FP64 polar factors of state s+1 (or null: recompute)
+  const double* Rm;   // same for state s-1
   int* box_m;
   int* box_m_reset;
   Clears clears;
@@ -554,7 +557,8 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
                                          const float C[D][D], const float E[D][D], const float* mu,
                                          const float* la, const int* group, const float* wact,
                                          float4* g, int* box_scene, float* sm, float* xr,
-                                         int* s_box, int* s_bbox, unsigned& err) {
+                                         int* s_box, int* s_bbox, unsigned& err,
+                                         const double* R_in, double* R_out, int64_t N) {
   Axes<D> s;
   bool ok = make_axes<D>(x, P, s) && active;
   if (active && !ok) err |= kErrOOB;
@@ -570,10 +574,11 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
     const float act = particle_act(P, basis, group, wact, scene, p, D, axis);
     float tau[D][D];
     StressCache<D> sc;
-    if (!kirchhoff<D, MAT>(E, mu[p], la[p], act, axis, tau, sc)) {
+    if (!kirchhoff<D, MAT>(E, mu[p], la[p], act, axis, tau, sc, R_in, N, p)) {
       err |= kErrNonFinite;
       ok = false;
     }
+    if (MAT == kFixedCorotated && R_out && active) polar_to_cache<D>(R_out, N, p, sc.pol);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       mv[i] = P.p_mass * v[i];
@@ -716,7 +721,7 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
   if (MODE != kG2POnlyFull)
     p2g_pass<D, MAT>(P, P.basis, active, scene, p, tile.z, x, v, C, E, A.mu, A.la, A.group, A.wact,
                      A.PMw + (int64_t)scene * P.nnodes, A.box_w + scene * 8, sm, xr, s_box, s_bbox,
-                     err);
+                     err, nullptr, A.Rw, N);
   if (err) atomicOr(A.err, err);
 }
 
@@ -786,7 +791,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     const float mu = A.mu[p], la = A.la[p];
     float tau[D][D];
     StressCache<D> sc;
-    if (!kirchhoff<D, MAT>(E, mu, la, act, axis, tau, sc) && ok) {
+    if (!kirchhoff<D, MAT>(E, mu, la, act, axis, tau, sc, A.R1, N, p) && ok) {
       err |= kErrNonFinite;
       ok = false;
     }
@@ -1061,7 +1066,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     load_E<D>(A.stm, N, p, P.f_diag, E);
     p2g_pass<D, MAT>(P, P.basis2, active, scene, p, tile.z, x, v, C, E, A.mu, A.la, A.group, A.wact,
                      A.PMm + (int64_t)scene * P.nnodes, A.box_m + scene * 8, sm, xr, s_box, s_bbox_pm,
-                     err);
+                     err, A.Rm, nullptr, N);
   }
   if (err) atomicOr(A.err, err);
 }

@@ -265,6 +265,24 @@ def test_graphs_and_tiles_do_not_change_results(mpm):
             assert rel_l2(g["grad"][key], ref["grad"][key]) <= 1e-4, (opts, key)
 
 
+def test_polar_cache_does_not_change_results(mpm):
+    """3D fixed-corotated: backward passes that read the FP64 polar factors cached by the
+    re-simulation give the gradients of the passes that recompute them (both against the
+    oracle, and against each other to FP32 atomic-order rounding)."""
+    scene = scenes.make("robots3d", n_scenes=2, dims=(16, 8, 8))
+    T = 20
+    scene["desc"]["ckpt_every"] = 6  # ragged last segment: 0, 6, 12, 18
+    seeds = _random_seeds(scene, np.random.default_rng(4))
+    on = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    off = _run_gpu(mpm, scene, T, seeds=seeds, loss=False, options={mpm.MPM_OPT_POLAR_CACHE: 0})
+    o = _oracle_grad_linear(scene, T, {k: v.astype(np.float64) for k, v in seeds.items()})
+    keys = ["gx0", "gv0", "gC0", "gF0", "gE", "gnu", "gw"]
+    _compare_grads(on["grad"], o, keys)
+    _compare_grads(off["grad"], o, keys)
+    for key in keys:
+        assert rel_l2(on["grad"][key], off["grad"][key]) <= 1e-4, key
+
+
 def test_batched_equals_unbatched(mpm):
     base = scenes.make("rects2d", n_scenes=5)
     T = 20
