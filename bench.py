@@ -32,8 +32,7 @@ if ROOT not in sys.path:
 METRIC = "particle-steps/s fwd+bwd (3D MLS-MPM, FP32 bulk, FP64 polar)"
 UNIT = "particle-steps/s"
 
-# algorithmic bytes per unit of each kernel category (3D, FP32 state rows):
-#   particle passes: per particle; node passes: per node of the touched box.
+# algorithmic bytes per particle of each pass category (3D, FP32 state rows):
 # x, v: 12 B each; C, F: 36 B each; mu, la: 8 B; full state 96 B.
 ALG_BYTES_3D = {
     "p2g": 96 + 8,                       # read x, v, C, F, mu, la
@@ -45,6 +44,60 @@ ALG_BYTES_3D = {
                                                    # mu la, mubar labar (rw), state s-1 (P2G)
     "adj_p2g": 96 + 48 + 8 + 16 + 96,
 }
+
+
+def pass_bytes(N, T, K):
+    """Algorithmic bytes of one bench step per kernel category, for both launch forms:
+    the per-pass categories and the persistent launches that run the same passes."""
+    a = ALG_BYTES_3D
+    ckpt_inner = (T - 1) // K                 # full-state writes at t = K, 2K, ... < T
+    fwd = a["p2g"] + (T - 1 - ckpt_inner) * a["g2p_p2g"] + ckpt_inner * a["g2p_p2g_full"] + a["g2p"]
+    resim = 0
+    for s0 in range(0, T, K):
+        n = min(K, T - s0)
+        resim += a["p2g"] + (n - 1) * a["g2p_p2g_full"] + a["g2p"]
+    adj = a["adj_g2p"] + (T - 1) * a["adj_fused"] + a["adj_p2g"]
+    segs = -(-T // K)
+    by = {"p2g": (1 + segs) * a["p2g"], "g2p_p2g": (T - 1 - ckpt_inner) * a["g2p_p2g"],
+          "g2p_p2g_full": (ckpt_inner + (T - segs)) * a["g2p_p2g_full"], "g2p": (1 + segs) * a["g2p"],
+          "adj_g2p": a["adj_g2p"], "adj_fused": (T - 1) * a["adj_fused"], "adj_p2g": a["adj_p2g"],
+          "persistent_step": fwd + resim, "persistent_adj": adj}
+    return {k: v * N for k, v in by.items()}
+
+
+def source_digest():
+    """Digest of the CUDA sources and the C header: a DRAM-traffic figure read from a
+    profile summary counts only if the summary was taken on these exact sources."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1910_00935_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "mpm.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, category):
+    """DRAM bytes per launch (read + write) from profiles/ncu_<category>_<workload>.md when
+    that summary carries this source digest; else None."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{category}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    if f"source digest: {source_digest()}" not in text:
+        return None
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    total = 0.0
+    for metric in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        row = [ln for ln in text.splitlines() if ln.startswith(f"| `{metric}` |")]
+        if not row:
+            return None
+        cells = [c.strip() for c in row[0].strip("|").split("|")]
+        vals = [float(c) for c in cells[1:-1]]
+        total += statistics.mean(vals) * scale.get(cells[-1], float("nan"))
+    return total
 
 
 def _env_int(k, d):
@@ -193,6 +246,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-per-scene", action="store_true",
                     help="also time the same batch one scene per launch sequence")
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="1: run each run of same-kind passes as one persistent launch")
     args = ap.parse_args()
 
     world = _env_int("WORLD_SIZE", 1)
@@ -226,6 +281,7 @@ def main():
     a = scene["arrays"]
     G = desc.get("n_groups", 0)
     sim = mpm.Simulator(desc, T, device=dev)
+    sim.set_option(mpm.MPM_OPT_PERSISTENT, args.persistent)
     names = ["x0", "v0", "C0", "F0", "E", "nu"]
     host = {k: torch.as_tensor(a[k]).pin_memory() for k in names + ["target"]}
     if G:
@@ -343,23 +399,16 @@ def main():
     dom = max(prof, key=lambda k: prof[k][1])
     n_launch, dom_ms = prof[dom]
     hbm, peak_src = measured_peaks()
-    alg = ALG_BYTES_3D if desc["dim"] == 3 else None
-    per_unit = alg.get(dom) if alg else None
-    units = N  # particle passes process every particle once
+    step_bytes = pass_bytes(N, T, desc["ckpt_every"]) if desc["dim"] == 3 else {}
     roof = None
-    if per_unit and n_launch:
+    if dom in step_bytes and n_launch:
         avg_ms = dom_ms / n_launch
-        achieved = per_unit * units / (avg_ms / 1e3) / 1e9
-        traffic = None
-        tpath = os.path.join(ROOT, "profiles", f"traffic_{args.workload}_{dom}.json")
-        if os.path.exists(tpath):
-            try:
-                traffic = json.load(open(tpath)).get("bytes_per_launch")
-            except Exception:
-                traffic = None
+        alg_per_launch = step_bytes[dom] / n_launch
+        achieved = alg_per_launch / (avg_ms / 1e3) / 1e9
+        traffic = profiled_traffic(args.workload, dom)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
-                "alg_bytes_per_launch": per_unit * units, "avg_launch_ms": avg_ms,
+                "alg_bytes_per_launch": alg_per_launch, "avg_launch_ms": avg_ms,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                 else "fallback 6.8 TB/s",
                 "share_of_step": dom_ms / total_prof}
@@ -410,7 +459,8 @@ def main():
                    "ckpt_every": desc["ckpt_every"], "grid": f"{desc['n_grid']}^{desc['dim']}",
                    "l2": "flushed between timed iterations (512 MiB write)",
                    "precision": "FP32 state/grid, FP64 polar decomposition",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "launch_form": "persistent" if args.persistent else "one launch per pass"},
         "forward": {"value": N * T / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms},
         "one_scene_per_launch": per_scene,
         "e2e": e2e,

@@ -78,6 +78,23 @@ extern "C" {
                                      FP64 polar factor for the two backward passes that need it
                                      instead of recomputing it [1] */
 #define MPM_OPT_GRID_BLOCKS 6     /* CTAs per scene of the end-of-sequence grid clear; 0 = automatic [0] */
+#define MPM_OPT_PERSISTENT 8      /* 1: each run of same-kind passes (a whole forward; the
+                                     re-simulation and the adjoint passes of each backward
+                                     segment) is one cooperative launch of resident CTAs that
+                                     step through a recorded pass plan with a grid-wide
+                                     barrier between passes [0].  Results equal the
+                                     one-launch-per-pass form up to FP32 atomic order. */
+#define MPM_OPT_BARRIER_TIMEOUT_US 9 /* limit of one grid-barrier wait in the persistent form,
+                                     microseconds, 1..6e8 [2000000].  A wait that runs out sets
+                                     MPM_ERR_TIMEOUT (reported by mpm_sync_status, after which the
+                                     handle needs mpm_set_initial) and every CTA returns. */
+#define MPM_OPT_PERSISTENT_CHUNK 11 /* persistent form: at most this many passes per launch
+                                     (0 = a whole run of same-kind passes) [0]; bounds the
+                                     duration of any one launch */
+#define MPM_OPT_BARRIER_TEST_EXTRA 10 /* test hook, 0..1024 [0]: arrivals every grid barrier
+                                     waits for beyond the launch's own CTAs.  Nonzero values
+                                     can never be met, so each persistent launch ends through
+                                     the timeout path; nothing else changes. */
 
 /* kernel categories for mpm_get_profile */
 #define MPM_KERNEL_P2G 1          /* P2G from a full state (segment starts, grid recompute) */
@@ -89,6 +106,8 @@ extern "C" {
 #define MPM_KERNEL_ADJ_FUSED 7    /* P2G adjoint of step s+1 + G2P adjoint of step s +
                                      recomputed P2G of step s-1 */
 #define MPM_KERNEL_ADJ_P2G 8      /* P2G adjoint of step 0 */
+#define MPM_KERNEL_PERSISTENT_STEP 9 /* persistent launch of forward-kind passes (categories 1-4) */
+#define MPM_KERNEL_PERSISTENT_ADJ 10 /* persistent launch of adjoint passes (categories 6-8) */
 
 
 /* queries for mpm_get_info */

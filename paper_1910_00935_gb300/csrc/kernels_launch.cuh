@@ -1,0 +1,124 @@
+// kernels_launch.cuh -- launch wrappers of the particle passes, the persistent pass
+// interpreters and the grid clear, templated on the dimension.  kernels_2d.cu and
+// kernels_3d.cu each instantiate one dimension (material and mode are compile-time and
+// dispatched here), so the two dimensions compile in parallel.
+#pragma once
+
+#include "mpm_internal.h"
+#include "mpm_kernels.cuh"
+
+namespace mpm {
+
+namespace {
+template <typename K>
+cudaError_t allow_smem(K k, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int D, int MAT, int MODE>
+cudaError_t step_one(const SimParams& P, const StepArgs& A, int n_tiles, cudaStream_t s) {
+  const size_t smem = pass_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
+  auto k = step_kernel<D, MAT, MODE>;
+  cudaError_t e = allow_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<n_tiles, kTile, smem, s>>>(P, A);
+  return cudaGetLastError();
+}
+
+template <int D, int MAT, int MODE>
+cudaError_t adj_one(const SimParams& P, const AdjArgs& A, int n_tiles, cudaStream_t s) {
+  const size_t smem = pass_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
+  auto k = adjoint_kernel<D, MAT, MODE>;
+  cudaError_t e = allow_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<n_tiles, kTile, smem, s>>>(P, A);
+  return cudaGetLastError();
+}
+
+template <int D, int MAT>
+cudaError_t step_mat(int mode, const SimParams& P, const StepArgs& A, int n_tiles, cudaStream_t s) {
+  switch (mode) {
+    case kP2GOnly: return step_one<D, MAT, kP2GOnly>(P, A, n_tiles, s);
+    case kG2PP2G: return step_one<D, MAT, kG2PP2G>(P, A, n_tiles, s);
+    case kG2PP2GFull: return step_one<D, MAT, kG2PP2GFull>(P, A, n_tiles, s);
+    case kG2POnlyFull: return step_one<D, MAT, kG2POnlyFull>(P, A, n_tiles, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D, int MAT>
+cudaError_t adj_mat(int mode, const SimParams& P, const AdjArgs& A, int n_tiles, cudaStream_t s) {
+  switch (mode) {
+    case kAdjG2P: return adj_one<D, MAT, kAdjG2P>(P, A, n_tiles, s);
+    case kAdjFused: return adj_one<D, MAT, kAdjFused>(P, A, n_tiles, s);
+    case kAdjP2G: return adj_one<D, MAT, kAdjP2G>(P, A, n_tiles, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Cooperative launch of a persistent pass interpreter: as many CTAs as can be resident
+// at once (occupancy x SMs), at most one per tile.
+template <typename K>
+cudaError_t persistent_one(K k, size_t smem, const PassEntry* plan, int n_pass, int n_tiles,
+                           const PersistCtl& ctl, cudaStream_t s, int* grid_out) {
+  cudaError_t e = allow_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTile, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  int grid = per_sm * sms;
+  if (grid > n_tiles) grid = n_tiles;
+  if (grid_out) *grid_out = grid;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kTile);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, plan, n_pass, n_tiles, ctl);
+}
+}  // namespace
+
+template <int D>
+cudaError_t launch_step(int material, int mode, const SimParams& P, const StepArgs& A,
+                        int n_tiles, cudaStream_t s) {
+  return material == kFixedCorotated ? step_mat<D, kFixedCorotated>(mode, P, A, n_tiles, s)
+                                     : step_mat<D, kNeoHookean>(mode, P, A, n_tiles, s);
+}
+
+template <int D>
+cudaError_t launch_adjoint(int material, int mode, const SimParams& P, const AdjArgs& A,
+                           int n_tiles, cudaStream_t s) {
+  return material == kFixedCorotated ? adj_mat<D, kFixedCorotated>(mode, P, A, n_tiles, s)
+                                     : adj_mat<D, kNeoHookean>(mode, P, A, n_tiles, s);
+}
+
+template <int D>
+cudaError_t launch_persistent(int kind, int material, const SimParams& P, const PassEntry* plan,
+                              int n_pass, int n_tiles, const PersistCtl& ctl, cudaStream_t s,
+                              int* grid_out) {
+  const size_t smem = pass_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
+  const bool fcr = material == kFixedCorotated;
+  if (kind == kPassStep)
+    return fcr ? persistent_one(step_persistent_kernel<D, kFixedCorotated>, smem, plan, n_pass, n_tiles, ctl, s, grid_out)
+               : persistent_one(step_persistent_kernel<D, kNeoHookean>, smem, plan, n_pass, n_tiles, ctl, s, grid_out);
+  return fcr ? persistent_one(adjoint_persistent_kernel<D, kFixedCorotated>, smem, plan, n_pass, n_tiles, ctl, s, grid_out)
+             : persistent_one(adjoint_persistent_kernel<D, kNeoHookean>, smem, plan, n_pass, n_tiles, ctl, s, grid_out);
+}
+
+template <int D>
+cudaError_t launch_clear(const Clears& C, int nnodes, int n_grid, int n_scenes, int blocks_per_scene,
+                         cudaStream_t s) {
+  clear_kernel<D><<<dim3(blocks_per_scene, n_scenes), 256, 0, s>>>(C, nnodes, n_grid);
+  return cudaGetLastError();
+}
+
+}  // namespace mpm

@@ -19,11 +19,19 @@
 //
 // Launch sequences are captured into CUDA graphs (one per forward length T and one
 // per backward length), cached on the handle and replayed on the caller's stream.
+//
+// Persistent form (MPM_OPT_PERSISTENT).  The same issue code runs first in record mode,
+// which collects every pass (kernel parameters included) into a plan; the plan is copied
+// to the workspace when it differs from the copy already there, and the sequence then
+// runs each maximal run of same-kind passes as one cooperative launch that steps
+// through the plan with a bounded grid barrier between passes: one launch for a forward,
+// two per segment for a backward.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mpm.h"
@@ -43,13 +51,14 @@ constexpr int kUBSlots = 4;  // velocity-adjoint grids in flight (need: 3)
 
 struct Layout {
   size_t perm, keys0, keys1, idx0, sort_tmp, sort_tmp_bytes;
-  size_t tiles, scene_off, scene_tiles;
-  size_t mu, la, E, nu, group, wact, wbar, mubar, labar;
+  size_t tiles, scene_off, scene_tiles, scene_tile_off;
+  size_t mu, la, E, nu, group, wact, wbar_tile, mubar, labar;
   size_t fin, cur, ckpt, seg, adj;
   size_t rcache;  // (K+1) x [9][N] FP64 polar factors of a re-simulated segment (3D FCR)
   size_t grids;  // kPMSlots + kUBSlots dense grids
   size_t boxes;  // (kPMSlots + kUBSlots) x 2 parities x [scene][8]
-  size_t err, com;
+  size_t err, com, com_part;
+  size_t plan_fwd, plan_bwd, gsync;  // persistent-form pass plans and barrier counters
   size_t total;
 };
 
@@ -57,7 +66,13 @@ struct Dims {
   int D, Q, S, K, n_ckpt, n_tiles, n_grid;
   int64_t N, nnodes;
   bool polar_cache;  // 3D fixed-corotated: FP64 polar factors are cached per segment
+  int T_max;         // max_steps
 };
+
+// passes of the longest forward (T + 1) and backward (re-simulation T + segments, adjoint
+// T + 1) sequences
+int64_t plan_fwd_cap(const Dims& m) { return (int64_t)m.T_max + 1; }
+int64_t plan_bwd_cap(const Dims& m) { return 2 * (int64_t)m.T_max + m.n_ckpt + 1; }
 
 bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
   auto fail = [&](const char* m) {
@@ -100,6 +115,7 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
   m.n_ckpt = (max_steps - 1) / m.K + 1;  // states 0, K, 2K, ... < max_steps
   m.n_grid = d->n_grid;
   m.polar_cache = d->dim == 3 && d->material == MPM_FIXED_COROTATED;
+  m.T_max = max_steps;
   m.nnodes = 1;
   for (int a = 0; a < m.D; ++a) m.nnodes *= d->n_grid;
   m.N = 0;
@@ -129,13 +145,14 @@ Layout make_layout(const Dims& m) {
   L.tiles = take((size_t)m.n_tiles * sizeof(int4));
   L.scene_off = take((S + 1) * 8);
   L.scene_tiles = take(S * 4);
+  L.scene_tile_off = take((S + 1) * 4);
   L.mu = take(N * 4);
   L.la = take(N * 4);
   L.E = take(N * 4);
   L.nu = take(N * 4);
   L.group = take(N * 4);
   L.wact = take(S * kMaxGroups * kMaxBasis * 4);
-  L.wbar = take(S * kMaxGroups * kMaxBasis * 4);
+  L.wbar_tile = take((size_t)m.n_tiles * kMaxGroups * kMaxBasis * 4);
   L.mubar = take(N * 4);
   L.labar = take(N * 4);
   L.fin = take(Q * N * 4);
@@ -149,6 +166,10 @@ Layout make_layout(const Dims& m) {
   L.boxes = take((size_t)(kPMSlots + kUBSlots) * 2 * S * 8 * 4);
   L.err = take(4);
   L.com = take(S * 6 * 8);
+  L.com_part = take(com_scratch_doubles(m.S) * 8);
+  L.plan_fwd = take((size_t)plan_fwd_cap(m) * sizeof(PassEntry));
+  L.plan_bwd = take((size_t)plan_bwd_cap(m) * sizeof(PassEntry));
+  L.gsync = take(sizeof(GridSync));
   L.total = o;
   return L;
 }
@@ -172,6 +193,11 @@ struct mpm_handle {
   int gather_capacity = 1024;
   int grid_blocks = 0;  // CTAs per scene of the end-of-sequence grid clear (0 = automatic)
   bool use_polar_cache = true;
+  bool persistent = false;               // MPM_OPT_PERSISTENT
+  int64_t barrier_timeout_us = 2000000;  // MPM_OPT_BARRIER_TIMEOUT_US
+  unsigned barrier_extra = 0;            // MPM_OPT_BARRIER_TEST_EXTRA
+  int persistent_chunk = 0;              // MPM_OPT_PERSISTENT_CHUNK (0: unlimited)
+  std::vector<PassEntry> plan_copy[2];   // what the workspace plan regions hold (fwd, bwd)
   // graphs
   cudaStream_t cap_stream = nullptr;
   std::map<int64_t, std::pair<cudaGraphExec_t, int64_t>> graphs;  // key -> (exec, launches)
@@ -326,10 +352,92 @@ void after_launch(mpm_handle* h) {
 
 // ------------------------------ launch helpers ------------------------------
 
+enum LaunchMode : int {
+  kDirect = 0,     // one kernel launch per pass
+  kRecord = 1,     // append every pass to *rec, launch nothing (ring bookkeeping still runs)
+  kPersistent = 2  // run the recorded plan (dplan, same order) as cooperative launches
+};
+
 struct Launcher {
   mpm_handle* h;
   cudaStream_t s;
   int64_t count = 0;
+  int mode = kDirect;
+  std::vector<PassEntry>* rec = nullptr;
+  const PassEntry* dplan = nullptr;
+  int next = 0;        // passes issued so far (kPersistent)
+  int run_kind = -1;   // kind of the pending run of passes
+  int run_first = 0;   // its first pass
+
+  // one pass: launched, recorded, or queued into the pending persistent run
+  template <typename Args>
+  cudaError_t pass(int kind, int pmode, int category, const SimParams& P, const Args& A) {
+    if (mode == kRecord) {
+      PassEntry e;
+      memset(&e, 0, sizeof(e));
+      e.kind = kind;
+      e.mode = pmode;
+      e.P = P;
+      if constexpr (std::is_same<Args, StepArgs>::value) e.S = A;
+      else e.A = A;
+      rec->push_back(e);
+      return cudaSuccess;
+    }
+    if (mode == kPersistent) {
+      if (run_kind != kind) {
+        cudaError_t e = flush();
+        if (e != cudaSuccess) return e;
+        run_kind = kind;
+        run_first = next;
+      }
+      ++next;
+      return cudaSuccess;
+    }
+    ++count;
+    const Dims& m = h->m;
+    return timed(category, [&] {
+      if constexpr (std::is_same<Args, StepArgs>::value)
+        return m.D == 2 ? launch_step<2>(h->desc.material, pmode, P, A, m.n_tiles, s)
+                        : launch_step<3>(h->desc.material, pmode, P, A, m.n_tiles, s);
+      else
+        return m.D == 2 ? launch_adjoint<2>(h->desc.material, pmode, P, A, m.n_tiles, s)
+                        : launch_adjoint<3>(h->desc.material, pmode, P, A, m.n_tiles, s);
+    });
+  }
+
+  // launch the pending run of same-kind passes as persistent launches of at most
+  // persistent_chunk passes each (one launch when the chunk is 0)
+  cudaError_t flush() {
+    while (mode == kPersistent && next > run_first) {
+      int n = next - run_first;
+      if (h->persistent_chunk > 0 && n > h->persistent_chunk) n = h->persistent_chunk;
+      cudaError_t e = launch_run(n);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  cudaError_t launch_run(int n) {
+    GridSync* gs = h->at<GridSync>(h->L.gsync);
+    cudaError_t e = cudaMemsetAsync(gs, 0, sizeof(GridSync), s);
+    if (e != cudaSuccess) return e;
+    PersistCtl c;
+    c.sync = gs;
+    c.err = h->at<unsigned>(h->L.err);
+    c.timeout_ns = h->barrier_timeout_us * 1000;
+    c.extra = h->barrier_extra;
+    const SimParams P = params_for(h, 0);  // shared-memory capacities
+    const int kind = run_kind;
+    const PassEntry* plan = dplan + run_first;
+    const Dims& m = h->m;
+    ++count;
+    e = timed(kind == kPassStep ? MPM_KERNEL_PERSISTENT_STEP : MPM_KERNEL_PERSISTENT_ADJ, [&] {
+      return m.D == 2 ? launch_persistent<2>(kind, h->desc.material, P, plan, n, m.n_tiles, c, s, nullptr)
+                      : launch_persistent<3>(kind, h->desc.material, P, plan, n, m.n_tiles, c, s, nullptr);
+    });
+    run_first += n;
+    return e;
+  }
 
   // bracket one launch with events when profiling (category = MPM_KERNEL_*)
   template <typename Fn>
@@ -352,7 +460,7 @@ struct Launcher {
 
   // one forward particle pass: G2P of step t-1 from grid `read` (-1: none), P2G of step
   // t into a new grid (returned in *written, -1 for G2P only)
-  cudaError_t step(int mode, int t, const float* in, float* out, int read, int* written,
+  cudaError_t step(int smode, int t, const float* in, float* out, int read, int* written,
                    double* R_out = nullptr) {
     const Dims& m = h->m;
     SimParams P = params_for(h, t);
@@ -379,14 +487,10 @@ struct Launcher {
       *written = w.id;
     }
     A.clears = take_clears(h);
-    ++count;
-    const int cat = mode == kP2GOnly ? MPM_KERNEL_P2G
-                    : mode == kG2PP2G ? MPM_KERNEL_G2P_P2G
-                    : mode == kG2PP2GFull ? MPM_KERNEL_G2P_P2G_FULL : MPM_KERNEL_G2P;
-    cudaError_t e = timed(cat, [&] {
-      return m.D == 2 ? launch_step<2>(h->desc.material, mode, P, A, m.n_tiles, s)
-                      : launch_step<3>(h->desc.material, mode, P, A, m.n_tiles, s);
-    });
+    const int cat = smode == kP2GOnly ? MPM_KERNEL_P2G
+                    : smode == kG2PP2G ? MPM_KERNEL_G2P_P2G
+                    : smode == kG2PP2GFull ? MPM_KERNEL_G2P_P2G_FULL : MPM_KERNEL_G2P;
+    cudaError_t e = pass(kPassStep, smode, cat, P, A);
     after_launch(h);
     return e;
   }
@@ -394,7 +498,7 @@ struct Launcher {
   // one adjoint pass (see the file comment); pm1/ub1: grids of step s+1 (-1 in kAdjG2P
   // mode), pm0: grid of step s; writes the velocity adjoint of step s (*ub_written) and,
   // when stm != null, the recomputed grid of step s-1 (*pm_written)
-  cudaError_t adjoint(int mode, int s_step, const float* st1, const float* st0, const float* stm,
+  cudaError_t adjoint(int amode, int s_step, const float* st1, const float* st0, const float* stm,
                       int pm1, int ub1, int pm0, int* ub_written, int* pm_written,
                       const double* R1 = nullptr, const double* Rm = nullptr) {
     const Dims& m = h->m;
@@ -416,7 +520,7 @@ struct Launcher {
     A.labar = h->at<float>(h->L.labar);
     A.group = h->at<int>(h->L.group);
     A.wact = h->at<float>(h->L.wact);
-    A.wbar = h->at<float>(h->L.wbar);
+    A.wbar_tile = h->at<float>(h->L.wbar_tile);
     A.err = h->at<unsigned>(h->L.err);
     A.R1 = R1;
     A.Rm = Rm;
@@ -442,36 +546,37 @@ struct Launcher {
       A.stm = nullptr;
     }
     A.clears = take_clears(h);
-    ++count;
-    const int cat = mode == kAdjG2P ? MPM_KERNEL_ADJ_G2P
-                    : mode == kAdjFused ? MPM_KERNEL_ADJ_FUSED : MPM_KERNEL_ADJ_P2G;
-    cudaError_t e = timed(cat, [&] {
-      return m.D == 2 ? launch_adjoint<2>(h->desc.material, mode, P, A, m.n_tiles, s)
-                      : launch_adjoint<3>(h->desc.material, mode, P, A, m.n_tiles, s);
-    });
+    const int cat = amode == kAdjG2P ? MPM_KERNEL_ADJ_G2P
+                    : amode == kAdjFused ? MPM_KERNEL_ADJ_FUSED : MPM_KERNEL_ADJ_P2G;
+    cudaError_t e = pass(kPassAdjoint, amode, cat, P, A);
     after_launch(h);
     return e;
   }
 
   // End of a launch sequence: zero every dirty buffer, reset every box.
   cudaError_t finish() {
+    cudaError_t e = flush();
+    if (e != cudaSuccess) return e;
     for (Ring* r : {&h->pm, &h->ub})
       for (int i = 0; i < r->n; ++i)
         if (r->state[i] == 1) r->state[i] = 2;
-    cudaError_t e = cudaSuccess;
     for (;;) {
       Clears C = take_clears(h);
       if (C.n == 0) break;
-      ++count;
-      e = timed(MPM_KERNEL_GRID_CLEAR, [&] {
-        return h->m.D == 2 ? launch_clear<2>(C, (int)h->m.nnodes, h->m.n_grid, h->m.S, grid_blocks_per_scene(h), s)
-                           : launch_clear<3>(C, (int)h->m.nnodes, h->m.n_grid, h->m.S, grid_blocks_per_scene(h), s);
-      });
+      if (mode != kRecord) {
+        ++count;
+        e = timed(MPM_KERNEL_GRID_CLEAR, [&] {
+          return h->m.D == 2 ? launch_clear<2>(C, (int)h->m.nnodes, h->m.n_grid, h->m.S, grid_blocks_per_scene(h), s)
+                             : launch_clear<3>(C, (int)h->m.nnodes, h->m.n_grid, h->m.S, grid_blocks_per_scene(h), s);
+        });
+      }
       after_launch(h);
       if (e != cudaSuccess) return e;
     }
-    ++count;
-    e = launch_reset_boxes(h->at<int>(h->L.boxes), (int64_t)(kPMSlots + kUBSlots) * 2 * h->m.S, s);
+    if (mode != kRecord) {
+      ++count;
+      e = launch_reset_boxes(h->at<int>(h->L.boxes), (int64_t)(kPMSlots + kUBSlots) * 2 * h->m.S, s);
+    }
     ring_reset(h->pm);
     ring_reset(h->ub);
     return e;
@@ -582,8 +687,40 @@ void drop_graphs(mpm_handle* h) {
 // Run a launch sequence on `stream`, through a cached CUDA graph when enabled.
 template <typename Fn>
 int run_sequence_impl(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
+  const PassEntry* dplan = nullptr;
+  if (h->persistent) {
+    // record the plan (forward keys are even, backward keys odd), refresh its device copy
+    const int region = (int)(key & 1);
+    std::vector<PassEntry> plan;
+    Launcher R{h, stream};
+    R.mode = kRecord;
+    R.rec = &plan;
+    int rc = issue(R);
+    if (rc) return rc;
+    const int64_t cap = region ? plan_bwd_cap(h->m) : plan_fwd_cap(h->m);
+    if ((int64_t)plan.size() > cap) return fail(h, MPM_ERR_STATE, "pass plan exceeds its workspace region");
+    PassEntry* dst = h->at<PassEntry>(region ? h->L.plan_bwd : h->L.plan_fwd);
+    std::vector<PassEntry>& have = h->plan_copy[region];
+    if (have.size() != plan.size() ||
+        memcmp(have.data(), plan.data(), plan.size() * sizeof(PassEntry)) != 0) {
+      drop_graphs(h);  // captured persistent launches read the region being replaced
+      // pageable source: the call returns once the bytes are staged, and the copy runs in
+      // stream order before the launches that read it
+      CK(cudaMemcpyAsync(dst, plan.data(), plan.size() * sizeof(PassEntry), cudaMemcpyHostToDevice,
+                         stream));
+      have.swap(plan);
+    }
+    dplan = dst;
+  }
+  auto configure = [&](Launcher& Lc) {
+    if (dplan) {
+      Lc.mode = kPersistent;
+      Lc.dplan = dplan;
+    }
+  };
   if (!h->use_graphs || h->profile) {
     Launcher Lc{h, stream};
+    configure(Lc);
     int rc = issue(Lc);
     h->launches += Lc.count;
     return rc;
@@ -593,6 +730,7 @@ int run_sequence_impl(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issu
     if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     Launcher Lc{h, h->cap_stream};
+    configure(Lc);
     int rc = issue(Lc);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
@@ -683,6 +821,11 @@ int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_byt
   if (e == cudaSuccess)
     e = cudaMemcpy(h->at<int>(L.scene_tiles), scene_tiles.data(), scene_tiles.size() * 4,
                    cudaMemcpyHostToDevice);
+  std::vector<int> tile_off(m.S + 1, 0);
+  for (int s = 0; s < m.S; ++s) tile_off[s + 1] = tile_off[s] + scene_tiles[s];
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->at<int>(L.scene_tile_off), tile_off.data(), tile_off.size() * 4,
+                   cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->at<char>(L.err), 0, 4);
   if (e != cudaSuccess) {
     delete h;
@@ -772,9 +915,8 @@ int mpm_loss(mpm_handle* h, int32_t kind, const float* target, float* loss, floa
   h->last_stream = s;
   const Dims& m = h->m;
   double* com = h->at<double>(h->L.com);
-  CK(cudaMemsetAsync(com, 0, (size_t)m.S * 6 * sizeof(double), s));
   CK(launch_com(m.D, m.N, m.S, h->at<int64_t>(h->L.scene_off), h->at<int>(h->L.perm),
-                h->at<float>(h->L.fin), h->state(h->L.ckpt, 0), com, s));
+                h->at<float>(h->L.fin), h->state(h->L.ckpt, 0), h->at<double>(h->L.com_part), com, s));
   CK(launch_loss_seed(m.D, kind, m.N, m.S, h->at<int64_t>(h->L.scene_off), h->at<int>(h->L.perm),
                       com, target, loss, dL_dxT, dL_dx0, s));
   h->launches += 2;
@@ -802,7 +944,8 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   }
   CK(cudaMemsetAsync(h->at<float>(L.mubar), 0, (size_t)m.N * 4, s));
   CK(cudaMemsetAsync(h->at<float>(L.labar), 0, (size_t)m.N * 4, s));
-  CK(cudaMemsetAsync(h->at<float>(L.wbar), 0, (size_t)m.S * kMaxGroups * kMaxBasis * 4, s));
+  const int GK = h->desc.n_groups * h->desc.n_basis;
+  if (GK) CK(cudaMemsetAsync(h->at<float>(L.wbar_tile), 0, (size_t)m.n_tiles * GK * 4, s));
   h->launches += 4;
   const int T = h->T_recorded;
   int rc = run_sequence(h, (int64_t)T * 2 + 1, s, [&](Launcher& Lc) { return issue_backward(h, Lc, T); });
@@ -821,8 +964,10 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
                             h->at<float>(L.labar), gE, gnu, s));
     ++h->launches;
   }
-  const size_t wbytes = (size_t)m.S * h->desc.n_groups * h->desc.n_basis * sizeof(float);
-  if (gw && wbytes) CK(cudaMemcpyAsync(gw, h->at<float>(L.wbar), wbytes, cudaMemcpyDeviceToDevice, s));
+  if (gw && GK) {
+    CK(launch_wbar_reduce(m.S, GK, h->at<int>(L.scene_tile_off), h->at<float>(L.wbar_tile), gw, s));
+    ++h->launches;
+  }
   return MPM_OK;
 }
 
@@ -837,7 +982,12 @@ int mpm_sync_status(mpm_handle* h) {
     cudaMemset(h->at<unsigned>(h->L.err), 0, 4);
     if (err & kErrOOB) return fail(h, MPM_ERR_OOB, "a particle's stencil left the grid");
     if (err & kErrNonFinite) return fail(h, MPM_ERR_NONFINITE, "non-finite value or det F <= 0");
-    if (err & kErrTimeout) return fail(h, MPM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (err & kErrTimeout) {
+      // passes after the barrier that gave up never ran: grid buffers may be dirty
+      h->initialized = false;
+      h->T_recorded = 0;
+      return fail(h, MPM_ERR_TIMEOUT, "a bounded device wait gave up (call mpm_set_initial again)");
+    }
   }
   return MPM_OK;
 }
@@ -857,6 +1007,19 @@ int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
       h->grid_blocks = (int)value;
       break;
     case MPM_OPT_POLAR_CACHE: h->use_polar_cache = value != 0; break;
+    case MPM_OPT_PERSISTENT: h->persistent = value != 0; break;
+    case MPM_OPT_PERSISTENT_CHUNK:
+      if (value < 0 || value > (1 << 30)) return fail(h, MPM_ERR_ARG, "persistent chunk must be >= 0");
+      h->persistent_chunk = (int)value;
+      break;
+    case MPM_OPT_BARRIER_TIMEOUT_US:
+      if (value < 1 || value > 600000000) return fail(h, MPM_ERR_ARG, "barrier timeout must be in [1 us, 600 s]");
+      h->barrier_timeout_us = value;
+      break;
+    case MPM_OPT_BARRIER_TEST_EXTRA:
+      if (value < 0 || value > 1024) return fail(h, MPM_ERR_ARG, "barrier test arrivals must be in [0, 1024]");
+      h->barrier_extra = (unsigned)value;
+      break;
     case MPM_OPT_PROFILE:
       h->profile = value != 0;
       h->ev_records.clear();

@@ -13,6 +13,8 @@ namespace mpm {
 struct StepArgs;
 struct AdjArgs;
 struct Clears;
+struct PassEntry;
+struct PersistCtl;
 
 // kernels_2d.cu / kernels_3d.cu (templated on dimension)
 template <int D>
@@ -21,6 +23,13 @@ cudaError_t launch_step(int material, int mode, const SimParams& P, const StepAr
 template <int D>
 cudaError_t launch_adjoint(int material, int mode, const SimParams& P, const AdjArgs& A, int n_tiles,
                            cudaStream_t s);
+// one cooperative launch running plan[0..n_pass) (all of PassKind `kind`) with a bounded
+// grid barrier between passes; P supplies the shared-memory capacities; *grid_out gets
+// the CTA count
+template <int D>
+cudaError_t launch_persistent(int kind, int material, const SimParams& P, const PassEntry* plan,
+                              int n_pass, int n_tiles, const PersistCtl& ctl, cudaStream_t s,
+                              int* grid_out);
 template <int D>
 cudaError_t launch_clear(const Clears& C, int nnodes, int n_grid, int n_scenes, int blocks_per_scene,
                          cudaStream_t s);
@@ -45,8 +54,13 @@ cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const floa
 cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, const float* nu,
                                  const float* mubar, const float* labar, float* gE, float* gnu,
                                  cudaStream_t s);
+// per-scene sums of x_T and x_0 into com[scene][6]; part: com_scratch_doubles(n_scenes)
+size_t com_scratch_doubles(int n_scenes);
 cudaError_t launch_com(int dim, int64_t N, int n_scenes, const int64_t* scene_off, const int* perm,
-                       const float* xT, const float* x0, double* com, cudaStream_t s);
+                       const float* xT, const float* x0, double* part, double* com, cudaStream_t s);
+// out[scene][gk] = sum over the scene's tiles (tile_off[scene] .. tile_off[scene+1]) in order
+cudaError_t launch_wbar_reduce(int n_scenes, int gk, const int* tile_off, const float* wbar_tile,
+                               float* out, cudaStream_t s);
 cudaError_t launch_loss_seed(int dim, int kind, int64_t N, int n_scenes, const int64_t* scene_off,
                              const int* perm, const double* com, const float* target, float* loss,
                              float* dL_dxT, float* dL_dx0, cudaStream_t s);

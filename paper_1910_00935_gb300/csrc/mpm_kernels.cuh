@@ -90,7 +90,7 @@ struct AdjArgs {
   float* labar;
   const int* group;
   const float* wact;
-  float* wbar;        // [scene][group][basis]
+  float* wbar_tile;   // [tile][group][basis] per-tile dL/dw partial sums (this pass adds)
   const float4* PM1;  // grid (m, p) of step s+1 (P2G-adjoint)
   const float4* UB1;  // grid-velocity adjoint of step s+1
   const float4* PM0;  // grid of step s (G2P-adjoint)
@@ -106,6 +106,16 @@ struct AdjArgs {
   unsigned* err;
 };
 
+// Grid reads in the particle passes.  A grid written by an earlier launch is read through
+// the read-only data path (NC); inside a persistent launch the grid was written by an
+// earlier pass of the same launch, so it is read with coherent loads, which the barrier's
+// acquire makes current.
+template <bool NC>
+__device__ __forceinline__ float4 grid_load(const float4* p) {
+  if (NC) return __ldg(p);
+  return *p;
+}
+
 template <int D>
 struct Rows {
   static constexpr int X = 0, V = D, C = 2 * D, F = 2 * D + D * D, Q = 2 * D + 2 * D * D;
@@ -117,6 +127,9 @@ struct Xch {
   static constexpr int kWidth = 1 + 2 * D + D * D;
   static constexpr int kStride = kTile + kTile / 8;  // padded: conflict-free in both orders
 };
+
+// per-warp group sums of the dL/dw reduction
+constexpr int kWbarSlots = (kTile / 32) * kMaxGroups;
 
 __device__ __forceinline__ int scatter_slot(int t) { return (t & 31) * (kTile / 32) + (t >> 5); }
 __device__ __forceinline__ int xidx(int j) { return j + (j >> 3); }
@@ -522,12 +535,16 @@ __device__ __forceinline__ void run_clears(const Clears& C, int scene, int rank,
                                            int nnodes, int n) {
   for (int c = 0; c < C.n; ++c) {
     const int* bb = C.job[c].box + scene * 8;
+    // An empty box (lo = INT_MAX, hi = INT_MIN: a buffer that was allocated but never
+    // scattered into, e.g. after a pass that gave up) clears nothing; hi - lo is formed
+    // only for a non-empty box, and the box is clipped to the grid.
     int lo[D], ext[D], vol = 1;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      lo[a] = bb[a];
-      ext[a] = bb[4 + a] - bb[a] + 1;
-      vol = ext[a] > 0 ? vol * ext[a] : 0;
+      lo[a] = bb[a] > 0 ? bb[a] : 0;
+      const int hi = bb[4 + a] < n - 1 ? bb[4 + a] : n - 1;
+      ext[a] = hi >= lo[a] ? hi - lo[a] + 1 : 0;
+      vol *= ext[a];
     }
     float4* g = C.job[c].grid + (int64_t)scene * nnodes;
     for (int l = rank * blockDim.x + threadIdx.x; l < vol; l += nranks * blockDim.x) {
@@ -613,15 +630,16 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
 // ---------------------------------------------------------------------------
 // forward particle pass: [G2P of step t-1] then [P2G of step t]
 // ---------------------------------------------------------------------------
-template <int D, int MAT, int MODE>
-__global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P, StepArgs A) {
+// One tile of a forward pass; every thread of the CTA calls it.  sm: dynamic shared memory
+// (pass_smem_bytes), s_box / s_bbox: 8 ints each.  A CTA that runs several tiles must
+// synchronise between them.
+template <int D, int MAT, int MODE, bool NC>
+__device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A, int tile_index,
+                                          float* sm, int* s_box, int* s_bbox) {
   using R = Rows<D>;
-  extern __shared__ __align__(16) float sm[];
-  __shared__ int s_box[8];
-  __shared__ int s_bbox[8];
   cta_bbox_reset(s_bbox);
   float* xr = sm + box_floats(P.tile_capacity, P.gather_capacity);
-  const int4 tile = A.tiles[blockIdx.x];
+  const int4 tile = A.tiles[tile_index];
   const int scene = tile.x;
   const bool active = (int)threadIdx.x < tile.z;
   const int64_t p = (int64_t)tile.y + (active ? threadIdx.x : 0);
@@ -660,7 +678,7 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
       for (int b = 0; b < D; ++b) B[a][b] = 0.0f;
     }
     const float4* PMg = A.PMr + (int64_t)scene * P.nnodes;
-    auto velocity = [&](const int idx[D]) { return node_velocity<D>(__ldg(PMg + node_flat<D>(idx, n)), idx, P); };
+    auto velocity = [&](const int idx[D]) { return node_velocity<D>(grid_load<NC>(PMg + node_flat<D>(idx, n)), idx, P); };
     BoxInfo<D> gbx;
     gbx.use_tile = false;
     if (P.gather_capacity > 0) {
@@ -725,23 +743,28 @@ __global__ void __launch_bounds__(kTile, D == 3 ? 3 : 4) step_kernel(SimParams P
   if (err) atomicOr(A.err, err);
 }
 
+template <int D, int MAT, int MODE>
+__global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D) step_kernel(const __grid_constant__ SimParams P, const __grid_constant__ StepArgs A) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_box[8];
+  __shared__ int s_bbox[8];
+  step_tile<D, MAT, MODE, true>(P, A, blockIdx.x, sm, s_box, s_bbox);
+}
+
 // ---------------------------------------------------------------------------
 // adjoint particle pass: [P2G-adjoint of step s+1] [G2P-adjoint of step s]
 // [recomputed P2G of step s-1, the grid the next adjoint pass needs (Appendix D.1)]
 // ---------------------------------------------------------------------------
-template <int D, int MAT, int MODE>
-__global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs A) {
+// One tile of an adjoint pass (same calling rules as step_tile; s_wbar: kWbarSlots floats).
+template <int D, int MAT, int MODE, bool NC>
+__device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& A, int tile_index,
+                                             float* sm, int* s_box, int* s_bbox_ub, int* s_bbox_pm,
+                                             float* s_wbar) {
   using R = Rows<D>;
-  extern __shared__ __align__(16) float sm[];
-  __shared__ int s_box[8];
-  __shared__ int s_bbox_ub[8];
-  __shared__ int s_bbox_pm[8];
-  __shared__ float s_wbar[kMaxGroups * kMaxBasis];
   cta_bbox_reset(s_bbox_ub);
   cta_bbox_reset(s_bbox_pm);
-  if (threadIdx.x < kMaxGroups * kMaxBasis) s_wbar[threadIdx.x] = 0.0f;
   float* xr = sm + box_floats(P.tile_capacity, P.gather_capacity);
-  const int4 tile = A.tiles[blockIdx.x];
+  const int4 tile = A.tiles[tile_index];
   const int scene = tile.x;
   const bool active = (int)threadIdx.x < tile.z;
   const int64_t p = (int64_t)tile.y + (active ? threadIdx.x : 0);
@@ -754,7 +777,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     reset_box(A.box_ub_reset, scene);
     reset_box(A.box_m_reset, scene);
   }
-  __syncthreads();  // shared boxes and s_wbar reset
+  __syncthreads();  // shared boxes reset
 
   // adjoint of state s+1: xb, vb, Cb, Fb (Fb = dL/dE = dL/dF)
   float xb[D], vb[D], Cb[D][D], Fb[D][D];
@@ -815,7 +838,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     const float4* PMg = A.PM1 + (int64_t)scene * P.nnodes;
     auto pbar = [&](const int idx[D]) {
       const int f = node_flat<D>(idx, n);
-      return node_adjoint<D>(__ldg(UBg + f), __ldg(PMg + f), idx, P);
+      return node_adjoint<D>(grid_load<NC>(UBg + f), grid_load<NC>(PMg + f), idx, P);
     };
     BoxInfo<D> gbx;
     gbx.use_tile = false;
@@ -897,18 +920,31 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
       A.labar[p] += lab;
     }
     if (P.n_groups > 0) {
+      // dL/dw_gk += basis_k * sum of abar over this tile's particles of group g, reduced in
+      // a fixed order (warp butterfly, then warps in order) into the tile's own slot, so
+      // the result does not depend on scheduling; the tiles are summed in order at the end
+      int g = -1;
       if (ok) {
-        int g = A.group[p];
-        if (g >= 0 && g < P.n_groups) {
+        g = A.group[p];
+        if (g < 0 || g >= P.n_groups) g = -1;
+      }
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-          for (int k = 0; k < kMaxBasis; ++k)
-            if (k < P.n_basis) atomicAdd(&s_wbar[g * P.n_basis + k], abar * P.basis[k]);
+      for (int gg = 0; gg < kMaxGroups; ++gg) {
+        if (gg < P.n_groups) {
+          float v = (g == gg) ? abar : 0.0f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) s_wbar[warp * kMaxGroups + gg] = v;
         }
       }
       __syncthreads();
-      if ((int)threadIdx.x < P.n_groups * P.n_basis) {
-        float wv = s_wbar[threadIdx.x];
-        if (wv != 0.0f) atomicAdd(&A.wbar[(int64_t)scene * P.n_groups * P.n_basis + threadIdx.x], wv);
+      const int GK = P.n_groups * P.n_basis;
+      if ((int)threadIdx.x < GK) {
+        const int gg = threadIdx.x / P.n_basis, k = threadIdx.x % P.n_basis;
+        float sum = 0.0f;
+        for (int w = 0; w < kTile / 32; ++w) sum += s_wbar[w * kMaxGroups + gg];
+        A.wbar_tile[(int64_t)tile_index * GK + threadIdx.x] += sum * P.basis[k];
       }
     }
     if (MODE == kAdjP2G) {
@@ -958,7 +994,7 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
     const bool ok = make_axes<D>(x0, P, s) && active;
     if (active && !ok) err |= kErrOOB;
     const float4* PMg = A.PM0 + (int64_t)scene * P.nnodes;
-    auto velocity = [&](const int idx[D]) { return node_velocity<D>(__ldg(PMg + node_flat<D>(idx, n)), idx, P); };
+    auto velocity = [&](const int idx[D]) { return node_velocity<D>(grid_load<NC>(PMg + node_flat<D>(idx, n)), idx, P); };
     const int cap_box = P.tile_capacity > P.gather_capacity ? P.tile_capacity : P.gather_capacity;
     BoxInfo<D> bx;
     bx.use_tile = false;
@@ -1071,9 +1107,169 @@ __global__ void __launch_bounds__(kTile, 2) adjoint_kernel(SimParams P, AdjArgs 
   if (err) atomicOr(A.err, err);
 }
 
+template <int D, int MAT, int MODE>
+__global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM) adjoint_kernel(const __grid_constant__ SimParams P, const __grid_constant__ AdjArgs A) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_box[8];
+  __shared__ int s_bbox_ub[8];
+  __shared__ int s_bbox_pm[8];
+  __shared__ float s_wbar[kWbarSlots];
+  adjoint_tile<D, MAT, MODE, true>(P, A, blockIdx.x, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+}
+
+// ---------------------------------------------------------------------------
+// persistent launches: one co-resident (cooperative) grid runs a list of passes of one
+// kind with a grid-wide barrier between consecutive passes.  The list is recorded on the
+// host by the same code that issues the one-launch-per-pass form, so the two run the
+// same passes on the same buffers in the same order.
+// ---------------------------------------------------------------------------
+enum PassKind : int { kPassStep = 0, kPassAdjoint = 1 };
+
+struct __align__(16) PassEntry {
+  int kind;  // PassKind
+  int mode;  // StepMode or AdjMode
+  int pad[2];
+  SimParams P;
+  StepArgs S;  // kPassStep
+  AdjArgs A;   // kPassAdjoint
+};
+
+struct GridSync {
+  unsigned arrived;  // CTA arrivals at the barriers of this launch (reset before it)
+  unsigned abort;    // set by a CTA whose wait ran out; every CTA then leaves
+};
+
+struct PersistCtl {
+  GridSync* sync;
+  unsigned* err;
+  long long timeout_ns;  // limit of one barrier wait
+  unsigned extra;        // arrivals a barrier waits for beyond the grid's own (0; a nonzero
+                         // value makes every wait run out: the timeout path's test hook)
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier: returns when `target` arrivals have been counted, or false when the
+// wait ran out (err |= kErrTimeout, abort raised) or another CTA aborted.  The wait is
+// bounded twice: by the global nanosecond timer and by the SM cycle counter (4 cycles per
+// ns of limit, at least twice the limit at any SM clock up to 2 GHz), so it ends even if
+// one of the two clocks stalls.
+__device__ __forceinline__ bool grid_barrier(const PersistCtl& c, unsigned target, int* s_go) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's grid and state writes before its arrival
+    atomicAdd(&c.sync->arrived, 1u);
+    int go = 1;
+    const unsigned long long t0 = globaltimer_ns();
+    const long long c0 = clock64();
+    const long long cycle_limit = 4 * c.timeout_ns;
+    for (unsigned it = 1;; ++it) {
+      if (ld_acquire_gpu(&c.sync->arrived) >= target) break;
+      if (ld_relaxed_gpu(&c.sync->abort)) {
+        go = 0;
+        break;
+      }
+      if ((it & 15u) == 0 && ((long long)(globaltimer_ns() - t0) > c.timeout_ns ||
+                              clock64() - c0 > cycle_limit)) {
+        atomicExch(&c.sync->abort, 1u);
+        atomicOr(c.err, kErrTimeout);
+        go = 0;
+        break;
+      }
+      __nanosleep(128);
+    }
+    __threadfence();
+    *s_go = go;
+  }
+  __syncthreads();
+  return *s_go != 0;
+}
+
+// Copy a 16-byte-multiple object to shared memory with the whole CTA (no barrier).
+template <typename T>
+__device__ __forceinline__ void cta_copy(T* dst, const T* src) {
+  static_assert(sizeof(T) % 16 == 0, "16-byte multiple");
+  const int4* s4 = reinterpret_cast<const int4*>(src);
+  int4* d4 = reinterpret_cast<int4*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 16); i += blockDim.x) d4[i] = s4[i];
+}
+
+// Forward-kind passes plan[0..n_pass): each CTA takes tiles blockIdx.x, +gridDim.x, ...
+template <int D, int MAT>
+__global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D)
+    step_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_box[8];
+  __shared__ int s_bbox[8];
+  __shared__ int s_go;
+  __shared__ PassEntry e;
+  for (int i = 0; i < n_pass; ++i) {
+    if (i > 0 && !grid_barrier(ctl, (unsigned)i * gridDim.x + ctl.extra, &s_go)) return;
+    __syncthreads();
+    cta_copy(&e, plan + i);
+    __syncthreads();
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      switch (e.mode) {
+        case kP2GOnly: step_tile<D, MAT, kP2GOnly, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
+        case kG2PP2G: step_tile<D, MAT, kG2PP2G, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
+        case kG2PP2GFull: step_tile<D, MAT, kG2PP2GFull, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
+        default: step_tile<D, MAT, kG2POnlyFull, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Adjoint-kind passes plan[0..n_pass).
+template <int D, int MAT>
+__global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
+    adjoint_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_box[8];
+  __shared__ int s_bbox_ub[8];
+  __shared__ int s_bbox_pm[8];
+  __shared__ float s_wbar[kWbarSlots];
+  __shared__ int s_go;
+  __shared__ PassEntry e;
+  for (int i = 0; i < n_pass; ++i) {
+    if (i > 0 && !grid_barrier(ctl, (unsigned)i * gridDim.x + ctl.extra, &s_go)) return;
+    __syncthreads();
+    cta_copy(&e, plan + i);
+    __syncthreads();
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      switch (e.mode) {
+        case kAdjG2P:
+          adjoint_tile<D, MAT, kAdjG2P, false>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          break;
+        case kAdjFused:
+          adjoint_tile<D, MAT, kAdjFused, false>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          break;
+        default:
+          adjoint_tile<D, MAT, kAdjP2G, false>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          break;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Zero the dirty boxes of the clear jobs (end of a launch sequence); blockIdx.y = scene.
 template <int D>
-__global__ void clear_kernel(Clears C, int nnodes, int n) {
+__global__ void clear_kernel(const __grid_constant__ Clears C, int nnodes, int n) {
   run_clears<D>(C, blockIdx.y, blockIdx.x, gridDim.x, nnodes, n);
 }
 

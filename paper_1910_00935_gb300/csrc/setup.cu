@@ -129,10 +129,12 @@ __global__ void material_grad_kernel(int64_t N, const int* perm, const float* E,
   }
 }
 
-// per-scene sums of x_T and x_0 (FP64), com[scene][6]: one CTA per (scene, chunk),
-// CTA-reduced in shared memory, one FP64 atomic per CTA and component
+// per-scene sums of x_T and x_0 (FP64): one CTA per (scene, chunk) writes its partial
+// sums part[scene][chunk][6]; com_final_kernel adds the chunks in order (no atomics, so
+// the sums do not depend on scheduling)
+constexpr int kComChunks = 64;
 __global__ void com_kernel(int dim, int n_scenes, const int64_t* off, int64_t N, const float* xT,
-                           const float* x0, double* com) {
+                           const float* x0, double* part) {
   __shared__ double red[6][256 / 32];
   const int s = blockIdx.y;
   const int64_t b = off[s], e = off[s + 1];
@@ -153,8 +155,28 @@ __global__ void com_kernel(int dim, int n_scenes, const int64_t* off, int64_t N,
   if (threadIdx.x < 6) {
     double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-    if (v != 0.0) atomicAdd(&com[s * 6 + threadIdx.x], v);
+    part[((int64_t)s * kComChunks + blockIdx.x) * 6 + threadIdx.x] = v;
   }
+}
+
+__global__ void com_final_kernel(int n_scenes, const double* part, double* com) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_scenes * 6) return;
+  const int s = i / 6, c = i % 6;
+  double v = 0.0;
+  for (int k = 0; k < kComChunks; ++k) v += part[((int64_t)s * kComChunks + k) * 6 + c];
+  com[i] = v;
+}
+
+// dL/dw[scene][g][k] = sum over the scene's tiles, in tile order, of the per-tile partials
+__global__ void wbar_reduce_kernel(int n_scenes, int gk, const int* tile_off, const float* wbar_tile,
+                                   float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_scenes * gk) return;
+  const int s = i / gk, c = i % gk;
+  float v = 0.0f;
+  for (int t = tile_off[s]; t < tile_off[s + 1]; ++t) v += wbar_tile[(int64_t)t * gk + c];
+  out[i] = v;
 }
 
 __global__ void loss_seed_kernel(int dim, int kind, int64_t N, int n_scenes, const int64_t* off,
@@ -251,10 +273,21 @@ cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, con
   return cudaGetLastError();
 }
 
+size_t com_scratch_doubles(int n_scenes) { return (size_t)n_scenes * kComChunks * 6; }
+
 cudaError_t launch_com(int dim, int64_t N, int n_scenes, const int64_t* scene_off, const int* perm,
-                       const float* xT, const float* x0, double* com, cudaStream_t s) {
+                       const float* xT, const float* x0, double* part, double* com, cudaStream_t s) {
   (void)perm;
-  com_kernel<<<dim3(64, n_scenes), 256, 0, s>>>(dim, n_scenes, scene_off, N, xT, x0, com);
+  com_kernel<<<dim3(kComChunks, n_scenes), 256, 0, s>>>(dim, n_scenes, scene_off, N, xT, x0, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  com_final_kernel<<<(n_scenes * 6 + 255) / 256, 256, 0, s>>>(n_scenes, part, com);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wbar_reduce(int n_scenes, int gk, const int* tile_off, const float* wbar_tile,
+                               float* out, cudaStream_t s) {
+  wbar_reduce_kernel<<<(n_scenes * gk + 255) / 256, 256, 0, s>>>(n_scenes, gk, tile_off, wbar_tile, out);
   return cudaGetLastError();
 }
 
