@@ -26,6 +26,7 @@
 // runs each maximal run of same-kind passes as one cooperative launch that steps
 // through the plan with a bounded grid barrier between passes: one launch for a forward,
 // two per segment for a backward.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -169,7 +170,8 @@ Layout make_layout(const Dims& m) {
   L.com_part = take(com_scratch_doubles(m.S) * 8);
   L.plan_fwd = take((size_t)plan_fwd_cap(m) * sizeof(PassEntry));
   L.plan_bwd = take((size_t)plan_bwd_cap(m) * sizeof(PassEntry));
-  L.gsync = take(sizeof(GridSync));
+  // barrier counters, then one tile-ticket counter per pass of the longest plan
+  L.gsync = take(16 + 4 * (size_t)std::max(plan_fwd_cap(m), plan_bwd_cap(m)));
   L.total = o;
   return L;
 }
@@ -418,11 +420,13 @@ struct Launcher {
   }
 
   cudaError_t launch_run(int n) {
+    static_assert(sizeof(GridSync) <= 16, "barrier counters fit the first 16 bytes");
     GridSync* gs = h->at<GridSync>(h->L.gsync);
-    cudaError_t e = cudaMemsetAsync(gs, 0, sizeof(GridSync), s);
+    cudaError_t e = cudaMemsetAsync(gs, 0, 16 + 4 * (size_t)n, s);
     if (e != cudaSuccess) return e;
     PersistCtl c;
     c.sync = gs;
+    c.tickets = reinterpret_cast<unsigned*>(h->at<char>(h->L.gsync) + 16);
     c.err = h->at<unsigned>(h->L.err);
     c.timeout_ns = h->barrier_timeout_us * 1000;
     c.extra = h->barrier_extra;

@@ -1141,6 +1141,7 @@ struct GridSync {
 
 struct PersistCtl {
   GridSync* sync;
+  unsigned* tickets;     // [n_pass] tile tickets (reset before the launch)
   unsigned* err;
   long long timeout_ns;  // limit of one barrier wait
   unsigned extra;        // arrivals a barrier waits for beyond the grid's own (0; a nonzero
@@ -1208,21 +1209,29 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src) {
   for (int i = threadIdx.x; i < (int)(sizeof(T) / 16); i += blockDim.x) d4[i] = s4[i];
 }
 
-// Forward-kind passes plan[0..n_pass): each CTA takes tiles blockIdx.x, +gridDim.x, ...
+// Next tile of pass i for this CTA (tickets in tile order, so tiles are taken in the order
+// the hardware would dispatch one CTA per tile, and a CTA that finishes early takes more);
+// a value >= n_tiles ends the pass.  Synchronises the CTA.
+__device__ __forceinline__ int next_tile(const PersistCtl& c, int i, int* s_tile) {
+  if (threadIdx.x == 0) *s_tile = (int)atomicAdd(&c.tickets[i], 1u);
+  __syncthreads();
+  return *s_tile;
+}
+
+// Forward-kind passes plan[0..n_pass), tiles handed out by tickets.
 template <int D, int MAT>
 __global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D)
     step_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8];
   __shared__ int s_bbox[8];
-  __shared__ int s_go;
+  __shared__ int s_go, s_tile;
   __shared__ PassEntry e;
   for (int i = 0; i < n_pass; ++i) {
     if (i > 0 && !grid_barrier(ctl, (unsigned)i * gridDim.x + ctl.extra, &s_go)) return;
     __syncthreads();
     cta_copy(&e, plan + i);
-    __syncthreads();
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    for (int t; (t = next_tile(ctl, i, &s_tile)) < n_tiles;) {
       switch (e.mode) {
         case kP2GOnly: step_tile<D, MAT, kP2GOnly, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
         case kG2PP2G: step_tile<D, MAT, kG2PP2G, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
@@ -1243,14 +1252,13 @@ __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
   __shared__ int s_bbox_ub[8];
   __shared__ int s_bbox_pm[8];
   __shared__ float s_wbar[kWbarSlots];
-  __shared__ int s_go;
+  __shared__ int s_go, s_tile;
   __shared__ PassEntry e;
   for (int i = 0; i < n_pass; ++i) {
     if (i > 0 && !grid_barrier(ctl, (unsigned)i * gridDim.x + ctl.extra, &s_go)) return;
     __syncthreads();
     cta_copy(&e, plan + i);
-    __syncthreads();
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    for (int t; (t = next_tile(ctl, i, &s_tile)) < n_tiles;) {
       switch (e.mode) {
         case kAdjG2P:
           adjoint_tile<D, MAT, kAdjG2P, false>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
