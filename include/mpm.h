@@ -53,6 +53,7 @@ extern "C" {
 #define MPM_ERR_STATE 6      /* call out of order (backward before forward, T > max) */
 #define MPM_ERR_WORKSPACE 7  /* workspace NULL, misaligned or too small */
 #define MPM_ERR_TOO_LARGE 8  /* mpm_step_noalloc: problem larger than its fixed scratch */
+#define MPM_ERR_RANGE 9      /* deterministic mode: a grid contribution left the fixed-point range */
 
 /* materials */
 #define MPM_FIXED_COROTATED 0
@@ -134,7 +135,18 @@ typedef struct mpm_scene_desc {
   int32_t n_basis;             /* sine terms per group, 0..8 */
   float act_period;            /* P of sin(2 pi k t / P + phase), t = step index */
   float act_phase;
-  int32_t deterministic_p2g;   /* reserved: must be 0 */
+  int32_t deterministic_p2g;   /* 1: every grid sum (P2G, the recomputed P2G, the velocity-
+                                  adjoint scatter) is accumulated in 64-bit fixed point, so the
+                                  forward and backward are bitwise reproducible whatever the
+                                  order of the atomic adds (run to run, graphs or not, persistent
+                                  or not).  Grids take twice the memory and four 64-bit integer
+                                  adds replace one float4 add per contribution.  Scales: mass
+                                  m_p -> 2^40, momentum m_p dx/dt -> 2^40, velocity adjoint: its
+                                  first scatter's largest contribution -> below 2^36 (a measuring
+                                  pass per backward); a contribution beyond 2^55 is refused with
+                                  MPM_ERR_RANGE.  The shared scatter box is not used.  0: FP32
+                                  atomic sums (default, faster).  No counterpart in the paper,
+                                  whose GPU atomics are order-dependent as well. */
 } mpm_scene_desc;
 
 /* Device bytes the workspace needs for this description and at most max_steps

@@ -1,7 +1,8 @@
 // kernels_launch.cuh -- launch wrappers of the particle passes, the persistent pass
-// interpreters and the grid clear, templated on the dimension.  kernels_2d.cu and
-// kernels_3d.cu each instantiate one dimension (material and mode are compile-time and
-// dispatched here), so the two dimensions compile in parallel.
+// interpreters and the grid clear, templated on dimension, material and accumulation
+// (FP32 or deterministic fixed point).  The kernels_*.cu translation units each
+// instantiate a share of the variants so that they compile in parallel; the dispatch on
+// the runtime material and mode is in mpm_internal.h and here.
 #pragma once
 
 #include "mpm_internal.h"
@@ -16,45 +17,24 @@ cudaError_t allow_smem(K k, size_t smem) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int D, int MAT, int MODE>
+template <int D, int MAT, int MODE, bool DET>
 cudaError_t step_one(const SimParams& P, const StepArgs& A, int n_tiles, cudaStream_t s) {
-  const size_t smem = pass_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
-  auto k = step_kernel<D, MAT, MODE>;
+  const size_t smem = step_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
+  auto k = step_kernel<D, MAT, MODE, DET>;
   cudaError_t e = allow_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<n_tiles, kTile, smem, s>>>(P, A);
   return cudaGetLastError();
 }
 
-template <int D, int MAT, int MODE>
+template <int D, int MAT, int MODE, bool DET>
 cudaError_t adj_one(const SimParams& P, const AdjArgs& A, int n_tiles, cudaStream_t s) {
-  const size_t smem = pass_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
-  auto k = adjoint_kernel<D, MAT, MODE>;
+  const size_t smem = adj_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
+  auto k = adjoint_kernel<D, MAT, MODE, DET>;
   cudaError_t e = allow_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<n_tiles, kTile, smem, s>>>(P, A);
   return cudaGetLastError();
-}
-
-template <int D, int MAT>
-cudaError_t step_mat(int mode, const SimParams& P, const StepArgs& A, int n_tiles, cudaStream_t s) {
-  switch (mode) {
-    case kP2GOnly: return step_one<D, MAT, kP2GOnly>(P, A, n_tiles, s);
-    case kG2PP2G: return step_one<D, MAT, kG2PP2G>(P, A, n_tiles, s);
-    case kG2PP2GFull: return step_one<D, MAT, kG2PP2GFull>(P, A, n_tiles, s);
-    case kG2POnlyFull: return step_one<D, MAT, kG2POnlyFull>(P, A, n_tiles, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int D, int MAT>
-cudaError_t adj_mat(int mode, const SimParams& P, const AdjArgs& A, int n_tiles, cudaStream_t s) {
-  switch (mode) {
-    case kAdjG2P: return adj_one<D, MAT, kAdjG2P>(P, A, n_tiles, s);
-    case kAdjFused: return adj_one<D, MAT, kAdjFused>(P, A, n_tiles, s);
-    case kAdjP2G: return adj_one<D, MAT, kAdjP2G>(P, A, n_tiles, s);
-  }
-  return cudaErrorInvalidValue;
 }
 
 // Cooperative launch of a persistent pass interpreter: as many CTAs as can be resident
@@ -87,31 +67,37 @@ cudaError_t persistent_one(K k, size_t smem, const PassEntry* plan, int n_pass, 
 }
 }  // namespace
 
-template <int D>
-cudaError_t launch_step(int material, int mode, const SimParams& P, const StepArgs& A,
-                        int n_tiles, cudaStream_t s) {
-  return material == kFixedCorotated ? step_mat<D, kFixedCorotated>(mode, P, A, n_tiles, s)
-                                     : step_mat<D, kNeoHookean>(mode, P, A, n_tiles, s);
+template <int D, int MAT, bool DET>
+cudaError_t step_variant(int mode, const SimParams& P, const StepArgs& A, int n_tiles, cudaStream_t s) {
+  switch (mode) {
+    case kP2GOnly: return step_one<D, MAT, kP2GOnly, DET>(P, A, n_tiles, s);
+    case kG2PP2G: return step_one<D, MAT, kG2PP2G, DET>(P, A, n_tiles, s);
+    case kG2PP2GFull: return step_one<D, MAT, kG2PP2GFull, DET>(P, A, n_tiles, s);
+    case kG2POnlyFull: return step_one<D, MAT, kG2POnlyFull, DET>(P, A, n_tiles, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
-template <int D>
-cudaError_t launch_adjoint(int material, int mode, const SimParams& P, const AdjArgs& A,
-                           int n_tiles, cudaStream_t s) {
-  return material == kFixedCorotated ? adj_mat<D, kFixedCorotated>(mode, P, A, n_tiles, s)
-                                     : adj_mat<D, kNeoHookean>(mode, P, A, n_tiles, s);
+template <int D, int MAT, bool DET>
+cudaError_t adj_variant(int mode, const SimParams& P, const AdjArgs& A, int n_tiles, cudaStream_t s) {
+  switch (mode) {
+    case kAdjG2P: return adj_one<D, MAT, kAdjG2P, DET>(P, A, n_tiles, s);
+    case kAdjFused: return adj_one<D, MAT, kAdjFused, DET>(P, A, n_tiles, s);
+    case kAdjP2G: return adj_one<D, MAT, kAdjP2G, DET>(P, A, n_tiles, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
-template <int D>
-cudaError_t launch_persistent(int kind, int material, const SimParams& P, const PassEntry* plan,
-                              int n_pass, int n_tiles, const PersistCtl& ctl, cudaStream_t s,
-                              int* grid_out) {
-  const size_t smem = pass_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
-  const bool fcr = material == kFixedCorotated;
+template <int D, int MAT, bool DET>
+cudaError_t persistent_variant(int kind, const SimParams& P, const PassEntry* plan, int n_pass,
+                               int n_tiles, const PersistCtl& ctl, cudaStream_t s, int* grid_out) {
   if (kind == kPassStep)
-    return fcr ? persistent_one(step_persistent_kernel<D, kFixedCorotated>, smem, plan, n_pass, n_tiles, ctl, s, grid_out)
-               : persistent_one(step_persistent_kernel<D, kNeoHookean>, smem, plan, n_pass, n_tiles, ctl, s, grid_out);
-  return fcr ? persistent_one(adjoint_persistent_kernel<D, kFixedCorotated>, smem, plan, n_pass, n_tiles, ctl, s, grid_out)
-             : persistent_one(adjoint_persistent_kernel<D, kNeoHookean>, smem, plan, n_pass, n_tiles, ctl, s, grid_out);
+    return persistent_one(step_persistent_kernel<D, MAT, DET>,
+                          step_smem_bytes<D>(P.tile_capacity, P.gather_capacity), plan, n_pass, n_tiles,
+                          ctl, s, grid_out);
+  return persistent_one(adjoint_persistent_kernel<D, MAT, DET>,
+                        adj_smem_bytes<D>(P.tile_capacity, P.gather_capacity), plan, n_pass, n_tiles,
+                        ctl, s, grid_out);
 }
 
 template <int D>

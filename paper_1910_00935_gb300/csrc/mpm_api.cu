@@ -58,7 +58,7 @@ struct Layout {
   size_t rcache;  // (K+1) x [9][N] FP64 polar factors of a re-simulated segment (3D FCR)
   size_t grids;  // kPMSlots + kUBSlots dense grids
   size_t boxes;  // (kPMSlots + kUBSlots) x 2 parities x [scene][8]
-  size_t err, com, com_part;
+  size_t err, com, com_part, ub_m0;
   size_t plan_fwd, plan_bwd, gsync;  // persistent-form pass plans and barrier counters
   size_t total;
 };
@@ -67,13 +67,14 @@ struct Dims {
   int D, Q, S, K, n_ckpt, n_tiles, n_grid;
   int64_t N, nnodes;
   bool polar_cache;  // 3D fixed-corotated: FP64 polar factors are cached per segment
+  int words;         // float4 slots per grid node: 2 for fixed-point grids (deterministic)
   int T_max;         // max_steps
 };
 
 // passes of the longest forward (T + 1) and backward (re-simulation T + segments, adjoint
-// T + 1) sequences
+// T + 1, plus the measuring pass of the deterministic mode) sequences
 int64_t plan_fwd_cap(const Dims& m) { return (int64_t)m.T_max + 1; }
-int64_t plan_bwd_cap(const Dims& m) { return 2 * (int64_t)m.T_max + m.n_ckpt + 1; }
+int64_t plan_bwd_cap(const Dims& m) { return 2 * (int64_t)m.T_max + m.n_ckpt + 2; }
 
 bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
   auto fail = [&](const char* m) {
@@ -101,7 +102,7 @@ bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
   if (d->n_basis < 0 || d->n_basis > kMaxBasis) return fail("n_basis must be in [0, 8]");
   if (d->n_groups > 0 && (d->n_basis < 1 || !(d->act_period != 0.0f)))
     return fail("actuation needs n_basis >= 1 and act_period != 0");
-  if (d->deterministic_p2g != 0) return fail("deterministic_p2g is reserved (must be 0)");
+  if (d->deterministic_p2g != 0 && d->deterministic_p2g != 1) return fail("deterministic_p2g must be 0 or 1");
   if (max_steps < 1) return fail("max_steps must be >= 1");
   if (max_steps > (1 << 24)) return fail("max_steps too large");
   return true;
@@ -117,6 +118,7 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
   m.n_grid = d->n_grid;
   m.polar_cache = d->dim == 3 && d->material == MPM_FIXED_COROTATED;
   m.T_max = max_steps;
+  m.words = d->deterministic_p2g ? 2 : 1;
   m.nnodes = 1;
   for (int a = 0; a < m.D; ++a) m.nnodes *= d->n_grid;
   m.N = 0;
@@ -162,10 +164,11 @@ Layout make_layout(const Dims& m) {
   L.seg = take((size_t)(m.K + 1) * Q * N * 4);
   L.adj = take(Q * N * 4);
   L.rcache = m.polar_cache ? take((size_t)(m.K + 1) * 9 * N * 8) : take(0);
-  const size_t grid = S * (size_t)m.nnodes * sizeof(float4);
+  const size_t grid = S * (size_t)m.nnodes * sizeof(float4) * m.words;
   L.grids = take(grid * (kPMSlots + kUBSlots));
   L.boxes = take((size_t)(kPMSlots + kUBSlots) * 2 * S * 8 * 4);
   L.err = take(4);
+  L.ub_m0 = take(4);
   L.com = take(S * 6 * 8);
   L.com_part = take(com_scratch_doubles(m.S) * 8);
   L.plan_fwd = take((size_t)plan_fwd_cap(m) * sizeof(PassEntry));
@@ -270,9 +273,22 @@ SimParams params_for(const mpm_handle* h, int t) {
   for (int k = 1; k <= d.n_basis; ++k)
     P.basis[k - 1] =
         (float)std::sin(two_pi * k * (double)t / (double)d.act_period + (double)d.act_phase);
-  P.tile_capacity = h->smem_tile ? h->tile_capacity : 0;
+  // the shared scatter box sums in FP32 in arbitrary order: not in the deterministic mode
+  P.tile_capacity = h->smem_tile && !d.deterministic_p2g ? h->tile_capacity : 0;
   P.gather_capacity = h->gather_capacity;
   P.f_diag = 0.0f;  // the workspace holds E = F - I
+  P.det = d.deterministic_p2g;
+  P.node_words = h->m.words;
+  if (P.det) {
+    // fixed-point scales: a particle's mass maps to 2^40, momentum at the grid speed dx/dt
+    // to 2^40 (2^15 of headroom before the 2^55 limit, resolution 2^-40 of the unit)
+    const int em = 40 - (std::ilogb((double)P.p_mass) + 1);
+    const int ep = 40 - (std::ilogb((double)P.p_mass * (double)P.dx / (double)P.dt) + 1);
+    P.fix_m = std::ldexp(1.0f, em);
+    P.unfix_m = std::ldexp(1.0f, -em);
+    P.fix_p = std::ldexp(1.0f, ep);
+    P.unfix_p = std::ldexp(1.0f, -ep);
+  }
   return P;
 }
 
@@ -295,7 +311,7 @@ void ring_reset(Ring& r) {
 }
 
 float4* ring_grid(const mpm_handle* h, const Ring& r, int id) {
-  return h->at<float4>(h->L.grids) + (size_t)(r.first + id) * h->m.S * h->m.nnodes;
+  return h->at<float4>(h->L.grids) + (size_t)(r.first + id) * h->m.S * h->m.nnodes * h->m.words;
 }
 
 int* ring_box(const mpm_handle* h, const Ring& r, int id, int parity) {
@@ -331,6 +347,7 @@ void ring_release(Ring& r, int id) {
 Clears take_clears(mpm_handle* h) {
   Clears C;
   memset(&C, 0, sizeof(C));
+  C.words = h->m.words;
   for (Ring* r : {&h->pm, &h->ub})
     for (int i = 0; i < r->n && C.n < kMaxClears; ++i)
       if (r->state[i] == 2) {
@@ -504,7 +521,7 @@ struct Launcher {
   // when stm != null, the recomputed grid of step s-1 (*pm_written)
   cudaError_t adjoint(int amode, int s_step, const float* st1, const float* st0, const float* stm,
                       int pm1, int ub1, int pm0, int* ub_written, int* pm_written,
-                      const double* R1 = nullptr, const double* Rm = nullptr) {
+                      const double* R1 = nullptr, const double* Rm = nullptr, int measure = 0) {
     const Dims& m = h->m;
     SimParams P = params_for(h, s_step + 1);
     SimParams P2 = params_for(h, s_step - 1 >= 0 ? s_step - 1 : 0);
@@ -528,6 +545,8 @@ struct Launcher {
     A.err = h->at<unsigned>(h->L.err);
     A.R1 = R1;
     A.Rm = Rm;
+    A.ub_m0 = h->at<unsigned>(h->L.ub_m0);
+    A.measure = measure;
     if (pm1 >= 0) A.PM1 = ring_grid(h, h->pm, pm1);
     if (ub1 >= 0) A.UB1 = ring_grid(h, h->ub, ub1);
     if (pm0 >= 0) A.PM0 = ring_grid(h, h->pm, pm0);
@@ -667,6 +686,9 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T) {
     // was never the P2G input of this re-simulation), state s-1 always when present
     const double* R1 = (s + 1 < top) ? h->rslot(s + 1 - s0) : nullptr;
     const double* Rm = (s - 1 >= s0) ? h->rslot(s - 1 - s0) : nullptr;
+    if (s == T - 1 && h->m.words == 2)  // deterministic: bound of the first ubar scatter
+      LK(Lc.adjoint(kAdjG2P, s, st_s1, st_s, nullptr, -1, -1, pm_s, nullptr, nullptr, nullptr,
+                    nullptr, 1));
     LK(Lc.adjoint(s == T - 1 ? kAdjG2P : kAdjFused, s, st_s1, st_s, st_sm,
                   s == T - 1 ? -1 : pm_s1, s == T - 1 ? -1 : ub_s1, pm_s, &ub_s, &pm_sm, R1, Rm));
     ring_release(h->pm, pm_s1);
@@ -861,7 +883,7 @@ int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float
                            h->at<float>(L.E), h->at<float>(L.nu), h->at<int>(L.group), s));
   const size_t wbytes = (size_t)m.S * h->desc.n_groups * h->desc.n_basis * sizeof(float);
   if (wbytes) CK(cudaMemcpyAsync(h->at<float>(L.wact), w, wbytes, cudaMemcpyDeviceToDevice, s));
-  const size_t grid = (size_t)m.S * m.nnodes * sizeof(float4);
+  const size_t grid = (size_t)m.S * m.nnodes * sizeof(float4) * m.words;
   CK(cudaMemsetAsync(h->at<char>(L.grids), 0, grid * (kPMSlots + kUBSlots), s));
   CK(launch_reset_boxes(h->at<int>(L.boxes), (int64_t)(kPMSlots + kUBSlots) * 2 * m.S, s));
   ring_reset(h->pm);
@@ -949,6 +971,7 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   CK(cudaMemsetAsync(h->at<float>(L.mubar), 0, (size_t)m.N * 4, s));
   CK(cudaMemsetAsync(h->at<float>(L.labar), 0, (size_t)m.N * 4, s));
   const int GK = h->desc.n_groups * h->desc.n_basis;
+  if (m.words == 2) CK(cudaMemsetAsync(h->at<unsigned>(L.ub_m0), 0, 4, s));
   if (GK) CK(cudaMemsetAsync(h->at<float>(L.wbar_tile), 0, (size_t)m.n_tiles * GK * 4, s));
   h->launches += 4;
   const int T = h->T_recorded;
@@ -986,6 +1009,8 @@ int mpm_sync_status(mpm_handle* h) {
     cudaMemset(h->at<unsigned>(h->L.err), 0, 4);
     if (err & kErrOOB) return fail(h, MPM_ERR_OOB, "a particle's stencil left the grid");
     if (err & kErrNonFinite) return fail(h, MPM_ERR_NONFINITE, "non-finite value or det F <= 0");
+    if (err & kErrRange)
+      return fail(h, MPM_ERR_RANGE, "deterministic mode: a fixed-point grid contribution left its range");
     if (err & kErrTimeout) {
       // passes after the barrier that gave up never ran: grid buffers may be dirty
       h->initialized = false;

@@ -40,6 +40,7 @@ constexpr int kMaxGroups = 8;
 constexpr unsigned kErrOOB = 1u;
 constexpr unsigned kErrNonFinite = 2u;
 constexpr unsigned kErrTimeout = 4u;
+constexpr unsigned kErrRange = 8u;  // a fixed-point grid contribution left its range
 
 enum Material : int { kFixedCorotated = 0, kNeoHookean = 1 };
 
@@ -58,7 +59,68 @@ struct SimParams {
   int tile_capacity;       // max nodes of a CTA's shared scatter box (0 = global reductions)
   int gather_capacity;     // max nodes of a CTA's shared gather box (0 = gathers through L1)
   float f_diag;            // the F rows of the state hold F - f_diag I (0: E = F - I, 1: F)
+  // deterministic accumulation: grids hold 64-bit fixed-point sums (node_words = 2 float4
+  // slots per node), channel c of a contribution v enters as round(v * fix_c); mass uses
+  // fix_m, momentum fix_p (the velocity adjoint's scale is set per backward on the device)
+  int det;
+  int node_words;          // float4 slots per grid node: 1 (FP32 sums) or 2 (fixed point)
+  float fix_m, fix_p, unfix_m, unfix_p;
 };
+
+// ---------------------------------------------------------------------------
+// 64-bit fixed-point grid nodes (deterministic mode).  Integer addition is associative,
+// so the node sums, and everything computed from them, do not depend on the order in
+// which particles add their contributions.  A contribution is rounded once,
+// round(v * 2^e); a contribution beyond 2^55 (so that 256 of them cannot overflow the
+// 64-bit sum) is refused and flagged instead.
+// ---------------------------------------------------------------------------
+constexpr float kFixLimit = 36028797018963968.0f;  // 2^55
+
+// channels 0..nch-1 of v into the fixed-point node `node` of grid g (two float4 slots
+// per node); channel 0 is scaled by f0, the others by f1
+__device__ __forceinline__ void fix_red(float4* g, int64_t node, float4 v, float f0, float f1,
+                                        int nch, unsigned& err) {
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(g + 2 * node);
+  const float c[4] = {v.x * f0, v.y * f1, v.z * f1, v.w * f1};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k >= nch || c[k] == 0.0f) continue;
+    if (!(fabsf(c[k]) <= kFixLimit)) {
+      err |= kErrRange;
+      continue;
+    }
+    atomicAdd(q + k, (unsigned long long)__float2ll_rn(c[k]));
+  }
+}
+
+// the fixed-point node as floats: channel 0 times u0, the others times u1
+template <bool NC>
+__device__ __forceinline__ float4 fix_load(const float4* g, int64_t node, float u0, float u1) {
+  const longlong2* q = reinterpret_cast<const longlong2*>(g + 2 * node);
+  longlong2 a, b;
+  if (NC) {
+    a = __ldg(q);
+    b = __ldg(q + 1);
+  } else {
+    a = q[0];
+    b = q[1];
+  }
+  return make_float4((float)((double)a.x * (double)u0), (float)((double)a.y * (double)u1),
+                     (float)((double)b.x * (double)u1), (float)((double)b.y * (double)u1));
+}
+
+// scale pair of the velocity-adjoint grids of one backward from the largest contribution
+// bound m0 of its first scatter: m0 maps to below 2^36, leaving 2^19 of growth before the
+// 2^55 limit and 2^-36 m0 resolution
+__device__ __forceinline__ void fix_scales_from(float m0, float& fix, float& unfix) {
+  int k = 0;
+  if (m0 > 0.0f && m0 <= 3.0e38f) {
+    k = 36 - (ilogbf(m0) + 1);
+    k = k > 120 ? 120 : (k < -120 ? -120 : k);
+  }
+  fix = ldexpf(1.0f, k);
+  unfix = ldexpf(1.0f, -k);
+}
 
 // ---------------------------------------------------------------------------
 // quadratic B-spline stencil (MLS-MPM, Hu et al. 2018), kept per axis: the weight of

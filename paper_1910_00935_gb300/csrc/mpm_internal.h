@@ -16,23 +16,50 @@ struct Clears;
 struct PassEntry;
 struct PersistCtl;
 
-// kernels_2d.cu / kernels_3d.cu (templated on dimension)
-template <int D>
-cudaError_t launch_step(int material, int mode, const SimParams& P, const StepArgs& A, int n_tiles,
-                        cudaStream_t s);
-template <int D>
-cudaError_t launch_adjoint(int material, int mode, const SimParams& P, const AdjArgs& A, int n_tiles,
-                           cudaStream_t s);
+// kernels_*.cu (templates in kernels_launch.cuh; DET: deterministic fixed-point grids)
+template <int D, int MAT, bool DET>
+cudaError_t step_variant(int mode, const SimParams& P, const StepArgs& A, int n_tiles, cudaStream_t s);
+template <int D, int MAT, bool DET>
+cudaError_t adj_variant(int mode, const SimParams& P, const AdjArgs& A, int n_tiles, cudaStream_t s);
 // one cooperative launch running plan[0..n_pass) (all of PassKind `kind`) with a bounded
 // grid barrier between passes; P supplies the shared-memory capacities; *grid_out gets
 // the CTA count
-template <int D>
-cudaError_t launch_persistent(int kind, int material, const SimParams& P, const PassEntry* plan,
-                              int n_pass, int n_tiles, const PersistCtl& ctl, cudaStream_t s,
-                              int* grid_out);
+template <int D, int MAT, bool DET>
+cudaError_t persistent_variant(int kind, const SimParams& P, const PassEntry* plan, int n_pass,
+                               int n_tiles, const PersistCtl& ctl, cudaStream_t s, int* grid_out);
 template <int D>
 cudaError_t launch_clear(const Clears& C, int nnodes, int n_grid, int n_scenes, int blocks_per_scene,
                          cudaStream_t s);
+
+// dispatch on the runtime material and accumulation mode (P.det)
+template <int D>
+inline cudaError_t launch_step(int material, int mode, const SimParams& P, const StepArgs& A,
+                               int n_tiles, cudaStream_t s) {
+  if (material == kFixedCorotated)
+    return P.det ? step_variant<D, kFixedCorotated, true>(mode, P, A, n_tiles, s)
+                 : step_variant<D, kFixedCorotated, false>(mode, P, A, n_tiles, s);
+  return P.det ? step_variant<D, kNeoHookean, true>(mode, P, A, n_tiles, s)
+               : step_variant<D, kNeoHookean, false>(mode, P, A, n_tiles, s);
+}
+template <int D>
+inline cudaError_t launch_adjoint(int material, int mode, const SimParams& P, const AdjArgs& A,
+                                  int n_tiles, cudaStream_t s) {
+  if (material == kFixedCorotated)
+    return P.det ? adj_variant<D, kFixedCorotated, true>(mode, P, A, n_tiles, s)
+                 : adj_variant<D, kFixedCorotated, false>(mode, P, A, n_tiles, s);
+  return P.det ? adj_variant<D, kNeoHookean, true>(mode, P, A, n_tiles, s)
+               : adj_variant<D, kNeoHookean, false>(mode, P, A, n_tiles, s);
+}
+template <int D>
+inline cudaError_t launch_persistent(int kind, int material, const SimParams& P, const PassEntry* plan,
+                                     int n_pass, int n_tiles, const PersistCtl& ctl, cudaStream_t s,
+                                     int* grid_out) {
+  if (material == kFixedCorotated)
+    return P.det ? persistent_variant<D, kFixedCorotated, true>(kind, P, plan, n_pass, n_tiles, ctl, s, grid_out)
+                 : persistent_variant<D, kFixedCorotated, false>(kind, P, plan, n_pass, n_tiles, ctl, s, grid_out);
+  return P.det ? persistent_variant<D, kNeoHookean, true>(kind, P, plan, n_pass, n_tiles, ctl, s, grid_out)
+               : persistent_variant<D, kNeoHookean, false>(kind, P, plan, n_pass, n_tiles, ctl, s, grid_out);
+}
 
 // setup.cu
 size_t sort_temp_bytes(int64_t n);

@@ -55,6 +55,7 @@ constexpr int kMaxClears = 3;
 struct Clears {
   ClearJob job[kMaxClears];
   int n;
+  int words;  // float4 slots per node (1, or 2 for fixed-point grids)
 };
 
 struct StepArgs {
@@ -98,6 +99,10 @@ struct AdjArgs {
   int* box_ub;
   int* box_ub_reset;
   float4* PMm;        // grid of step s-1 (recomputed P2G) or null
+  unsigned* ub_m0;    // deterministic mode: largest velocity-adjoint contribution bound of
+                      // the backward's first scatter (FP32 bits; the measuring pass raises it,
+                      // every pass derives the fixed-point scale of the ubar grids from it)
+  int measure;        // 1: this kAdjG2P pass only measures that bound (no scatter, no writes)
   const double* R1;   // [9][N] cached FP64 polar factors of state s+1 (or null: recompute)
   const double* Rm;   // same for state s-1
   int* box_m;
@@ -116,6 +121,35 @@ __device__ __forceinline__ float4 grid_load(const float4* p) {
   return *p;
 }
 
+// node `node` of a scene's (m, p) grid as floats (DET: fixed-point grid)
+template <bool NC, bool DET>
+__device__ __forceinline__ float4 pm_load(const float4* g, int64_t node, const SimParams& P) {
+  if (DET) return fix_load<NC>(g, node, P.unfix_m, P.unfix_p);
+  return grid_load<NC>(g + node);
+}
+// fixed-point scale pair of this backward's velocity-adjoint grids (deterministic mode)
+__device__ __forceinline__ void ub_scales(const unsigned* m0, float& fix, float& unfix) {
+  fix_scales_from(__uint_as_float(*(const volatile unsigned*)m0), fix, unfix);
+}
+// node of a scene's velocity-adjoint grid
+template <bool NC, bool DET>
+__device__ __forceinline__ float4 ub_load(const float4* g, int64_t node, const SimParams& P,
+                                          const unsigned* m0) {
+  if (DET) {
+    float fix, unfix;
+    ub_scales(m0, fix, unfix);
+    return fix_load<NC>(g, node, unfix, unfix);
+  }
+  return grid_load<NC>(g + node);
+}
+// a scene's grid inside a buffer of per-scene grids
+__device__ __forceinline__ float4* scene_grid(float4* g, int scene, const SimParams& P) {
+  return g + (int64_t)scene * P.nnodes * P.node_words;
+}
+__device__ __forceinline__ const float4* scene_grid(const float4* g, int scene, const SimParams& P) {
+  return g + (int64_t)scene * P.nnodes * P.node_words;
+}
+
 template <int D>
 struct Rows {
   static constexpr int X = 0, V = D, C = 2 * D, F = 2 * D + D * D, Q = 2 * D + 2 * D * D;
@@ -131,6 +165,29 @@ struct Xch {
 // per-warp group sums of the dL/dw reduction
 constexpr int kWbarSlots = (kTile / 32) * kMaxGroups;
 
+// Particle rows staged ahead of use with asynchronous copies (cp.async, no registers held
+// while in flight): stage row r holds component r of the CTA's particles at
+// [r * kTile + threadIdx.x]; each thread copies and later reads only its own column.
+template <int D>
+struct Stage {
+  static constexpr int kStep = 2;                   // mu, la (read by the P2G stress)
+  static constexpr int kAdjB = D + D * D;           // x, F rows of state s (G2P-adjoint)
+  static constexpr int kAdjC = 2 * D + 2 * D * D;   // full state s-1 (recomputed P2G)
+  static constexpr int kAdj = kAdjB + kAdjC + 2;    // + mu, la
+};
+__device__ __forceinline__ void stage_row(float* stage, int r, const float* src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(stage + r * kTile + threadIdx.x);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's copy groups are still in flight (the passes use
+// N = 0 before the first read of any staged row)
+template <int N>
+__device__ __forceinline__ void stage_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float staged(const float* stage, int r) { return stage[r * kTile + threadIdx.x]; }
+
 __device__ __forceinline__ int scatter_slot(int t) { return (t & 31) * (kTile / 32) + (t >> 5); }
 __device__ __forceinline__ int xidx(int j) { return j + (j >> 3); }
 
@@ -144,6 +201,15 @@ template <int D>
 inline size_t pass_smem_bytes(int scatter_cap, int gather_cap) {
   return sizeof(float) * ((size_t)box_floats(scatter_cap, gather_cap) +
                           (size_t)Xch<D>::kWidth * Xch<D>::kStride);
+}
+// + the staged rows of a forward / adjoint pass
+template <int D>
+inline size_t step_smem_bytes(int scatter_cap, int gather_cap) {
+  return pass_smem_bytes<D>(scatter_cap, gather_cap) + sizeof(float) * Stage<D>::kStep * kTile;
+}
+template <int D>
+inline size_t adj_smem_bytes(int scatter_cap, int gather_cap) {
+  return pass_smem_bytes<D>(scatter_cap, gather_cap) + sizeof(float) * Stage<D>::kAdj * kTile;
 }
 
 // Scene bounding box of the nodes a scatter touches: each warp reduces its valid lanes
@@ -371,10 +437,11 @@ __device__ __forceinline__ void put_record(float* xr, bool valid, const int base
 //   mass  W * mass_c                      (when WITH_MASS)
 //   vec   W * (a + B dpos)
 // into the shared box (or global memory g when the box did not fit).
-template <int D, bool WITH_MASS>
+template <int D, bool WITH_MASS, bool DET>
 __device__ __forceinline__ void scatter_records(const float* xr, int count, const BoxInfo<D>& bx,
                                                 float* sm, int cap, float4* g, int n,
-                                                const SimParams& P, float mass_c) {
+                                                const SimParams& P, float mass_c, float fix0,
+                                                float fix1, unsigned& err) {
   constexpr int S = Xch<D>::kStride;
   const int j = scatter_slot(threadIdx.x);
   if (j >= count) return;
@@ -442,6 +509,19 @@ __device__ __forceinline__ void scatter_records(const float* xr, int count, cons
         }
       }
     }
+  } else if (DET) {
+    const int64_t nb = node_flat<D>(base, n);
+    for_nodes<D>(w, [&](int i, int jj, int k, float W) {
+      float q[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        q[c] = a[c] + B[c][0] * dp[0][i] + B[c][1] * dp[1][jj];
+        if (D == 3) q[c] += B[c][D - 1] * dp[D - 1][k];
+      }
+      float4 v = WITH_MASS ? make_float4(W * mass_c, W * q[0], W * q[1], D == 3 ? W * q[2] : 0.0f)
+                           : make_float4(W * q[0], W * q[1], D == 3 ? W * q[2] : 0.0f, 0.0f);
+      fix_red(g, nb + stencil_off<D>(i, jj, k, n), v, fix0, fix1, WITH_MASS ? D + 1 : D, err);
+    });
   } else {
     float4* gb = g + node_flat<D>(base, n);
     for_nodes<D>(w, [&](int i, int jj, int k, float W) {
@@ -495,34 +575,37 @@ __device__ __forceinline__ bool is_wall(const int idx[D], const SimParams& P) {
   return wall;
 }
 
-// grid_op: v = p/m + dt g for m > 0 off the sticky walls, else 0 (w keeps m)
+// grid_op: v = p/m + dt g for m > 0 off the sticky walls, else 0 (w keeps m).  Rounding is
+// spelled out (no compiler-chosen contraction), so a node gives the same bits whether it
+// is staged in the shared gather box or read directly.
 template <int D>
 __device__ __forceinline__ float4 node_velocity(float4 pm, const int idx[D], const SimParams& P) {
   float4 u = make_float4(0.0f, 0.0f, 0.0f, pm.x);
   if (pm.x > 0.0f && !is_wall<D>(idx, P)) {
-    const float im = 1.0f / pm.x;
-    u.x = pm.y * im + P.dt * P.gravity[0];
-    u.y = pm.z * im + P.dt * P.gravity[1];
-    if (D == 3) u.z = pm.w * im + P.dt * P.gravity[2];
+    const float im = __fdiv_rn(1.0f, pm.x);
+    u.x = __fmaf_rn(pm.y, im, __fmul_rn(P.dt, P.gravity[0]));
+    u.y = __fmaf_rn(pm.z, im, __fmul_rn(P.dt, P.gravity[1]));
+    if (D == 3) u.z = __fmaf_rn(pm.w, im, __fmul_rn(P.dt, P.gravity[2]));
   }
   return u;
 }
 
 // grid_op.grad: pbar = ubar / m and mbar = -ubar . (p / m) / m for m > 0 off the walls
+// (rounding spelled out as in node_velocity)
 template <int D>
 __device__ __forceinline__ float4 node_adjoint(float4 ub, float4 pm, const int idx[D],
                                                const SimParams& P) {
   float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (pm.x > 0.0f && !is_wall<D>(idx, P)) {
-    const float im = 1.0f / pm.x;
-    r.x = ub.x * im;
-    r.y = ub.y * im;
-    float dot = ub.x * pm.y + ub.y * pm.z;
+    const float im = __fdiv_rn(1.0f, pm.x);
+    r.x = __fmul_rn(ub.x, im);
+    r.y = __fmul_rn(ub.y, im);
+    float dot = __fmaf_rn(ub.y, pm.z, __fmul_rn(ub.x, pm.y));
     if (D == 3) {
-      r.z = ub.z * im;
-      dot += ub.z * pm.w;
+      r.z = __fmul_rn(ub.z, im);
+      dot = __fmaf_rn(ub.z, pm.w, dot);
     }
-    r.w = -dot * im * im;
+    r.w = __fmul_rn(__fmul_rn(-dot, im), im);
   }
   return r;
 }
@@ -546,7 +629,8 @@ __device__ __forceinline__ void run_clears(const Clears& C, int scene, int rank,
       ext[a] = hi >= lo[a] ? hi - lo[a] + 1 : 0;
       vol *= ext[a];
     }
-    float4* g = C.job[c].grid + (int64_t)scene * nnodes;
+    const int w = C.words;
+    float4* g = C.job[c].grid + (int64_t)scene * nnodes * w;
     for (int l = rank * blockDim.x + threadIdx.x; l < vol; l += nranks * blockDim.x) {
       int idx[D], r = l;
 #pragma unroll
@@ -554,7 +638,9 @@ __device__ __forceinline__ void run_clears(const Clears& C, int scene, int rank,
         idx[a] = lo[a] + r % ext[a];
         r /= ext[a];
       }
-      g[node_flat<D>(idx, n)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float4* q = g + (int64_t)node_flat<D>(idx, n) * w;
+      q[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (w == 2) q[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
   }
 }
@@ -568,11 +654,11 @@ __device__ __forceinline__ void reset_box(int* box, int scene) {
 // (m, m v + A dpos) into the scene grid g, fold the touched box into box_scene.
 // Every thread calls it; s_bbox must have been reset before an earlier barrier.
 // ---------------------------------------------------------------------------
-template <int D, int MAT>
+template <int D, int MAT, bool DET>
 __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis, bool active, int scene,
                                          int64_t p, int count, const float x[D], const float v[D],
-                                         const float C[D][D], const float E[D][D], const float* mu,
-                                         const float* la, const int* group, const float* wact,
+                                         const float C[D][D], const float E[D][D], float mu_p,
+                                         float la_p, const int* group, const float* wact,
                                          float4* g, int* box_scene, float* sm, float* xr,
                                          int* s_box, int* s_bbox, unsigned& err,
                                          const double* R_in, double* R_out, int64_t N) {
@@ -591,7 +677,7 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
     const float act = particle_act(P, basis, group, wact, scene, p, D, axis);
     float tau[D][D];
     StressCache<D> sc;
-    if (!kirchhoff<D, MAT>(E, mu[p], la[p], act, axis, tau, sc, R_in, N, p)) {
+    if (!kirchhoff<D, MAT>(E, mu_p, la_p, act, axis, tau, sc, R_in, N, p)) {
       err |= kErrNonFinite;
       ok = false;
     }
@@ -608,7 +694,8 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
   if (P.tile_capacity > 0) {
     const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
     box_zero<D>(bx, sm, P.tile_capacity);
-    scatter_records<D, true>(xr, count, bx, sm, P.tile_capacity, g, P.n_grid, P, P.p_mass);
+    scatter_records<D, true, DET>(xr, count, bx, sm, P.tile_capacity, g, P.n_grid, P, P.p_mass, P.fix_m,
+                             P.fix_p, err);
     box_flush<D>(bx, sm, P.tile_capacity, g, P.n_grid);
     if (threadIdx.x == 0 && bx.vol > 0) {
 #pragma unroll
@@ -623,7 +710,7 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
     cta_bbox_flush<D>(s_bbox, box_scene);
     BoxInfo<D> none;
     none.use_tile = false;
-    scatter_records<D, true>(xr, count, none, sm, 0, g, P.n_grid, P, P.p_mass);
+    scatter_records<D, true, DET>(xr, count, none, sm, 0, g, P.n_grid, P, P.p_mass, P.fix_m, P.fix_p, err);
   }
 }
 
@@ -633,7 +720,7 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
 // One tile of a forward pass; every thread of the CTA calls it.  sm: dynamic shared memory
 // (pass_smem_bytes), s_box / s_bbox: 8 ints each.  A CTA that runs several tiles must
 // synchronise between them.
-template <int D, int MAT, int MODE, bool NC>
+template <int D, int MAT, int MODE, bool NC, bool DET>
 __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A, int tile_index,
                                           float* sm, int* s_box, int* s_bbox) {
   using R = Rows<D>;
@@ -648,6 +735,12 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
   unsigned err = 0;
   run_clears<D>(A.clears, scene, tile.w, A.scene_tiles[scene], P.nnodes, n);
   if (tile.w == 0) reset_box(A.box_reset, scene);
+  float* stage = xr + Xch<D>::kWidth * Xch<D>::kStride;
+  if (MODE != kG2POnlyFull) {
+    stage_row(stage, 0, A.mu + p);
+    stage_row(stage, 1, A.la + p);
+  }
+  stage_commit();
   __syncthreads();  // s_bbox reset
 
   float x[D], v[D], C[D][D], E[D][D];
@@ -677,8 +770,8 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
 #pragma unroll
       for (int b = 0; b < D; ++b) B[a][b] = 0.0f;
     }
-    const float4* PMg = A.PMr + (int64_t)scene * P.nnodes;
-    auto velocity = [&](const int idx[D]) { return node_velocity<D>(grid_load<NC>(PMg + node_flat<D>(idx, n)), idx, P); };
+    const float4* PMg = scene_grid(A.PMr, scene, P);
+    auto velocity = [&](const int idx[D]) { return node_velocity<D>(pm_load<NC, DET>(PMg, node_flat<D>(idx, n), P), idx, P); };
     BoxInfo<D> gbx;
     gbx.use_tile = false;
     if (P.gather_capacity > 0) {
@@ -736,19 +829,23 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
     }
   }
 
-  if (MODE != kG2POnlyFull)
-    p2g_pass<D, MAT>(P, P.basis, active, scene, p, tile.z, x, v, C, E, A.mu, A.la, A.group, A.wact,
-                     A.PMw + (int64_t)scene * P.nnodes, A.box_w + scene * 8, sm, xr, s_box, s_bbox,
+  if (MODE != kG2POnlyFull) {
+    stage_wait<0>();
+    p2g_pass<D, MAT, DET>(P, P.basis, active, scene, p, tile.z, x, v, C, E, staged(stage, 0),
+                          staged(stage, 1), A.group, A.wact,
+                     scene_grid(A.PMw, scene, P), A.box_w + scene * 8, sm, xr, s_box, s_bbox,
                      err, nullptr, A.Rw, N);
+  }
   if (err) atomicOr(A.err, err);
 }
 
-template <int D, int MAT, int MODE>
-__global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D) step_kernel(const __grid_constant__ SimParams P, const __grid_constant__ StepArgs A) {
+template <int D, int MAT, int MODE, bool DET>
+__global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D)
+    step_kernel(const __grid_constant__ SimParams P, const __grid_constant__ StepArgs A) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8];
   __shared__ int s_bbox[8];
-  step_tile<D, MAT, MODE, true>(P, A, blockIdx.x, sm, s_box, s_bbox);
+  step_tile<D, MAT, MODE, true, DET>(P, A, blockIdx.x, sm, s_box, s_bbox);
 }
 
 // ---------------------------------------------------------------------------
@@ -756,7 +853,7 @@ __global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_
 // [recomputed P2G of step s-1, the grid the next adjoint pass needs (Appendix D.1)]
 // ---------------------------------------------------------------------------
 // One tile of an adjoint pass (same calling rules as step_tile; s_wbar: kWbarSlots floats).
-template <int D, int MAT, int MODE, bool NC>
+template <int D, int MAT, int MODE, bool NC, bool DET>
 __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& A, int tile_index,
                                              float* sm, int* s_box, int* s_bbox_ub, int* s_bbox_pm,
                                              float* s_wbar) {
@@ -778,6 +875,23 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     reset_box(A.box_m_reset, scene);
   }
   __syncthreads();  // shared boxes reset
+  // stage what the G2P-adjoint (state s: x, F) and the recomputed P2G (state s-1, mu, la)
+  // read, so that those loads are in flight during the P2G-adjoint
+  float* stage = xr + Xch<D>::kWidth * Xch<D>::kStride;
+  if (MODE != kAdjP2G) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) stage_row(stage, a, A.st0 + (int64_t)(R::X + a) * N + p);
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) stage_row(stage, D + i, A.st0 + (int64_t)(R::F + i) * N + p);
+  }
+  stage_commit();
+  if (MODE != kAdjP2G && A.stm) {  // the recomputed P2G runs whenever state s-1 is given
+#pragma unroll
+    for (int r = 0; r < R::Q; ++r) stage_row(stage, Stage<D>::kAdjB + r, A.stm + (int64_t)r * N + p);
+    stage_row(stage, Stage<D>::kAdjB + R::Q, A.mu + p);
+    stage_row(stage, Stage<D>::kAdjB + R::Q + 1, A.la + p);
+  }
+  stage_commit();
 
   // adjoint of state s+1: xb, vb, Cb, Fb (Fb = dL/dE = dL/dF)
   float xb[D], vb[D], Cb[D][D], Fb[D][D];
@@ -834,11 +948,11 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
 #pragma unroll
       for (int b = 0; b < D; ++b) Ab[a][b] = 0.0f;
     }
-    const float4* UBg = A.UB1 + (int64_t)scene * P.nnodes;
-    const float4* PMg = A.PM1 + (int64_t)scene * P.nnodes;
+    const float4* UBg = scene_grid(A.UB1, scene, P);
+    const float4* PMg = scene_grid(A.PM1, scene, P);
     auto pbar = [&](const int idx[D]) {
       const int f = node_flat<D>(idx, n);
-      return node_adjoint<D>(grid_load<NC>(UBg + f), grid_load<NC>(PMg + f), idx, P);
+      return node_adjoint<D>(ub_load<NC, DET>(UBg, f, P, A.ub_m0), pm_load<NC, DET>(PMg, f, P), idx, P);
     };
     BoxInfo<D> gbx;
     gbx.use_tile = false;
@@ -969,8 +1083,13 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
   {
     float x0[D], E0[D][D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) x0[a] = A.st0[(R::X + a) * N + p];
-    load_E<D>(A.st0, N, p, P.f_diag, E0);
+    stage_wait<0>();
+#pragma unroll
+    for (int a = 0; a < D; ++a) x0[a] = staged(stage, a);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) E0[i][j] = staged(stage, D + i * D + j) - (i == j ? P.f_diag : 0.0f);
     float vt[D], Ct[D][D], Fb0[D][D], xb0[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -993,8 +1112,30 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     Axes<D> s;
     const bool ok = make_axes<D>(x0, P, s) && active;
     if (active && !ok) err |= kErrOOB;
-    const float4* PMg = A.PM0 + (int64_t)scene * P.nnodes;
-    auto velocity = [&](const int idx[D]) { return node_velocity<D>(grid_load<NC>(PMg + node_flat<D>(idx, n)), idx, P); };
+    if (MODE == kAdjG2P && DET && A.measure) {
+      // bound of this particle's ubar contributions W (vt + c4 Ct dpos), W <= 1, |dpos| <= 1.5 dx
+      float bound = 0.0f;
+      if (ok) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float r = fabsf(vt[a]);
+#pragma unroll
+          for (int b = 0; b < D; ++b) r += 1.5f * P.dx * c4 * fabsf(Ct[a][b]);
+          bound = fmaxf(bound, r);
+        }
+        if (!(bound <= 3.0e38f)) {
+          err |= kErrNonFinite;
+          bound = 0.0f;
+        }
+      }
+      // non-negative floats order like their bit patterns
+      const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(bound));
+      if ((threadIdx.x & 31) == 0 && mb != 0u) atomicMax(A.ub_m0, mb);
+      if (err) atomicOr(A.err, err);
+      return;
+    }
+    const float4* PMg = scene_grid(A.PM0, scene, P);
+    auto velocity = [&](const int idx[D]) { return node_velocity<D>(pm_load<NC, DET>(PMg, node_flat<D>(idx, n), P), idx, P); };
     const int cap_box = P.tile_capacity > P.gather_capacity ? P.tile_capacity : P.gather_capacity;
     BoxInfo<D> bx;
     bx.use_tile = false;
@@ -1064,13 +1205,15 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) Bs[i][j] = c4 * Ct[i][j];
-    float4* UBs = A.UB0 + (int64_t)scene * P.nnodes;
+    float4* UBs = scene_grid(A.UB0, scene, P);
+    float fix_u = 1.0f, unfix_u = 1.0f;
+    if (DET) ub_scales(A.ub_m0, fix_u, unfix_u);
     put_record<D>(xr, ok, s.base, s.f, vt, Bs);
     if (P.tile_capacity > 0) {
       BoxInfo<D> sbx = bx;
       sbx.use_tile = bx.use_tile && bx.vol <= P.tile_capacity;
       box_zero<D>(sbx, sm, P.tile_capacity);  // same extent as the gather box
-      scatter_records<D, false>(xr, tile.z, sbx, sm, P.tile_capacity, UBs, n, P, 0.0f);
+      scatter_records<D, false, DET>(xr, tile.z, sbx, sm, P.tile_capacity, UBs, n, P, 0.0f, fix_u, fix_u, err);
       box_flush<D>(sbx, sm, P.tile_capacity, UBs, n);
       if (threadIdx.x == 0 && sbx.vol > 0) {
 #pragma unroll
@@ -1085,36 +1228,43 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
       cta_bbox_flush<D>(s_bbox_ub, A.box_ub + scene * 8);
       BoxInfo<D> none;
       none.use_tile = false;
-      scatter_records<D, false>(xr, tile.z, none, sm, 0, UBs, n, P, 0.0f);
+      scatter_records<D, false, DET>(xr, tile.z, none, sm, 0, UBs, n, P, 0.0f, fix_u, fix_u, err);
     }
   }
 
   // ---- recomputed P2G of step s-1 (the grid of the next adjoint pass) ----
   if (A.stm) {
     float x[D], v[D], C[D][D], E[D][D];
+    stage_wait<0>();
+    constexpr int b = Stage<D>::kAdjB;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      x[a] = A.stm[(R::X + a) * N + p];
-      v[a] = A.stm[(R::V + a) * N + p];
+      x[a] = staged(stage, b + R::X + a);
+      v[a] = staged(stage, b + R::V + a);
     }
 #pragma unroll
-    for (int i = 0; i < D * D; ++i) C[i / D][i % D] = A.stm[(R::C + i) * N + p];
-    load_E<D>(A.stm, N, p, P.f_diag, E);
-    p2g_pass<D, MAT>(P, P.basis2, active, scene, p, tile.z, x, v, C, E, A.mu, A.la, A.group, A.wact,
-                     A.PMm + (int64_t)scene * P.nnodes, A.box_m + scene * 8, sm, xr, s_box, s_bbox_pm,
+    for (int i = 0; i < D * D; ++i) C[i / D][i % D] = staged(stage, b + R::C + i);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) E[i][j] = staged(stage, b + R::F + i * D + j) - (i == j ? P.f_diag : 0.0f);
+    p2g_pass<D, MAT, DET>(P, P.basis2, active, scene, p, tile.z, x, v, C, E, staged(stage, b + R::Q),
+                          staged(stage, b + R::Q + 1), A.group, A.wact,
+                     scene_grid(A.PMm, scene, P), A.box_m + scene * 8, sm, xr, s_box, s_bbox_pm,
                      err, A.Rm, nullptr, N);
   }
   if (err) atomicOr(A.err, err);
 }
 
-template <int D, int MAT, int MODE>
-__global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM) adjoint_kernel(const __grid_constant__ SimParams P, const __grid_constant__ AdjArgs A) {
+template <int D, int MAT, int MODE, bool DET>
+__global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
+    adjoint_kernel(const __grid_constant__ SimParams P, const __grid_constant__ AdjArgs A) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8];
   __shared__ int s_bbox_ub[8];
   __shared__ int s_bbox_pm[8];
   __shared__ float s_wbar[kWbarSlots];
-  adjoint_tile<D, MAT, MODE, true>(P, A, blockIdx.x, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+  adjoint_tile<D, MAT, MODE, true, DET>(P, A, blockIdx.x, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
 }
 
 // ---------------------------------------------------------------------------
@@ -1219,7 +1369,7 @@ __device__ __forceinline__ int next_tile(const PersistCtl& c, int i, int* s_tile
 }
 
 // Forward-kind passes plan[0..n_pass), tiles handed out by tickets.
-template <int D, int MAT>
+template <int D, int MAT, bool DET>
 __global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D)
     step_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
   extern __shared__ __align__(16) float sm[];
@@ -1233,10 +1383,10 @@ __global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_
     cta_copy(&e, plan + i);
     for (int t; (t = next_tile(ctl, i, &s_tile)) < n_tiles;) {
       switch (e.mode) {
-        case kP2GOnly: step_tile<D, MAT, kP2GOnly, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
-        case kG2PP2G: step_tile<D, MAT, kG2PP2G, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
-        case kG2PP2GFull: step_tile<D, MAT, kG2PP2GFull, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
-        default: step_tile<D, MAT, kG2POnlyFull, false>(e.P, e.S, t, sm, s_box, s_bbox); break;
+        case kP2GOnly: step_tile<D, MAT, kP2GOnly, false, DET>(e.P, e.S, t, sm, s_box, s_bbox); break;
+        case kG2PP2G: step_tile<D, MAT, kG2PP2G, false, DET>(e.P, e.S, t, sm, s_box, s_bbox); break;
+        case kG2PP2GFull: step_tile<D, MAT, kG2PP2GFull, false, DET>(e.P, e.S, t, sm, s_box, s_bbox); break;
+        default: step_tile<D, MAT, kG2POnlyFull, false, DET>(e.P, e.S, t, sm, s_box, s_bbox); break;
       }
       __syncthreads();
     }
@@ -1244,7 +1394,7 @@ __global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_
 }
 
 // Adjoint-kind passes plan[0..n_pass).
-template <int D, int MAT>
+template <int D, int MAT, bool DET>
 __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
     adjoint_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
   extern __shared__ __align__(16) float sm[];
@@ -1261,13 +1411,13 @@ __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
     for (int t; (t = next_tile(ctl, i, &s_tile)) < n_tiles;) {
       switch (e.mode) {
         case kAdjG2P:
-          adjoint_tile<D, MAT, kAdjG2P, false>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          adjoint_tile<D, MAT, kAdjG2P, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
           break;
         case kAdjFused:
-          adjoint_tile<D, MAT, kAdjFused, false>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          adjoint_tile<D, MAT, kAdjFused, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
           break;
         default:
-          adjoint_tile<D, MAT, kAdjP2G, false>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          adjoint_tile<D, MAT, kAdjP2G, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
           break;
       }
       __syncthreads();

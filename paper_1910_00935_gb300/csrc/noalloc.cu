@@ -74,6 +74,8 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
   if (d->n_scenes != 1 || !d->n_particles)
     return reject(MPM_ERR_ARG, "mpm_step_noalloc: exactly one scene");
   if (d->n_groups != 0) return reject(MPM_ERR_ARG, "mpm_step_noalloc: no actuation");
+  if (d->deterministic_p2g != 0)
+    return reject(MPM_ERR_ARG, "mpm_step_noalloc: the deterministic mode needs the workspace form");
   if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN)
     return reject(MPM_ERR_ARG, "mpm_step_noalloc: unknown material");
   if (d->n_grid < 8 || !(d->dt > 0.0f) || !(d->rho > 0.0f) || d->wall_cells < 0 ||
@@ -145,6 +147,7 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
   P.kappa = (float)(-(double)d->dt * vol * 4.0 / (dx * dx));
   P.tile_capacity = 1024;
   P.f_diag = 1.0f;  // the caller's state rows hold F itself
+  P.node_words = 1;
 
   StepArgs A;
   memset(&A, 0, sizeof(A));

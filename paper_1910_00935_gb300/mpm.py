@@ -25,7 +25,7 @@ from . import build as _build
 
 MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOB = 0, 1, 2, 3
 MPM_ERR_NONFINITE, MPM_ERR_TIMEOUT, MPM_ERR_STATE, MPM_ERR_WORKSPACE = 4, 5, 6, 7
-MPM_ERR_TOO_LARGE = 8
+MPM_ERR_TOO_LARGE, MPM_ERR_RANGE = 8, 9
 MPM_NOALLOC_MAX_NODES = MPM_NOALLOC_MAX_PARTICLES = 1 << 18
 MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN = 0, 1
 MPM_LOSS_COM_TARGET, MPM_LOSS_COM_X_DISP = 0, 1

@@ -55,13 +55,17 @@ def test_host_side_validation_without_gpu(libpath):
     assert b2 > b1 > 0
     for bad in (dict(dim=4), dict(n_grid=4), dict(dt=0.0), dict(ckpt_every=0),
                 dict(n_particles=[0]), dict(wall_cells=40), dict(material=7),
-                dict(n_groups=9), dict(n_groups=2, n_basis=0), dict(deterministic_p2g=1)):
+                dict(n_groups=9), dict(n_groups=2, n_basis=0), dict(deterministic_p2g=2)):
         with pytest.raises(mpm.MPMError) as e:
             mpm.mpm_workspace_bytes(mpm.make_desc({**good, **bad}), 64)
         assert e.value.code == mpm.MPM_ERR_ARG
     with pytest.raises(mpm.MPMError) as e:
         mpm.mpm_workspace_bytes(d, 0)
     assert e.value.code == mpm.MPM_ERR_ARG
+    # the deterministic mode keeps 64-bit fixed-point grids: twice the grid memory
+    bd = mpm.mpm_workspace_bytes(mpm.make_desc({**good, "deterministic_p2g": 1}), 64)
+    grids = 10 * 2 * 64 ** 3 * 16  # ten (m, p) and ubar buffers, two scenes, float4 nodes
+    assert bd - b1 >= grids
     # NULL or misaligned workspace is rejected before any CUDA call
     with pytest.raises(mpm.MPMError) as e:
         mpm.mpm_create(d, 0, b1, 64)

@@ -1,0 +1,113 @@
+"""Deterministic accumulation (mpm_scene_desc.deterministic_p2g = 1).
+
+Every grid sum (P2G mass and momentum, the recomputed P2G, the velocity-adjoint scatter)
+is accumulated as 64-bit fixed-point integers, whose sums do not depend on the order of
+the atomic adds; the dL/dw and centre-of-mass reductions are fixed-order in every mode.
+So for a given compiled pass the whole forward and backward is bitwise reproducible:
+across repeated runs, with graphs on or off, for a scene simulated alone or inside a batch,
+and in the persistent form across runs whose dynamic tile hand-out orders the scatters
+differently (and with one pass per launch).  The per-pass and the persistent kernels, or
+gathers read straight from the grid instead of the shared gather box, are different
+compiled code and agree to rounding, not necessarily bitwise.  The mode must also meet
+the oracle bars of the default mode.
+"""
+import numpy as np
+import pytest
+
+from mpm_testlib import rel_l2, scene_slice, subset_scenes
+from paper_1910_00935_gb300 import scenes
+from test_gpu_parity import (POS_TOL, _compare_grads, _compare_states, _oracle_grad_linear,
+                             _oracle_states, _random_seeds, _run_gpu)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    from paper_1910_00935_gb300 import build, mpm as m
+    build.build()
+    return m
+
+
+CASES = [
+    ("rects2d", dict(n_scenes=4, n_min=300, n_max=1500), 20, 6),
+    ("cube3d", dict(n_side=16, n_grid=64), 10, 4),
+    ("robots3d", dict(n_scenes=2, dims=(16, 8, 8)), 10, 4),
+]
+
+
+def _det_scene(name, kw, k):
+    scene = scenes.make(name, **kw)
+    scene["desc"]["ckpt_every"] = k
+    scene["desc"]["deterministic_p2g"] = 1
+    return scene
+
+
+@pytest.mark.parametrize("name,kw,T,k", CASES)
+def test_deterministic_mode_matches_oracle(mpm, name, kw, T, k):
+    scene = _det_scene(name, kw, k)
+    seeds = _random_seeds(scene, np.random.default_rng(21))
+    g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    _compare_states(g["state"], _oracle_states(scene, T), scene, POS_TOL)
+    o = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
+    keys = ["gx0", "gv0", "gC0", "gF0", "gE", "gnu"] + (["gw"] if scene["desc"]["n_groups"] else [])
+    _compare_grads(g["grad"], o, keys)
+
+
+@pytest.mark.parametrize("name,kw,T,k", CASES)
+def test_deterministic_mode_is_bitwise_reproducible(mpm, name, kw, T, k):
+    scene = _det_scene(name, kw, k)
+    seeds = _random_seeds(scene, np.random.default_rng(22))
+    pers = {mpm.MPM_OPT_PERSISTENT: 1}
+    groups = [[{}, {}, {mpm.MPM_OPT_USE_GRAPHS: 0}],
+              [pers, pers, {**pers, mpm.MPM_OPT_PERSISTENT_CHUNK: 1, mpm.MPM_OPT_USE_GRAPHS: 0}]]
+    refs = []
+    for forms in groups:
+        runs = [_run_gpu(mpm, scene, T, seeds=seeds, loss=False, options=f) for f in forms]
+        ref = runs[0]
+        refs.append(ref)
+        for f, r in zip(forms[1:], runs[1:]):
+            for i in range(4):
+                assert np.array_equal(r["state"][i], ref["state"][i]), (f, "state", i)
+            for key, v in ref["grad"].items():
+                if v is not None:
+                    assert np.array_equal(r["grad"][key], v), (f, key)
+    a, b = refs
+    for i in range(4):
+        assert rel_l2(a["state"][i], b["state"][i]) <= 1e-5, i
+    for key, v in a["grad"].items():
+        if v is not None:
+            assert rel_l2(b["grad"][key], v) <= 1e-4, key
+
+
+def test_deterministic_scene_alone_equals_scene_in_batch(mpm):
+    """Scene 2 of a 4-scene batch, bitwise, against the same scene simulated alone."""
+    name, kw, T, k = CASES[0]
+    batch = _det_scene(name, kw, k)
+    alone = subset_scenes(batch, [2])
+    seeds = _random_seeds(batch, np.random.default_rng(24))
+    sl = scene_slice(batch, 2)
+    seeds_alone = {kk: np.ascontiguousarray(v[:, sl]) for kk, v in seeds.items()}
+    a = _run_gpu(mpm, batch, T, seeds=seeds, loss=False)
+    b = _run_gpu(mpm, alone, T, seeds=seeds_alone, loss=False)
+    for i in range(4):
+        assert np.array_equal(a["state"][i][:, sl], b["state"][i]), i
+    for key in ("gx0", "gv0", "gC0", "gF0"):
+        assert np.array_equal(a["grad"][key][:, sl], b["grad"][key]), key
+    for key in ("gE", "gnu"):
+        assert np.array_equal(a["grad"][key][sl], b["grad"][key]), key
+
+
+def test_default_mode_is_not_required_to_be_reproducible_but_agrees(mpm):
+    """The float-atomic default and the fixed-point mode agree to FP32 rounding."""
+    name, kw, T, k = CASES[1]
+    det = _det_scene(name, kw, k)
+    flt = scenes.make(name, **kw)
+    flt["desc"]["ckpt_every"] = k
+    seeds = _random_seeds(det, np.random.default_rng(23))
+    a = _run_gpu(mpm, det, T, seeds=seeds, loss=False)
+    b = _run_gpu(mpm, flt, T, seeds=seeds, loss=False)
+    assert rel_l2(a["state"][0], b["state"][0]) <= 1e-5
+    for key in ("gx0", "gv0", "gF0", "gE"):
+        assert rel_l2(a["grad"][key], b["grad"][key]) <= 1e-4, key

@@ -92,3 +92,5 @@ def test_noalloc_rejects_problems_beyond_its_scratch(mpm):
     assert mpm.mpm_step_noalloc(mpm.make_desc(two), 256, 256, 256, 512, None, 0) == mpm.MPM_ERR_ARG
     act = dict(big_grid, n_grid=64, n_groups=2, n_basis=1)
     assert mpm.mpm_step_noalloc(mpm.make_desc(act), 256, 256, 256, 512, None, 0) == mpm.MPM_ERR_ARG
+    det = dict(big_grid, n_grid=64, deterministic_p2g=1)
+    assert mpm.mpm_step_noalloc(mpm.make_desc(det), 256, 256, 256, 512, None, 0) == mpm.MPM_ERR_ARG
