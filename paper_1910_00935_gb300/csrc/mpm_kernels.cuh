@@ -302,17 +302,19 @@ struct BoxInfo {
   bool use_tile;
 };
 
+// Each box computation of a tile has its own 8-int slot of s_box (kBoxSlots slots, reset
+// together by reset_box_slots before the tile's first barrier), so a box costs one barrier.
+constexpr int kBoxSlots = 3;
+__device__ __forceinline__ void reset_box_slots(int* s_box) {
+  if (threadIdx.x < 8 * kBoxSlots) s_box[threadIdx.x] = (threadIdx.x & 4) ? INT_MIN : INT_MAX;
+}
+
 // Extent of the node box covering the stencils of the CTA's valid particles.  Every
-// thread of the CTA must call this; it synchronises before touching s_box (so it may
-// follow any earlier use of s_box or of the shared box) and after computing it.
+// thread of the CTA must call this; s_box is a slot reset before an earlier barrier and
+// not used since.  Ends with a barrier, which also orders every earlier read of the
+// shared node box before the box_load that follows.
 template <int D>
 __device__ __forceinline__ BoxInfo<D> box_extent(bool valid, const int base[D], int cap, int* s_box) {
-  __syncthreads();
-  if (threadIdx.x < D) {
-    s_box[threadIdx.x] = INT_MAX;
-    s_box[4 + threadIdx.x] = INT_MIN;
-  }
-  __syncthreads();
   const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -357,10 +359,10 @@ __device__ __forceinline__ void box_zero(const BoxInfo<D>& b, float* sm, int cap
 }
 
 // Fill the shared gather box (float4 per node, box-local order) with value(idx) for every
-// node idx of the box, one node per thread.  Synchronises on both sides.
+// node idx of the box, one node per thread.  Called right after box_extent (whose barrier
+// separates it from earlier readers of the box); synchronises after.
 template <int D, typename Value>
 __device__ __forceinline__ void box_load(const BoxInfo<D>& b, float4* sm4, Value&& value) {
-  __syncthreads();
   if (b.use_tile)
     for (int l = threadIdx.x; l < b.vol; l += blockDim.x) {
       int idx[D], r = l;
@@ -692,7 +694,7 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
   __syncthreads();  // the record area may still be read by an earlier scatter
   put_record<D>(xr, ok, s.base, s.f, mv, Am);
   if (P.tile_capacity > 0) {
-    const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box);
+    const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box + 16);
     box_zero<D>(bx, sm, P.tile_capacity);
     scatter_records<D, true, DET>(xr, count, bx, sm, P.tile_capacity, g, P.n_grid, P, P.p_mass, P.fix_m,
                              P.fix_p, err);
@@ -718,13 +720,14 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
 // forward particle pass: [G2P of step t-1] then [P2G of step t]
 // ---------------------------------------------------------------------------
 // One tile of a forward pass; every thread of the CTA calls it.  sm: dynamic shared memory
-// (pass_smem_bytes), s_box / s_bbox: 8 ints each.  A CTA that runs several tiles must
+// (step_smem_bytes), s_box: 8 * kBoxSlots ints, s_bbox: 8 ints.  A CTA that runs several tiles must
 // synchronise between them.
 template <int D, int MAT, int MODE, bool NC, bool DET>
 __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A, int tile_index,
                                           float* sm, int* s_box, int* s_bbox) {
   using R = Rows<D>;
   cta_bbox_reset(s_bbox);
+  reset_box_slots(s_box);
   float* xr = sm + box_floats(P.tile_capacity, P.gather_capacity);
   const int4 tile = A.tiles[tile_index];
   const int scene = tile.x;
@@ -775,7 +778,7 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
     BoxInfo<D> gbx;
     gbx.use_tile = false;
     if (P.gather_capacity > 0) {
-      gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);
+      gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);  // slot 0
       box_load<D>(gbx, reinterpret_cast<float4*>(sm), velocity);
     }
     if (ok) {
@@ -843,7 +846,7 @@ template <int D, int MAT, int MODE, bool DET>
 __global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D)
     step_kernel(const __grid_constant__ SimParams P, const __grid_constant__ StepArgs A) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ int s_box[8];
+  __shared__ int s_box[8 * kBoxSlots];
   __shared__ int s_bbox[8];
   step_tile<D, MAT, MODE, true, DET>(P, A, blockIdx.x, sm, s_box, s_bbox);
 }
@@ -860,6 +863,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
   using R = Rows<D>;
   cta_bbox_reset(s_bbox_ub);
   cta_bbox_reset(s_bbox_pm);
+  reset_box_slots(s_box);
   float* xr = sm + box_floats(P.tile_capacity, P.gather_capacity);
   const int4 tile = A.tiles[tile_index];
   const int scene = tile.x;
@@ -957,7 +961,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     BoxInfo<D> gbx;
     gbx.use_tile = false;
     if (P.gather_capacity > 0) {
-      gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);
+      gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);  // slot 0
       box_load<D>(gbx, reinterpret_cast<float4*>(sm), pbar);
     }
     if (ok) with_nodes<D>(gbx, reinterpret_cast<const float4*>(sm), s.base, pbar, [&](auto load) {
@@ -1139,7 +1143,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     const int cap_box = P.tile_capacity > P.gather_capacity ? P.tile_capacity : P.gather_capacity;
     BoxInfo<D> bx;
     bx.use_tile = false;
-    if (cap_box > 0) bx = box_extent<D>(ok, s.base, cap_box, s_box);
+    if (cap_box > 0) bx = box_extent<D>(ok, s.base, cap_box, s_box + 8);
     BoxInfo<D> gbx = bx;
     gbx.use_tile = bx.use_tile && P.gather_capacity > 0 && bx.vol <= P.gather_capacity;
     if (P.gather_capacity > 0) box_load<D>(gbx, reinterpret_cast<float4*>(sm), velocity);
@@ -1260,7 +1264,7 @@ template <int D, int MAT, int MODE, bool DET>
 __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
     adjoint_kernel(const __grid_constant__ SimParams P, const __grid_constant__ AdjArgs A) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ int s_box[8];
+  __shared__ int s_box[8 * kBoxSlots];
   __shared__ int s_bbox_ub[8];
   __shared__ int s_bbox_pm[8];
   __shared__ float s_wbar[kWbarSlots];
@@ -1373,7 +1377,7 @@ template <int D, int MAT, bool DET>
 __global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D)
     step_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ int s_box[8];
+  __shared__ int s_box[8 * kBoxSlots];
   __shared__ int s_bbox[8];
   __shared__ int s_go, s_tile;
   __shared__ PassEntry e;
@@ -1398,7 +1402,7 @@ template <int D, int MAT, bool DET>
 __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
     adjoint_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ int s_box[8];
+  __shared__ int s_box[8 * kBoxSlots];
   __shared__ int s_bbox_ub[8];
   __shared__ int s_bbox_pm[8];
   __shared__ float s_wbar[kWbarSlots];
