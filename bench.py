@@ -34,22 +34,30 @@ UNIT = "particle-steps/s"
 
 # algorithmic bytes per particle of each pass category (3D, FP32 state rows):
 # x, v: 12 B each; C, F: 36 B each; mu, la: 8 B; full state 96 B.
-ALG_BYTES_3D = {
-    "p2g": 96 + 8,                       # read x, v, C, F, mu, la
-    "g2p_p2g": 48 + 8 + 48,              # read x, F, mu, la; write x, F
-    "g2p_p2g_full": 48 + 8 + 96,         # read x, F, mu, la; write x, v, C, F
-    "g2p": 48 + 96,                      # read x, F; write the full state
-    "adj_g2p": 96 + 48 + 48 + 48,        # read adj, C', x, F; write adj x, F
-    "adj_fused": 96 + 48 + 48 + 8 + 16 + 48 + 96,  # state s+1, x F of state s, adj x F (rw),
-                                                   # mu la, mubar labar (rw), state s-1 (P2G)
-    "adj_p2g": 96 + 48 + 8 + 16 + 96,
-}
+def alg_bytes(d):
+    """Algorithmic bytes per particle of each pass category (FP32 state rows; the minimum
+    each pass must move).  S: full state x, v, C, F; XF: x and F rows; M: mu, la;
+    MB: mu-bar, la-bar read and written."""
+    S, XF, X, C = 4 * (2 * d + 2 * d * d), 4 * (d + d * d), 4 * d, 4 * d * d
+    M, MB = 8, 16
+    return {
+        "p2g": S + M,                       # read x, v, C, F, mu, la
+        "g2p_p2g": XF + M + XF,             # read x, F, mu, la; write x, F
+        "g2p_p2g_full": XF + M + S,         # read x, F, mu, la; write x, v, C, F
+        "g2p": XF + S,                      # read x, F; write the full state
+        "adj_g2p": S + XF + (X + C) + XF,   # read adj, x F of state s, x C of state s+1; write adj x F
+        "adj_fused": S + XF + 2 * XF + M + MB + S,  # state s+1, x F of state s, adj x F (rw),
+                                                    # mu la, mubar labar (rw), state s-1 (P2G)
+        "adj_p2g": S + XF + M + MB + S,     # state 0, adj x F, mu la, mubar labar; write full adj
+    }
 
 
-def pass_bytes(N, T, K):
+
+
+def pass_bytes(N, T, K, dim=3):
     """Algorithmic bytes of one bench step per kernel category, for both launch forms:
     the per-pass categories and the persistent launches that run the same passes."""
-    a = ALG_BYTES_3D
+    a = alg_bytes(dim)
     ckpt_inner = (T - 1) // K                 # full-state writes at t = K, 2K, ... < T
     fwd = a["p2g"] + (T - 1 - ckpt_inner) * a["g2p_p2g"] + ckpt_inner * a["g2p_p2g_full"] + a["g2p"]
     resim = 0
@@ -399,7 +407,7 @@ def main():
     dom = max(prof, key=lambda k: prof[k][1])
     n_launch, dom_ms = prof[dom]
     hbm, peak_src = measured_peaks()
-    step_bytes = pass_bytes(N, T, desc["ckpt_every"]) if desc["dim"] == 3 else {}
+    step_bytes = pass_bytes(N, T, desc["ckpt_every"], desc["dim"])
     roof = None
     if dom in step_bytes and n_launch:
         avg_ms = dom_ms / n_launch
