@@ -74,7 +74,7 @@ extern "C" {
                                      setting it clears the collected timings */
 
 #define MPM_OPT_GATHER_CAPACITY 5 /* max nodes of a CTA's shared gather box; 0 = gathers
-                                     read the grid through L1 [1024] */
+                                     read the grid through L1 [512] */
 #define MPM_OPT_POLAR_CACHE 7     /* 3D fixed-corotated: the re-simulation stores each state's
                                      FP64 polar factor for the two backward passes that need it
                                      instead of recomputing it [1] */

@@ -2,8 +2,9 @@
 
 The knobs are the library's runtime options: the capacity of the shared gather box
 (MPM_OPT_GATHER_CAPACITY), the scatter path (MPM_OPT_SMEM_TILE: shared node box vs. float4
-reductions straight to the grid), the shared box capacity (MPM_OPT_TILE_CAPACITY) and the
-CTA count of the node passes (MPM_OPT_GRID_BLOCKS).  `tune` times a short forward+backward
+reductions straight to the grid), the shared box capacity (MPM_OPT_TILE_CAPACITY), the
+CTA count of the end-of-sequence grid clear (MPM_OPT_GRID_BLOCKS) and the launch form
+(MPM_OPT_PERSISTENT: one launch per pass, or persistent launches over the pass plan).  `tune` times a short forward+backward
 of the caller's own simulator for each candidate, one knob at a time (coordinate descent
 from the defaults), keeps the fastest, and caches the result in a JSON file keyed by the
 workload's shape class and the device name.  Results never change numerics beyond FP32
@@ -16,14 +17,17 @@ import math
 import os
 
 SPACE = {
-    "gather_capacity": [1024, 0, 512, 2048],
+    "gather_capacity": [512, 0, 1024, 2048],
     "smem_tile": [0, 1],
     "tile_capacity": [1024, 2048],
     "grid_blocks": [0, 32, 64, 128],
+    "persistent": [0, 1],
 }
-DEFAULTS = {"gather_capacity": 1024, "smem_tile": 0, "tile_capacity": 1024, "grid_blocks": 0}
+DEFAULTS = {"gather_capacity": 512, "smem_tile": 0, "tile_capacity": 1024, "grid_blocks": 0,
+            "persistent": 0}
 
-_OPTION_IDS = {"gather_capacity": 5, "smem_tile": 2, "tile_capacity": 3, "grid_blocks": 6}
+_OPTION_IDS = {"gather_capacity": 5, "smem_tile": 2, "tile_capacity": 3, "grid_blocks": 6,
+               "persistent": 8}
 
 
 def default_cache_path() -> str:

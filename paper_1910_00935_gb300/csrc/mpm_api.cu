@@ -195,7 +195,7 @@ struct mpm_handle {
   bool use_graphs = true;
   bool smem_tile = false;  // measured on GB300: global float4 reductions beat shared FP32 atomics
   int tile_capacity = 1024;
-  int gather_capacity = 1024;
+  int gather_capacity = 512;  // nodes; a 128-particle tile's stencil box is ~150-300
   int grid_blocks = 0;  // CTAs per scene of the end-of-sequence grid clear (0 = automatic)
   bool use_polar_cache = true;
   bool persistent = false;               // MPM_OPT_PERSISTENT
