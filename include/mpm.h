@@ -58,6 +58,10 @@ extern "C" {
 /* materials */
 #define MPM_FIXED_COROTATED 0
 #define MPM_NEO_HOOKEAN 1
+#define MPM_LIQUID 3 /* weakly compressible liquid: the paper's liquid simulator follows the
+                        weakly compressible model of Tampubolon et al. 2017; here in Tait form,
+                        Kirchhoff stress kappa (J - J^(1-7)) I with kappa = lambda + 2 mu / dim
+                        the bulk modulus of the particle's (E, nu); no shear stress */
 
 /* losses computed by mpm_loss (the compute_loss pattern of Section 3.2) */
 #define MPM_LOSS_COM_TARGET 0 /* L_s = |COM_s(x_T) - target_s|^2 */
@@ -128,7 +132,7 @@ typedef struct mpm_scene_desc {
   float dt;                    /* time step */
   float gravity[3];            /* added as dt*g in the grid update */
   int32_t wall_cells;          /* sticky walls: node i with any i_k < wall or i_k >= n-wall gets v = 0 */
-  int32_t material;            /* MPM_FIXED_COROTATED or MPM_NEO_HOOKEAN */
+  int32_t material;            /* MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN or MPM_LIQUID */
   float rho;                   /* density; particle volume (dx/2)^dim, mass rho*volume */
   int32_t ckpt_every;          /* k: full state stored every k steps (Appendix D.2), >= 1 */
   int32_t n_groups;            /* actuator groups, 0..8 (0 = no actuation) */

@@ -37,7 +37,7 @@ _LIBDIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 
 OK, ERR_ARG, ERR_MEM, ERR_OOB, ERR_DOMAIN = 0, 1, 2, 3, 4
-FIXED_COROTATED, NEO_HOOKEAN, NO_ELASTICITY = 0, 1, 2
+FIXED_COROTATED, NEO_HOOKEAN, NO_ELASTICITY, LIQUID = 0, 1, 2, 3
 LOSS_COM_TARGET, LOSS_COM_X_DISP = 0, 1
 
 _lock = threading.Lock()

@@ -52,6 +52,14 @@
 #define ORC_FIXED_COROTATED 0
 #define ORC_NEO_HOOKEAN 1
 #define ORC_NO_ELASTICITY 2
+#define ORC_LIQUID 3          /* weakly compressible liquid (the paper's liquid simulator) */
+
+/* Liquid equation of state (Tait form of the weakly compressible model the paper's liquid
+   simulator follows, Tampubolon et al. 2017): psi(J) = kappa (J - J^(1-g)/(1-g)), so the
+   pressure is p = -psi'(J) = kappa (J^-g - 1) and the Kirchhoff stress tau = psi'(J) J I =
+   kappa (J - J^(1-g)) I; kappa = lambda + 2 mu / d is the bulk modulus of the particle's
+   (E, nu) and g = 7. */
+#define ORC_LIQUID_GAMMA 7.0
 
 #define ORC_LOSS_COM_TARGET 0   /* L = |COM(x_T) - target|^2            */
 #define ORC_LOSS_COM_X_DISP 1   /* L = -(COM_x(x_T) - COM_x(x_0))       */
@@ -62,7 +70,7 @@ typedef struct {
   double dt;
   double gravity[3];
   int32_t wall_cells; /* sticky boundary thickness in nodes; 0 = no walls */
-  int32_t material;   /* ORC_FIXED_COROTATED / ORC_NEO_HOOKEAN / ORC_NO_ELASTICITY */
+  int32_t material;   /* ORC_FIXED_COROTATED / ORC_NEO_HOOKEAN / ORC_NO_ELASTICITY / ORC_LIQUID */
   double rho;         /* density; particle volume (dx/2)^dim, mass rho * volume */
   int32_t n_groups;   /* actuation groups (0 = no actuation) */
   int32_t n_basis;    /* sine terms per group */
@@ -484,6 +492,12 @@ static int kirchhoff(const orc_params* P, const mat3 F, double mu, double la, do
     for (int i = 0; i < d; i++)
       for (int j = 0; j < d; j++) tau[i][j] = mu * (FFt[i][j] - (i == j ? 1.0 : 0.0));
     for (int i = 0; i < d; i++) tau[i][i] += la * log(J);
+  } else if (P->material == ORC_LIQUID) {
+    double J = mdet(d, F);
+    if (!(J > 0.0)) return ORC_ERR_DOMAIN;
+    double kap = la + 2.0 * mu / d;
+    double g = J - pow(J, 1.0 - ORC_LIQUID_GAMMA);
+    for (int i = 0; i < d; i++) tau[i][i] = kap * g;
   } else if (P->material != ORC_NO_ELASTICITY) {
     return ORC_ERR_ARG;
   }
@@ -575,6 +589,21 @@ static int kirchhoff_adjoint(const orc_params* P, const mat3 F, double mu, doubl
     for (int i = 0; i < d; i++) FFt[i][i] -= 1.0;
     *mubar += mdot(d, tb, FFt);
     *labar += trtb * log(J);
+  } else if (P->material == ORC_LIQUID) {
+    /* tau = kappa g(J) I, g(J) = J - J^(1-gamma), g'(J) = 1 + (gamma - 1) J^-gamma,
+       dJ/dF = cof F; kappa = la + 2 mu / d */
+    double J = mdet(d, F);
+    if (!(J > 0.0)) return ORC_ERR_DOMAIN;
+    double kap = la + 2.0 * mu / d;
+    double g = J - pow(J, 1.0 - ORC_LIQUID_GAMMA);
+    double gp = 1.0 + (ORC_LIQUID_GAMMA - 1.0) * pow(J, -ORC_LIQUID_GAMMA);
+    mat3 cof;
+    mcof(d, F, cof);
+    for (int i = 0; i < d; i++)
+      for (int j = 0; j < d; j++) Fbar[i][j] += trtb * kap * gp * cof[i][j];
+    double kbar = trtb * g;
+    *labar += kbar;
+    *mubar += 2.0 * kbar / d;
   }
   if (act != 0.0 || abar) {
     double fe[3] = {0, 0, 0};

@@ -16,6 +16,8 @@ MPM_INSTANTIATE(2, kFixedCorotated, false)
 MPM_INSTANTIATE(2, kNeoHookean, false)
 MPM_INSTANTIATE(2, kFixedCorotated, true)
 MPM_INSTANTIATE(2, kNeoHookean, true)
+MPM_INSTANTIATE(2, kLiquid, false)
+MPM_INSTANTIATE(2, kLiquid, true)
 template cudaError_t launch_clear<2>(const Clears&, int, int, int, int, cudaStream_t);
 template cudaError_t launch_clear<3>(const Clears&, int, int, int, int, cudaStream_t);
 

@@ -94,7 +94,8 @@ bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
   if (N > (int64_t)INT32_MAX / 32) return fail("too many particles");
   if (!(d->dt > 0.0f) || !std::isfinite(d->dt)) return fail("dt must be > 0");
   if (d->wall_cells < 0 || 2 * d->wall_cells >= d->n_grid) return fail("bad wall_cells");
-  if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN)
+  if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN &&
+      d->material != MPM_LIQUID)
     return fail("unknown material");
   if (!(d->rho > 0.0f)) return fail("rho must be > 0");
   if (d->ckpt_every < 1) return fail("ckpt_every must be >= 1");

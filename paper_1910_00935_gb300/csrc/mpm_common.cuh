@@ -43,7 +43,10 @@ constexpr unsigned kErrNonFinite = 2u;
 constexpr unsigned kErrTimeout = 4u;
 constexpr unsigned kErrRange = 8u;  // a fixed-point grid contribution left its range
 
-enum Material : int { kFixedCorotated = 0, kNeoHookean = 1 };
+enum Material : int { kFixedCorotated = 0, kNeoHookean = 1, kLiquid = 3 };
+// weakly compressible liquid (Tait form of the model the paper's liquid simulator follows,
+// Tampubolon et al. 2017): tau = kappa (J - J^(1-g)) I, kappa = la + 2 mu / d, g = 7
+constexpr float kLiquidGamma = 7.0f;
 
 // Scalars every kernel of one launch needs (passed by value).
 struct SimParams {
@@ -538,6 +541,7 @@ struct StressCache {
 
 // tau = 2 mu (F - R) F^T + la (J - 1) J I        (fixed-corotated)
 // tau = mu (F F^T - I) + la ln(J) I               (neo-Hookean)
+// tau = kappa (J - J^(1-g)) I                     (liquid; no shear stress)
 // tau += act (F e)(F e)^T, e = unit vector of `axis` (actuation fibre)
 // with F = I + E; every product is formed on E (or on F - R) so small strains keep
 // their relative precision.
@@ -570,6 +574,15 @@ __device__ __forceinline__ bool kirchhoff(const float E[D][D], float mu, float l
     float vol = la * sc.Jm1 * sc.J;
 #pragma unroll
     for (int i = 0; i < D; ++i) tau[i][i] += vol;
+  } else if (MAT == kLiquid) {
+    ok = sc.J > 0.0f;
+    // J - J^(1-g) = (J - 1) - (J^(1-g) - 1), both terms from J - 1 (no cancellation at J ~ 1)
+    const float kap = la + 2.0f * mu / (float)D;
+    const float g = sc.Jm1 - expm1f((1.0f - kLiquidGamma) * log1pf(sc.Jm1));
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) tau[i][j] = (i == j) ? kap * g : 0.0f;
   } else {
     ok = sc.J > 0.0f;
     // F F^T - I = E + E^T + E E^T
@@ -635,6 +648,21 @@ __device__ __forceinline__ float kirchhoff_adjoint(const float E[D][D], float mu
       for (int j = 0; j < D; ++j) Fbar[i][j] += c * cof[i][j];
     mubar += 2.0f * mub;
     labar += trtb * sc.Jm1 * sc.J;
+  } else if (MAT == kLiquid) {
+    // tau = kappa g(J) I: Fbar += tr(tb) kappa g'(J) cof F, g'(J) = 1 + (g - 1) J^-g;
+    // kappa-bar = tr(tb) g(J) -> labar += kappa-bar, mubar += 2 kappa-bar / d
+    const float kap = la + 2.0f * mu / (float)D;
+    const float lj = log1pf(sc.Jm1);
+    const float g = sc.Jm1 - expm1f((1.0f - kLiquidGamma) * lj);
+    const float gp = 1.0f + (kLiquidGamma - 1.0f) * expf(-kLiquidGamma * lj);
+    const float c = trtb * kap * gp;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) Fbar[i][j] += c * cof[i][j];
+    const float kbar = trtb * g;
+    labar += kbar;
+    mubar += 2.0f * kbar / (float)D;
   } else {
     float iJ = 1.0f / sc.J;
     float c = la * trtb * iJ;

@@ -32,34 +32,35 @@ cudaError_t launch_clear(const Clears& C, int nnodes, int n_grid, int n_scenes, 
                          cudaStream_t s);
 
 // dispatch on the runtime material and accumulation mode (P.det)
+#define MPM_DISPATCH_MATERIAL(FN, ...)                                                   \
+  switch (material) {                                                                   \
+    case kFixedCorotated:                                                               \
+      return P.det ? FN<D, kFixedCorotated, true>(__VA_ARGS__)                          \
+                   : FN<D, kFixedCorotated, false>(__VA_ARGS__);                        \
+    case kNeoHookean:                                                                   \
+      return P.det ? FN<D, kNeoHookean, true>(__VA_ARGS__) : FN<D, kNeoHookean, false>(__VA_ARGS__); \
+    case kLiquid:                                                                       \
+      return P.det ? FN<D, kLiquid, true>(__VA_ARGS__) : FN<D, kLiquid, false>(__VA_ARGS__); \
+  }                                                                                     \
+  return cudaErrorInvalidValue;
+
 template <int D>
 inline cudaError_t launch_step(int material, int mode, const SimParams& P, const StepArgs& A,
                                int n_tiles, cudaStream_t s) {
-  if (material == kFixedCorotated)
-    return P.det ? step_variant<D, kFixedCorotated, true>(mode, P, A, n_tiles, s)
-                 : step_variant<D, kFixedCorotated, false>(mode, P, A, n_tiles, s);
-  return P.det ? step_variant<D, kNeoHookean, true>(mode, P, A, n_tiles, s)
-               : step_variant<D, kNeoHookean, false>(mode, P, A, n_tiles, s);
+  MPM_DISPATCH_MATERIAL(step_variant, mode, P, A, n_tiles, s)
 }
 template <int D>
 inline cudaError_t launch_adjoint(int material, int mode, const SimParams& P, const AdjArgs& A,
                                   int n_tiles, cudaStream_t s) {
-  if (material == kFixedCorotated)
-    return P.det ? adj_variant<D, kFixedCorotated, true>(mode, P, A, n_tiles, s)
-                 : adj_variant<D, kFixedCorotated, false>(mode, P, A, n_tiles, s);
-  return P.det ? adj_variant<D, kNeoHookean, true>(mode, P, A, n_tiles, s)
-               : adj_variant<D, kNeoHookean, false>(mode, P, A, n_tiles, s);
+  MPM_DISPATCH_MATERIAL(adj_variant, mode, P, A, n_tiles, s)
 }
 template <int D>
 inline cudaError_t launch_persistent(int kind, int material, const SimParams& P, const PassEntry* plan,
                                      int n_pass, int n_tiles, const PersistCtl& ctl, cudaStream_t s,
                                      int* grid_out) {
-  if (material == kFixedCorotated)
-    return P.det ? persistent_variant<D, kFixedCorotated, true>(kind, P, plan, n_pass, n_tiles, ctl, s, grid_out)
-                 : persistent_variant<D, kFixedCorotated, false>(kind, P, plan, n_pass, n_tiles, ctl, s, grid_out);
-  return P.det ? persistent_variant<D, kNeoHookean, true>(kind, P, plan, n_pass, n_tiles, ctl, s, grid_out)
-               : persistent_variant<D, kNeoHookean, false>(kind, P, plan, n_pass, n_tiles, ctl, s, grid_out);
+  MPM_DISPATCH_MATERIAL(persistent_variant, kind, P, plan, n_pass, n_tiles, ctl, s, grid_out)
 }
+#undef MPM_DISPATCH_MATERIAL
 
 // setup.cu
 size_t sort_temp_bytes(int64_t n);

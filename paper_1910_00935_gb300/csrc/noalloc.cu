@@ -76,7 +76,8 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
   if (d->n_groups != 0) return reject(MPM_ERR_ARG, "mpm_step_noalloc: no actuation");
   if (d->deterministic_p2g != 0)
     return reject(MPM_ERR_ARG, "mpm_step_noalloc: the deterministic mode needs the workspace form");
-  if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN)
+  if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN &&
+      d->material != MPM_LIQUID)
     return reject(MPM_ERR_ARG, "mpm_step_noalloc: unknown material");
   if (d->n_grid < 8 || !(d->dt > 0.0f) || !(d->rho > 0.0f) || d->wall_cells < 0 ||
       2 * d->wall_cells >= d->n_grid)

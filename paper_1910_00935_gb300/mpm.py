@@ -27,7 +27,7 @@ MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOB = 0, 1, 2, 3
 MPM_ERR_NONFINITE, MPM_ERR_TIMEOUT, MPM_ERR_STATE, MPM_ERR_WORKSPACE = 4, 5, 6, 7
 MPM_ERR_TOO_LARGE, MPM_ERR_RANGE = 8, 9
 MPM_NOALLOC_MAX_NODES = MPM_NOALLOC_MAX_PARTICLES = 1 << 18
-MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN = 0, 1
+MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN, MPM_LIQUID = 0, 1, 3
 MPM_LOSS_COM_TARGET, MPM_LOSS_COM_X_DISP = 0, 1
 MPM_OPT_USE_GRAPHS, MPM_OPT_SMEM_TILE, MPM_OPT_TILE_CAPACITY, MPM_OPT_PROFILE = 1, 2, 3, 4
 MPM_OPT_GATHER_CAPACITY, MPM_OPT_GRID_BLOCKS, MPM_OPT_POLAR_CACHE = 5, 6, 7

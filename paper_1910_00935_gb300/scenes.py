@@ -20,7 +20,7 @@ import math
 
 import numpy as np
 
-FIXED_COROTATED, NEO_HOOKEAN = 0, 1
+FIXED_COROTATED, NEO_HOOKEAN, LIQUID = 0, 1, 3
 LOSS_COM_TARGET, LOSS_COM_X_DISP = 0, 1
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -179,8 +179,32 @@ def actuated_robots_3d(seed=0, n_scenes=16, steps=2048, dims=(64, 32, 32), n_gri
     return _assemble(desc, parts)
 
 
+def liquid_column(seed=0, dim=3, steps=256, n_grid=64, cols=(32, 48, 32), E=500.0, nu=0.3,
+                  ckpt_every=32):
+    """Dam break: a column of weakly compressible liquid (cols particles per axis, 2 per
+    cell per axis) standing in the low-x corner on the sticky floor, released at t = 0;
+    v0 = U(+-0.05); bulk modulus from E, nu (E = 500, nu = 0.3: kappa = 417 in 3D, sound
+    speed sqrt(7 kappa / rho) = 54 within the dt = 1e-4, dx = 1/64 stability limit);
+    loss |COM_T - target|^2 with the target downstream on the floor."""
+    h = 0.5 / n_grid
+    cols = tuple(cols[:dim])
+    lo = [0.1, 4.0 / n_grid] + ([0.5 - cols[2] * h / 2] if dim == 3 else [])
+    x0, _ = lattice(dim, cols, tuple(lo), h)
+    n = x0.shape[1]
+    v0 = _noise(seed, 1, (dim, n))
+    desc = _base_desc(dim=dim, n_grid=n_grid, dt=1e-4, material=LIQUID, steps=steps,
+                      ckpt_every=ckpt_every)
+    target = np.array([0.4, 0.1, 0.5][:dim])
+    return _assemble(desc, [dict(x0=x0, v0=v0, E=np.full(n, E), nu=np.full(n, nu), target=target)])
+
+
 def make(name: str, seed: int = 0, **kw):
-    """Named workloads: 'square2d', 'square2d_grad', 'cube3d', 'rects2d', 'robots3d'."""
+    """Named workloads: 'square2d', 'square2d_grad', 'cube3d', 'rects2d', 'robots3d',
+    'liquid2d', 'liquid3d'."""
+    if name == "liquid2d":
+        return liquid_column(seed, **{"dim": 2, "n_grid": 128, "cols": (64, 96), **kw})
+    if name == "liquid3d":
+        return liquid_column(seed, **{"dim": 3, **kw})
     if name == "square2d":
         return elastic_square_2d(seed, **{"steps": 128, **kw})
     if name == "square2d_grad":

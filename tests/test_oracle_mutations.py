@@ -46,6 +46,12 @@ MUTANTS = {
                     "la[p] = E[p] * nu[p] / ((1.0 + nu[p]) * (1.0 - nu[p]));"),
     "nh_adjoint_cof": ("Fbar[i][j] += mu * A1[i][j] + la * trtb * cof[i][j] / J;",
                        "Fbar[i][j] += mu * A1[i][j] + la * trtb * cof[j][i] / J;"),
+    "liquid_exponent": ("double g = J - pow(J, 1.0 - ORC_LIQUID_GAMMA);\n    for (int i = 0; i < d; i++) tau[i][i] = kap * g;",
+                        "double g = J - pow(J, -ORC_LIQUID_GAMMA);\n    for (int i = 0; i < d; i++) tau[i][i] = kap * g;"),
+    "liquid_bulk_modulus": ("double kap = la + 2.0 * mu / d;\n    double g = J - pow(J, 1.0 - ORC_LIQUID_GAMMA);\n    for (int i",
+                            "double kap = la + mu / d;\n    double g = J - pow(J, 1.0 - ORC_LIQUID_GAMMA);\n    for (int i"),
+    "liquid_adjoint_slope": ("double gp = 1.0 + (ORC_LIQUID_GAMMA - 1.0) * pow(J, -ORC_LIQUID_GAMMA);",
+                             "double gp = 1.0 + ORC_LIQUID_GAMMA * pow(J, -ORC_LIQUID_GAMMA);"),
 }
 
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py"]

@@ -101,7 +101,8 @@ def _blob(dim, n_side, n_grid, centre=0.5, spacing=None, jitter=0.2, rng=RNG):
 
 
 @pytest.mark.parametrize("dim,material", [(2, oracle.FIXED_COROTATED), (3, oracle.FIXED_COROTATED),
-                                          (2, oracle.NEO_HOOKEAN), (3, oracle.NEO_HOOKEAN)])
+                                          (2, oracle.NEO_HOOKEAN), (3, oracle.NEO_HOOKEAN),
+                                          (2, oracle.LIQUID), (3, oracle.LIQUID)])
 def test_momentum_conserved_without_gravity_and_walls(dim, material):
     n_grid = 16
     P = _params(dim, n_grid, dt=1e-3, gravity=(0, 0, 0), walls=0, material=material)
@@ -255,9 +256,18 @@ def _psi_nh(F, mu, la):
     return 0.5 * mu * (np.sum(F * F) - d) - mu * np.log(J) + 0.5 * la * np.log(J) ** 2
 
 
+def _psi_liquid(F, mu, la, gamma=7.0):
+    """Tait-form weakly compressible liquid energy: kappa (J - J^(1-g)/(1-g)), kappa the
+    bulk modulus la + 2 mu / d (no shear energy)."""
+    J = np.linalg.det(F)
+    kap = la + 2.0 * mu / F.shape[0]
+    return kap * (J - J ** (1.0 - gamma) / (1.0 - gamma))
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("material,psi", [(oracle.FIXED_COROTATED, _psi_fcr),
-                                          (oracle.NEO_HOOKEAN, _psi_nh)])
+                                          (oracle.NEO_HOOKEAN, _psi_nh),
+                                          (oracle.LIQUID, _psi_liquid)])
 def test_kirchhoff_is_energy_derivative(dim, material, psi):
     P = _params(dim, material=material)
     mu, la = 417.0, 278.0
@@ -280,6 +290,40 @@ def test_stress_zero_at_rest(dim):
     R = _random_rotation(dim)
     np.testing.assert_allclose(oracle.kirchhoff(Pf, R, 500.0, 300.0), 0, atol=1e-11)
     np.testing.assert_allclose(oracle.kirchhoff(Pn, np.eye(dim), 500.0, 300.0), 0, atol=1e-13)
+    # the liquid carries no shear: zero at any isochoric F (J = 1), rotated or sheared
+    Pl = _params(dim, material=oracle.LIQUID)
+    shear = np.eye(dim)
+    shear[0, 1] = 0.7
+    for F in (R, shear, R @ shear):
+        np.testing.assert_allclose(oracle.kirchhoff(Pl, F, 500.0, 300.0), 0, atol=1e-11)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_liquid_stress_is_hydrostatic_tait_pressure(dim):
+    """tau = -J p I with the Tait pressure p = kappa (J^-7 - 1): compression pushes out."""
+    P = _params(dim, material=oracle.LIQUID)
+    mu, la = 417.0, 278.0
+    kap = la + 2 * mu / dim
+    for F in _random_F(dim, 10, spread=0.3):
+        J = np.linalg.det(F)
+        tau = oracle.kirchhoff(P, F, mu, la)
+        p = kap * (J ** -7.0 - 1.0)
+        np.testing.assert_allclose(tau, -J * p * np.eye(dim), rtol=1e-12, atol=1e-9)
+    t = oracle.kirchhoff(P, 0.95 ** (1.0 / dim) * np.eye(dim), mu, la)
+    assert np.all(np.diag(t) < 0)  # J < 1: negative Kirchhoff stress (positive pressure)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_liquid_small_strain_limit(dim):
+    """Linearised: tau = kappa * gamma * tr(e) I (bulk response only, tangent modulus
+    kappa * gamma at J = 1)."""
+    P = _params(dim, material=oracle.LIQUID)
+    mu, la = 417.0, 278.0
+    e = 1e-7 * RNG.standard_normal((dim, dim))
+    e = 0.5 * (e + e.T)
+    tau = oracle.kirchhoff(P, np.eye(dim) + e, mu, la)
+    kap = la + 2 * mu / dim
+    np.testing.assert_allclose(tau, 7.0 * kap * np.trace(e) * np.eye(dim), rtol=1e-5, atol=1e-12)
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -380,7 +424,7 @@ def test_p2g_stress_momentum_is_minus_energy_gradient(material, psi):
     np.testing.assert_allclose(gp, dt * force, rtol=1e-6, atol=1e-14)
 
 
-@pytest.mark.parametrize("material", [oracle.FIXED_COROTATED, oracle.NEO_HOOKEAN])
+@pytest.mark.parametrize("material", [oracle.FIXED_COROTATED, oracle.NEO_HOOKEAN, oracle.LIQUID])
 def test_stretched_block_contracts(material):
     dim, n_grid = 2, 32
     P = _params(dim, n_grid, dt=1e-4, gravity=(0, 0, 0), walls=0, material=material)
