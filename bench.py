@@ -298,9 +298,14 @@ def main():
     devin = {k: v.to(dev) for k, v in host.items()}
     stream = torch.cuda.current_stream()
 
+    if desc.get("material") == mpm.MPM_MIXED:
+        devin["material"] = torch.as_tensor(a["material"]).to(dev)
+
     def device_step():
         mpm.mpm_set_initial(sim.h, devin["x0"], devin["v0"], devin["C0"], devin["F0"], devin["E"],
                             devin["nu"], devin.get("group"), devin.get("w"))
+        if "material" in devin:
+            mpm.mpm_set_particle_materials(sim.h, devin["material"])
         mpm.mpm_forward(sim.h, T)
         mpm.mpm_loss(sim.h, desc["loss_kind"], devin["target"], bufs["loss"], bufs["gT"], bufs["g0"])
         mpm.mpm_backward(sim.h, bufs["gT"], None, None, None, bufs["gx0"], bufs["gv0"], None, None,
@@ -354,6 +359,8 @@ def main():
     flush.fill_(1)
     mpm.mpm_set_initial(sim.h, devin["x0"], devin["v0"], devin["C0"], devin["F0"], devin["E"],
                         devin["nu"], devin.get("group"), devin.get("w"))
+    if "material" in devin:
+        mpm.mpm_set_particle_materials(sim.h, devin["material"])
     f0.record(stream)
     mpm.mpm_forward(sim.h, T)
     f1.record(stream)

@@ -62,6 +62,10 @@ extern "C" {
                         weakly compressible model of Tampubolon et al. 2017; here in Tait form,
                         Kirchhoff stress kappa (J - J^(1-7)) I with kappa = lambda + 2 mu / dim
                         the bulk modulus of the particle's (E, nu); no shear stress */
+#define MPM_MIXED 4  /* each particle carries its own material id (MPM_FIXED_COROTATED,
+                        MPM_NEO_HOOKEAN or MPM_LIQUID; any other id acts as MPM_LIQUID), set
+                        with mpm_set_particle_materials: a solid and a liquid two-way coupled
+                        through one grid, as in the paper's robot-in-liquid experiment */
 
 /* losses computed by mpm_loss (the compute_loss pattern of Section 3.2) */
 #define MPM_LOSS_COM_TARGET 0 /* L_s = |COM_s(x_T) - target_s|^2 */
@@ -132,7 +136,7 @@ typedef struct mpm_scene_desc {
   float dt;                    /* time step */
   float gravity[3];            /* added as dt*g in the grid update */
   int32_t wall_cells;          /* sticky walls: node i with any i_k < wall or i_k >= n-wall gets v = 0 */
-  int32_t material;            /* MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN or MPM_LIQUID */
+  int32_t material;            /* MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN, MPM_LIQUID or MPM_MIXED */
   float rho;                   /* density; particle volume (dx/2)^dim, mass rho*volume */
   int32_t ckpt_every;          /* k: full state stored every k steps (Appendix D.2), >= 1 */
   int32_t n_groups;            /* actuator groups, 0..8 (0 = no actuation) */
@@ -173,6 +177,14 @@ int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_byt
 int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float* C0,
                     const float* F0, const float* E, const float* nu, const int32_t* group,
                     const float* w, void* stream);
+
+/* MPM_MIXED scenes: the material of every particle (device int32 [N], caller order:
+ * MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN or MPM_LIQUID), copied in and permuted like the
+ * state.  Call after each mpm_set_initial and before mpm_forward (which otherwise fails
+ * with MPM_ERR_STATE); discards any recorded forward.  MPM_ERR_ARG when the scene is not
+ * MPM_MIXED or material is NULL.  The paper couples its 3D robot with its liquid simulator
+ * in one grid; its own API has no separate call for this (materials are fields there). */
+int mpm_set_particle_materials(mpm_handle* h, const int32_t* material, void* stream);
 
 /* Run T steps (1 <= T <= max_steps) from the initial state and record the tape.
  * Stores the full state at steps 0, k, 2k, ... (k = ckpt_every). */

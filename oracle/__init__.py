@@ -37,7 +37,7 @@ _LIBDIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 
 OK, ERR_ARG, ERR_MEM, ERR_OOB, ERR_DOMAIN = 0, 1, 2, 3, 4
-FIXED_COROTATED, NEO_HOOKEAN, NO_ELASTICITY, LIQUID = 0, 1, 2, 3
+FIXED_COROTATED, NEO_HOOKEAN, NO_ELASTICITY, LIQUID, MIXED = 0, 1, 2, 3, 4
 LOSS_COM_TARGET, LOSS_COM_X_DISP = 0, 1
 
 _lock = threading.Lock()
@@ -61,6 +61,7 @@ class Params(ctypes.Structure):
         ("n_basis", ctypes.c_int32),
         ("act_period", ctypes.c_double),
         ("act_phase", ctypes.c_double),
+        ("particle_material", ctypes.c_void_p),
     ]
 
 
@@ -153,6 +154,16 @@ def make_params(dim, n_grid, dt, gravity=(0.0, -9.8, 0.0), wall_cells=3,
     return Params(int(dim), int(n_grid), float(dt), (ctypes.c_double * 3)(*g[:3]),
                   int(wall_cells), int(material), float(rho), int(n_groups), int(n_basis),
                   float(act_period), float(act_phase))
+
+
+def with_materials(params: Params, material) -> Params:
+    """A copy of params whose per-particle material array (MIXED scenes) is `material`
+    (int32, indexed like mu and la; kept alive by the returned object)."""
+    q = Params.from_buffer_copy(params)
+    arr = np.ascontiguousarray(material, dtype=np.int32)
+    q.particle_material = arr.ctypes.data
+    q._material_ref = arr
+    return q
 
 
 def params_from_desc(desc: dict) -> Params:
@@ -364,14 +375,22 @@ def _scene_inputs(scene, sl, si):
     return x0, v0, C0, F0, mu, la, grp, w
 
 
+def scene_params(scene, sl):
+    """Parameters of the scene slice sl (with its per-particle materials when MIXED)."""
+    p = params_from_desc(scene["desc"])
+    if scene["desc"]["material"] == MIXED:
+        p = with_materials(p, scene["arrays"]["material"][sl])
+    return p
+
+
 def simulate(scene, T, keep_all=False):
     """Forward T steps of every scene; returns a list of per-scene state blocks
     (states[T+1] per scene if keep_all, else the final block)."""
-    p = params_from_desc(scene["desc"])
     out = []
     for si, sl in enumerate(_scene_slices(scene)):
         x0, v0, C0, F0, mu, la, grp, w = _scene_inputs(scene, sl, si)
-        out.append(run(p, T, x0, v0, C0, F0, mu, la, grp, w, keep_all=keep_all))
+        out.append(run(scene_params(scene, sl), T, x0, v0, C0, F0, mu, la, grp, w,
+                       keep_all=keep_all))
     return out
 
 
@@ -380,7 +399,6 @@ def loss_and_grad(scene, T):
     all in FP64.  Returns dict with loss, per-scene losses, final states, gx0, gv0,
     gC0, gF0 (component-major, concatenated like the inputs), gE, gnu, gw[S,G,K]."""
     desc = scene["desc"]
-    p = params_from_desc(desc)
     d = desc["dim"]
     a = scene["arrays"]
     N = int(sum(desc["n_particles"]))
@@ -394,6 +412,7 @@ def loss_and_grad(scene, T):
     for si, sl in enumerate(_scene_slices(scene)):
         x0, v0, C0, F0, mu, la, grp, w = _scene_inputs(scene, sl, si)
         n = mu.size
+        p = scene_params(scene, sl)
         states = run(p, T, x0, v0, C0, F0, mu, la, grp, w, keep_all=True)
         xT = unpack_state(states[-1], d, n)[0]
         tgt = a["target"][si] if "target" in a else None

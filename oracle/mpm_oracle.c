@@ -53,6 +53,8 @@
 #define ORC_NEO_HOOKEAN 1
 #define ORC_NO_ELASTICITY 2
 #define ORC_LIQUID 3          /* weakly compressible liquid (the paper's liquid simulator) */
+#define ORC_MIXED 4           /* per-particle material (0, 1 or 3) from particle_material[]:
+                                 the two-way coupling of a solid and a liquid in one grid */
 
 /* Liquid equation of state (Tait form of the weakly compressible model the paper's liquid
    simulator follows, Tampubolon et al. 2017): psi(J) = kappa (J - J^(1-g)/(1-g)), so the
@@ -76,6 +78,8 @@ typedef struct {
   int32_t n_basis;    /* sine terms per group */
   double act_period;  /* P in sin(2 pi k t / P + phi) */
   double act_phase;   /* phi */
+  const int32_t* particle_material; /* [np] material of each particle when material is
+                                       ORC_MIXED (indexed like mu, la), else unused */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -453,11 +457,16 @@ double orc_actuation(const orc_params* P, const double* wact, int g, int t) {
 /* Kirchhoff stress and its adjoint                                    */
 /* ------------------------------------------------------------------ */
 
-static int kirchhoff(const orc_params* P, const mat3 F, double mu, double la, double act, int axis,
-                     mat3 tau) {
+/* the constitutive model of particle p */
+static int material_of(const orc_params* P, int64_t p) {
+  return P->material == ORC_MIXED ? P->particle_material[p] : P->material;
+}
+
+static int kirchhoff_m(const orc_params* P, int material, const mat3 F, double mu, double la,
+                       double act, int axis, mat3 tau) {
   int d = P->dim;
   mzero(tau);
-  if (P->material == ORC_FIXED_COROTATED) {
+  if (material == ORC_FIXED_COROTATED) {
     mat3 R, S, FmR, Ft;
     double J = mdet(d, F);
     if (d == 2) {
@@ -483,7 +492,7 @@ static int kirchhoff(const orc_params* P, const mat3 F, double mu, double la, do
     for (int i = 0; i < d; i++)
       for (int j = 0; j < d; j++) tau[i][j] *= 2.0 * mu;
     for (int i = 0; i < d; i++) tau[i][i] += la * (J - 1.0) * J;
-  } else if (P->material == ORC_NEO_HOOKEAN) {
+  } else if (material == ORC_NEO_HOOKEAN) {
     double J = mdet(d, F);
     if (!(J > 0.0)) return ORC_ERR_DOMAIN;
     mat3 Ft, FFt;
@@ -492,13 +501,13 @@ static int kirchhoff(const orc_params* P, const mat3 F, double mu, double la, do
     for (int i = 0; i < d; i++)
       for (int j = 0; j < d; j++) tau[i][j] = mu * (FFt[i][j] - (i == j ? 1.0 : 0.0));
     for (int i = 0; i < d; i++) tau[i][i] += la * log(J);
-  } else if (P->material == ORC_LIQUID) {
+  } else if (material == ORC_LIQUID) {
     double J = mdet(d, F);
     if (!(J > 0.0)) return ORC_ERR_DOMAIN;
     double kap = la + 2.0 * mu / d;
     double g = J - pow(J, 1.0 - ORC_LIQUID_GAMMA);
     for (int i = 0; i < d; i++) tau[i][i] = kap * g;
-  } else if (P->material != ORC_NO_ELASTICITY) {
+  } else if (material != ORC_NO_ELASTICITY) {
     return ORC_ERR_ARG;
   }
   if (act != 0.0) {
@@ -518,23 +527,23 @@ int orc_kirchhoff(const orc_params* P, const double* Fin, double mu, double la, 
   mzero(F);
   for (int i = 0; i < d; i++)
     for (int j = 0; j < d; j++) F[i][j] = Fin[i * d + j];
-  int rc = kirchhoff(P, F, mu, la, act, axis, tau);
+  int rc = kirchhoff_m(P, P->material, F, mu, la, act, axis, tau);
   for (int i = 0; i < d; i++)
     for (int j = 0; j < d; j++) tau_out[i * d + j] = tau[i][j];
   return rc;
 }
 
 /* adjoint of kirchhoff(): given taubar, accumulate Fbar, mubar, labar, abar */
-static int kirchhoff_adjoint(const orc_params* P, const mat3 F, double mu, double la, double act,
-                             int axis, const mat3 tb, mat3 Fbar, double* mubar, double* labar,
-                             double* abar) {
+static int kirchhoff_adjoint_m(const orc_params* P, int material, const mat3 F, double mu,
+                               double la, double act, int axis, const mat3 tb, mat3 Fbar,
+                               double* mubar, double* labar, double* abar) {
   int d = P->dim;
   mat3 tsum; /* taubar + taubar^T */
   mzero(tsum);
   for (int i = 0; i < d; i++)
     for (int j = 0; j < d; j++) tsum[i][j] = tb[i][j] + tb[j][i];
   double trtb = mtrace(d, tb);
-  if (P->material == ORC_FIXED_COROTATED) {
+  if (material == ORC_FIXED_COROTATED) {
     mat3 R, S, Ft;
     double J = mdet(d, F);
     if (d == 2) {
@@ -576,7 +585,7 @@ static int kirchhoff_adjoint(const orc_params* P, const mat3 F, double mu, doubl
     mmul(d, FmR, Ft, FmRFt);
     *mubar += 2.0 * mdot(d, tb, FmRFt);
     *labar += trtb * (J - 1.0) * J;
-  } else if (P->material == ORC_NEO_HOOKEAN) {
+  } else if (material == ORC_NEO_HOOKEAN) {
     double J = mdet(d, F);
     if (!(J > 0.0)) return ORC_ERR_DOMAIN;
     mat3 A1, cof, Ft, FFt;
@@ -589,7 +598,7 @@ static int kirchhoff_adjoint(const orc_params* P, const mat3 F, double mu, doubl
     for (int i = 0; i < d; i++) FFt[i][i] -= 1.0;
     *mubar += mdot(d, tb, FFt);
     *labar += trtb * log(J);
-  } else if (P->material == ORC_LIQUID) {
+  } else if (material == ORC_LIQUID) {
     /* tau = kappa g(J) I, g(J) = J - J^(1-gamma), g'(J) = 1 + (gamma - 1) J^-gamma,
        dJ/dF = cof F; kappa = la + 2 mu / d */
     double J = mdet(d, F);
@@ -637,7 +646,7 @@ int orc_kirchhoff_adjoint(const orc_params* P, const double* Fin, double mu, dou
       tb[i][j] = tbar_in[i * d + j];
     }
   *mubar = *labar = *abar = 0.0;
-  int rc = kirchhoff_adjoint(P, F, mu, la, act, axis, tb, Fb, mubar, labar, abar);
+  int rc = kirchhoff_adjoint_m(P, P->material, F, mu, la, act, axis, tb, Fb, mubar, labar, abar);
   for (int i = 0; i < d; i++)
     for (int j = 0; j < d; j++) Fbar_out[i * d + j] = Fb[i][j];
   return rc;
@@ -690,7 +699,7 @@ int orc_p2g(const orc_params* P, int64_t np, int t, const double* x, const doubl
     load_mat(d, C, np, p, Cp);
     int axis;
     double act = particle_act(P, grp, wact, p, t, &axis);
-    rc = kirchhoff(P, Fp, mu[p], la[p], act, axis, tau);
+    rc = kirchhoff_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tau);
     if (rc) return rc;
     mzero(A);
     for (int i = 0; i < d; i++)
@@ -963,7 +972,7 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
     load_mat(d, C, np, p, Cp);
     int axis;
     double act = particle_act(P, grp, wact, p, t, &axis);
-    rc = kirchhoff(P, Fp, mu[p], la[p], act, axis, tau);
+    rc = kirchhoff_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tau);
     if (rc) goto done;
     mzero(A);
     for (int i = 0; i < d; i++)
@@ -1003,7 +1012,8 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
       }
     load_mat(d, Fb, np, p, Fbp);
     double abar = 0.0;
-    rc = kirchhoff_adjoint(P, Fp, mu[p], la[p], act, axis, tb, Fbp, &mubar[p], &labar[p], &abar);
+    rc = kirchhoff_adjoint_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tb, Fbp, &mubar[p],
+                             &labar[p], &abar);
     if (rc) goto done;
     if (P->n_groups > 0 && grp && wact && wbar) {
       int gi = grp[p];

@@ -19,8 +19,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["kernels_3d_fcr.cu", "kernels_3d_fcr_det.cu", "kernels_3d_nh.cu", "kernels_3d_nh_det.cu",
-           "kernels_3d_liq.cu", "kernels_3d_liq_det.cu", "kernels_2d.cu", "setup.cu", "mpm_api.cu",
-           "noalloc.cu"]
+           "kernels_3d_liq.cu", "kernels_3d_liq_det.cu", "kernels_3d_mixed.cu",
+           "kernels_3d_mixed_det.cu", "kernels_2d.cu", "setup.cu", "mpm_api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE]
@@ -43,7 +43,8 @@ def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(f) > t for f in _deps())
+    objs = [os.path.join(OUT_DIR, src.replace(".cu", ".o")) for src in SOURCES]
+    return any(not os.path.exists(o) for o in objs) or any(os.path.getmtime(f) > t for f in _deps())
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:

@@ -18,6 +18,8 @@ MPM_INSTANTIATE(2, kFixedCorotated, true)
 MPM_INSTANTIATE(2, kNeoHookean, true)
 MPM_INSTANTIATE(2, kLiquid, false)
 MPM_INSTANTIATE(2, kLiquid, true)
+MPM_INSTANTIATE(2, kMixed, false)
+MPM_INSTANTIATE(2, kMixed, true)
 template cudaError_t launch_clear<2>(const Clears&, int, int, int, int, cudaStream_t);
 template cudaError_t launch_clear<3>(const Clears&, int, int, int, int, cudaStream_t);
 

@@ -53,7 +53,7 @@ constexpr int kUBSlots = 4;  // velocity-adjoint grids in flight (need: 3)
 struct Layout {
   size_t perm, keys0, keys1, idx0, sort_tmp, sort_tmp_bytes;
   size_t tiles, scene_off, scene_tiles, scene_tile_off;
-  size_t mu, la, E, nu, group, wact, wbar_tile, mubar, labar;
+  size_t mu, la, E, nu, group, matid, wact, wbar_tile, mubar, labar;
   size_t fin, cur, ckpt, seg, adj;
   size_t rcache;  // (K+1) x [9][N] FP64 polar factors of a re-simulated segment (3D FCR)
   size_t grids;  // kPMSlots + kUBSlots dense grids
@@ -95,7 +95,7 @@ bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
   if (!(d->dt > 0.0f) || !std::isfinite(d->dt)) return fail("dt must be > 0");
   if (d->wall_cells < 0 || 2 * d->wall_cells >= d->n_grid) return fail("bad wall_cells");
   if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN &&
-      d->material != MPM_LIQUID)
+      d->material != MPM_LIQUID && d->material != MPM_MIXED)
     return fail("unknown material");
   if (!(d->rho > 0.0f)) return fail("rho must be > 0");
   if (d->ckpt_every < 1) return fail("ckpt_every must be >= 1");
@@ -117,7 +117,7 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
   m.K = d->ckpt_every < max_steps ? d->ckpt_every : max_steps;
   m.n_ckpt = (max_steps - 1) / m.K + 1;  // states 0, K, 2K, ... < max_steps
   m.n_grid = d->n_grid;
-  m.polar_cache = d->dim == 3 && d->material == MPM_FIXED_COROTATED;
+  m.polar_cache = d->dim == 3 && (d->material == MPM_FIXED_COROTATED || d->material == MPM_MIXED);
   m.T_max = max_steps;
   m.words = d->deterministic_p2g ? 2 : 1;
   m.nnodes = 1;
@@ -155,6 +155,7 @@ Layout make_layout(const Dims& m) {
   L.E = take(N * 4);
   L.nu = take(N * 4);
   L.group = take(N * 4);
+  L.matid = take(N * 4);
   L.wact = take(S * kMaxGroups * kMaxBasis * 4);
   L.wbar_tile = take((size_t)m.n_tiles * kMaxGroups * kMaxBasis * 4);
   L.mubar = take(N * 4);
@@ -191,6 +192,7 @@ struct mpm_handle {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool initialized = false;
+  bool materials_set = false;  // MPM_MIXED: per-particle materials given since the last set-up
   int32_t T_recorded = 0;
   // options
   bool use_graphs = true;
@@ -496,6 +498,7 @@ struct Launcher {
     A.mu = h->at<float>(h->L.mu);
     A.la = h->at<float>(h->L.la);
     A.group = h->at<int>(h->L.group);
+    A.matid = h->at<int>(h->L.matid);
     A.wact = h->at<float>(h->L.wact);
     A.err = h->at<unsigned>(h->L.err);
     if (read >= 0) A.PMr = ring_grid(h, h->pm, read);
@@ -541,6 +544,7 @@ struct Launcher {
     A.mubar = h->at<float>(h->L.mubar);
     A.labar = h->at<float>(h->L.labar);
     A.group = h->at<int>(h->L.group);
+    A.matid = h->at<int>(h->L.matid);
     A.wact = h->at<float>(h->L.wact);
     A.wbar_tile = h->at<float>(h->L.wbar_tile);
     A.err = h->at<unsigned>(h->L.err);
@@ -891,13 +895,30 @@ int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float
   ring_reset(h->ub);
   h->launches += 3;
   h->initialized = true;
+  h->materials_set = false;
   h->T_recorded = 0;
+  return MPM_OK;
+}
+
+int mpm_set_particle_materials(mpm_handle* h, const int32_t* material, void* stream) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  if (!material) return fail(h, MPM_ERR_ARG, "material is NULL");
+  if (h->desc.material != MPM_MIXED) return fail(h, MPM_ERR_ARG, "the scene is not MPM_MIXED");
+  if (!h->initialized) return fail(h, MPM_ERR_STATE, "mpm_set_initial has not been called");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  CK(launch_gather_int(h->m.N, h->at<int>(h->L.perm), material, h->at<int>(h->L.matid), s));
+  ++h->launches;
+  h->T_recorded = 0;
+  h->materials_set = true;
   return MPM_OK;
 }
 
 int mpm_forward(mpm_handle* h, int32_t T, void* stream) {
   if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
   if (!h->initialized) return fail(h, MPM_ERR_STATE, "mpm_set_initial has not been called");
+  if (h->desc.material == MPM_MIXED && !h->materials_set)
+    return fail(h, MPM_ERR_STATE, "MPM_MIXED: mpm_set_particle_materials has not been called");
   if (T < 1 || T > h->max_steps) return fail(h, MPM_ERR_STATE, "T must be in [1, max_steps]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   h->last_stream = s;

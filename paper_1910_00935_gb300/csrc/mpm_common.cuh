@@ -43,7 +43,9 @@ constexpr unsigned kErrNonFinite = 2u;
 constexpr unsigned kErrTimeout = 4u;
 constexpr unsigned kErrRange = 8u;  // a fixed-point grid contribution left its range
 
-enum Material : int { kFixedCorotated = 0, kNeoHookean = 1, kLiquid = 3 };
+// kMixed: each particle carries one of the other three (a solid and a liquid coupled
+// through one grid)
+enum Material : int { kFixedCorotated = 0, kNeoHookean = 1, kLiquid = 3, kMixed = 4 };
 // weakly compressible liquid (Tait form of the model the paper's liquid simulator follows,
 // Tampubolon et al. 2017): tau = kappa (J - J^(1-g)) I, kappa = la + 2 mu / d, g = 7
 constexpr float kLiquidGamma = 7.0f;
@@ -550,7 +552,14 @@ struct StressCache {
 template <int D, int MAT>
 __device__ __forceinline__ bool kirchhoff(const float E[D][D], float mu, float la, float act, int axis,
                                           float tau[D][D], StressCache<D>& sc,
-                                          const double* Rc = nullptr, int64_t N = 0, int64_t p = 0) {
+                                          const double* Rc = nullptr, int64_t N = 0, int64_t p = 0,
+                                          int mat_p = MAT) {
+  if (MAT == kMixed) {  // the particle's own model (mat_p)
+    if (mat_p == kFixedCorotated)
+      return kirchhoff<D, kFixedCorotated>(E, mu, la, act, axis, tau, sc, Rc, N, p);
+    if (mat_p == kNeoHookean) return kirchhoff<D, kNeoHookean>(E, mu, la, act, axis, tau, sc);
+    return kirchhoff<D, kLiquid>(E, mu, la, act, axis, tau, sc);
+  }
   bool ok = true;
   sc.Jm1 = det_minus_one<D>(E);
   sc.J = 1.0f + sc.Jm1;
@@ -614,7 +623,14 @@ template <int D, int MAT>
 __device__ __forceinline__ float kirchhoff_adjoint(const float E[D][D], float mu, float la, float act,
                                                    int axis, const StressCache<D>& sc,
                                                    const float tb[D][D], float Fbar[D][D],
-                                                   float& mubar, float& labar) {
+                                                   float& mubar, float& labar, int mat_p = MAT) {
+  if (MAT == kMixed) {
+    if (mat_p == kFixedCorotated)
+      return kirchhoff_adjoint<D, kFixedCorotated>(E, mu, la, act, axis, sc, tb, Fbar, mubar, labar);
+    if (mat_p == kNeoHookean)
+      return kirchhoff_adjoint<D, kNeoHookean>(E, mu, la, act, axis, sc, tb, Fbar, mubar, labar);
+    return kirchhoff_adjoint<D, kLiquid>(E, mu, la, act, axis, sc, tb, Fbar, mubar, labar);
+  }
   float trtb = 0.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i) trtb += tb[i][i];

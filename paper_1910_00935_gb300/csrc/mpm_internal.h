@@ -41,6 +41,8 @@ cudaError_t launch_clear(const Clears& C, int nnodes, int n_grid, int n_scenes, 
       return P.det ? FN<D, kNeoHookean, true>(__VA_ARGS__) : FN<D, kNeoHookean, false>(__VA_ARGS__); \
     case kLiquid:                                                                       \
       return P.det ? FN<D, kLiquid, true>(__VA_ARGS__) : FN<D, kLiquid, false>(__VA_ARGS__); \
+    case kMixed:                                                                        \
+      return P.det ? FN<D, kMixed, true>(__VA_ARGS__) : FN<D, kMixed, false>(__VA_ARGS__); \
   }                                                                                     \
   return cudaErrorInvalidValue;
 
@@ -76,6 +78,9 @@ cudaError_t launch_gather_initial(int dim, int64_t N, const int* perm, const flo
 cudaError_t launch_reset_boxes(int* boxes, int64_t n_boxes, cudaStream_t s);
 cudaError_t launch_gather_rows(int rows, int64_t N, const int* perm, const float* src_caller,
                                float* dst_internal, cudaStream_t s);
+// dst[i] = src[perm[i]] for int32 rows (per-particle material ids)
+cudaError_t launch_gather_int(int64_t N, const int* perm, const int* src_caller, int* dst_internal,
+                              cudaStream_t s);
 // identity_dim > 0: rows are a dim x dim matrix per particle and I is added on the way out
 cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const float* src_internal,
                                 float* dst_caller, int identity_dim, cudaStream_t s);

@@ -67,6 +67,7 @@ struct StepArgs {
   const float* mu;
   const float* la;
   const int* group;
+  const int* matid;        // per-particle material (kMixed scenes) or null
   const float* wact;       // [scene][group][basis]
   const float4* PMr;       // grid (m, p) of step t-1, read by G2P (null: P2G only)
   float4* PMw;             // grid of step t, accumulated by P2G (null: G2P only)
@@ -90,6 +91,7 @@ struct AdjArgs {
   float* mubar;
   float* labar;
   const int* group;
+  const int* matid;   // per-particle material (kMixed scenes) or null
   const float* wact;
   float* wbar_tile;   // [tile][group][basis] per-tile dL/dw partial sums (this pass adds)
   const float4* PM1;  // grid (m, p) of step s+1 (P2G-adjoint)
@@ -660,7 +662,7 @@ template <int D, int MAT, bool DET>
 __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis, bool active, int scene,
                                          int64_t p, int count, const float x[D], const float v[D],
                                          const float C[D][D], const float E[D][D], float mu_p,
-                                         float la_p, const int* group, const float* wact,
+                                         float la_p, int mat_p, const int* group, const float* wact,
                                          float4* g, int* box_scene, float* sm, float* xr,
                                          int* s_box, int* s_bbox, unsigned& err,
                                          const double* R_in, double* R_out, int64_t N) {
@@ -679,11 +681,12 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
     const float act = particle_act(P, basis, group, wact, scene, p, D, axis);
     float tau[D][D];
     StressCache<D> sc;
-    if (!kirchhoff<D, MAT>(E, mu_p, la_p, act, axis, tau, sc, R_in, N, p)) {
+    if (!kirchhoff<D, MAT>(E, mu_p, la_p, act, axis, tau, sc, R_in, N, p, mat_p)) {
       err |= kErrNonFinite;
       ok = false;
     }
-    if (MAT == kFixedCorotated && R_out && active) polar_to_cache<D>(R_out, N, p, sc.pol);
+    if ((MAT == kFixedCorotated || (MAT == kMixed && mat_p == kFixedCorotated)) && R_out && active)
+      polar_to_cache<D>(R_out, N, p, sc.pol);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       mv[i] = P.p_mass * v[i];
@@ -835,7 +838,7 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
   if (MODE != kG2POnlyFull) {
     stage_wait<0>();
     p2g_pass<D, MAT, DET>(P, P.basis, active, scene, p, tile.z, x, v, C, E, staged(stage, 0),
-                          staged(stage, 1), A.group, A.wact,
+                          staged(stage, 1), MAT == kMixed ? A.matid[p] : MAT, A.group, A.wact,
                      scene_grid(A.PMw, scene, P), A.box_w + scene * 8, sm, xr, s_box, s_bbox,
                      err, nullptr, A.Rw, N);
   }
@@ -932,7 +935,8 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     const float mu = A.mu[p], la = A.la[p];
     float tau[D][D];
     StressCache<D> sc;
-    if (!kirchhoff<D, MAT>(E, mu, la, act, axis, tau, sc, A.R1, N, p) && ok) {
+    const int mat_p = MAT == kMixed ? A.matid[p] : MAT;
+    if (!kirchhoff<D, MAT>(E, mu, la, act, axis, tau, sc, A.R1, N, p, mat_p) && ok) {
       err |= kErrNonFinite;
       ok = false;
     }
@@ -1032,7 +1036,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
         tb[i][j] = P.kappa * Ab[i][j];
       }
     float mub = 0.0f, lab = 0.0f, abar = 0.0f;
-    if (ok) abar = kirchhoff_adjoint<D, MAT>(E, mu, la, act, axis, sc, tb, Fb, mub, lab);
+    if (ok) abar = kirchhoff_adjoint<D, MAT>(E, mu, la, act, axis, sc, tb, Fb, mub, lab, mat_p);
     if (active) {
       A.mubar[p] += mub;
       A.labar[p] += lab;
@@ -1253,7 +1257,8 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
 #pragma unroll
       for (int j = 0; j < D; ++j) E[i][j] = staged(stage, b + R::F + i * D + j) - (i == j ? P.f_diag : 0.0f);
     p2g_pass<D, MAT, DET>(P, P.basis2, active, scene, p, tile.z, x, v, C, E, staged(stage, b + R::Q),
-                          staged(stage, b + R::Q + 1), A.group, A.wact,
+                          staged(stage, b + R::Q + 1), MAT == kMixed ? A.matid[p] : MAT, A.group,
+                          A.wact,
                      scene_grid(A.PMm, scene, P), A.box_m + scene * 8, sm, xr, s_box, s_bbox_pm,
                      err, A.Rm, nullptr, N);
   }

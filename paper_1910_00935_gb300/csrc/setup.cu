@@ -93,6 +93,12 @@ __global__ void reset_boxes_kernel(int* boxes, int64_t n) {
     boxes[i] = (i % 8) < 4 ? INT_MAX : INT_MIN;
 }
 
+__global__ void gather_int_kernel(int64_t N, const int* perm, const int* src, int* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[perm[i]];
+}
+
 __global__ void gather_rows_kernel(int rows, int64_t N, const int* perm, const float* src,
                                    float* dst) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
@@ -256,6 +262,12 @@ cudaError_t launch_reset_boxes(int* boxes, int64_t n_boxes, cudaStream_t s) {
 cudaError_t launch_gather_rows(int rows, int64_t N, const int* perm, const float* src_caller,
                                float* dst_internal, cudaStream_t s) {
   gather_rows_kernel<<<grid_for(N), 256, 0, s>>>(rows, N, perm, src_caller, dst_internal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_int(int64_t N, const int* perm, const int* src_caller, int* dst_internal,
+                              cudaStream_t s) {
+  gather_int_kernel<<<grid_for(N), 256, 0, s>>>(N, perm, src_caller, dst_internal);
   return cudaGetLastError();
 }
 

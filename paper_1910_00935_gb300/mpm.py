@@ -27,7 +27,7 @@ MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOB = 0, 1, 2, 3
 MPM_ERR_NONFINITE, MPM_ERR_TIMEOUT, MPM_ERR_STATE, MPM_ERR_WORKSPACE = 4, 5, 6, 7
 MPM_ERR_TOO_LARGE, MPM_ERR_RANGE = 8, 9
 MPM_NOALLOC_MAX_NODES = MPM_NOALLOC_MAX_PARTICLES = 1 << 18
-MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN, MPM_LIQUID = 0, 1, 3
+MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN, MPM_LIQUID, MPM_MIXED = 0, 1, 3, 4
 MPM_LOSS_COM_TARGET, MPM_LOSS_COM_X_DISP = 0, 1
 MPM_OPT_USE_GRAPHS, MPM_OPT_SMEM_TILE, MPM_OPT_TILE_CAPACITY, MPM_OPT_PROFILE = 1, 2, 3, 4
 MPM_OPT_GATHER_CAPACITY, MPM_OPT_GRID_BLOCKS, MPM_OPT_POLAR_CACHE = 5, 6, 7
@@ -41,7 +41,7 @@ MPM_INFO_KERNEL_LAUNCHES, MPM_INFO_N_TOTAL, MPM_INFO_STEPS_RECORDED = 1, 2, 3
 EXPORTED = ["mpm_workspace_bytes", "mpm_create", "mpm_set_initial", "mpm_forward",
             "mpm_get_state", "mpm_loss", "mpm_backward", "mpm_sync_status", "mpm_set_option",
             "mpm_get_info", "mpm_get_profile", "mpm_last_error", "mpm_destroy",
-            "mpm_step_noalloc"]
+            "mpm_step_noalloc", "mpm_set_particle_materials"]
 
 
 class MPMError(RuntimeError):
@@ -104,6 +104,7 @@ def lib(load_only: bool = False):
             "mpm_last_error": (ctypes.c_char_p, [vp]),
             "mpm_destroy": (None, [vp]),
             "mpm_step_noalloc": (ctypes.c_int, [D, vp, vp, vp, vp, vp, vp]),
+            "mpm_set_particle_materials": (ctypes.c_int, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -170,6 +171,10 @@ def mpm_create(desc: SceneDesc, workspace, workspace_bytes: int, max_steps: int)
 def mpm_set_initial(h, x0, v0, C0, F0, E, nu, group=None, w=None, stream=None):
     _check(lib().mpm_set_initial(h, _ptr(x0), _ptr(v0), _ptr(C0), _ptr(F0), _ptr(E), _ptr(nu),
                                  _ptr(group), _ptr(w), _stream(stream)), h)
+
+
+def mpm_set_particle_materials(h, material, stream=None):
+    _check(lib().mpm_set_particle_materials(h, _ptr(material), _stream(stream)), h)
 
 
 def mpm_forward(h, T: int, stream=None):
@@ -276,12 +281,18 @@ class Simulator:
     def _f(self, t, rows=None):
         return None if t is None else t.to(self.device, torch.float32).contiguous()
 
-    def set_initial(self, x0, v0, C0=None, F0=None, E=None, nu=None, group=None, w=None):
+    def set_initial(self, x0, v0, C0=None, F0=None, E=None, nu=None, group=None, w=None,
+                    material=None):
+        """material: int32 [N] per-particle material ids (MPM_MIXED scenes only)."""
         self._inputs = [self._f(x0), self._f(v0), self._f(C0), self._f(F0), self._f(E),
                         self._f(nu),
                         None if group is None else group.to(self.device, torch.int32).contiguous(),
                         self._f(w)]
         mpm_set_initial(self.h, *self._inputs)
+        if material is not None:
+            self._material = material.to(self.device, torch.int32).contiguous()
+        if self.desc.get("material") == MPM_MIXED:  # every set-up re-sorts the particles
+            mpm_set_particle_materials(self.h, self._material)
 
     def forward(self, T):
         mpm_forward(self.h, int(T))
@@ -358,5 +369,6 @@ def from_scene(scene, max_steps=None, device="cuda"):
     G = desc.get("n_groups", 0)
     t = lambda k: torch.as_tensor(a[k])
     sim.set_initial(t("x0"), t("v0"), t("C0"), t("F0"), t("E"), t("nu"),
-                    t("group") if G else None, t("w") if G else None)
+                    t("group") if G else None, t("w") if G else None,
+                    t("material") if desc.get("material") == MPM_MIXED else None)
     return sim

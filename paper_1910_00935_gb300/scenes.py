@@ -20,7 +20,7 @@ import math
 
 import numpy as np
 
-FIXED_COROTATED, NEO_HOOKEAN, LIQUID = 0, 1, 3
+FIXED_COROTATED, NEO_HOOKEAN, LIQUID, MIXED = 0, 1, 3, 4
 LOSS_COM_TARGET, LOSS_COM_X_DISP = 0, 1
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -198,13 +198,47 @@ def liquid_column(seed=0, dim=3, steps=256, n_grid=64, cols=(32, 48, 32), E=500.
     return _assemble(desc, [dict(x0=x0, v0=v0, E=np.full(n, E), nu=np.full(n, nu), target=target)])
 
 
+def robot_in_liquid(seed=0, steps=256, n_grid=64, robot=(32, 16, 16), pool=(96, 12, 48),
+                    ckpt_every=32, w_scale=50.0):
+    """Two-way coupling in one grid (the paper's robot-in-liquid experiment): an actuated
+    fixed-corotated robot (robot particles per axis, 8 octant groups, 4 sine terms, w ~
+    U(+-w_scale)) standing in a shallow pool of weakly compressible liquid (pool particles
+    per axis, 2 per cell per axis, on the sticky floor).  Robot E = 5e3, nu = 0.3; liquid
+    E = 500, nu = 0.3.  Per-particle materials (MIXED); loss -(COM_x(T) - COM_x(0)) of the
+    whole scene.  The robot stands on the floor beside the pool's far end."""
+    h = 0.5 / n_grid
+    floor = 4.0 / n_grid
+    px0 = 0.1
+    xl, _ = lattice(3, pool, (px0, floor, 0.5 - pool[2] * h / 2), h)
+    rx0 = px0 + 2 * h
+    xr, _ = lattice(3, robot, (rx0, floor + pool[1] * h * 0.5, 0.5 - robot[2] * h / 2), h)
+    nr, nl = xr.shape[1], xl.shape[1]
+    x0 = np.concatenate([xr, xl], axis=1)
+    n = nr + nl
+    v0 = _noise(seed, 1, (3, n))
+    rel = (xr - xr.min(1, keepdims=True)) / (xr.max(1, keepdims=True) - xr.min(1, keepdims=True))
+    bits = (rel > 0.5).astype(np.int32)
+    group = np.concatenate([bits[0] + 2 * bits[1] + 4 * bits[2], np.full(nl, -1, np.int32)])
+    G, K = 8, 4
+    w = (uniform(seed, 2, G * K).reshape(G, K) * 2.0 - 1.0) * w_scale
+    E = np.concatenate([np.full(nr, 5e3), np.full(nl, 500.0)])
+    desc = _base_desc(dim=3, n_grid=n_grid, dt=1e-4, material=MIXED, steps=steps,
+                      ckpt_every=ckpt_every, n_groups=G, n_basis=K, loss_kind=LOSS_COM_X_DISP)
+    scene = _assemble(desc, [dict(x0=x0, v0=v0, E=E, nu=np.full(n, 0.3), group=group, w=w)])
+    scene["arrays"]["material"] = np.ascontiguousarray(
+        np.concatenate([np.full(nr, FIXED_COROTATED), np.full(nl, LIQUID)]).astype(np.int32))
+    return scene
+
+
 def make(name: str, seed: int = 0, **kw):
     """Named workloads: 'square2d', 'square2d_grad', 'cube3d', 'rects2d', 'robots3d',
-    'liquid2d', 'liquid3d'."""
+    'liquid2d', 'liquid3d', 'robot_in_liquid'."""
     if name == "liquid2d":
         return liquid_column(seed, **{"dim": 2, "n_grid": 128, "cols": (64, 96), **kw})
     if name == "liquid3d":
         return liquid_column(seed, **{"dim": 3, **kw})
+    if name == "robot_in_liquid":
+        return robot_in_liquid(seed, **kw)
     if name == "square2d":
         return elastic_square_2d(seed, **{"steps": 128, **kw})
     if name == "square2d_grad":

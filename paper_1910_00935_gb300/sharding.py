@@ -33,7 +33,8 @@ def subset(scene, idx):
     off = np.concatenate([[0], np.cumsum(desc["n_particles"])])
     sl = [slice(int(off[i]), int(off[i + 1])) for i in idx]
     cols = lambda k: np.ascontiguousarray(np.concatenate([a[k][..., s] for s in sl], axis=-1))
-    arr = {k: cols(k) for k in ("x0", "v0", "C0", "F0", "E", "nu", "group")}
+    arr = {k: cols(k) for k in ("x0", "v0", "C0", "F0", "E", "nu", "group") + (
+        ("material",) if "material" in a else ())}
     arr["w"] = np.ascontiguousarray(a["w"][idx])
     arr["target"] = np.ascontiguousarray(a["target"][idx])
     desc["n_particles"] = [int(desc["n_particles"][i]) for i in idx]

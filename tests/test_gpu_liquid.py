@@ -66,3 +66,49 @@ def test_liquid_loss_gradient_and_deterministic_mode(mpm):
         assert np.array_equal(a["grad"][key], b["grad"][key]), key
     od = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
     _compare_grads(a["grad"], od, ["gx0", "gv0", "gF0", "gE"], GRAD_TOL)
+
+
+# ---------------------------------------------------------------------------
+# two-way coupling: an actuated fixed-corotated robot in a liquid pool, one grid
+# (MPM_MIXED, per-particle materials)
+# ---------------------------------------------------------------------------
+
+COUPLED = dict(robot=(16, 8, 8), pool=(48, 8, 24))
+
+
+def test_robot_in_liquid_one_step_and_forward(mpm):
+    scene = scenes.make("robot_in_liquid", **COUPLED)
+    g = _run_gpu(mpm, scene, 1, loss=False)
+    _compare_states(g["state"], _oracle_states(scene, 1), scene, STEP_TOL)
+    T = 60
+    g = _run_gpu(mpm, scene, T, loss=False)
+    _compare_states(g["state"], _oracle_states(scene, T), scene, POS_TOL)
+
+
+def test_robot_in_liquid_gradients(mpm):
+    """Random linear functionals of the final state: every adjoint term of both materials,
+    the actuation weights (only the robot is actuated) and the polar cache of the robot's
+    particles."""
+    scene = scenes.make("robot_in_liquid", **COUPLED)
+    T, k = 24, 10
+    scene["desc"]["ckpt_every"] = k
+    seeds = _random_seeds(scene, np.random.default_rng(33))
+    g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    o = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
+    _compare_grads(g["grad"], o, ["gx0", "gv0", "gC0", "gF0", "gE", "gnu", "gw"])
+
+
+def test_mixed_scene_needs_its_materials(mpm):
+    scene = scenes.make("robot_in_liquid", robot=(8, 8, 8), pool=(16, 4, 16))
+    sim = mpm.Simulator(scene["desc"], 4)
+    a = scene["arrays"]
+    t = lambda key: torch.as_tensor(a[key])
+    mpm.mpm_set_initial(sim.h, *[t(k).cuda().contiguous() for k in ("x0", "v0", "C0", "F0", "E", "nu")],
+                        t("group").cuda().contiguous(), t("w").cuda().contiguous())
+    with pytest.raises(mpm.MPMError) as ei:
+        sim.forward(4)
+    assert ei.value.code == mpm.MPM_ERR_STATE
+    mpm.mpm_set_particle_materials(sim.h, t("material").cuda().contiguous())
+    sim.forward(4)
+    assert mpm.mpm_sync_status(sim.h) == mpm.MPM_OK
+    sim.close()

@@ -80,12 +80,12 @@ def _random_seeds(scene, rng, scale=1.0):
 def _oracle_grad_linear(scene, T, seeds):
     """Oracle gradient of L = <seeds, state_T> (per scene)."""
     desc = scene["desc"]
-    p = oracle.params_from_desc(desc)
     d = desc["dim"]
     a = scene["arrays"]
     res = {k: [] for k in ("gx0", "gv0", "gC0", "gF0", "gE", "gnu", "gw")}
     for si in range(len(desc["n_particles"])):
         sl = scene_slice(scene, si)
+        p = oracle.scene_params(scene, sl)  # with the slice's per-particle materials if any
         mu, la = oracle.lame(a["E"][sl], a["nu"][sl])
         grp = a["group"][sl] if desc["n_groups"] else None
         w = a["w"][si] if desc["n_groups"] else None
