@@ -194,6 +194,7 @@ struct mpm_handle {
   bool initialized = false;
   bool materials_set = false;  // MPM_MIXED: per-particle materials given since the last set-up
   int32_t T_recorded = 0;
+  int32_t resident_T = 0;  // T of the forward whose last segment is still in the segment buffer
   // options
   bool use_graphs = true;
   bool smem_tile = false;  // measured on GB300: global float4 reductions beat shared FP32 atomics
@@ -618,26 +619,35 @@ struct Launcher {
   } while (0)
 
 // forward: states 0..T; full state stored at multiples of K and at T (fin)
+// first step of the last segment of a T-step run: the forward leaves that segment's states
+// (and their FP64 polar factors) in the segment buffer, so the backward starts without
+// re-simulating it -- with ckpt_every >= T nothing is re-simulated at all
+int last_segment_start(const mpm_handle* h, int T) { return ((T - 1) / h->m.K) * h->m.K; }
+
 int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
   const int K = h->m.K;
+  const int sL = last_segment_start(h, T);
   ring_reset(h->pm);
   ring_reset(h->ub);
   const float* src = h->state(h->L.ckpt, 0);
   float* cur = h->at<float>(h->L.cur);
   int g = -1;
-  LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g));
+  LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g, sL == 0 ? h->rslot(0) : nullptr));
   for (int t = 1; t < T; ++t) {
     float* dst;
     int mode;
     if (t % K == 0) {
       dst = h->state(h->L.ckpt, t / K);
       mode = kG2PP2GFull;
+    } else if (t > sL) {
+      dst = h->state(h->L.seg, t - sL);
+      mode = kG2PP2GFull;
     } else {
       dst = cur;
       mode = kG2PP2G;
     }
     int g_next = -1;
-    LK(Lc.step(mode, t, src, dst, g, &g_next));
+    LK(Lc.step(mode, t, src, dst, g, &g_next, t >= sL ? h->rslot(t - sL) : nullptr));
     ring_release(h->pm, g);
     g = g_next;
     src = dst;
@@ -668,7 +678,7 @@ int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top, int* grid_top_minu
   return MPM_OK;
 }
 
-int issue_backward(mpm_handle* h, Launcher& Lc, int T) {
+int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident) {
   const int K = h->m.K;
   ring_reset(h->pm);
   ring_reset(h->ub);
@@ -677,12 +687,16 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T) {
   for (int s = T - 1; s >= 0; --s) {
     const int j = s / K, s0 = j * K;
     const int top = (s0 + K < T) ? s0 + K : T;
-    if (s == top - 1) {
+    if (s == T - 1 && resident) {
+      // the forward left this segment's states in place: only the grid of step T-1
+      const float* st = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
+      LK(Lc.step(kP2GOnly, s, st, nullptr, -1, &pm_s));
+    } else if (s == top - 1) {
       int rc = issue_resim(h, Lc, s0, top, &pm_s);
       if (rc) return rc;
     }
     const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
-    const float* st_s1 = h->state(h->L.seg, s + 1 - s0);
+    const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->state(h->L.seg, s + 1 - s0);
     const float* st_sm = (s - 1 >= s0) ? ((s - 1 == s0) ? h->state(h->L.ckpt, j)
                                                           : h->state(h->L.seg, s - 1 - s0))
                                         : nullptr;
@@ -925,6 +939,7 @@ int mpm_forward(mpm_handle* h, int32_t T, void* stream) {
   int rc = run_sequence(h, (int64_t)T * 2, s, [&](Launcher& Lc) { return issue_forward(h, Lc, T); });
   if (rc) return rc;
   h->T_recorded = T;
+  h->resident_T = T;
   return MPM_OK;
 }
 
@@ -997,8 +1012,13 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   if (GK) CK(cudaMemsetAsync(h->at<float>(L.wbar_tile), 0, (size_t)m.n_tiles * GK * 4, s));
   h->launches += 4;
   const int T = h->T_recorded;
-  int rc = run_sequence(h, (int64_t)T * 2 + 1, s, [&](Launcher& Lc) { return issue_backward(h, Lc, T); });
+  const bool resident = h->resident_T == T;
+  const int64_t key = (int64_t)T * 2 + 1 + (resident ? 0 : ((int64_t)1 << 40));
+  int rc = run_sequence(h, key, s, [&](Launcher& Lc) { return issue_backward(h, Lc, T, resident); });
   if (rc) return rc;
+  // re-simulating the earlier segments reused the segment buffer: a later backward of
+  // the same forward re-simulates the last segment as well
+  if (last_segment_start(h, T) > 0) h->resident_T = 0;
   float* outs[4] = {gx0, gv0, gC0, gF0};
   r0 = 0;
   for (int k = 0; k < 4; ++k) {

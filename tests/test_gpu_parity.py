@@ -265,6 +265,38 @@ def test_graphs_and_tiles_do_not_change_results(mpm):
             assert rel_l2(g["grad"][key], ref["grad"][key]) <= 1e-4, (opts, key)
 
 
+def test_backward_twice_and_single_segment(mpm):
+    """The forward leaves its last segment in the segment buffer, so the backward starts
+    without re-simulating it (nothing is re-simulated when ckpt_every >= T).  A second
+    backward of the same forward must still be right (the earlier segments' re-simulation
+    reused that buffer), and the single-segment run needs no re-simulation passes."""
+    scene = scenes.make("robots3d", n_scenes=2, dims=(16, 8, 8))
+    T = 20
+    seeds = _random_seeds(scene, np.random.default_rng(6))
+    o = _oracle_grad_linear(scene, T, {k: v.astype(np.float64) for k, v in seeds.items()})
+    keys = ["gx0", "gv0", "gC0", "gF0", "gE", "gnu", "gw"]
+    for k in (6, 20):
+        scene["desc"]["ckpt_every"] = k
+        sim = mpm.from_scene(scene, max_steps=T)
+        sim.set_option(mpm.MPM_OPT_USE_GRAPHS, 0)
+        sim.forward(T)
+        grads, launches = [], []
+        for _ in range(2):
+            n0 = sim.info(mpm.MPM_INFO_KERNEL_LAUNCHES)
+            g = sim.backward(**{kk: torch.as_tensor(v) for kk, v in seeds.items()})
+            launches.append(sim.info(mpm.MPM_INFO_KERNEL_LAUNCHES) - n0)
+            grads.append({kk: v.cpu().numpy() for kk, v in g.items()})
+        assert mpm.mpm_sync_status(sim.h) == mpm.MPM_OK
+        sim.close()
+        for g in grads:
+            _compare_grads(g, o, keys)
+        if k == T:
+            # one P2G pass for the grid of step T-1, T + 1 adjoint passes, clean-up and I/O
+            assert launches[0] == launches[1] and launches[0] < T + 1 + 20, launches
+        else:
+            assert launches[1] > launches[0], launches  # the second one re-simulates it
+
+
 def test_polar_cache_does_not_change_results(mpm):
     """3D fixed-corotated: backward passes that read the FP64 polar factors cached by the
     re-simulation give the gradients of the passes that recompute them (both against the
