@@ -97,6 +97,10 @@ extern "C" {
                                      microseconds, 1..6e8 [2000000].  A wait that runs out sets
                                      MPM_ERR_TIMEOUT (reported by mpm_sync_status, after which the
                                      handle needs mpm_set_initial) and every CTA returns. */
+#define MPM_OPT_GRID_RECOMPUTE 12 /* 1: every adjoint pass recomputes the grid of the step before
+                                     (Appendix D.1) even when the re-simulated segment's grids fit
+                                     in the workspace (K + 4 grid buffers within 8 GiB, decided at
+                                     create); 0: keep them [0] */
 #define MPM_OPT_PERSISTENT_CHUNK 11 /* persistent form: at most this many passes per launch
                                      (0 = a whole run of same-kind passes) [0]; bounds the
                                      duration of any one launch */

@@ -49,6 +49,10 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 constexpr int kPMSlots = 6;  // mass/momentum grids in flight (measured need: 4)
 constexpr int kUBSlots = 4;  // velocity-adjoint grids in flight (need: 3)
+// Grids of a re-simulated segment are kept for its adjoint passes (instead of each adjoint
+// pass recomputing the grid of the step before, Appendix D.1) when the ring of K + 4 grid
+// buffers fits this budget; otherwise the per-step recompute is used.
+constexpr size_t kStoredGridBudget = (size_t)8 << 30;
 
 struct Layout {
   size_t perm, keys0, keys1, idx0, sort_tmp, sort_tmp_bytes;
@@ -56,8 +60,8 @@ struct Layout {
   size_t mu, la, E, nu, group, matid, wact, wbar_tile, mubar, labar;
   size_t fin, cur, ckpt, seg, adj;
   size_t rcache;  // (K+1) x [9][N] FP64 polar factors of a re-simulated segment (3D FCR)
-  size_t grids;  // kPMSlots + kUBSlots dense grids
-  size_t boxes;  // (kPMSlots + kUBSlots) x 2 parities x [scene][8]
+  size_t grids;  // pm_slots + kUBSlots dense grids
+  size_t boxes;  // (pm_slots + kUBSlots) x 2 parities x [scene][8]
   size_t err, com, com_part, ub_m0;
   size_t plan_fwd, plan_bwd, gsync;  // persistent-form pass plans and barrier counters
   size_t total;
@@ -67,6 +71,8 @@ struct Dims {
   int D, Q, S, K, n_ckpt, n_tiles, n_grid;
   int64_t N, nnodes;
   bool polar_cache;  // 3D fixed-corotated: FP64 polar factors are cached per segment
+  bool store_grids;  // a re-simulated segment's grids stay live for its adjoint passes
+  int pm_slots;      // (m, p) grid buffers: kPMSlots, or K + 4 when store_grids
   int words;         // float4 slots per grid node: 2 for fixed-point grids (deterministic)
   int T_max;         // max_steps
 };
@@ -120,6 +126,13 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
   m.polar_cache = d->dim == 3 && (d->material == MPM_FIXED_COROTATED || d->material == MPM_MIXED);
   m.T_max = max_steps;
   m.words = d->deterministic_p2g ? 2 : 1;
+  {
+    int64_t nn = 1;
+    for (int a = 0; a < d->dim; ++a) nn *= d->n_grid;
+    const size_t grid_bytes = (size_t)d->n_scenes * nn * 16 * m.words;
+    m.store_grids = (size_t)(m.K + 4) * grid_bytes <= kStoredGridBudget;
+    m.pm_slots = m.store_grids ? m.K + 4 : kPMSlots;
+  }
   m.nnodes = 1;
   for (int a = 0; a < m.D; ++a) m.nnodes *= d->n_grid;
   m.N = 0;
@@ -167,8 +180,8 @@ Layout make_layout(const Dims& m) {
   L.adj = take(Q * N * 4);
   L.rcache = m.polar_cache ? take((size_t)(m.K + 1) * 9 * N * 8) : take(0);
   const size_t grid = S * (size_t)m.nnodes * sizeof(float4) * m.words;
-  L.grids = take(grid * (kPMSlots + kUBSlots));
-  L.boxes = take((size_t)(kPMSlots + kUBSlots) * 2 * S * 8 * 4);
+  L.grids = take(grid * (m.pm_slots + kUBSlots));
+  L.boxes = take((size_t)(m.pm_slots + kUBSlots) * 2 * S * 8 * 4);
   L.err = take(4);
   L.ub_m0 = take(4);
   L.com = take(S * 6 * 8);
@@ -202,6 +215,7 @@ struct mpm_handle {
   int gather_capacity = 512;  // nodes; a 128-particle tile's stencil box is ~150-300
   int grid_blocks = 0;  // CTAs per scene of the end-of-sequence grid clear (0 = automatic)
   bool use_polar_cache = true;
+  bool grid_recompute = false;           // MPM_OPT_GRID_RECOMPUTE
   bool persistent = false;               // MPM_OPT_PERSISTENT
   int64_t barrier_timeout_us = 2000000;  // MPM_OPT_BARRIER_TIMEOUT_US
   unsigned barrier_extra = 0;            // MPM_OPT_BARRIER_TEST_EXTRA
@@ -604,7 +618,7 @@ struct Launcher {
     }
     if (mode != kRecord) {
       ++count;
-      e = launch_reset_boxes(h->at<int>(h->L.boxes), (int64_t)(kPMSlots + kUBSlots) * 2 * h->m.S, s);
+      e = launch_reset_boxes(h->at<int>(h->L.boxes), (int64_t)(h->m.pm_slots + kUBSlots) * 2 * h->m.S, s);
     }
     ring_reset(h->pm);
     ring_reset(h->ub);
@@ -660,7 +674,11 @@ int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
 
 // re-simulate segment [s0, top): seg slot i <- state s0 + i (i = 1..top-s0); returns the
 // grid of step top-1 (kept live for the adjoint passes)
-int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top, int* grid_top_minus_1) {
+// re-simulate segment [s0, top): seg slot i <- state s0 + i (i = 1..top-s0); returns the
+// grid of step top-1 (kept live for the adjoint passes); with seg_grids, every grid of the
+// segment is kept live too (seg_grids[t - s0] = grid of step t)
+int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top, int* grid_top_minus_1,
+                int* seg_grids) {
   const float* ck = h->state(h->L.ckpt, s0 / h->m.K);
   int g = -1;
   LK(Lc.step(kP2GOnly, s0, ck, nullptr, -1, &g, h->rslot(0)));
@@ -669,11 +687,13 @@ int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top, int* grid_top_minu
     float* dst = h->state(h->L.seg, t - s0);
     int g_next = -1;
     LK(Lc.step(kG2PP2GFull, t, prev, dst, g, &g_next, h->rslot(t - s0)));
-    ring_release(h->pm, g);
+    if (seg_grids) seg_grids[t - 1 - s0] = g;
+    else ring_release(h->pm, g);
     g = g_next;
     prev = dst;
   }
   LK(Lc.step(kG2POnlyFull, top, prev, h->state(h->L.seg, top - s0), g, nullptr));
+  if (seg_grids) seg_grids[top - 1 - s0] = g;
   *grid_top_minus_1 = g;
   return MPM_OK;
 }
@@ -684,6 +704,8 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident) {
   ring_reset(h->ub);
   // live grids: PM of steps s+1 and s, UB of step s+1
   int pm_s1 = -1, pm_s = -1, ub_s1 = -1;
+  std::vector<int> seg_grids(K, -1);
+  bool stored = false;  // this segment's grids were kept by its re-simulation
   for (int s = T - 1; s >= 0; --s) {
     const int j = s / K, s0 = j * K;
     const int top = (s0 + K < T) ? s0 + K : T;
@@ -691,15 +713,18 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident) {
       // the forward left this segment's states in place: only the grid of step T-1
       const float* st = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
       LK(Lc.step(kP2GOnly, s, st, nullptr, -1, &pm_s));
+      stored = false;
     } else if (s == top - 1) {
-      int rc = issue_resim(h, Lc, s0, top, &pm_s);
+      stored = h->m.store_grids && !h->grid_recompute;
+      int rc = issue_resim(h, Lc, s0, top, &pm_s, stored ? seg_grids.data() : nullptr);
       if (rc) return rc;
     }
     const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
     const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->state(h->L.seg, s + 1 - s0);
-    const float* st_sm = (s - 1 >= s0) ? ((s - 1 == s0) ? h->state(h->L.ckpt, j)
-                                                          : h->state(h->L.seg, s - 1 - s0))
-                                        : nullptr;
+    // the recomputed P2G of step s-1 runs only when this segment's grids were not kept
+    const float* st_sm = (s - 1 >= s0 && !stored)
+                             ? ((s - 1 == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - 1 - s0))
+                             : nullptr;
     int ub_s = -1, pm_sm = -1;
     // cached polar factors: state s+1 only inside this segment (the segment's top state
     // was never the P2G input of this re-simulation), state s-1 always when present
@@ -714,7 +739,9 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident) {
     ring_release(h->ub, ub_s1);
     pm_s1 = pm_s;
     ub_s1 = ub_s;
-    pm_s = pm_sm;  // -1 at a segment start: the next segment's re-simulation provides it
+    // the grid of step s-1: kept, recomputed by this pass, or (at a segment start) provided
+    // by the next segment's re-simulation
+    pm_s = stored ? (s - 1 >= s0 ? seg_grids[s - 1 - s0] : -1) : pm_sm;
   }
   const float* st0 = h->state(h->L.ckpt, 0);
   LK(Lc.adjoint(kAdjP2G, -1, st0, st0, nullptr, pm_s1, ub_s1, -1, nullptr, nullptr));
@@ -847,6 +874,8 @@ int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_byt
   h->m = m;
   h->L = L;
   h->ws = static_cast<char*>(workspace);
+  h->pm.n = m.pm_slots;
+  h->ub.first = m.pm_slots;
   h->ws_bytes = workspace_bytes;
   // tile table and scene offsets (host -> device once)
   std::vector<int4> tiles;
@@ -903,8 +932,8 @@ int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float
   const size_t wbytes = (size_t)m.S * h->desc.n_groups * h->desc.n_basis * sizeof(float);
   if (wbytes) CK(cudaMemcpyAsync(h->at<float>(L.wact), w, wbytes, cudaMemcpyDeviceToDevice, s));
   const size_t grid = (size_t)m.S * m.nnodes * sizeof(float4) * m.words;
-  CK(cudaMemsetAsync(h->at<char>(L.grids), 0, grid * (kPMSlots + kUBSlots), s));
-  CK(launch_reset_boxes(h->at<int>(L.boxes), (int64_t)(kPMSlots + kUBSlots) * 2 * m.S, s));
+  CK(cudaMemsetAsync(h->at<char>(L.grids), 0, grid * (m.pm_slots + kUBSlots), s));
+  CK(launch_reset_boxes(h->at<int>(L.boxes), (int64_t)(m.pm_slots + kUBSlots) * 2 * m.S, s));
   ring_reset(h->pm);
   ring_reset(h->ub);
   h->launches += 3;
@@ -1078,6 +1107,7 @@ int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
       h->grid_blocks = (int)value;
       break;
     case MPM_OPT_POLAR_CACHE: h->use_polar_cache = value != 0; break;
+    case MPM_OPT_GRID_RECOMPUTE: h->grid_recompute = value != 0; break;
     case MPM_OPT_PERSISTENT: h->persistent = value != 0; break;
     case MPM_OPT_PERSISTENT_CHUNK:
       if (value < 0 || value > (1 << 30)) return fail(h, MPM_ERR_ARG, "persistent chunk must be >= 0");

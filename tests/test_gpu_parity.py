@@ -297,6 +297,24 @@ def test_backward_twice_and_single_segment(mpm):
             assert launches[1] > launches[0], launches  # the second one re-simulates it
 
 
+def test_kept_segment_grids_equal_recomputed_grids(mpm):
+    """A re-simulated segment's grids kept for its adjoint passes give the gradients of the
+    per-step recompute of Appendix D.1 (both against the oracle, and against each other
+    to FP32 atomic-order rounding)."""
+    scene = scenes.make("robots3d", n_scenes=2, dims=(16, 8, 8))
+    T = 20
+    scene["desc"]["ckpt_every"] = 6  # segments 0-5, 6-11, 12-17 re-simulated; 18-19 resident
+    seeds = _random_seeds(scene, np.random.default_rng(8))
+    kept = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    rec = _run_gpu(mpm, scene, T, seeds=seeds, loss=False, options={mpm.MPM_OPT_GRID_RECOMPUTE: 1})
+    o = _oracle_grad_linear(scene, T, {k: v.astype(np.float64) for k, v in seeds.items()})
+    keys = ["gx0", "gv0", "gC0", "gF0", "gE", "gnu", "gw"]
+    _compare_grads(kept["grad"], o, keys)
+    _compare_grads(rec["grad"], o, keys)
+    for key in keys:
+        assert rel_l2(kept["grad"][key], rec["grad"][key]) <= 1e-4, key
+
+
 def test_polar_cache_does_not_change_results(mpm):
     """3D fixed-corotated: backward passes that read the FP64 polar factors cached by the
     re-simulation give the gradients of the passes that recompute them (both against the
