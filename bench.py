@@ -54,23 +54,43 @@ def alg_bytes(d):
 
 
 
-def pass_bytes(N, T, K, dim=3):
-    """Algorithmic bytes of one bench step per kernel category, for both launch forms:
-    the per-pass categories and the persistent launches that run the same passes."""
+def pass_bytes(N, T, K, dim=3, kept=True):
+    """Algorithmic bytes of one bench step per kernel category, for both launch forms (the
+    per-pass categories and the persistent launches that run the same passes), following
+    the library's schedule: the forward writes the full state at checkpoints and over its
+    last segment (left resident); the backward computes the grid of step T-1 with one P2G
+    pass, re-simulates every other segment, and each fused adjoint pass also recomputes
+    the grid of the step before unless the segment's grids were kept (kept=True) -- the
+    resident segment always recomputes."""
     a = alg_bytes(dim)
-    ckpt_inner = (T - 1) // K                 # full-state writes at t = K, 2K, ... < T
-    fwd = a["p2g"] + (T - 1 - ckpt_inner) * a["g2p_p2g"] + ckpt_inner * a["g2p_p2g_full"] + a["g2p"]
-    resim = 0
-    for s0 in range(0, T, K):
+    state_s_minus_1 = 4 * (2 * dim + 2 * dim * dim)
+    by = {k: 0 for k in ("p2g", "g2p_p2g", "g2p_p2g_full", "g2p", "adj_g2p", "adj_fused",
+                         "adj_p2g")}
+    sL = ((T - 1) // K) * K
+    by["p2g"] += a["p2g"]
+    for t in range(1, T):
+        by["g2p_p2g_full" if (t % K == 0 or t > sL) else "g2p_p2g"] += 1
+    by["g2p_p2g"] *= a["g2p_p2g"]
+    by["g2p_p2g_full"] *= a["g2p_p2g_full"]
+    by["g2p"] += a["g2p"]
+    fwd = sum(by.values())
+    back = {k: 0 for k in by}
+    back["p2g"] += a["p2g"]  # grid of step T-1 (resident last segment)
+    for s0 in range(0, sL, K):
         n = min(K, T - s0)
-        resim += a["p2g"] + (n - 1) * a["g2p_p2g_full"] + a["g2p"]
-    adj = a["adj_g2p"] + (T - 1) * a["adj_fused"] + a["adj_p2g"]
-    segs = -(-T // K)
-    by = {"p2g": (1 + segs) * a["p2g"], "g2p_p2g": (T - 1 - ckpt_inner) * a["g2p_p2g"],
-          "g2p_p2g_full": (ckpt_inner + (T - segs)) * a["g2p_p2g_full"], "g2p": (1 + segs) * a["g2p"],
-          "adj_g2p": a["adj_g2p"], "adj_fused": (T - 1) * a["adj_fused"], "adj_p2g": a["adj_p2g"],
-          "persistent_step": fwd + resim, "persistent_adj": adj}
-    return {k: v * N for k, v in by.items()}
+        back["p2g"] += a["p2g"]
+        back["g2p_p2g_full"] += (n - 1) * a["g2p_p2g_full"]
+        back["g2p"] += a["g2p"]
+    back["adj_g2p"] += a["adj_g2p"]
+    for s in range(T - 2, -1, -1):
+        s0 = (s // K) * K
+        recompute = s - 1 >= s0 and (s0 == sL or not kept)
+        back["adj_fused"] += a["adj_fused"] - (0 if recompute else state_s_minus_1)
+    back["adj_p2g"] += a["adj_p2g"]
+    out = {k: by[k] + back[k] for k in by}
+    out["persistent_step"] = fwd + back["p2g"] + back["g2p_p2g_full"] + back["g2p"]
+    out["persistent_adj"] = back["adj_g2p"] + back["adj_fused"] + back["adj_p2g"]
+    return {k: v * N for k, v in out.items()}
 
 
 def source_digest():
@@ -414,7 +434,8 @@ def main():
     dom = max(prof, key=lambda k: prof[k][1])
     n_launch, dom_ms = prof[dom]
     hbm, peak_src = measured_peaks()
-    step_bytes = pass_bytes(N, T, desc["ckpt_every"], desc["dim"])
+    step_bytes = pass_bytes(N, T, desc["ckpt_every"], desc["dim"],
+                            kept=bool(sim.info(mpm.MPM_INFO_KEEPS_SEGMENT_GRIDS)))
     roof = None
     if dom in step_bytes and n_launch:
         avg_ms = dom_ms / n_launch

@@ -127,6 +127,8 @@ extern "C" {
 #define MPM_INFO_KERNEL_LAUNCHES 1 /* kernels launched by this handle so far */
 #define MPM_INFO_N_TOTAL 2         /* total particles N */
 #define MPM_INFO_STEPS_RECORDED 3  /* T of the last mpm_forward (0 = none) */
+#define MPM_INFO_KEEPS_SEGMENT_GRIDS 4 /* 1: a re-simulated segment's grids are kept for its
+                                          adjoint passes (see MPM_OPT_GRID_RECOMPUTE) */
 
 typedef struct mpm_handle mpm_handle;
 

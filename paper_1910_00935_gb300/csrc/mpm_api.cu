@@ -1141,6 +1141,7 @@ int mpm_get_info(mpm_handle* h, int32_t key, int64_t* value) {
     case MPM_INFO_KERNEL_LAUNCHES: *value = h->launches; return MPM_OK;
     case MPM_INFO_N_TOTAL: *value = h->m.N; return MPM_OK;
     case MPM_INFO_STEPS_RECORDED: *value = h->T_recorded; return MPM_OK;
+    case MPM_INFO_KEEPS_SEGMENT_GRIDS: *value = h->m.store_grids && !h->grid_recompute; return MPM_OK;
   }
   return fail(h, MPM_ERR_ARG, "unknown info key");
 }
