@@ -270,6 +270,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube3d")
     ap.add_argument("--T", type=int, default=0, help="override the workload's step count")
+    ap.add_argument("--ckpt-every", type=int, default=0, help="override the checkpoint interval")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-per-scene", action="store_true",
@@ -305,6 +306,8 @@ def main():
     scene, N, T, descr = make_workload(args.workload, seed=rank)
     if args.T:
         T = args.T
+    if args.ckpt_every:
+        scene["desc"]["ckpt_every"] = args.ckpt_every
     desc = scene["desc"]
     a = scene["arrays"]
     G = desc.get("n_groups", 0)
