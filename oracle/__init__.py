@@ -17,7 +17,9 @@ What is pinned and where (each pin is a test under ``tests/test_oracle_*.py``):
 * adjoint: every sub-stage and whole runs against central finite differences of
   the oracle's own forward pass (the adjoint is derived by hand, the forward is
   pinned independently above);
-* actuation: closed-form special cases of the sine basis.
+* actuation: closed-form special cases of the sine basis; the closed-loop controller
+  against the definition of its inputs and a torch evaluation of its MLP, invariants,
+  and finite differences (test_oracle_controller.py).
 
 Sections of the paper followed: Section 3.2 (tape), Section 4.1 and Appendix D
 (diffmpm's advance / advance_grad), Appendix C (polar/SVD with a custom gradient).
@@ -62,6 +64,8 @@ class Params(ctypes.Structure):
         ("act_period", ctypes.c_double),
         ("act_phase", ctypes.c_double),
         ("particle_material", ctypes.c_void_p),
+        ("ctrl_hidden", ctypes.c_int32),
+        ("ctrl_scale", ctypes.c_double),
     ]
 
 
@@ -108,6 +112,9 @@ def lib():
                                          d, d, d, d, d, d, d, d, d, d, d]),
                 "orc_grad": (I, [P, I64, I, d, d, i32, d, d, d, d, d, d]),
                 "orc_com_loss": (I, [I, I64, I, d, d, d, d, d, d]),
+                "orc_ctrl_n_inputs": (I, [P]),
+                "orc_ctrl_n_params": (I64, [P]),
+                "orc_controller": (I, [P, d, I64, I, d, d, i32, d, d]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -149,11 +156,35 @@ def _check(rc, what):
 
 def make_params(dim, n_grid, dt, gravity=(0.0, -9.8, 0.0), wall_cells=3,
                 material=FIXED_COROTATED, rho=1.0, n_groups=0, n_basis=0,
-                act_period=50.0, act_phase=0.0) -> Params:
+                act_period=50.0, act_phase=0.0, ctrl_hidden=0, ctrl_scale=1.0) -> Params:
     g = list(gravity) + [0.0] * (3 - len(gravity))
-    return Params(int(dim), int(n_grid), float(dt), (ctypes.c_double * 3)(*g[:3]),
-                  int(wall_cells), int(material), float(rho), int(n_groups), int(n_basis),
-                  float(act_period), float(act_phase))
+    p = Params(int(dim), int(n_grid), float(dt), (ctypes.c_double * 3)(*g[:3]),
+               int(wall_cells), int(material), float(rho), int(n_groups), int(n_basis),
+               float(act_period), float(act_phase))
+    p.ctrl_hidden = int(ctrl_hidden)
+    p.ctrl_scale = float(ctrl_scale)
+    return p
+
+
+def n_act_params(params) -> int:
+    """Actuation parameters per scene: G*K sine weights (open loop) or the controller's
+    theta (closed loop)."""
+    if params.n_groups <= 0:
+        return 0
+    if params.ctrl_hidden > 0:
+        return int(lib().orc_ctrl_n_params(ctypes.byref(params)))
+    return params.n_groups * params.n_basis
+
+
+def controller(params, theta, t, x, v, grp):
+    """The closed-loop controller at step t on state (x, v): (act[G], inputs u[n_in])."""
+    x, v, theta = _f64(x), _f64(v), _f64(theta).reshape(-1)
+    n = x.shape[-1]
+    act = np.zeros(params.n_groups)
+    u = np.zeros(int(lib().orc_ctrl_n_inputs(ctypes.byref(params))))
+    _check(lib().orc_controller(ctypes.byref(params), _d(theta), n, int(t), _d(x), _d(v),
+                                _i(_grp(grp, n)), _d(act), _d(u)), "controller")
+    return act, u
 
 
 def with_materials(params: Params, material) -> Params:
@@ -170,7 +201,8 @@ def params_from_desc(desc: dict) -> Params:
     return make_params(desc["dim"], desc["n_grid"], desc["dt"], desc["gravity"],
                        desc["wall_cells"], desc["material"], desc["rho"],
                        desc.get("n_groups", 0), desc.get("n_basis", 0),
-                       desc.get("act_period", 50.0), desc.get("act_phase", 0.0))
+                       desc.get("act_period", 50.0), desc.get("act_phase", 0.0),
+                       desc.get("ctrl_hidden", 0), desc.get("ctrl_scale", 1.0))
 
 
 def state_block_len(dim, n):
@@ -320,13 +352,14 @@ def step_adjoint(params, t, state, mu, la, adj_next, grp=None, w=None):
     out = [np.empty_like(xs), np.empty_like(vs), np.empty_like(Cs), np.empty_like(Fs)]
     mub, lab = np.zeros(n), np.zeros(n)
     G, K = params.n_groups, params.n_basis
-    wb = np.zeros(max(G * K, 1))
+    nw = n_act_params(params)
+    wb = np.zeros(max(nw, 1))
     w = _f64(w).reshape(-1) if w is not None else None
     _check(lib().orc_step_adjoint(ctypes.byref(params), n, t, _d(xs), _d(vs), _d(Cs), _d(Fs),
                                   _d(mu), _d(la), _i(_grp(grp, n)), _d(w), _d(xb1), _d(vb1),
                                   _d(Cb1), _d(Fb1), *[_d(o) for o in out], _d(mub), _d(lab),
                                   _d(wb)), "step_adjoint")
-    return pack_state(*out), mub, lab, wb[:G * K].reshape(G, K) if G * K else wb[:0]
+    return pack_state(*out), mub, lab, _shape_wbar(params, wb[:nw])
 
 
 def grad(params, T, states, adj_T, mu, la, grp=None, w=None):
@@ -335,13 +368,20 @@ def grad(params, T, states, adj_T, mu, la, grp=None, w=None):
     n = mu.size
     adj = _f64(adj_T).copy()
     mub, lab = np.zeros(n), np.zeros(n)
-    G, K = params.n_groups, params.n_basis
-    wb = np.zeros(max(G * K, 1))
+    nw = n_act_params(params)
+    wb = np.zeros(max(nw, 1))
     w = _f64(w).reshape(-1) if w is not None else None
     states = np.ascontiguousarray(states, dtype=np.float64)
     _check(lib().orc_grad(ctypes.byref(params), n, T, _d(mu), _d(la), _i(_grp(grp, n)), _d(w),
                           _d(states), _d(adj), _d(mub), _d(lab), _d(wb)), "grad")
-    return adj, mub, lab, wb[:G * K].reshape(G, K) if G * K else wb[:0]
+    return adj, mub, lab, _shape_wbar(params, wb[:nw])
+
+
+def _shape_wbar(params, wb):
+    """dL/dw as [G, K] (open loop) or dL/dtheta flat (closed loop)."""
+    if params.ctrl_hidden > 0 or wb.size == 0:
+        return wb
+    return wb.reshape(params.n_groups, params.n_basis)
 
 
 def com_loss(dim, kind, xT, x0, target=None):
@@ -407,7 +447,8 @@ def loss_and_grad(scene, T):
     gE, gnu = np.zeros(N), np.zeros(N)
     S = len(desc["n_particles"])
     G, K = desc.get("n_groups", 0), desc.get("n_basis", 0)
-    gw = np.zeros((S, G, K))
+    nw = n_act_params(params_from_desc(desc))
+    gw = np.zeros((S, nw)) if desc.get("ctrl_hidden", 0) > 0 else np.zeros((S, G, K))
     losses, finals = [], []
     for si, sl in enumerate(_scene_slices(scene)):
         x0, v0, C0, F0, mu, la, grp, w = _scene_inputs(scene, sl, si)
@@ -426,7 +467,7 @@ def loss_and_grad(scene, T):
         g["gF0"][:, sl] = gF
         eb, nb = lame_adjoint(a["E"][sl], a["nu"][sl], mub, lab)
         gE[sl], gnu[sl] = eb, nb
-        if G * K:
+        if nw:
             gw[si] = wb
         losses.append(L)
         finals.append(states[-1].copy())

@@ -19,7 +19,9 @@
  *             x' = x + dt v', F' = (I + dt C') F.
  *     stress  fixed-corotated tau = 2 mu (F - R) F^T + lambda (J - 1) J I,
  *             neo-Hookean     tau = mu (F F^T - I) + lambda ln(J) I,
- *             actuation       tau += a (F e)(F e)^T, a = sum_k w_gk sin(2 pi k t/P + phi).
+ *             actuation       tau += a (F e)(F e)^T, a = sum_k w_gk sin(2 pi k t/P + phi),
+ *             or (closed loop) a = the controller's output for the particle's group,
+ *             evaluated on the state of step s (orc_controller).
  *   the adjoint of one step (Appendix D.1 "advance_grad"): recompute the grid
  *   from state_s (clear_grid, p2g, grid_op), then g2p.grad, grid_op.grad,
  *   p2g.grad and the actuation/stress adjoint, in that order.
@@ -63,6 +65,11 @@
    (E, nu) and g = 7. */
 #define ORC_LIQUID_GAMMA 7.0
 
+/* limits of the closed-loop controller (Section 4.1's neural-network controllers) */
+#define ORC_CTRL_MAX_GROUPS 8
+#define ORC_CTRL_MAX_HIDDEN 64
+#define ORC_CTRL_MAX_INPUTS (8 + 2 * 3 * ORC_CTRL_MAX_GROUPS)
+
 #define ORC_LOSS_COM_TARGET 0   /* L = |COM(x_T) - target|^2            */
 #define ORC_LOSS_COM_X_DISP 1   /* L = -(COM_x(x_T) - COM_x(x_0))       */
 
@@ -80,6 +87,9 @@ typedef struct {
   double act_phase;   /* phi */
   const int32_t* particle_material; /* [np] material of each particle when material is
                                        ORC_MIXED (indexed like mu, la), else unused */
+  int32_t ctrl_hidden; /* 0: open-loop sine actuation, wact = w[G][K]; H > 0: closed-loop
+                          controller with H hidden units, wact = theta (see orc_controller) */
+  double ctrl_scale;   /* controller output scale: a_g = ctrl_scale tanh(.) */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -454,6 +464,153 @@ double orc_actuation(const orc_params* P, const double* wact, int g, int t) {
 }
 
 /* ------------------------------------------------------------------ */
+/* closed-loop controller (the neural-network controllers of Section   */
+/* 4.1: sensors of the current state -> a small MLP -> the actuation   */
+/* of every group, evaluated at every step and differentiated with it) */
+/* ------------------------------------------------------------------ */
+
+/* inputs u, n_in = K + 2 d G of them: the K time-basis values sin(2 pi k t / P + phi),
+   then for each group g the offset of the group's centre of mass from the whole body's
+   (d values) and the group's mean velocity (d values); a group without particles reads
+   zeros.  hidden h = tanh(W1 u + b1) (H units); output a_g = scale tanh(W2 h + b2)_g.
+   theta = [W1 (H x n_in, row-major) | b1 (H) | W2 (G x H, row-major) | b2 (G)]. */
+int orc_ctrl_n_inputs(const orc_params* P) { return P->n_basis + 2 * P->dim * P->n_groups; }
+
+int64_t orc_ctrl_n_params(const orc_params* P) {
+  int64_t H = P->ctrl_hidden, I = orc_ctrl_n_inputs(P), G = P->n_groups;
+  return H * I + H + G * H + G;
+}
+
+/* the sensors of state (x, v): u[n_in] and the group sizes cnt[G] */
+static void ctrl_sensors(const orc_params* P, int64_t np, int t, const double* x,
+                         const double* v, const int32_t* grp, double* u, double* cnt) {
+  int d = P->dim, G = P->n_groups, K = P->n_basis;
+  double com[3] = {0, 0, 0}, sx[ORC_CTRL_MAX_GROUPS][3], sv[ORC_CTRL_MAX_GROUPS][3];
+  for (int g = 0; g < G; g++) {
+    cnt[g] = 0.0;
+    for (int a = 0; a < 3; a++) sx[g][a] = sv[g][a] = 0.0;
+  }
+  for (int64_t p = 0; p < np; p++) {
+    int g = grp ? grp[p] : -1;
+    for (int a = 0; a < d; a++) com[a] += x[a * np + p];
+    if (g < 0 || g >= G) continue;
+    cnt[g] += 1.0;
+    for (int a = 0; a < d; a++) {
+      sx[g][a] += x[a * np + p];
+      sv[g][a] += v[a * np + p];
+    }
+  }
+  for (int a = 0; a < d; a++) com[a] /= (double)np;
+  for (int k = 1; k <= K; k++) u[k - 1] = act_basis(P, k, t);
+  for (int g = 0; g < G; g++)
+    for (int a = 0; a < d; a++) {
+      double* ug = u + K + g * 2 * d;
+      ug[a] = cnt[g] > 0.0 ? sx[g][a] / cnt[g] - com[a] : 0.0;
+      ug[d + a] = cnt[g] > 0.0 ? sv[g][a] / cnt[g] : 0.0;
+    }
+}
+
+/* hidden layer h[H] and actuation a[G] from the inputs u */
+static void ctrl_mlp(const orc_params* P, const double* th, const double* u, double* h,
+                     double* a) {
+  int H = P->ctrl_hidden, I = orc_ctrl_n_inputs(P), G = P->n_groups;
+  const double *W1 = th, *b1 = th + H * I, *W2 = b1 + H, *b2 = W2 + G * H;
+  for (int j = 0; j < H; j++) {
+    double z = b1[j];
+    for (int i = 0; i < I; i++) z += W1[j * I + i] * u[i];
+    h[j] = tanh(z);
+  }
+  for (int g = 0; g < G; g++) {
+    double z = b2[g];
+    for (int j = 0; j < H; j++) z += W2[g * H + j] * h[j];
+    a[g] = P->ctrl_scale * tanh(z);
+  }
+}
+
+/* the actuation of every group at step t: the open-loop sine series, or the controller
+   evaluated on state (x, v) */
+static int group_actuation(const orc_params* P, int64_t np, int t, const double* x,
+                           const double* v, const int32_t* grp, const double* wact,
+                           double* act) {
+  for (int g = 0; g < ORC_CTRL_MAX_GROUPS; g++) act[g] = 0.0;
+  if (P->n_groups <= 0 || !grp || !wact) return ORC_OK;
+  if (P->n_groups > ORC_CTRL_MAX_GROUPS) return ORC_ERR_ARG;
+  if (P->ctrl_hidden <= 0) {
+    for (int g = 0; g < P->n_groups; g++) act[g] = orc_actuation(P, wact, g, t);
+    return ORC_OK;
+  }
+  if (P->ctrl_hidden > ORC_CTRL_MAX_HIDDEN) return ORC_ERR_ARG;
+  double u[ORC_CTRL_MAX_INPUTS], h[ORC_CTRL_MAX_HIDDEN], cnt[ORC_CTRL_MAX_GROUPS];
+  ctrl_sensors(P, np, t, x, v, grp, u, cnt);
+  ctrl_mlp(P, wact, u, h, act);
+  return ORC_OK;
+}
+
+/* controller output and inputs at state (x, v), for the pins */
+int orc_controller(const orc_params* P, const double* theta, int64_t np, int t,
+                   const double* x, const double* v, const int32_t* grp, double* act,
+                   double* u_out) {
+  if (P->ctrl_hidden <= 0 || P->ctrl_hidden > ORC_CTRL_MAX_HIDDEN || P->n_groups <= 0 ||
+      P->n_groups > ORC_CTRL_MAX_GROUPS)
+    return ORC_ERR_ARG;
+  double u[ORC_CTRL_MAX_INPUTS], h[ORC_CTRL_MAX_HIDDEN], cnt[ORC_CTRL_MAX_GROUPS];
+  double a[ORC_CTRL_MAX_GROUPS];
+  ctrl_sensors(P, np, t, x, v, grp, u, cnt);
+  ctrl_mlp(P, theta, u, h, a);
+  for (int g = 0; g < P->n_groups; g++) act[g] = a[g];
+  for (int i = 0; i < orc_ctrl_n_inputs(P); i++) u_out[i] = u[i];
+  return ORC_OK;
+}
+
+/* Adjoint of the controller at step t given abar[g] = dL/da_g: accumulates dL/dtheta into
+   thbar and adds the sensor terms to the adjoint of the state, xb and vb (every particle
+   moves its group's centre of mass by 1/N_g of its displacement and the body's by 1/N). */
+static void ctrl_adjoint(const orc_params* P, int64_t np, int t, const double* x,
+                         const double* v, const int32_t* grp, const double* th,
+                         const double* abar, double* thbar, double* xb, double* vb) {
+  int d = P->dim, H = P->ctrl_hidden, I = orc_ctrl_n_inputs(P), G = P->n_groups,
+      K = P->n_basis;
+  double u[ORC_CTRL_MAX_INPUTS], h[ORC_CTRL_MAX_HIDDEN], cnt[ORC_CTRL_MAX_GROUPS];
+  double a[ORC_CTRL_MAX_GROUPS], z2b[ORC_CTRL_MAX_GROUPS], z1b[ORC_CTRL_MAX_HIDDEN];
+  double ub[ORC_CTRL_MAX_INPUTS];
+  ctrl_sensors(P, np, t, x, v, grp, u, cnt);
+  ctrl_mlp(P, th, u, h, a);
+  const double *W1 = th, *W2 = th + H * I + H;
+  double *W1b = thbar, *b1b = thbar + H * I, *W2b = b1b + H, *b2b = W2b + G * H;
+  for (int g = 0; g < G; g++) {
+    double y = a[g] / P->ctrl_scale; /* tanh(z2) */
+    z2b[g] = abar[g] * P->ctrl_scale * (1.0 - y * y);
+    b2b[g] += z2b[g];
+    for (int j = 0; j < H; j++) W2b[g * H + j] += z2b[g] * h[j];
+  }
+  for (int j = 0; j < H; j++) {
+    double hb = 0.0;
+    for (int g = 0; g < G; g++) hb += W2[g * H + j] * z2b[g];
+    z1b[j] = hb * (1.0 - h[j] * h[j]);
+    b1b[j] += z1b[j];
+    for (int i = 0; i < I; i++) W1b[j * I + i] += z1b[j] * u[i];
+  }
+  for (int i = 0; i < I; i++) {
+    ub[i] = 0.0;
+    for (int j = 0; j < H; j++) ub[i] += W1[j * I + i] * z1b[j];
+  }
+  /* u_xg = mean_{p in g} x_p - mean_p x_p ; u_vg = mean_{p in g} v_p */
+  double body[3] = {0, 0, 0};
+  for (int g = 0; g < G; g++)
+    if (cnt[g] > 0.0)
+      for (int a2 = 0; a2 < d; a2++) body[a2] += ub[K + g * 2 * d + a2];
+  for (int64_t p = 0; p < np; p++) {
+    int g = grp ? grp[p] : -1;
+    for (int a2 = 0; a2 < d; a2++) xb[a2 * np + p] -= body[a2] / (double)np;
+    if (g < 0 || g >= G) continue;
+    for (int a2 = 0; a2 < d; a2++) {
+      xb[a2 * np + p] += ub[K + g * 2 * d + a2] / cnt[g];
+      vb[a2 * np + p] += ub[K + g * 2 * d + d + a2] / cnt[g];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* Kirchhoff stress and its adjoint                                    */
 /* ------------------------------------------------------------------ */
 
@@ -666,14 +823,15 @@ static int is_wall(const orc_params* P, const int idx[3]) {
   return 0;
 }
 
-static double particle_act(const orc_params* P, const int32_t* grp, const double* wact,
-                           int64_t p, int t, int* axis) {
+/* actuation of particle p from its group's value gact[g] (group_actuation) */
+static double particle_act(const orc_params* P, const int32_t* grp, const double* gact,
+                           int64_t p, int* axis) {
   *axis = 0;
-  if (P->n_groups <= 0 || !grp || !wact) return 0.0;
+  if (P->n_groups <= 0 || !grp) return 0.0;
   int g = grp[p];
   if (g < 0 || g >= P->n_groups) return 0.0;
   *axis = g % P->dim;
-  return orc_actuation(P, wact, g, t);
+  return gact[g];
 }
 
 /* P2G (Appendix D "p2g"): scatter mass and APIC/MLS momentum.  gm[n^d] and
@@ -688,6 +846,9 @@ int orc_p2g(const orc_params* P, int64_t np, int t, const double* x, const doubl
   double dx = 1.0 / n, vol = particle_volume(P), m = P->rho * vol;
   double kappa = -P->dt * vol * 4.0 / (dx * dx);
   int nst = (int)ipow(3, d);
+  double gact[ORC_CTRL_MAX_GROUPS];
+  int rca = group_actuation(P, np, t, x, v, grp, wact, gact);
+  if (rca) return rca;
   for (int64_t p = 0; p < np; p++) {
     double xp[3] = {0, 0, 0};
     for (int a = 0; a < d; a++) xp[a] = x[a * np + p];
@@ -698,7 +859,7 @@ int orc_p2g(const orc_params* P, int64_t np, int t, const double* x, const doubl
     load_mat(d, F, np, p, Fp);
     load_mat(d, C, np, p, Cp);
     int axis;
-    double act = particle_act(P, grp, wact, p, t, &axis);
+    double act = particle_act(P, grp, gact, p, &axis);
     rc = kirchhoff_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tau);
     if (rc) return rc;
     mzero(A);
@@ -840,7 +1001,8 @@ int orc_run(const orc_params* P, int64_t np, int T, const double* mu, const doub
 
 /* Given state_s and the adjoint of state_{s+1} (xb1, vb1, Cb1, Fb1), write the
    adjoint of state_s into (xb, vb, Cb, Fb) and accumulate mubar, labar (per
-   particle) and wbar[g * K + k] (actuation weights). */
+   particle) and wbar (the actuation parameters: w[g * K + k] open-loop, the controller's
+   theta closed-loop). */
 int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, const double* v,
                      const double* C, const double* F, const double* mu, const double* la,
                      const int32_t* grp, const double* wact, const double* xb1,
@@ -958,6 +1120,10 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
   }
 
   /* p2g.grad and the stress / actuation adjoint */
+  double gact[ORC_CTRL_MAX_GROUPS], gabar[ORC_CTRL_MAX_GROUPS];
+  rc = group_actuation(P, np, t, x, v, grp, wact, gact);
+  if (rc) goto done;
+  for (int g = 0; g < ORC_CTRL_MAX_GROUPS; g++) gabar[g] = 0.0;
   for (int64_t p = 0; p < np; p++) {
     double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0};
     for (int a = 0; a < d; a++) {
@@ -971,7 +1137,7 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
     load_mat(d, F, np, p, Fp);
     load_mat(d, C, np, p, Cp);
     int axis;
-    double act = particle_act(P, grp, wact, p, t, &axis);
+    double act = particle_act(P, grp, gact, p, &axis);
     rc = kirchhoff_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tau);
     if (rc) goto done;
     mzero(A);
@@ -1017,9 +1183,13 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
     if (rc) goto done;
     if (P->n_groups > 0 && grp && wact && wbar) {
       int gi = grp[p];
-      if (gi >= 0 && gi < P->n_groups)
-        for (int k = 1; k <= P->n_basis; k++)
-          wbar[gi * P->n_basis + (k - 1)] += abar * act_basis(P, k, t);
+      if (gi >= 0 && gi < P->n_groups) {
+        if (P->ctrl_hidden > 0)
+          gabar[gi] += abar;
+        else
+          for (int k = 1; k <= P->n_basis; k++)
+            wbar[gi * P->n_basis + (k - 1)] += abar * act_basis(P, k, t);
+      }
     }
     for (int a = 0; a < d; a++) {
       xb[a * np + p] += xbp[a];
@@ -1028,6 +1198,10 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
     store_mat(d, Cb, np, p, Cbp);
     store_mat(d, Fb, np, p, Fbp);
   }
+  /* the controller read this state: its adjoint reaches the weights and, through the
+     sensors, the positions and velocities */
+  if (P->ctrl_hidden > 0 && P->n_groups > 0 && grp && wact && wbar)
+    ctrl_adjoint(P, np, t, x, v, grp, wact, gabar, wbar, xb, vb);
   rc = ORC_OK;
 done:
   free(gub);

@@ -52,9 +52,19 @@ MUTANTS = {
                             "double kap = la + mu / d;\n    double g = J - pow(J, 1.0 - ORC_LIQUID_GAMMA);\n    for (int i"),
     "liquid_adjoint_slope": ("double gp = 1.0 + (ORC_LIQUID_GAMMA - 1.0) * pow(J, -ORC_LIQUID_GAMMA);",
                              "double gp = 1.0 + ORC_LIQUID_GAMMA * pow(J, -ORC_LIQUID_GAMMA);"),
+    "ctrl_centre_offset": ("ug[a] = cnt[g] > 0.0 ? sx[g][a] / cnt[g] - com[a] : 0.0;",
+                           "ug[a] = cnt[g] > 0.0 ? sx[g][a] / cnt[g] : 0.0;"),
+    "ctrl_tanh_derivative": ("z1b[j] = hb * (1.0 - h[j] * h[j]);", "z1b[j] = hb * (1.0 - h[j]);"),
+    "ctrl_sensor_x_dropped": ("xb[a2 * np + p] += ub[K + g * 2 * d + a2] / cnt[g];",
+                              "xb[a2 * np + p] += 0.0 * ub[K + g * 2 * d + a2] / cnt[g];"),
+    "ctrl_body_term_dropped": ("xb[a2 * np + p] -= body[a2] / (double)np;",
+                               "xb[a2 * np + p] -= 0.0 * body[a2] / (double)np;"),
+    "ctrl_velocity_mean": ("vb[a2 * np + p] += ub[K + g * 2 * d + d + a2] / cnt[g];",
+                           "vb[a2 * np + p] += ub[K + g * 2 * d + d + a2] / (double)np;"),
 }
 
-PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py"]
+PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py",
+             "tests/test_oracle_controller.py"]
 
 
 @pytest.fixture(scope="module")
