@@ -93,6 +93,40 @@ def pass_bytes(N, T, K, dim=3, kept=True):
     return {k: v * N for k, v in out.items()}
 
 
+def pass_bytes_ctrl(N, T, K, dim=3, kept=True):
+    """pass_bytes for a closed-loop controller scene (ctrl_hidden > 0), following its split
+    schedule: the forward runs G2P (full state written), the controller and P2G (from the
+    full state) for every step; the backward runs, per step, the P2G adjoint of step s+1
+    (full adjoint written), the controller's reverse and the G2P adjoint of step s (from the
+    full adjoint), recomputing a grid with its own P2G pass where it is neither kept nor
+    re-simulated.  The controller's sensing reads x, v and the group id; its reverse adds to
+    the x and v rows of the adjoint."""
+    a = alg_bytes(dim)
+    S = 4 * (2 * dim + 2 * dim * dim)
+    XF, M, MB = 4 * (dim + dim * dim), 8, 16
+    sense, sense_adj = 4 * 2 * dim + 4, 4 + 2 * 4 * 2 * dim
+    by = {k: 0 for k in ("p2g", "g2p_p2g", "g2p_p2g_full", "g2p", "adj_g2p", "adj_fused",
+                         "adj_p2g", "controller")}
+    by["p2g"] += T * a["p2g"]
+    by["g2p"] += T * a["g2p"]
+    by["controller"] += T * sense
+    sL = ((T - 1) // K) * K
+    by["p2g"] += a["p2g"]  # grid of step T-1 (resident last segment)
+    for s0 in range(0, sL, K):
+        n = min(K, T - s0)
+        by["p2g"] += a["p2g"]
+        by["g2p_p2g_full"] += (n - 1) * a["g2p_p2g_full"]
+        by["g2p"] += a["g2p"]
+        if not kept:
+            by["p2g"] += (n - 1) * a["p2g"]
+    by["p2g"] += (T - 1 - sL) * a["p2g"]  # the resident segment's grids
+    adj_p2g = S + XF + M + MB + S
+    by["adj_p2g"] += T * adj_p2g
+    by["controller"] += T * sense_adj
+    by["adj_g2p"] += T * a["adj_g2p"]
+    return {k: v * N for k, v in by.items()}
+
+
 def source_digest():
     """Digest of the CUDA sources and the C header: a DRAM-traffic figure read from a
     profile summary counts only if the summary was taken on these exact sources."""
@@ -214,6 +248,9 @@ def make_workload(name, seed=0):
                     "fixed-corotated (FP64 polar), 8 groups x 4 sine terms, T=2048, ckpt 64",
         "rects2d": "64 batched 2D rectangles (1k-16k particles), 128^2 grids, T=512",
         "square2d_grad": "2D square 4,096 particles, 128^2 grid, T=512, ckpt 32",
+        "robots_nn": "4 batched 3D robots x 27,648 particles, 64^3 grids, fixed-corotated, "
+                     "8 groups driven by a closed-loop MLP controller (52 inputs, 32 tanh "
+                     "units), T=512, ckpt 64",
     }.get(name, name)
     return scene, N, d["steps"], descr
 
@@ -224,10 +261,15 @@ def cpu_baseline(name, seconds_hint=20.0):
     import oracle
     from paper_1910_00935_gb300 import scenes
     scene, N, T, _ = make_workload(name)
-    sample_T = {"cube3d": 2, "robots3d": 1, "rects2d": 4, "square2d_grad": 32}.get(name, 2)
+    sample_T = {"cube3d": 2, "robots3d": 1, "rects2d": 4, "square2d_grad": 32,
+                "robots_nn": 4}.get(name, 2)
     if name == "robots3d":  # one of the 16 independent scenes
         from paper_1910_00935_gb300.scenes import actuated_robots_3d
         scene = actuated_robots_3d(n_scenes=1)
+        N = sum(scene["desc"]["n_particles"])
+    if name == "robots_nn":  # one of the 4 independent scenes
+        from paper_1910_00935_gb300.scenes import controlled_robots_3d
+        scene = controlled_robots_3d(n_scenes=1)
         N = sum(scene["desc"]["n_particles"])
     t0 = time.perf_counter()
     oracle.loss_and_grad(scenes.oracle_view(scene), sample_T)
@@ -437,8 +479,9 @@ def main():
     dom = max(prof, key=lambda k: prof[k][1])
     n_launch, dom_ms = prof[dom]
     hbm, peak_src = measured_peaks()
-    step_bytes = pass_bytes(N, T, desc["ckpt_every"], desc["dim"],
-                            kept=bool(sim.info(mpm.MPM_INFO_KEEPS_SEGMENT_GRIDS)))
+    step_bytes = (pass_bytes_ctrl if desc.get("ctrl_hidden", 0) else pass_bytes)(
+        N, T, desc["ckpt_every"], desc["dim"],
+        kept=bool(sim.info(mpm.MPM_INFO_KEEPS_SEGMENT_GRIDS)))
     roof = None
     if dom in step_bytes and n_launch:
         avg_ms = dom_ms / n_launch

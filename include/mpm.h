@@ -14,7 +14,9 @@
  *   recomputing each step's grid (Appendix D.1, "advance_grad").
  *   Materials: fixed-corotated (polar factor and its adjoint in FP64) or
  *   neo-Hookean; optional actuation stress a_g(t) (F e)(F e)^T with
- *   a_g(t) = sum_k w_gk sin(2 pi k t / act_period + act_phase), k = 1..n_basis.
+ *   a_g(t) = sum_k w_gk sin(2 pi k t / act_period + act_phase), k = 1..n_basis
+ *   (open loop), or a_g(t) = the output of a closed-loop controller evaluated on
+ *   state t (the neural-network controllers of Section 4.1; see ctrl_hidden).
  *
  * Conventions (every entry point)
  *   - Returns an int status (MPM_OK = 0 or an MPM_ERR_* code); no exception
@@ -121,6 +123,7 @@ extern "C" {
 #define MPM_KERNEL_ADJ_P2G 8      /* P2G adjoint of step 0 */
 #define MPM_KERNEL_PERSISTENT_STEP 9 /* persistent launch of forward-kind passes (categories 1-4) */
 #define MPM_KERNEL_PERSISTENT_ADJ 10 /* persistent launch of adjoint passes (categories 6-8) */
+#define MPM_KERNEL_CONTROLLER 11  /* closed-loop controller: sensing + MLP, or its reverse */
 
 
 /* queries for mpm_get_info */
@@ -129,6 +132,8 @@ extern "C" {
 #define MPM_INFO_STEPS_RECORDED 3  /* T of the last mpm_forward (0 = none) */
 #define MPM_INFO_KEEPS_SEGMENT_GRIDS 4 /* 1: a re-simulated segment's grids are kept for its
                                           adjoint passes (see MPM_OPT_GRID_RECOMPUTE) */
+#define MPM_INFO_ACT_PARAMS 5      /* actuation parameters per scene: n_groups * n_basis, or
+                                      the controller's theta when ctrl_hidden > 0 */
 
 typedef struct mpm_handle mpm_handle;
 
@@ -161,6 +166,20 @@ typedef struct mpm_scene_desc {
                                   MPM_ERR_RANGE.  The shared scatter box is not used.  0: FP32
                                   atomic sums (default, faster).  No counterpart in the paper,
                                   whose GPU atomics are order-dependent as well. */
+  int32_t ctrl_hidden;         /* 0: open-loop sine actuation (w = sine weights).  H in 1..64:
+                                  closed-loop controller with H hidden units, evaluated at every
+                                  step on the current state: inputs u = [sin(2 pi k t / P +
+                                  phase), k = 1..n_basis] followed, for each group g, by the
+                                  offset of g's centre of mass from the scene's (dim values) and
+                                  g's mean velocity (dim values; an empty group reads zeros);
+                                  h = tanh(W1 u + b1), a_g = ctrl_scale tanh(W2 h + b2)_g.  w is
+                                  then theta = [W1 (H x n_in, row-major) | b1 (H) | W2 (n_groups x
+                                  H) | b2 (n_groups)] per scene, n_in = n_basis + 2 dim n_groups
+                                  (MPM_INFO_ACT_PARAMS gives the count).  Needs n_groups >= 1;
+                                  n_basis may be 0.  The forward splits each fused particle pass
+                                  around the controller, the backward each fused adjoint pass
+                                  around its reverse; the persistent form is not used. */
+  float ctrl_scale;            /* controller output scale (ctrl_hidden > 0) */
 } mpm_scene_desc;
 
 /* Device bytes the workspace needs for this description and at most max_steps
@@ -176,7 +195,8 @@ int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_byt
 /* Copy the initial state in (device pointers, component-major, N particles).
  * C0 may be NULL (zero), F0 NULL (identity).  E, nu: Young's modulus and Poisson
  * ratio per particle.  group: int32 [N] actuator group in [0, n_groups) (NULL if
- * n_groups == 0); w: float [n_scenes][n_groups][n_basis] actuation weights.
+ * n_groups == 0); w: float [n_scenes][n_groups][n_basis] actuation weights, or
+ * [n_scenes][MPM_INFO_ACT_PARAMS] controller parameters theta when ctrl_hidden > 0.
  * Particles are reordered internally by a spatial (Morton) key per scene so that
  * P2G tiles are compact; all outputs come back in the caller's order.
  * Invalidates any recorded forward. */
@@ -211,8 +231,9 @@ int mpm_loss(mpm_handle* h, int32_t kind, const float* target, float* loss, floa
 /* Reverse pass of the last forward (the tape is replayed in reverse, Section 3.2):
  * given dL/dstate_T (device, caller order; any of the four may be NULL = zero),
  * write dL/dstate_0 (gx0, gv0, gC0, gF0: device [dim|dim*dim][N]), dL/dE and dL/dnu
- * (device [N]) and dL/dw (device [n_scenes][n_groups][n_basis]).  Any output may be
- * NULL.  May be called more than once per forward. */
+ * (device [N]) and dL/dw (device [n_scenes][n_groups][n_basis], or dL/dtheta
+ * [n_scenes][MPM_INFO_ACT_PARAMS] with the controller).  Any output may be NULL.  May
+ * be called more than once per forward. */
 int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const float* dL_dC,
                  const float* dL_dF, float* gx0, float* gv0, float* gC0, float* gF0,
                  float* gE, float* gnu, float* gw, void* stream);

@@ -1,0 +1,255 @@
+// controller.cu -- the closed-loop controller of the actuated bodies (the neural-network
+// controllers of Section 4.1): at every step the sensors of the current state feed a
+// small MLP whose outputs are the actuation of the groups, and the reverse pass carries
+// the actuation adjoint back through the MLP to its weights and to the sensed state.
+//
+//   inputs u (n_in = K + 2 d G): sin(2 pi k t / P + phi) for k = 1..K, then per group g
+//     the offset of its centre of mass from the body's (d values) and its mean velocity
+//     (d values); an empty group reads zeros
+//   h = tanh(W1 u + b1) (H units), a_g = scale tanh(W2 h + b2)_g
+//   theta per scene = [W1 (H x n_in, row-major) | b1 (H) | W2 (G x H, row-major) | b2 (G)]
+//
+// Weights arrive in FP32; sensor sums and the MLP run in FP64 (a few thousand operations
+// per scene and step).  Every sum runs in a fixed order (a tile's particles in order, a
+// scene's tiles in order), so the controller adds nothing order-dependent to a
+// deterministic run.
+#include "mpm_internal.h"
+
+namespace mpm {
+
+namespace {
+
+constexpr int kSenseThreads = kTile;  // one CTA per particle tile
+static_assert(kTile <= 512, "the sensing CTA stages a tile's values in static shared memory");
+constexpr int kCtrlThreads = 128;     // one CTA per scene for the MLP passes
+constexpr int kSenseVals = 7;       // x (d), v (d), count: at most 7
+constexpr int kSenseSlots = kMaxGroups + 1;  // slot 0: particles in no group
+
+// Per-tile sums of x, v and the particle count by group slot, in particle order:
+// part[tile][slot][value] (FP64), value = x_0..x_{d-1}, v_0..v_{d-1}, count.
+__global__ void ctrl_sense_kernel(int dim, int G, int64_t N, const int4* tiles, const float* st,
+                                  const int* group, double* part) {
+  __shared__ double vals[kSenseVals][kSenseThreads];
+  __shared__ int slot[kSenseThreads];
+  const int4 tile = tiles[blockIdx.x];
+  const int i = threadIdx.x;
+  const int nv = 2 * dim + 1, ns = G + 1;
+  if (i < tile.z) {
+    const int64_t p = (int64_t)tile.y + i;
+    const int g = group[p];
+    slot[i] = (g >= 0 && g < G) ? g + 1 : 0;
+    for (int a = 0; a < dim; ++a) {
+      vals[a][i] = (double)st[(int64_t)a * N + p];
+      vals[dim + a][i] = (double)st[(int64_t)(dim + a) * N + p];
+    }
+    vals[2 * dim][i] = 1.0;
+  }
+  __syncthreads();
+  for (int j = i; j < ns * nv; j += blockDim.x) {
+    const int sl = j / nv, c = j % nv;
+    double acc = 0.0;
+    for (int q = 0; q < tile.z; ++q)
+      if (slot[q] == sl) acc += vals[c][q];
+    part[(int64_t)blockIdx.x * ns * nv + j] = acc;
+  }
+}
+
+// One CTA per scene: reduce the scene's tile sums in order, form the inputs, run the MLP
+// and store u, h, y = tanh(W2 h + b2) (kept for the reverse pass), the actuation
+// a = scale y, and the group sizes.
+__global__ void ctrl_forward_kernel(CtrlStep cs, const int* tile_off, const double* part,
+                                    const float* theta, double* u_out, double* h_out,
+                                    double* y_out, float* act_out, double* cnt_out) {
+  __shared__ double sums[kSenseSlots * kSenseVals];
+  __shared__ double u[kCtrlMaxInputs];
+  __shared__ double hs[kCtrlMaxHidden];
+  const int s = blockIdx.x;
+  const int dim = cs.dim, G = cs.G, K = cs.K, H = cs.H;
+  const int nv = 2 * dim + 1, ns = G + 1;
+  const int n_in = K + 2 * dim * G;
+  const int n_par = H * n_in + H + G * H + G;
+  const float* th = theta + (int64_t)s * n_par;
+  for (int j = threadIdx.x; j < ns * nv; j += blockDim.x) {
+    double acc = 0.0;
+    for (int t = tile_off[s]; t < tile_off[s + 1]; ++t) acc += part[(int64_t)t * ns * nv + j];
+    sums[j] = acc;
+  }
+  __syncthreads();
+  // inputs: the time basis, then per group (centre offset, mean velocity)
+  for (int i = threadIdx.x; i < n_in; i += blockDim.x) {
+    double val;
+    if (i < K) {
+      val = cs.basis[i];
+    } else {
+      const int r = i - K, g = r / (2 * dim), c = r % (2 * dim);
+      const double n_g = sums[(g + 1) * nv + 2 * dim];
+      if (n_g <= 0.0) {
+        val = 0.0;
+      } else if (c < dim) {
+        double tot = 0.0, cnt = 0.0;
+        for (int q = 0; q < ns; ++q) {
+          tot += sums[q * nv + c];
+          cnt += sums[q * nv + 2 * dim];
+        }
+        val = sums[(g + 1) * nv + c] / n_g - tot / cnt;
+      } else {
+        val = sums[(g + 1) * nv + c] / n_g;
+      }
+    }
+    u[i] = val;
+    u_out[(int64_t)s * n_in + i] = val;
+  }
+  if ((int)threadIdx.x < ns) cnt_out[s * ns + threadIdx.x] = sums[threadIdx.x * nv + 2 * dim];
+  __syncthreads();
+  const float* W1 = th;
+  const float* b1 = th + H * n_in;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + G * H;
+  for (int j = threadIdx.x; j < H; j += blockDim.x) {
+    double z = (double)b1[j];
+    for (int i = 0; i < n_in; ++i) z += (double)W1[j * n_in + i] * u[i];
+    const double hj = tanh(z);
+    hs[j] = hj;
+    h_out[(int64_t)s * H + j] = hj;
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    double z = (double)b2[g];
+    for (int j = 0; j < H; ++j) z += (double)W2[g * H + j] * hs[j];
+    const double y = tanh(z);
+    y_out[(int64_t)s * G + g] = y;
+    act_out[(int64_t)s * G + g] = (float)((double)cs.scale * y);
+  }
+}
+
+// One CTA per scene, reverse of the controller at one step: abar_g = the scene's per-tile
+// actuation adjoints summed in tile order (and the tile slots cleared for the next step);
+// dL/dtheta accumulates in FP64 (thbar); the sensor adjoint becomes per-slot additions to
+// the state adjoint: add[scene][slot][0..d) to xbar, [d..2d) to vbar.
+__global__ void ctrl_backward_kernel(CtrlStep cs, const int* tile_off, float* abar_tile,
+                                     const float* theta, const double* u_in, const double* h_in,
+                                     const double* y_in, const double* cnt, double* thbar,
+                                     float* add) {
+  __shared__ double z2b[kMaxGroups];
+  __shared__ double z1b[kCtrlMaxHidden];
+  __shared__ double ub[kCtrlMaxInputs];
+  __shared__ double body[3];
+  const int s = blockIdx.x;
+  const int dim = cs.dim, G = cs.G, K = cs.K, H = cs.H;
+  const int ns = G + 1;
+  const int n_in = K + 2 * dim * G;
+  const int n_par = H * n_in + H + G * H + G;
+  const float* th = theta + (int64_t)s * n_par;
+  const float* W1 = th;
+  const float* W2 = th + H * n_in + H;
+  double* W1b = thbar + (int64_t)s * n_par;
+  double* b1b = W1b + H * n_in;
+  double* W2b = b1b + H;
+  double* b2b = W2b + G * H;
+  const double* u = u_in + (int64_t)s * n_in;
+  const double* h = h_in + (int64_t)s * H;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    double ab = 0.0;
+    for (int t = tile_off[s]; t < tile_off[s + 1]; ++t) {
+      ab += (double)abar_tile[(int64_t)t * G + g];
+      abar_tile[(int64_t)t * G + g] = 0.0f;
+    }
+    const double y = y_in[(int64_t)s * G + g];
+    const double zb = ab * (double)cs.scale * (1.0 - y * y);
+    z2b[g] = zb;
+    b2b[g] += zb;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < H; j += blockDim.x) {
+    double hb = 0.0;
+    for (int g = 0; g < G; ++g) {
+      W2b[g * H + j] += z2b[g] * h[j];
+      hb += (double)W2[g * H + j] * z2b[g];
+    }
+    const double zb = hb * (1.0 - h[j] * h[j]);
+    z1b[j] = zb;
+    b1b[j] += zb;
+    for (int i = 0; i < n_in; ++i) W1b[j * n_in + i] += zb * u[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_in; i += blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < H; ++j) acc += (double)W1[j * n_in + i] * z1b[j];
+    ub[i] = acc;
+  }
+  __syncthreads();
+  // u_xg = mean_{p in g} x_p - mean_p x_p: every particle carries -sum_g ub_xg / N, and
+  // its own group's ub_xg / N_g; u_vg = mean_{p in g} v_p: ub_vg / N_g
+  if ((int)threadIdx.x < dim) {
+    const int a = threadIdx.x;
+    double tot = 0.0, n = 0.0;
+    for (int q = 0; q < ns; ++q) n += cnt[s * ns + q];
+    for (int g = 0; g < G; ++g)
+      if (cnt[s * ns + g + 1] > 0.0) tot += ub[K + g * 2 * dim + a];
+    body[a] = n > 0.0 ? tot / n : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < ns * 2 * dim; j += blockDim.x) {
+    const int sl = j / (2 * dim), c = j % (2 * dim);
+    double v = 0.0;
+    if (c < dim) v = -body[c];
+    if (sl > 0) {
+      const double n_g = cnt[s * ns + sl];
+      if (n_g > 0.0) v += ub[K + (sl - 1) * 2 * dim + c] / n_g;
+    }
+    add[((int64_t)s * ns + sl) * 2 * dim + c] = (float)v;
+  }
+}
+
+// xbar_p += add[scene][slot(p)][0..d), vbar_p += add[scene][slot(p)][d..2d): one CTA per
+// particle tile
+__global__ void ctrl_sensor_adjoint_kernel(int dim, int G, int64_t N, const int4* tiles,
+                                           const int* group, const float* add, float* adj) {
+  const int4 tile = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= tile.z) return;
+  const int64_t p = (int64_t)tile.y + threadIdx.x;
+  const int g = group[p];
+  const int sl = (g >= 0 && g < G) ? g + 1 : 0;
+  const float* a = add + ((int64_t)tile.x * (G + 1) + sl) * 2 * dim;
+  for (int c = 0; c < 2 * dim; ++c) adj[(int64_t)c * N + p] += a[c];
+}
+
+// gw[scene][i] = thbar[scene][i] (FP64 -> FP32)
+__global__ void ctrl_grad_out_kernel(int64_t n, const double* thbar, float* gw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    gw[i] = (float)thbar[i];
+}
+
+}  // namespace
+
+cudaError_t launch_ctrl_forward(const CtrlStep& cs, int n_scenes, int n_tiles, int64_t N,
+                                const int4* tiles, const int* tile_off, const float* st,
+                                const int* group, double* part, const float* theta, double* u,
+                                double* h, double* y, float* act, double* cnt, cudaStream_t s) {
+  ctrl_sense_kernel<<<n_tiles, kSenseThreads, 0, s>>>(cs.dim, cs.G, N, tiles, st, group, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ctrl_forward_kernel<<<n_scenes, kCtrlThreads, 0, s>>>(cs, tile_off, part, theta, u, h, y, act, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_backward(const CtrlStep& cs, int n_scenes, int n_tiles, int64_t N,
+                                 const int4* tiles, const int* tile_off, const int* group,
+                                 float* abar_tile, const float* theta, const double* u,
+                                 const double* h, const double* y, const double* cnt,
+                                 double* thbar, float* add, float* adj, cudaStream_t s) {
+  ctrl_backward_kernel<<<n_scenes, kCtrlThreads, 0, s>>>(cs, tile_off, abar_tile, theta, u, h, y,
+                                                         cnt, thbar, add);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ctrl_sensor_adjoint_kernel<<<n_tiles, kSenseThreads, 0, s>>>(cs.dim, cs.G, N, tiles, group, add, adj);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_grad_out(int64_t n, const double* thbar, float* gw, cudaStream_t s) {
+  ctrl_grad_out_kernel<<<(int)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256), 256, 0, s>>>(n, thbar, gw);
+  return cudaGetLastError();
+}
+
+}  // namespace mpm

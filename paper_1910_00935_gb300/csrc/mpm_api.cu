@@ -64,6 +64,9 @@ struct Layout {
   size_t boxes;  // (pm_slots + kUBSlots) x 2 parities x [scene][8]
   size_t err, com, com_part, ub_m0;
   size_t plan_fwd, plan_bwd, gsync;  // persistent-form pass plans and barrier counters
+  // closed-loop controller: per-tile sensor sums, per-step inputs / hidden / outputs /
+  // actuation, group sizes, dL/dtheta (FP64) and the per-slot sensor adjoints
+  size_t ctrl_part, ctrl_u, ctrl_h, ctrl_y, act_tab, ctrl_cnt, ctrl_thbar, ctrl_add;
   size_t total;
 };
 
@@ -75,6 +78,10 @@ struct Dims {
   int pm_slots;      // (m, p) grid buffers: kPMSlots, or K + 4 when store_grids
   int words;         // float4 slots per grid node: 2 for fixed-point grids (deterministic)
   int T_max;         // max_steps
+  int G;             // actuation groups
+  int ctrl_H;        // controller hidden units (0: open-loop sine actuation)
+  int ctrl_in;       // controller inputs K + 2 D G
+  int64_t n_act;     // actuation parameters per scene: G K (open loop) or the controller's
 };
 
 // passes of the longest forward (T + 1) and backward (re-simulation T + segments, adjoint
@@ -107,8 +114,15 @@ bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
   if (d->ckpt_every < 1) return fail("ckpt_every must be >= 1");
   if (d->n_groups < 0 || d->n_groups > kMaxGroups) return fail("n_groups must be in [0, 8]");
   if (d->n_basis < 0 || d->n_basis > kMaxBasis) return fail("n_basis must be in [0, 8]");
-  if (d->n_groups > 0 && (d->n_basis < 1 || !(d->act_period != 0.0f)))
+  if (d->ctrl_hidden < 0 || d->ctrl_hidden > kCtrlMaxHidden)
+    return fail("ctrl_hidden must be in [0, 64]");
+  if (d->ctrl_hidden > 0) {
+    if (d->n_groups < 1) return fail("the controller needs n_groups >= 1");
+    if (!std::isfinite(d->ctrl_scale)) return fail("ctrl_scale must be finite");
+    if (d->n_basis > 0 && !(d->act_period != 0.0f)) return fail("time inputs need act_period != 0");
+  } else if (d->n_groups > 0 && (d->n_basis < 1 || !(d->act_period != 0.0f))) {
     return fail("actuation needs n_basis >= 1 and act_period != 0");
+  }
   if (d->deterministic_p2g != 0 && d->deterministic_p2g != 1) return fail("deterministic_p2g must be 0 or 1");
   if (max_steps < 1) return fail("max_steps must be >= 1");
   if (max_steps > (1 << 24)) return fail("max_steps too large");
@@ -126,6 +140,12 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
   m.polar_cache = d->dim == 3 && (d->material == MPM_FIXED_COROTATED || d->material == MPM_MIXED);
   m.T_max = max_steps;
   m.words = d->deterministic_p2g ? 2 : 1;
+  m.G = d->n_groups;
+  m.ctrl_H = d->ctrl_hidden;
+  m.ctrl_in = d->ctrl_hidden > 0 ? d->n_basis + 2 * d->dim * d->n_groups : 0;
+  m.n_act = d->ctrl_hidden > 0
+                ? (int64_t)m.ctrl_H * m.ctrl_in + m.ctrl_H + (int64_t)m.G * m.ctrl_H + m.G
+                : (int64_t)d->n_groups * d->n_basis;
   {
     int64_t nn = 1;
     for (int a = 0; a < d->dim; ++a) nn *= d->n_grid;
@@ -169,7 +189,7 @@ Layout make_layout(const Dims& m) {
   L.nu = take(N * 4);
   L.group = take(N * 4);
   L.matid = take(N * 4);
-  L.wact = take(S * kMaxGroups * kMaxBasis * 4);
+  L.wact = take(S * (size_t)std::max<int64_t>(kMaxGroups * kMaxBasis, m.n_act) * 4);
   L.wbar_tile = take((size_t)m.n_tiles * kMaxGroups * kMaxBasis * 4);
   L.mubar = take(N * 4);
   L.labar = take(N * 4);
@@ -190,6 +210,18 @@ Layout make_layout(const Dims& m) {
   L.plan_bwd = take((size_t)plan_bwd_cap(m) * sizeof(PassEntry));
   // barrier counters, then one tile-ticket counter per pass of the longest plan
   L.gsync = take(16 + 4 * (size_t)std::max(plan_fwd_cap(m), plan_bwd_cap(m)));
+  {
+    const bool c = m.ctrl_H > 0;
+    const size_t steps = (size_t)m.T_max + 1, slots = (size_t)kMaxGroups + 1;
+    L.ctrl_part = take(c ? (size_t)m.n_tiles * slots * 7 * 8 : 0);
+    L.ctrl_u = take(c ? steps * S * m.ctrl_in * 8 : 0);
+    L.ctrl_h = take(c ? steps * S * m.ctrl_H * 8 : 0);
+    L.ctrl_y = take(c ? steps * S * m.G * 8 : 0);
+    L.act_tab = take(c ? steps * S * m.G * 4 : 0);
+    L.ctrl_cnt = take(c ? S * slots * 8 : 0);
+    L.ctrl_thbar = take(c ? S * (size_t)m.n_act * 8 : 0);
+    L.ctrl_add = take(c ? S * slots * 6 * 4 : 0);
+  }
   L.total = o;
   return L;
 }
@@ -288,9 +320,16 @@ SimParams params_for(const mpm_handle* h, int t) {
   P.n_groups = d.n_groups;
   P.n_basis = d.n_basis;
   const double two_pi = 6.283185307179586476925286766559;
-  for (int k = 1; k <= d.n_basis; ++k)
-    P.basis[k - 1] =
-        (float)std::sin(two_pi * k * (double)t / (double)d.act_period + (double)d.act_phase);
+  if (d.ctrl_hidden > 0) {
+    // closed loop: a particle's actuation is its group's entry of this step's row of the
+    // controller's actuation table (one "basis" value of 1)
+    P.n_basis = 1;
+    P.basis[0] = 1.0f;
+  } else {
+    for (int k = 1; k <= d.n_basis; ++k)
+      P.basis[k - 1] =
+          (float)std::sin(two_pi * k * (double)t / (double)d.act_period + (double)d.act_phase);
+  }
   // the shared scatter box sums in FP32 in arbitrary order: not in the deterministic mode
   P.tile_capacity = h->smem_tile && !d.deterministic_p2g ? h->tile_capacity : 0;
   P.gather_capacity = h->gather_capacity;
@@ -308,6 +347,28 @@ SimParams params_for(const mpm_handle* h, int t) {
     P.unfix_p = std::ldexp(1.0f, -ep);
   }
   return P;
+}
+
+// the actuation parameters a pass reads at step t: the open-loop weights, or row t of the
+// closed-loop controller's actuation table [step][scene][group]
+const float* act_ptr(const mpm_handle* h, int t) {
+  if (h->m.ctrl_H > 0) return h->at<float>(h->L.act_tab) + (size_t)t * h->m.S * h->m.G;
+  return h->at<float>(h->L.wact);
+}
+
+CtrlStep ctrl_step(const mpm_handle* h, int t) {
+  const mpm_scene_desc& d = h->desc;
+  CtrlStep c;
+  memset(&c, 0, sizeof(c));
+  c.dim = d.dim;
+  c.G = d.n_groups;
+  c.K = d.n_basis;
+  c.H = d.ctrl_hidden;
+  c.scale = d.ctrl_scale;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int k = 1; k <= d.n_basis; ++k)
+    c.basis[k - 1] = std::sin(two_pi * k * (double)t / (double)d.act_period + (double)d.act_phase);
+  return c;
 }
 
 int grid_blocks_per_scene(const mpm_handle* h) {
@@ -514,7 +575,7 @@ struct Launcher {
     A.la = h->at<float>(h->L.la);
     A.group = h->at<int>(h->L.group);
     A.matid = h->at<int>(h->L.matid);
-    A.wact = h->at<float>(h->L.wact);
+    A.wact = act_ptr(h, t);
     A.err = h->at<unsigned>(h->L.err);
     if (read >= 0) A.PMr = ring_grid(h, h->pm, read);
     A.Rw = R_out;
@@ -560,7 +621,7 @@ struct Launcher {
     A.labar = h->at<float>(h->L.labar);
     A.group = h->at<int>(h->L.group);
     A.matid = h->at<int>(h->L.matid);
-    A.wact = h->at<float>(h->L.wact);
+    A.wact = act_ptr(h, s_step + 1);
     A.wbar_tile = h->at<float>(h->L.wbar_tile);
     A.err = h->at<unsigned>(h->L.err);
     A.R1 = R1;
@@ -594,6 +655,42 @@ struct Launcher {
     cudaError_t e = pass(kPassAdjoint, amode, cat, P, A);
     after_launch(h);
     return e;
+  }
+
+  // closed-loop controller at step t: sense state st and evaluate the MLP, giving row t of
+  // the actuation table (direct launches only: the persistent form is off with a controller)
+  cudaError_t ctrl_forward(int t, const float* st) {
+    if (mode != kDirect) return cudaErrorNotSupported;
+    const Dims& m = h->m;
+    const Layout& L = h->L;
+    const CtrlStep c = ctrl_step(h, t);
+    count += 2;
+    return timed(MPM_KERNEL_CONTROLLER, [&] {
+      return launch_ctrl_forward(c, m.S, m.n_tiles, m.N, h->at<int4>(L.tiles), h->at<int>(L.scene_tile_off), st,
+                                 h->at<int>(L.group), h->at<double>(L.ctrl_part), h->at<float>(L.wact),
+                                 h->at<double>(L.ctrl_u) + (size_t)t * m.S * m.ctrl_in,
+                                 h->at<double>(L.ctrl_h) + (size_t)t * m.S * m.ctrl_H,
+                                 h->at<double>(L.ctrl_y) + (size_t)t * m.S * m.G,
+                                 h->at<float>(L.act_tab) + (size_t)t * m.S * m.G, h->at<double>(L.ctrl_cnt), s);
+    });
+  }
+
+  // reverse of the controller at step t, after the P2G adjoint of step t left the
+  // per-tile actuation adjoints in wbar_tile and the adjoint of state t in adj
+  cudaError_t ctrl_backward(int t) {
+    if (mode != kDirect) return cudaErrorNotSupported;
+    const Dims& m = h->m;
+    const Layout& L = h->L;
+    const CtrlStep c = ctrl_step(h, t);
+    count += 2;
+    return timed(MPM_KERNEL_CONTROLLER, [&] {
+      return launch_ctrl_backward(c, m.S, m.n_tiles, m.N, h->at<int4>(L.tiles), h->at<int>(L.scene_tile_off),
+                                  h->at<int>(L.group), h->at<float>(L.wbar_tile), h->at<float>(L.wact),
+                                  h->at<double>(L.ctrl_u) + (size_t)t * m.S * m.ctrl_in,
+                                  h->at<double>(L.ctrl_h) + (size_t)t * m.S * m.ctrl_H,
+                                  h->at<double>(L.ctrl_y) + (size_t)t * m.S * m.G, h->at<double>(L.ctrl_cnt),
+                                  h->at<double>(L.ctrl_thbar), h->at<float>(L.ctrl_add), h->at<float>(L.adj), s);
+    });
   }
 
   // End of a launch sequence: zero every dirty buffer, reset every box.
@@ -751,6 +848,90 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident) {
   return MPM_OK;
 }
 
+// Closed-loop controller (desc.ctrl_hidden > 0).  The actuation of step t depends on
+// state t through the controller's sensors, so P2G of step t waits for the whole of
+// G2P of step t-1 and for the controller: the forward splits the fused pass into G2P
+// (state t written in full), the controller, and P2G.  The storage of states (checkpoints,
+// the resident last segment, the polar factors) is that of issue_forward, and the
+// actuation table the forward writes is what every later pass of that step reads.
+int issue_forward_ctrl(mpm_handle* h, Launcher& Lc, int T) {
+  const int K = h->m.K;
+  const int sL = last_segment_start(h, T);
+  ring_reset(h->pm);
+  ring_reset(h->ub);
+  const float* src = h->state(h->L.ckpt, 0);
+  float* cur = h->at<float>(h->L.cur);
+  int g = -1;
+  LK(Lc.ctrl_forward(0, src));
+  LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g, sL == 0 ? h->rslot(0) : nullptr));
+  for (int t = 1; t < T; ++t) {
+    float* dst = (t % K == 0) ? h->state(h->L.ckpt, t / K) : (t > sL) ? h->state(h->L.seg, t - sL) : cur;
+    LK(Lc.step(kG2POnlyFull, t, src, dst, g, nullptr));
+    ring_release(h->pm, g);
+    LK(Lc.ctrl_forward(t, dst));
+    LK(Lc.step(kP2GOnly, t, dst, nullptr, -1, &g, t >= sL ? h->rslot(t - sL) : nullptr));
+    src = dst;
+  }
+  LK(Lc.step(kG2POnlyFull, T, src, h->at<float>(h->L.fin), g, nullptr));
+  ring_release(h->pm, g);
+  LK(Lc.finish());
+  return MPM_OK;
+}
+
+// Backward with the controller: the sensor adjoint of state s+1 needs the actuation
+// adjoint of step s+1 summed over every particle, so the fused adjoint pass splits into
+// the P2G adjoint of step s+1 (adjoint of state s+1 written in full), the controller's
+// reverse (which adds the sensor terms to it), and the G2P adjoint of step s read from
+// it.  Re-simulation reads the recorded actuation table; a grid that is neither kept nor
+// re-simulated is recomputed by its own P2G pass.
+int issue_backward_ctrl(mpm_handle* h, Launcher& Lc, int T, bool resident) {
+  const int K = h->m.K;
+  ring_reset(h->pm);
+  ring_reset(h->ub);
+  int pm_s1 = -1, pm_s = -1, ub_s1 = -1;
+  std::vector<int> seg_grids(K, -1);
+  bool stored = false;
+  for (int s = T - 1; s >= 0; --s) {
+    const int j = s / K, s0 = j * K;
+    const int top = (s0 + K < T) ? s0 + K : T;
+    const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
+    const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->state(h->L.seg, s + 1 - s0);
+    const double* R1 = (s + 1 < top) ? h->rslot(s + 1 - s0) : nullptr;
+    if (s == T - 1 && resident) {
+      LK(Lc.step(kP2GOnly, s, st_s, nullptr, -1, &pm_s));
+      stored = false;
+    } else if (s == top - 1) {
+      stored = h->m.store_grids && !h->grid_recompute;
+      int rc = issue_resim(h, Lc, s0, top, &pm_s, stored ? seg_grids.data() : nullptr);
+      if (rc) return rc;
+    } else if (stored) {
+      pm_s = seg_grids[s - s0];
+    } else {
+      LK(Lc.step(kP2GOnly, s, st_s, nullptr, -1, &pm_s, nullptr));
+    }
+    if (s < T - 1) {
+      LK(Lc.adjoint(kAdjP2G, s, st_s1, st_s1, nullptr, pm_s1, ub_s1, -1, nullptr, nullptr, R1));
+      ring_release(h->pm, pm_s1);
+      ring_release(h->ub, ub_s1);
+      LK(Lc.ctrl_backward(s + 1));
+    } else if (h->m.words == 2) {  // deterministic: bound of the first ubar scatter
+      LK(Lc.adjoint(kAdjG2P, s, st_s1, st_s, nullptr, -1, -1, pm_s, nullptr, nullptr, nullptr,
+                    nullptr, 1));
+    }
+    int ub_s = -1;
+    LK(Lc.adjoint(kAdjG2P, s, st_s1, st_s, nullptr, -1, -1, pm_s, &ub_s, nullptr));
+    pm_s1 = pm_s;
+    ub_s1 = ub_s;
+  }
+  const float* st0 = h->state(h->L.ckpt, 0);
+  LK(Lc.adjoint(kAdjP2G, -1, st0, st0, nullptr, pm_s1, ub_s1, -1, nullptr, nullptr));
+  ring_release(h->pm, pm_s1);
+  ring_release(h->ub, ub_s1);
+  LK(Lc.ctrl_backward(0));
+  LK(Lc.finish());
+  return MPM_OK;
+}
+
 void drop_graphs(mpm_handle* h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.first);
   h->graphs.clear();
@@ -760,7 +941,7 @@ void drop_graphs(mpm_handle* h) {
 template <typename Fn>
 int run_sequence_impl(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
   const PassEntry* dplan = nullptr;
-  if (h->persistent) {
+  if (h->persistent && h->m.ctrl_H == 0) {  // the controller's kernels are not plan passes
     // record the plan (forward keys are even, backward keys odd), refresh its device copy
     const int region = (int)(key & 1);
     std::vector<PassEntry> plan;
@@ -929,7 +1110,7 @@ int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float
   CK(launch_gather_initial(m.D, m.N, h->at<int>(L.perm), x0, v0, C0, F0, E, nu, group,
                            h->state(L.ckpt, 0), h->at<float>(L.mu), h->at<float>(L.la),
                            h->at<float>(L.E), h->at<float>(L.nu), h->at<int>(L.group), s));
-  const size_t wbytes = (size_t)m.S * h->desc.n_groups * h->desc.n_basis * sizeof(float);
+  const size_t wbytes = (size_t)m.S * m.n_act * sizeof(float);
   if (wbytes) CK(cudaMemcpyAsync(h->at<float>(L.wact), w, wbytes, cudaMemcpyDeviceToDevice, s));
   const size_t grid = (size_t)m.S * m.nnodes * sizeof(float4) * m.words;
   CK(cudaMemsetAsync(h->at<char>(L.grids), 0, grid * (m.pm_slots + kUBSlots), s));
@@ -965,7 +1146,9 @@ int mpm_forward(mpm_handle* h, int32_t T, void* stream) {
   if (T < 1 || T > h->max_steps) return fail(h, MPM_ERR_STATE, "T must be in [1, max_steps]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   h->last_stream = s;
-  int rc = run_sequence(h, (int64_t)T * 2, s, [&](Launcher& Lc) { return issue_forward(h, Lc, T); });
+  int rc = run_sequence(h, (int64_t)T * 2, s, [&](Launcher& Lc) {
+    return h->m.ctrl_H > 0 ? issue_forward_ctrl(h, Lc, T) : issue_forward(h, Lc, T);
+  });
   if (rc) return rc;
   h->T_recorded = T;
   h->resident_T = T;
@@ -1036,14 +1219,20 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   }
   CK(cudaMemsetAsync(h->at<float>(L.mubar), 0, (size_t)m.N * 4, s));
   CK(cudaMemsetAsync(h->at<float>(L.labar), 0, (size_t)m.N * 4, s));
-  const int GK = h->desc.n_groups * h->desc.n_basis;
+  const bool ctrl = m.ctrl_H > 0;
+  // per-tile sums of the actuation adjoint: times the sine basis (open loop), or per step
+  // and group for the controller (cleared again by each controller reverse)
+  const int GK = ctrl ? m.G : h->desc.n_groups * h->desc.n_basis;
   if (m.words == 2) CK(cudaMemsetAsync(h->at<unsigned>(L.ub_m0), 0, 4, s));
   if (GK) CK(cudaMemsetAsync(h->at<float>(L.wbar_tile), 0, (size_t)m.n_tiles * GK * 4, s));
+  if (ctrl) CK(cudaMemsetAsync(h->at<double>(L.ctrl_thbar), 0, (size_t)m.S * m.n_act * 8, s));
   h->launches += 4;
   const int T = h->T_recorded;
   const bool resident = h->resident_T == T;
   const int64_t key = (int64_t)T * 2 + 1 + (resident ? 0 : ((int64_t)1 << 40));
-  int rc = run_sequence(h, key, s, [&](Launcher& Lc) { return issue_backward(h, Lc, T, resident); });
+  int rc = run_sequence(h, key, s, [&](Launcher& Lc) {
+    return ctrl ? issue_backward_ctrl(h, Lc, T, resident) : issue_backward(h, Lc, T, resident);
+  });
   if (rc) return rc;
   // re-simulating the earlier segments reused the segment buffer: a later backward of
   // the same forward re-simulates the last segment as well
@@ -1062,7 +1251,10 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
                             h->at<float>(L.labar), gE, gnu, s));
     ++h->launches;
   }
-  if (gw && GK) {
+  if (gw && ctrl) {
+    CK(launch_ctrl_grad_out((int64_t)m.S * m.n_act, h->at<double>(L.ctrl_thbar), gw, s));
+    ++h->launches;
+  } else if (gw && GK) {
     CK(launch_wbar_reduce(m.S, GK, h->at<int>(L.scene_tile_off), h->at<float>(L.wbar_tile), gw, s));
     ++h->launches;
   }
@@ -1142,6 +1334,7 @@ int mpm_get_info(mpm_handle* h, int32_t key, int64_t* value) {
     case MPM_INFO_N_TOTAL: *value = h->m.N; return MPM_OK;
     case MPM_INFO_STEPS_RECORDED: *value = h->T_recorded; return MPM_OK;
     case MPM_INFO_KEEPS_SEGMENT_GRIDS: *value = h->m.store_grids && !h->grid_recompute; return MPM_OK;
+    case MPM_INFO_ACT_PARAMS: *value = h->m.n_act; return MPM_OK;
   }
   return fail(h, MPM_ERR_ARG, "unknown info key");
 }

@@ -36,6 +36,17 @@ constexpr int kTile = MPM_TILE;   // particles (= threads) per CTA in particle p
 static_assert(kTile % 32 == 0 && kTile >= 64 && kTile <= 1024, "tile must be whole warps");
 constexpr int kMaxBasis = 8;
 constexpr int kMaxGroups = 8;
+// closed-loop controller (mpm_scene_desc.ctrl_hidden > 0): hidden units, and inputs
+// (time basis, then per group the centre offset and mean velocity)
+constexpr int kCtrlMaxHidden = 64;
+constexpr int kCtrlMaxInputs = kMaxBasis + 2 * 3 * kMaxGroups;
+
+// what the controller kernels of one step need (passed by value)
+struct CtrlStep {
+  int dim, G, K, H;   // dimension, groups, time-basis inputs, hidden units
+  float scale;        // output scale: a_g = scale tanh(.)
+  double basis[kMaxBasis];  // sin(2 pi k t / P + phi), k = 1..K, at this step
+};
 
 // device error bits (sticky, OR-ed into the handle's error word)
 constexpr unsigned kErrOOB = 1u;

@@ -98,4 +98,21 @@ cudaError_t launch_loss_seed(int dim, int kind, int64_t N, int n_scenes, const i
                              const int* perm, const double* com, const float* target, float* loss,
                              float* dL_dxT, float* dL_dx0, cudaStream_t s);
 
+// controller.cu (closed-loop controller): sensing + MLP of one forward step, writing the
+// step's inputs u, hidden h, pre-scale outputs y, actuation act[scene][G] and group sizes
+// cnt[scene][G+1]; part: n_tiles x (G+1) x 7 doubles
+cudaError_t launch_ctrl_forward(const CtrlStep& cs, int n_scenes, int n_tiles, int64_t N,
+                                const int4* tiles, const int* tile_off, const float* st,
+                                const int* group, double* part, const float* theta, double* u,
+                                double* h, double* y, float* act, double* cnt, cudaStream_t s);
+// reverse of one step: reads (and clears) the per-tile actuation adjoints abar_tile[tile][G],
+// accumulates dL/dtheta into thbar (FP64) and adds the sensor terms to the x and v rows of
+// the state adjoint adj; add: n_scenes x (G+1) x 2 dim floats of scratch
+cudaError_t launch_ctrl_backward(const CtrlStep& cs, int n_scenes, int n_tiles, int64_t N,
+                                 const int4* tiles, const int* tile_off, const int* group,
+                                 float* abar_tile, const float* theta, const double* u,
+                                 const double* h, const double* y, const double* cnt,
+                                 double* thbar, float* add, float* adj, cudaStream_t s);
+cudaError_t launch_ctrl_grad_out(int64_t n, const double* thbar, float* gw, cudaStream_t s);
+
 }  // namespace mpm

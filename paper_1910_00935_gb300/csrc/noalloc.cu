@@ -73,7 +73,7 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
   if (d->dim != 2 && d->dim != 3) return reject(MPM_ERR_ARG, "mpm_step_noalloc: dim must be 2 or 3");
   if (d->n_scenes != 1 || !d->n_particles)
     return reject(MPM_ERR_ARG, "mpm_step_noalloc: exactly one scene");
-  if (d->n_groups != 0) return reject(MPM_ERR_ARG, "mpm_step_noalloc: no actuation");
+  if (d->n_groups != 0 || d->ctrl_hidden != 0) return reject(MPM_ERR_ARG, "mpm_step_noalloc: no actuation");
   if (d->deterministic_p2g != 0)
     return reject(MPM_ERR_ARG, "mpm_step_noalloc: the deterministic mode needs the workspace form");
   if (d->material != MPM_FIXED_COROTATED && d->material != MPM_NEO_HOOKEAN &&

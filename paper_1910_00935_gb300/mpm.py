@@ -35,9 +35,9 @@ MPM_OPT_PERSISTENT, MPM_OPT_BARRIER_TIMEOUT_US, MPM_OPT_BARRIER_TEST_EXTRA = 8, 
 MPM_OPT_PERSISTENT_CHUNK, MPM_OPT_GRID_RECOMPUTE = 11, 12
 KERNEL_CATEGORIES = {1: "p2g", 2: "g2p_p2g", 3: "g2p_p2g_full", 4: "g2p", 5: "grid_clear",
                      6: "adj_g2p", 7: "adj_fused", 8: "adj_p2g", 9: "persistent_step",
-                     10: "persistent_adj"}
+                     10: "persistent_adj", 11: "controller"}
 MPM_INFO_KERNEL_LAUNCHES, MPM_INFO_N_TOTAL, MPM_INFO_STEPS_RECORDED = 1, 2, 3
-MPM_INFO_KEEPS_SEGMENT_GRIDS = 4
+MPM_INFO_KEEPS_SEGMENT_GRIDS, MPM_INFO_ACT_PARAMS = 4, 5
 
 EXPORTED = ["mpm_workspace_bytes", "mpm_create", "mpm_set_initial", "mpm_forward",
             "mpm_get_state", "mpm_loss", "mpm_backward", "mpm_sync_status", "mpm_set_option",
@@ -68,6 +68,8 @@ class SceneDesc(ctypes.Structure):
         ("act_period", ctypes.c_float),
         ("act_phase", ctypes.c_float),
         ("deterministic_p2g", ctypes.c_int32),
+        ("ctrl_hidden", ctypes.c_int32),
+        ("ctrl_scale", ctypes.c_float),
     ]
 
 
@@ -151,7 +153,8 @@ def make_desc(desc: dict) -> SceneDesc:
                   int(desc.get("material", MPM_FIXED_COROTATED)), float(desc.get("rho", 1.0)),
                   int(desc.get("ckpt_every", 32)), int(desc.get("n_groups", 0)),
                   int(desc.get("n_basis", 0)), float(desc.get("act_period", 50.0)),
-                  float(desc.get("act_phase", 0.0)), int(desc.get("deterministic_p2g", 0)))
+                  float(desc.get("act_phase", 0.0)), int(desc.get("deterministic_p2g", 0)),
+                  int(desc.get("ctrl_hidden", 0)), float(desc.get("ctrl_scale", 1.0)))
     d._keep = arr  # keep the particle-count array alive with the struct
     return d
 
@@ -319,15 +322,19 @@ class Simulator:
     def backward(self, dL_dx=None, dL_dv=None, dL_dC=None, dL_dF=None):
         d, N, S = self.dim, self.N, self.n_scenes
         G, K = int(self.desc.get("n_groups", 0)), int(self.desc.get("n_basis", 0))
+        n_act = mpm_get_info(self.h, MPM_INFO_ACT_PARAMS)
+        # dL/dw [S, G, K] (open loop) or dL/dtheta [S, n_params] (closed-loop controller)
+        gw = (torch.zeros(S, n_act, device=self.device) if self.desc.get("ctrl_hidden", 0)
+              else torch.zeros(S, G, K, device=self.device))
         out = dict(gx0=torch.empty(d, N, device=self.device),
                    gv0=torch.empty(d, N, device=self.device),
                    gC0=torch.empty(d * d, N, device=self.device),
                    gF0=torch.empty(d * d, N, device=self.device),
                    gE=torch.empty(N, device=self.device), gnu=torch.empty(N, device=self.device),
-                   gw=torch.zeros(S, G, K, device=self.device))
+                   gw=gw)
         mpm_backward(self.h, self._f(dL_dx), self._f(dL_dv), self._f(dL_dC), self._f(dL_dF),
                      out["gx0"], out["gv0"], out["gC0"], out["gF0"], out["gE"], out["gnu"],
-                     out["gw"] if G * K else None)
+                     out["gw"] if n_act else None)
         return out
 
     def check(self):

@@ -179,6 +179,50 @@ def actuated_robots_3d(seed=0, n_scenes=16, steps=2048, dims=(64, 32, 32), n_gri
     return _assemble(desc, parts)
 
 
+def controller_params(seed, stream, dim, n_groups, n_basis, hidden, sensor_gain=10.0):
+    """Seeded controller parameters theta = [W1 | b1 | W2 | b2] (the layout of
+    mpm_scene_desc.ctrl_hidden): uniform with variance 1/fan_in per layer, the columns of W1
+    that read the sensors (centre offsets, mean velocities) scaled by sensor_gain, biases
+    zero."""
+    n_in = n_basis + 2 * dim * n_groups
+    u = uniform(seed, stream, hidden * n_in + n_groups * hidden) * 2.0 - 1.0
+    W1 = u[:hidden * n_in].reshape(hidden, n_in) * np.sqrt(3.0 / n_in)
+    W1[:, n_basis:] *= sensor_gain
+    W2 = u[hidden * n_in:].reshape(n_groups, hidden) * np.sqrt(3.0 / hidden)
+    return np.concatenate([W1.reshape(-1), np.zeros(hidden), W2.reshape(-1), np.zeros(n_groups)])
+
+
+def controlled_robots_3d(seed=0, n_scenes=4, steps=512, dims=(48, 24, 24), n_grid=64,
+                         ckpt_every=64, n_basis=4, hidden=32, scale=50.0, sensor_gain=10.0,
+                         material=FIXED_COROTATED, bottom_dx=4.0):
+    """Closed-loop robots (the neural-network controllers of Section 4.1): n_scenes 3D box
+    robots of dims particles (48 x 24 x 24 = 27,648, about the paper's 30K-particle 3D
+    robot) at spacing dx/2 on the floor, 8 octant actuator groups (fibre axis g mod 3), each
+    driven at every step by its own controller: inputs sin(2 pi k t / 50), k = 1..n_basis,
+    and per group the centre-of-mass offset and mean velocity; hidden tanh layer of `hidden`
+    units; outputs scale * tanh(.).  E = 5e3, nu = 0.3; v0 = U(+-0.05); loss
+    -(COM_x(T) - COM_x(0)).  The bottom sits at y = bottom_dx * dx (at 3 dx its lowest
+    particles reach the sticky floor from the first step)."""
+    dx = 1.0 / n_grid
+    h = 0.5 * dx
+    corner = (0.1, bottom_dx * dx, 0.5 - dims[2] * h / 2)
+    parts = []
+    for s in range(n_scenes):
+        x0, idx = lattice(3, dims, corner, h)
+        n = x0.shape[1]
+        grp = ((idx[0] >= dims[0] // 2).astype(np.int32)
+               | ((idx[1] >= dims[1] // 2).astype(np.int32) << 1)
+               | ((idx[2] >= dims[2] // 2).astype(np.int32) << 2))
+        v0 = _noise(seed, 400 + s, (3, n))
+        th = controller_params(seed, 500 + s, 3, 8, n_basis, hidden, sensor_gain)
+        parts.append(dict(x0=x0, v0=v0, E=np.full(n, 5e3), nu=np.full(n, 0.3), group=grp, w=th))
+    desc = _base_desc(dim=3, n_grid=n_grid, dt=1e-4, steps=steps, ckpt_every=ckpt_every,
+                      material=material, n_groups=8, n_basis=n_basis, act_period=50.0,
+                      act_phase=0.0, loss_kind=LOSS_COM_X_DISP, ctrl_hidden=hidden,
+                      ctrl_scale=scale)
+    return _assemble(desc, parts)
+
+
 def liquid_column(seed=0, dim=3, steps=256, n_grid=64, cols=(32, 48, 32), E=500.0, nu=0.3,
                   ckpt_every=32):
     """Dam break: a column of weakly compressible liquid (cols particles per axis, 2 per
@@ -232,7 +276,9 @@ def robot_in_liquid(seed=0, steps=256, n_grid=64, robot=(32, 16, 16), pool=(96, 
 
 def make(name: str, seed: int = 0, **kw):
     """Named workloads: 'square2d', 'square2d_grad', 'cube3d', 'rects2d', 'robots3d',
-    'liquid2d', 'liquid3d', 'robot_in_liquid'."""
+    'liquid2d', 'liquid3d', 'robot_in_liquid', 'robots_nn'."""
+    if name == "robots_nn":
+        return controlled_robots_3d(seed, **kw)
     if name == "liquid2d":
         return liquid_column(seed, **{"dim": 2, "n_grid": 128, "cols": (64, 96), **kw})
     if name == "liquid3d":

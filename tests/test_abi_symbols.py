@@ -66,6 +66,19 @@ def test_host_side_validation_without_gpu(libpath):
     bd = mpm.mpm_workspace_bytes(mpm.make_desc({**good, "deterministic_p2g": 1}), 64)
     grids = 10 * 2 * 64 ** 3 * 16  # ten (m, p) and ubar buffers, two scenes, float4 nodes
     assert bd - b1 >= grids
+    # the closed-loop controller: limits, and its per-step tables in the workspace
+    ctrl = dict(good, n_groups=8, n_basis=4, ctrl_hidden=32, ctrl_scale=50.0)
+    for bad in (dict(ctrl_hidden=65), dict(ctrl_hidden=-1), dict(n_groups=0),
+                dict(ctrl_scale=float("inf")), dict(act_period=0.0)):
+        with pytest.raises(mpm.MPMError) as e:
+            mpm.mpm_workspace_bytes(mpm.make_desc({**ctrl, **bad}), 64)
+        assert e.value.code == mpm.MPM_ERR_ARG, bad
+    # no time inputs: n_basis 0 is allowed with the controller (not without it)
+    assert mpm.mpm_workspace_bytes(mpm.make_desc({**ctrl, "n_basis": 0}), 64) > 0
+    bc = mpm.mpm_workspace_bytes(mpm.make_desc(ctrl), 64)
+    n_in = 4 + 2 * 3 * 8
+    per_step = 2 * (n_in + 32 + 8) * 8 + 2 * 8 * 4  # u, h, y (FP64) and the actuation row
+    assert bc - b1 >= 65 * per_step
     # NULL or misaligned workspace is rejected before any CUDA call
     with pytest.raises(mpm.MPMError) as e:
         mpm.mpm_create(d, 0, b1, 64)
