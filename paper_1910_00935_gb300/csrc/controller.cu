@@ -25,6 +25,16 @@ constexpr int kCtrlThreads = 128;     // one CTA per scene for the MLP passes
 constexpr int kSenseVals = 7;       // x (d), v (d), count: at most 7
 constexpr int kSenseSlots = kMaxGroups + 1;  // slot 0: particles in no group
 
+// sum over t in [t0, t1) of a[t * stride + j], for one warp: lanes stride over t, then a
+// butterfly; the order depends only on (t0, t1), so the result is reproducible
+__device__ __forceinline__ double warp_tile_sum(const double* a, int t0, int t1, int stride, int j) {
+  double acc = 0.0;
+  for (int t = t0 + (int)(threadIdx.x & 31); t < t1; t += 32) acc += a[(int64_t)t * stride + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
 // Per-tile sums of x, v and the particle count by group slot, in particle order:
 // part[tile][slot][value] (FP64), value = x_0..x_{d-1}, v_0..v_{d-1}, count.
 __global__ void ctrl_sense_kernel(int dim, int G, int64_t N, const int4* tiles, const float* st,
@@ -69,10 +79,10 @@ __global__ void ctrl_forward_kernel(CtrlStep cs, const int* tile_off, const doub
   const int n_in = K + 2 * dim * G;
   const int n_par = H * n_in + H + G * H + G;
   const float* th = theta + (int64_t)s * n_par;
-  for (int j = threadIdx.x; j < ns * nv; j += blockDim.x) {
-    double acc = 0.0;
-    for (int t = tile_off[s]; t < tile_off[s + 1]; ++t) acc += part[(int64_t)t * ns * nv + j];
-    sums[j] = acc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  for (int j = warp; j < ns * nv; j += n_warps) {
+    const double acc = warp_tile_sum(part, tile_off[s], tile_off[s + 1], ns * nv, j);
+    if (lane == 0) sums[j] = acc;
   }
   __syncthreads();
   // inputs: the time basis, then per group (centre offset, mean velocity)
@@ -148,16 +158,22 @@ __global__ void ctrl_backward_kernel(CtrlStep cs, const int* tile_off, float* ab
   double* b2b = W2b + G * H;
   const double* u = u_in + (int64_t)s * n_in;
   const double* h = h_in + (int64_t)s * H;
-  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  for (int g = warp; g < G; g += n_warps) {
+    // the scene's per-tile actuation adjoints, read and cleared for the next step
     double ab = 0.0;
-    for (int t = tile_off[s]; t < tile_off[s + 1]; ++t) {
+    for (int t = tile_off[s] + lane; t < tile_off[s + 1]; t += 32) {
       ab += (double)abar_tile[(int64_t)t * G + g];
       abar_tile[(int64_t)t * G + g] = 0.0f;
     }
-    const double y = y_in[(int64_t)s * G + g];
-    const double zb = ab * (double)cs.scale * (1.0 - y * y);
-    z2b[g] = zb;
-    b2b[g] += zb;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, o);
+    if (lane == 0) {
+      const double y = y_in[(int64_t)s * G + g];
+      const double zb = ab * (double)cs.scale * (1.0 - y * y);
+      z2b[g] = zb;
+      b2b[g] += zb;
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < H; j += blockDim.x) {
@@ -169,9 +185,9 @@ __global__ void ctrl_backward_kernel(CtrlStep cs, const int* tile_off, float* ab
     const double zb = hb * (1.0 - h[j] * h[j]);
     z1b[j] = zb;
     b1b[j] += zb;
-    for (int i = 0; i < n_in; ++i) W1b[j * n_in + i] += zb * u[i];
   }
   __syncthreads();
+  for (int e = threadIdx.x; e < H * n_in; e += blockDim.x) W1b[e] += z1b[e / n_in] * u[e % n_in];
   for (int i = threadIdx.x; i < n_in; i += blockDim.x) {
     double acc = 0.0;
     for (int j = 0; j < H; ++j) acc += (double)W1[j * n_in + i] * z1b[j];

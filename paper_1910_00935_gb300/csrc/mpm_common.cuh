@@ -555,6 +555,16 @@ struct StressCache {
 // tau = 2 mu (F - R) F^T + la (J - 1) J I        (fixed-corotated)
 // tau = mu (F F^T - I) + la ln(J) I               (neo-Hookean)
 // tau = kappa (J - J^(1-g)) I                     (liquid; no shear stress)
+// row[axis] by selects: an array indexed with a runtime value would be placed in local
+// memory (stores of the whole matrix on every stress evaluation)
+template <int D>
+__device__ __forceinline__ float column_of(const float row[D], int axis) {
+  float v = row[0];
+  if (axis == 1) v = row[1];
+  if (D == 3 && axis == 2) v = row[D - 1];
+  return v;
+}
+
 // tau += act (F e)(F e)^T, e = unit vector of `axis` (actuation fibre)
 // with F = I + E; every product is formed on E (or on F - R) so small strains keep
 // their relative precision.
@@ -620,7 +630,7 @@ __device__ __forceinline__ bool kirchhoff(const float E[D][D], float mu, float l
   if (act != 0.0f) {
     float fe[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) fe[i] = E[i][axis] + (i == axis ? 1.0f : 0.0f);
+    for (int i = 0; i < D; ++i) fe[i] = column_of<D>(E[i], axis) + (i == axis ? 1.0f : 0.0f);
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -713,7 +723,7 @@ __device__ __forceinline__ float kirchhoff_adjoint(const float E[D][D], float mu
   // actuation: abar = (F e)^T tb (F e);  Fbar[:, axis] += act (tb + tb^T) F e
   float fe[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i) fe[i] = F[i][axis];
+  for (int i = 0; i < D; ++i) fe[i] = column_of<D>(F[i], axis);
   float abar = 0.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -724,7 +734,8 @@ __device__ __forceinline__ float kirchhoff_adjoint(const float E[D][D], float mu
       s += (tb[i][j] + tb[j][i]) * fe[j];
     }
     abar += fe[i] * r;
-    Fbar[i][axis] += act * s;
+#pragma unroll
+    for (int j = 0; j < D; ++j) Fbar[i][j] += j == axis ? act * s : 0.0f;
   }
   return abar;
 }

@@ -900,20 +900,26 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
   }
   stage_commit();
 
-  // adjoint of state s+1: xb, vb, Cb, Fb (Fb = dL/dE = dL/dF)
+  // adjoint of state s+1: xb, vb, Cb, Fb (Fb = dL/dE = dL/dF); C1 = C of state s+1.  After
+  // a P2G-adjoint the carried xb, Fb and the rows of state s+1 needed again (C, E, mu, la)
+  // are read after its gather -- fresh loads, as the gather's barriers order them -- so
+  // that none of them holds a register across the gather
   float xb[D], vb[D], Cb[D][D], Fb[D][D];
-  float C1[D][D];  // C of state s+1
+  float C1[D][D];
+  auto load_carried = [&]() {
 #pragma unroll
-  for (int a = 0; a < D; ++a) xb[a] = A.adj[(R::X + a) * N + p];
+    for (int a = 0; a < D; ++a) xb[a] = A.adj[(R::X + a) * N + p];
 #pragma unroll
-  for (int i = 0; i < D; ++i)
+    for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      Fb[i][j] = A.adj[(R::F + i * D + j) * N + p];
-      C1[i][j] = A.st1[(R::C + i * D + j) * N + p];
-    }
+      for (int j = 0; j < D; ++j) {
+        Fb[i][j] = A.adj[(R::F + i * D + j) * N + p];
+        C1[i][j] = A.st1[(R::C + i * D + j) * N + p];
+      }
+  };
 
   if (MODE == kAdjG2P) {
+    load_carried();
 #pragma unroll
     for (int a = 0; a < D; ++a) vb[a] = A.adj[(R::V + a) * N + p];
 #pragma unroll
@@ -945,7 +951,8 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     for (int i = 0; i < D; ++i) {
       mv[i] = P.p_mass * v[i];
 #pragma unroll
-      for (int j = 0; j < D; ++j) Am[i][j] = P.kappa * tau[i][j] + P.p_mass * C1[i][j];
+      for (int j = 0; j < D; ++j)
+        Am[i][j] = P.kappa * tau[i][j] + P.p_mass * A.st1[(R::C + i * D + j) * N + p];
     }
     float Ab[D][D], xg[D], sw[D];
 #pragma unroll
@@ -1018,6 +1025,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
         }
       }
     });
+    load_carried();
     // x += inv_dx sum Wbar gradW - A^T sum W dpbar
 #pragma unroll
     for (int b = 0; b < D; ++b) {
@@ -1036,7 +1044,15 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
         tb[i][j] = P.kappa * Ab[i][j];
       }
     float mub = 0.0f, lab = 0.0f, abar = 0.0f;
-    if (ok) abar = kirchhoff_adjoint<D, MAT>(E, mu, la, act, axis, sc, tb, Fb, mub, lab, mat_p);
+    load_E<D>(A.st1, N, p, P.f_diag, E);
+    if (MAT == kFixedCorotated || MAT == kMixed) {
+      // the polar factor again (from the cache, or recomputed where the state has no cached
+      // factor: one adjoint pass per segment), so that it holds no registers across the
+      // gather; the stress itself is not needed again
+      float tau_again[D][D];
+      kirchhoff<D, MAT>(E, A.mu[p], A.la[p], act, axis, tau_again, sc, A.R1, N, p, mat_p);
+    }
+    if (ok) abar = kirchhoff_adjoint<D, MAT>(E, A.mu[p], A.la[p], act, axis, sc, tb, Fb, mub, lab, mat_p);
     if (active) {
       A.mubar[p] += mub;
       A.labar[p] += lab;

@@ -74,8 +74,11 @@ def test_deterministic_mode_is_bitwise_reproducible(mpm, name, kw, T, k):
                 if v is not None:
                     assert np.array_equal(r["grad"][key], v), (f, key)
     a, b = refs
-    for i in range(4):
-        assert rel_l2(a["state"][i], b["state"][i]) <= 1e-5, i
+    # different compiled code: rounding-level agreement, with the velocity and affine
+    # fields (differences of positions over a step) at 10x and 100x the position bar, as
+    # in the oracle comparisons
+    for i, tol in enumerate((1e-5, 1e-4, 1e-3, 1e-5)):
+        assert rel_l2(a["state"][i], b["state"][i]) <= tol, i
     for key, v in a["grad"].items():
         if v is not None:
             assert rel_l2(b["grad"][key], v) <= 1e-4, key
