@@ -103,6 +103,11 @@ extern "C" {
                                      (Appendix D.1) even when the re-simulated segment's grids fit
                                      in the workspace (K + 4 grid buffers within 8 GiB, decided at
                                      create); 0: keep them [0] */
+#define MPM_OPT_OVERLAP_RESIM 13  /* 1: mpm_backward re-simulates segment j-1 on a second stream
+                                     while the adjoint passes of segment j run (independent
+                                     work that shares the SMs; results are the same as with 0,
+                                     bitwise in the deterministic mode).  Not used in the
+                                     persistent form, with a controller, or while profiling [1] */
 #define MPM_OPT_PERSISTENT_CHUNK 11 /* persistent form: at most this many passes per launch
                                      (0 = a whole run of same-kind passes) [0]; bounds the
                                      duration of any one launch */

@@ -50,16 +50,17 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 constexpr int kPMSlots = 6;  // mass/momentum grids in flight (measured need: 4)
 constexpr int kUBSlots = 4;  // velocity-adjoint grids in flight (need: 3)
 // Grids of a re-simulated segment are kept for its adjoint passes (instead of each adjoint
-// pass recomputing the grid of the step before, Appendix D.1) when the ring of K + 4 grid
-// buffers fits this budget; otherwise the per-step recompute is used.
-constexpr size_t kStoredGridBudget = (size_t)8 << 30;
+// pass recomputing the grid of the step before, Appendix D.1) when two pools of K + 3 grid
+// buffers (one per segment parity, see issue_backward_overlap) fit this budget; otherwise
+// the per-step recompute is used.
+constexpr size_t kStoredGridBudget = (size_t)16 << 30;
 
 struct Layout {
   size_t perm, keys0, keys1, idx0, sort_tmp, sort_tmp_bytes;
   size_t tiles, scene_off, scene_tiles, scene_tile_off;
   size_t mu, la, E, nu, group, matid, wact, wbar_tile, mubar, labar;
   size_t fin, cur, ckpt, seg, adj;
-  size_t rcache;  // (K+1) x [9][N] FP64 polar factors of a re-simulated segment (3D FCR)
+  size_t rcache;  // 2 x (K+1) x [9][N] FP64 polar factors of a segment (3D FCR), by parity
   size_t grids;  // pm_slots + kUBSlots dense grids
   size_t boxes;  // (pm_slots + kUBSlots) x 2 parities x [scene][8]
   size_t err, com, com_part, ub_m0;
@@ -75,7 +76,8 @@ struct Dims {
   int64_t N, nnodes;
   bool polar_cache;  // 3D fixed-corotated: FP64 polar factors are cached per segment
   bool store_grids;  // a re-simulated segment's grids stay live for its adjoint passes
-  int pm_slots;      // (m, p) grid buffers: kPMSlots, or K + 4 when store_grids
+  int pm_slots;      // (m, p) grid buffers: two pools of pm_pool
+  int pm_pool;       // kPMSlots, or K + 3 when store_grids
   int words;         // float4 slots per grid node: 2 for fixed-point grids (deterministic)
   int T_max;         // max_steps
   int G;             // actuation groups
@@ -150,8 +152,9 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
     int64_t nn = 1;
     for (int a = 0; a < d->dim; ++a) nn *= d->n_grid;
     const size_t grid_bytes = (size_t)d->n_scenes * nn * 16 * m.words;
-    m.store_grids = (size_t)(m.K + 4) * grid_bytes <= kStoredGridBudget;
-    m.pm_slots = m.store_grids ? m.K + 4 : kPMSlots;
+    m.store_grids = (size_t)2 * std::max(m.K + 3, kPMSlots) * grid_bytes <= kStoredGridBudget;
+    m.pm_pool = m.store_grids ? std::max(m.K + 3, kPMSlots) : kPMSlots;
+    m.pm_slots = 2 * m.pm_pool;
   }
   m.nnodes = 1;
   for (int a = 0; a < m.D; ++a) m.nnodes *= d->n_grid;
@@ -196,9 +199,9 @@ Layout make_layout(const Dims& m) {
   L.fin = take(Q * N * 4);
   L.cur = take(Q * N * 4);
   L.ckpt = take((size_t)m.n_ckpt * Q * N * 4);
-  L.seg = take((size_t)(m.K + 1) * Q * N * 4);
+  L.seg = take((size_t)2 * (m.K + 1) * Q * N * 4);  // two segment buffers (by parity)
   L.adj = take(Q * N * 4);
-  L.rcache = m.polar_cache ? take((size_t)(m.K + 1) * 9 * N * 8) : take(0);
+  L.rcache = m.polar_cache ? take((size_t)2 * (m.K + 1) * 9 * N * 8) : take(0);
   const size_t grid = S * (size_t)m.nnodes * sizeof(float4) * m.words;
   L.grids = take(grid * (m.pm_slots + kUBSlots));
   L.boxes = take((size_t)(m.pm_slots + kUBSlots) * 2 * S * 8 * 4);
@@ -263,7 +266,12 @@ struct mpm_handle {
     int n;
     std::vector<int> use;    // writes so far (box parity)
     std::vector<int> state;  // 0 free, 1 live, 2 pending clear, 3 clearing in this launch
-  } pm{0, kPMSlots, {}, {}}, ub{kPMSlots, kUBSlots, {}, {}};
+    std::vector<int> owner;  // stream (0 main, 1 side) that released it: it clears it
+    int sid = 0;             // stream of the passes being issued
+  } pm{0, kPMSlots, {}, {}, {}}, ub{kPMSlots, kUBSlots, {}, {}, {}};
+  cudaStream_t side_stream = nullptr;  // re-simulation overlapped with the adjoint passes
+  cudaEvent_t ev_fork = nullptr, ev_free = nullptr, ev_resim = nullptr, ev_join = nullptr;
+  bool overlap = true;  // MPM_OPT_OVERLAP_RESIM
   // live per-launch timing (MPM_OPT_PROFILE)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -278,8 +286,15 @@ struct mpm_handle {
   float* state(size_t base, int slot) const {
     return at<float>(base) + (size_t)slot * m.Q * m.N;
   }
-  double* rslot(int slot) const {
-    return m.polar_cache && use_polar_cache ? at<double>(L.rcache) + (size_t)slot * 9 * m.N : nullptr;
+  // state s0 + i of segment j (s0 = j K) in the segment buffer of j's parity
+  float* seg(int j, int i) const {
+    return at<float>(L.seg) + ((size_t)(j & 1) * (m.K + 1) + i) * m.Q * m.N;
+  }
+  // the cached FP64 polar factor of that state (3D fixed-corotated), or null
+  double* rslot(int j, int i) const {
+    return m.polar_cache && use_polar_cache
+               ? at<double>(L.rcache) + ((size_t)(j & 1) * (m.K + 1) + i) * 9 * m.N
+               : nullptr;
   }
 };
 
@@ -387,6 +402,8 @@ using Ring = mpm_handle::Ring;
 void ring_reset(Ring& r) {
   r.use.assign(r.n, 0);
   r.state.assign(r.n, 0);
+  r.owner.assign(r.n, 0);
+  r.sid = 0;
 }
 
 float4* ring_grid(const mpm_handle* h, const Ring& r, int id) {
@@ -405,8 +422,10 @@ struct WriteSlot {
   int* box_reset = nullptr;
 };
 
-bool ring_alloc(mpm_handle* h, Ring& r, WriteSlot& w) {
-  for (int i = 0; i < r.n; ++i)
+// a free buffer among [lo, hi) (hi < 0: the whole ring)
+bool ring_alloc(mpm_handle* h, Ring& r, WriteSlot& w, int lo = 0, int hi = -1) {
+  if (hi < 0 || hi > r.n) hi = r.n;
+  for (int i = lo; i < hi; ++i)
     if (r.state[i] == 0) {
       r.state[i] = 1;
       w.id = i;
@@ -418,18 +437,23 @@ bool ring_alloc(mpm_handle* h, Ring& r, WriteSlot& w) {
   return false;
 }
 
+// the buffer's last reader has been issued: it is cleared by a later launch on the same
+// stream (the stream that issued the release)
 void ring_release(Ring& r, int id) {
-  if (id >= 0 && r.state[id] == 1) r.state[id] = 2;
+  if (id >= 0 && r.state[id] == 1) {
+    r.state[id] = 2;
+    r.owner[id] = r.sid;
+  }
 }
 
-// Hand up to kMaxClears pending buffers to the next launch.
+// Hand up to kMaxClears pending buffers released on the issuing stream to the next launch.
 Clears take_clears(mpm_handle* h) {
   Clears C;
   memset(&C, 0, sizeof(C));
   C.words = h->m.words;
   for (Ring* r : {&h->pm, &h->ub})
     for (int i = 0; i < r->n && C.n < kMaxClears; ++i)
-      if (r->state[i] == 2) {
+      if (r->state[i] == 2 && r->owner[i] == r->sid) {
         C.job[C.n].grid = ring_grid(h, *r, i);
         C.job[C.n].box = ring_box(h, *r, i, r->use[i]);
         ++C.n;
@@ -466,6 +490,42 @@ struct Launcher {
   int next = 0;        // passes issued so far (kPersistent)
   int run_kind = -1;   // kind of the pending run of passes
   int run_first = 0;   // its first pass
+  // two-stream backward (issue_backward_overlap): the stream passes go to, and the range
+  // of (m, p) grid buffers they allocate from
+  cudaStream_t main_s = nullptr;  // (the caller's stream may be the legacy default, null)
+  bool main_known = false;
+  int pm_lo = 0, pm_hi = -1;
+
+  // issue on the main (0) or the side (1) stream from now on
+  void use_stream(int sid) {
+    if (!main_known) {
+      main_s = s;
+      main_known = true;
+    }
+    s = sid ? h->side_stream : main_s;
+    h->pm.sid = h->ub.sid = sid;
+  }
+  void use_pool(int p) {
+    pm_lo = p * h->m.pm_pool;
+    pm_hi = pm_lo + h->m.pm_pool;
+  }
+  cudaError_t signal(cudaEvent_t ev) { return cudaEventRecord(ev, s); }
+  cudaError_t wait(cudaEvent_t ev) { return cudaStreamWaitEvent(s, ev, 0); }
+
+  // clear, on the current stream, every buffer released on it and not yet cleared
+  cudaError_t flush_clears() {
+    for (;;) {
+      Clears C = take_clears(h);
+      if (C.n == 0) return cudaSuccess;
+      ++count;
+      cudaError_t e = timed(MPM_KERNEL_GRID_CLEAR, [&] {
+        return h->m.D == 2 ? launch_clear<2>(C, (int)h->m.nnodes, h->m.n_grid, h->m.S, grid_blocks_per_scene(h), s)
+                           : launch_clear<3>(C, (int)h->m.nnodes, h->m.n_grid, h->m.S, grid_blocks_per_scene(h), s);
+      });
+      after_launch(h);
+      if (e != cudaSuccess) return e;
+    }
+  }
 
   // one pass: launched, recorded, or queued into the pending persistent run
   template <typename Args>
@@ -581,7 +641,7 @@ struct Launcher {
     A.Rw = R_out;
     if (written) {
       WriteSlot w;
-      if (!ring_alloc(h, h->pm, w)) return cudaErrorMemoryAllocation;
+      if (!ring_alloc(h, h->pm, w, pm_lo, pm_hi)) return cudaErrorMemoryAllocation;
       A.PMw = w.grid;
       A.box_w = w.box;
       A.box_reset = w.box_reset;
@@ -641,7 +701,7 @@ struct Launcher {
     }
     if (stm && pm_written) {
       WriteSlot w;
-      if (!ring_alloc(h, h->pm, w)) return cudaErrorMemoryAllocation;
+      if (!ring_alloc(h, h->pm, w, pm_lo, pm_hi)) return cudaErrorMemoryAllocation;
       A.PMm = w.grid;
       A.box_m = w.box;
       A.box_m_reset = w.box_reset;
@@ -693,13 +753,17 @@ struct Launcher {
     });
   }
 
-  // End of a launch sequence: zero every dirty buffer, reset every box.
+  // End of a launch sequence (on the main stream, after any side-stream work has been
+  // joined): zero every dirty buffer, reset every box.
   cudaError_t finish() {
     cudaError_t e = flush();
     if (e != cudaSuccess) return e;
     for (Ring* r : {&h->pm, &h->ub})
       for (int i = 0; i < r->n; ++i)
-        if (r->state[i] == 1) r->state[i] = 2;
+        if (r->state[i] == 1 || r->state[i] == 2) {
+          r->state[i] = 2;
+          r->owner[i] = r->sid;
+        }
     for (;;) {
       Clears C = take_clears(h);
       if (C.n == 0) break;
@@ -743,7 +807,7 @@ int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
   const float* src = h->state(h->L.ckpt, 0);
   float* cur = h->at<float>(h->L.cur);
   int g = -1;
-  LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g, sL == 0 ? h->rslot(0) : nullptr));
+  LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g, sL == 0 ? h->rslot(sL / K, 0) : nullptr));
   for (int t = 1; t < T; ++t) {
     float* dst;
     int mode;
@@ -751,14 +815,14 @@ int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
       dst = h->state(h->L.ckpt, t / K);
       mode = kG2PP2GFull;
     } else if (t > sL) {
-      dst = h->state(h->L.seg, t - sL);
+      dst = h->seg(sL / K, t - sL);
       mode = kG2PP2GFull;
     } else {
       dst = cur;
       mode = kG2PP2G;
     }
     int g_next = -1;
-    LK(Lc.step(mode, t, src, dst, g, &g_next, t >= sL ? h->rslot(t - sL) : nullptr));
+    LK(Lc.step(mode, t, src, dst, g, &g_next, t >= sL ? h->rslot(sL / K, t - sL) : nullptr));
     ring_release(h->pm, g);
     g = g_next;
     src = dst;
@@ -778,55 +842,78 @@ int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top, int* grid_top_minu
                 int* seg_grids) {
   const float* ck = h->state(h->L.ckpt, s0 / h->m.K);
   int g = -1;
-  LK(Lc.step(kP2GOnly, s0, ck, nullptr, -1, &g, h->rslot(0)));
+  LK(Lc.step(kP2GOnly, s0, ck, nullptr, -1, &g, h->rslot(s0 / h->m.K, 0)));
   const float* prev = ck;
   for (int t = s0 + 1; t < top; ++t) {
-    float* dst = h->state(h->L.seg, t - s0);
+    float* dst = h->seg(s0 / h->m.K, t - s0);
     int g_next = -1;
-    LK(Lc.step(kG2PP2GFull, t, prev, dst, g, &g_next, h->rslot(t - s0)));
+    LK(Lc.step(kG2PP2GFull, t, prev, dst, g, &g_next, h->rslot(s0 / h->m.K, t - s0)));
     if (seg_grids) seg_grids[t - 1 - s0] = g;
     else ring_release(h->pm, g);
     g = g_next;
     prev = dst;
   }
-  LK(Lc.step(kG2POnlyFull, top, prev, h->state(h->L.seg, top - s0), g, nullptr));
+  LK(Lc.step(kG2POnlyFull, top, prev, h->seg(s0 / h->m.K, top - s0), g, nullptr));
   if (seg_grids) seg_grids[top - 1 - s0] = g;
   *grid_top_minus_1 = g;
   return MPM_OK;
 }
 
-int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident) {
+// Backward.  With `overlap`, segment j-1 is re-simulated on the side stream while the
+// adjoint passes of segment j run on the main stream: the two are independent (the
+// re-simulation reads only checkpoint j-1) and latency-bound, so they share the SMs
+// better than they run one after the other.  Segments alternate between two segment
+// buffers, polar caches and (m, p) grid pools by parity.  Hand-offs: the side stream
+// starts re-simulating segment j-1 (parity of j+1) once the first adjoint pass of segment
+// j has released the last grid of segment j+1 and the main stream has cleared that pool
+// (ev_free); the adjoint passes of segment j-1 start after its re-simulation (ev_resim).
+// A buffer released on a stream is cleared by a later launch on the same stream.
+int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident, bool overlap) {
   const int K = h->m.K;
   ring_reset(h->pm);
   ring_reset(h->ub);
+  const bool kept = h->m.store_grids && !h->grid_recompute;
   // live grids: PM of steps s+1 and s, UB of step s+1
   int pm_s1 = -1, pm_s = -1, ub_s1 = -1;
-  std::vector<int> seg_grids(K, -1);
-  bool stored = false;  // this segment's grids were kept by its re-simulation
+  std::vector<int> seg_grids[2] = {std::vector<int>(K, -1), std::vector<int>(K, -1)};
+  int side_top[2] = {-1, -1};  // grid of step top-1 of a segment re-simulated on the side
+  bool stored = false;         // this segment's grids were kept by its re-simulation
+  if (overlap) {
+    LK(Lc.signal(h->ev_fork));
+    Lc.use_stream(1);
+    LK(Lc.wait(h->ev_fork));
+    Lc.use_stream(0);
+  }
   for (int s = T - 1; s >= 0; --s) {
-    const int j = s / K, s0 = j * K;
+    const int j = s / K, s0 = j * K, pj = j & 1;
     const int top = (s0 + K < T) ? s0 + K : T;
+    if (overlap) Lc.use_pool(pj);
     if (s == T - 1 && resident) {
       // the forward left this segment's states in place: only the grid of step T-1
-      const float* st = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
+      const float* st = (s == s0) ? h->state(h->L.ckpt, j) : h->seg(j, s - s0);
       LK(Lc.step(kP2GOnly, s, st, nullptr, -1, &pm_s));
       stored = false;
     } else if (s == top - 1) {
-      stored = h->m.store_grids && !h->grid_recompute;
-      int rc = issue_resim(h, Lc, s0, top, &pm_s, stored ? seg_grids.data() : nullptr);
-      if (rc) return rc;
+      stored = kept;
+      if (overlap && s != T - 1) {  // re-simulated on the side stream meanwhile
+        LK(Lc.wait(h->ev_resim));
+        pm_s = side_top[pj];
+      } else {
+        int rc = issue_resim(h, Lc, s0, top, &pm_s, stored ? seg_grids[pj].data() : nullptr);
+        if (rc) return rc;
+      }
     }
-    const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
-    const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->state(h->L.seg, s + 1 - s0);
+    const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->seg(j, s - s0);
+    const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->seg(j, s + 1 - s0);
     // the recomputed P2G of step s-1 runs only when this segment's grids were not kept
     const float* st_sm = (s - 1 >= s0 && !stored)
-                             ? ((s - 1 == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - 1 - s0))
+                             ? ((s - 1 == s0) ? h->state(h->L.ckpt, j) : h->seg(j, s - 1 - s0))
                              : nullptr;
     int ub_s = -1, pm_sm = -1;
     // cached polar factors: state s+1 only inside this segment (the segment's top state
     // was never the P2G input of this re-simulation), state s-1 always when present
-    const double* R1 = (s + 1 < top) ? h->rslot(s + 1 - s0) : nullptr;
-    const double* Rm = (s - 1 >= s0) ? h->rslot(s - 1 - s0) : nullptr;
+    const double* R1 = (s + 1 < top) ? h->rslot(j, s + 1 - s0) : nullptr;
+    const double* Rm = (s - 1 >= s0) ? h->rslot(j, s - 1 - s0) : nullptr;
     if (s == T - 1 && h->m.words == 2)  // deterministic: bound of the first ubar scatter
       LK(Lc.adjoint(kAdjG2P, s, st_s1, st_s, nullptr, -1, -1, pm_s, nullptr, nullptr, nullptr,
                     nullptr, 1));
@@ -838,12 +925,33 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident) {
     ub_s1 = ub_s;
     // the grid of step s-1: kept, recomputed by this pass, or (at a segment start) provided
     // by the next segment's re-simulation
-    pm_s = stored ? (s - 1 >= s0 ? seg_grids[s - 1 - s0] : -1) : pm_sm;
+    pm_s = stored ? (s - 1 >= s0 ? seg_grids[pj][s - 1 - s0] : -1) : pm_sm;
+    if (overlap && s == top - 1 && j >= 1) {
+      // segment j+1's last grid is released: clear its pool, then re-simulate segment j-1
+      // into that pool and segment buffer on the side stream
+      LK(Lc.flush_clears());
+      LK(Lc.signal(h->ev_free));
+      Lc.use_stream(1);
+      Lc.use_pool(1 - pj);
+      LK(Lc.wait(h->ev_free));
+      int rc = issue_resim(h, Lc, s0 - K, s0, &side_top[1 - pj], kept ? seg_grids[1 - pj].data() : nullptr);
+      if (rc) return rc;
+      LK(Lc.flush_clears());
+      LK(Lc.signal(h->ev_resim));
+      Lc.use_stream(0);
+      Lc.use_pool(pj);
+    }
   }
   const float* st0 = h->state(h->L.ckpt, 0);
   LK(Lc.adjoint(kAdjP2G, -1, st0, st0, nullptr, pm_s1, ub_s1, -1, nullptr, nullptr));
   ring_release(h->pm, pm_s1);
   ring_release(h->ub, ub_s1);
+  if (overlap) {  // join (the side stream's last work is already waited for)
+    Lc.use_stream(1);
+    LK(Lc.signal(h->ev_join));
+    Lc.use_stream(0);
+    LK(Lc.wait(h->ev_join));
+  }
   LK(Lc.finish());
   return MPM_OK;
 }
@@ -863,13 +971,13 @@ int issue_forward_ctrl(mpm_handle* h, Launcher& Lc, int T) {
   float* cur = h->at<float>(h->L.cur);
   int g = -1;
   LK(Lc.ctrl_forward(0, src));
-  LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g, sL == 0 ? h->rslot(0) : nullptr));
+  LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g, sL == 0 ? h->rslot(sL / K, 0) : nullptr));
   for (int t = 1; t < T; ++t) {
-    float* dst = (t % K == 0) ? h->state(h->L.ckpt, t / K) : (t > sL) ? h->state(h->L.seg, t - sL) : cur;
+    float* dst = (t % K == 0) ? h->state(h->L.ckpt, t / K) : (t > sL) ? h->seg(sL / K, t - sL) : cur;
     LK(Lc.step(kG2POnlyFull, t, src, dst, g, nullptr));
     ring_release(h->pm, g);
     LK(Lc.ctrl_forward(t, dst));
-    LK(Lc.step(kP2GOnly, t, dst, nullptr, -1, &g, t >= sL ? h->rslot(t - sL) : nullptr));
+    LK(Lc.step(kP2GOnly, t, dst, nullptr, -1, &g, t >= sL ? h->rslot(sL / K, t - sL) : nullptr));
     src = dst;
   }
   LK(Lc.step(kG2POnlyFull, T, src, h->at<float>(h->L.fin), g, nullptr));
@@ -894,9 +1002,9 @@ int issue_backward_ctrl(mpm_handle* h, Launcher& Lc, int T, bool resident) {
   for (int s = T - 1; s >= 0; --s) {
     const int j = s / K, s0 = j * K;
     const int top = (s0 + K < T) ? s0 + K : T;
-    const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->state(h->L.seg, s - s0);
-    const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->state(h->L.seg, s + 1 - s0);
-    const double* R1 = (s + 1 < top) ? h->rslot(s + 1 - s0) : nullptr;
+    const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->seg(j, s - s0);
+    const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->seg(j, s + 1 - s0);
+    const double* R1 = (s + 1 < top) ? h->rslot(j, s + 1 - s0) : nullptr;
     if (s == T - 1 && resident) {
       LK(Lc.step(kP2GOnly, s, st_s, nullptr, -1, &pm_s));
       stored = false;
@@ -1057,6 +1165,15 @@ int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_byt
   h->ws = static_cast<char*>(workspace);
   h->pm.n = m.pm_slots;
   h->ub.first = m.pm_slots;
+  {
+    cudaError_t es = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&h->ev_fork, &h->ev_free, &h->ev_resim, &h->ev_join})
+      if (es == cudaSuccess) es = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (es != cudaSuccess) {
+      mpm_destroy(h);
+      return fail(nullptr, MPM_ERR_CUDA, std::string("mpm_create: ") + cudaGetErrorString(es));
+    }
+  }
   h->ws_bytes = workspace_bytes;
   // tile table and scene offsets (host -> device once)
   std::vector<int4> tiles;
@@ -1229,9 +1346,15 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   h->launches += 4;
   const int T = h->T_recorded;
   const bool resident = h->resident_T == T;
-  const int64_t key = (int64_t)T * 2 + 1 + (resident ? 0 : ((int64_t)1 << 40));
+  // the re-simulation overlaps the adjoint passes when there is a segment to re-simulate,
+  // except in the persistent form (one stream of plan passes) and while profiling (each
+  // launch timed alone)
+  const bool overlap = h->overlap && !h->persistent && !h->profile && !ctrl &&
+                       last_segment_start(h, T) > 0;
+  const int64_t key = (int64_t)T * 2 + 1 + (resident ? 0 : ((int64_t)1 << 40)) +
+                      (overlap ? ((int64_t)1 << 41) : 0);
   int rc = run_sequence(h, key, s, [&](Launcher& Lc) {
-    return ctrl ? issue_backward_ctrl(h, Lc, T, resident) : issue_backward(h, Lc, T, resident);
+    return ctrl ? issue_backward_ctrl(h, Lc, T, resident) : issue_backward(h, Lc, T, resident, overlap);
   });
   if (rc) return rc;
   // re-simulating the earlier segments reused the segment buffer: a later backward of
@@ -1301,6 +1424,7 @@ int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
     case MPM_OPT_POLAR_CACHE: h->use_polar_cache = value != 0; break;
     case MPM_OPT_GRID_RECOMPUTE: h->grid_recompute = value != 0; break;
     case MPM_OPT_PERSISTENT: h->persistent = value != 0; break;
+    case MPM_OPT_OVERLAP_RESIM: h->overlap = value != 0; break;
     case MPM_OPT_PERSISTENT_CHUNK:
       if (value < 0 || value > (1 << 30)) return fail(h, MPM_ERR_ARG, "persistent chunk must be >= 0");
       h->persistent_chunk = (int)value;
@@ -1366,6 +1490,12 @@ void mpm_destroy(mpm_handle* h) {
   if (!h) return;
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) {
+    cudaStreamSynchronize(h->side_stream);  // normally idle: its work is joined into the main stream
+    cudaStreamDestroy(h->side_stream);
+  }
+  for (cudaEvent_t ev : {h->ev_fork, h->ev_free, h->ev_resim, h->ev_join})
+    if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
 }
