@@ -845,8 +845,16 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
   if (err) atomicOr(A.err, err);
 }
 
+// resident CTAs per SM the forward passes are compiled for
+template <int D, int MAT>
+constexpr int step_ctas_per_sm() {
+  return D == 2 ? MPM_STEP_CTAS_PER_SM_2D
+                : (MAT == kFixedCorotated || MAT == kMixed) ? MPM_STEP_CTAS_PER_SM_3D_POLAR
+                                                           : MPM_STEP_CTAS_PER_SM_3D;
+}
+
 template <int D, int MAT, int MODE, bool DET>
-__global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D)
+__global__ void __launch_bounds__(kTile, step_ctas_per_sm<D, MAT>())
     step_kernel(const __grid_constant__ SimParams P, const __grid_constant__ StepArgs A) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8 * kBoxSlots];
@@ -1395,7 +1403,7 @@ __device__ __forceinline__ int next_tile(const PersistCtl& c, int i, int* s_tile
 
 // Forward-kind passes plan[0..n_pass), tiles handed out by tickets.
 template <int D, int MAT, bool DET>
-__global__ void __launch_bounds__(kTile, D == 3 ? MPM_STEP_CTAS_PER_SM_3D : MPM_STEP_CTAS_PER_SM_2D)
+__global__ void __launch_bounds__(kTile, step_ctas_per_sm<D, MAT>())
     step_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8 * kBoxSlots];
