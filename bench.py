@@ -128,16 +128,17 @@ def pass_bytes_ctrl(N, T, K, dim=3, kept=True):
 
 
 def source_digest():
-    """Digest of the CUDA sources and the C header: a DRAM-traffic figure read from a
-    profile summary counts only if the summary was taken on these exact sources."""
+    """Digest of the particle-pass kernels' sources (mpm_kernels.cuh, mpm_common.cuh,
+    kernels_launch.cuh, kernels_*.cu): a DRAM-traffic figure read from a profile summary
+    counts only if the summary was taken on these exact kernels."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_00935_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f in ("mpm_kernels.cuh", "mpm_common.cuh", "kernels_launch.cuh") or \
+                (f.startswith("kernels_") and f.endswith(".cu")):
             h.update(f.encode())
             h.update(open(os.path.join(csrc, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "mpm.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
