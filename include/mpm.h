@@ -139,6 +139,7 @@ extern "C" {
                                           adjoint passes (see MPM_OPT_GRID_RECOMPUTE) */
 #define MPM_INFO_ACT_PARAMS 5      /* actuation parameters per scene: n_groups * n_basis, or
                                       the controller's theta when ctrl_hidden > 0 */
+#define MPM_INFO_CKPT_EVERY 6      /* the checkpoint interval k in use */
 
 typedef struct mpm_handle mpm_handle;
 
@@ -154,7 +155,10 @@ typedef struct mpm_scene_desc {
   int32_t wall_cells;          /* sticky walls: node i with any i_k < wall or i_k >= n-wall gets v = 0 */
   int32_t material;            /* MPM_FIXED_COROTATED, MPM_NEO_HOOKEAN, MPM_LIQUID or MPM_MIXED */
   float rho;                   /* density; particle volume (dx/2)^dim, mass rho*volume */
-  int32_t ckpt_every;          /* k: full state stored every k steps (Appendix D.2), >= 1 */
+  int32_t ckpt_every;          /* k: full state stored every k steps (Appendix D.2), >= 1; 0:
+                                  ceil(sqrt(max_steps)), the interval that minimises the stored
+                                  states (T/k checkpoints + k segment states, Appendix D's
+                                  O(sqrt(T)) memory) */
   int32_t n_groups;            /* actuator groups, 0..8 (0 = no actuation) */
   int32_t n_basis;             /* sine terms per group, 0..8 */
   float act_period;            /* P of sin(2 pi k t / P + phase), t = step index */

@@ -3,8 +3,11 @@
 The knobs are the library's runtime options: the capacity of the shared gather box
 (MPM_OPT_GATHER_CAPACITY), the scatter path (MPM_OPT_SMEM_TILE: shared node box vs. float4
 reductions straight to the grid), the shared box capacity (MPM_OPT_TILE_CAPACITY), the
-CTA count of the end-of-sequence grid clear (MPM_OPT_GRID_BLOCKS) and the launch form
-(MPM_OPT_PERSISTENT: one launch per pass, or persistent launches over the pass plan).  `tune` times a short forward+backward
+CTA count of the end-of-sequence grid clear (MPM_OPT_GRID_BLOCKS), the launch form
+(MPM_OPT_PERSISTENT: one launch per pass, or persistent launches over the pass plan), and two
+memory-vs-recompute choices of the backward: a re-simulated segment's grids kept or recomputed
+per step (MPM_OPT_GRID_RECOMPUTE) and the re-simulation overlapped with the adjoint passes on a
+second stream or run before them (MPM_OPT_OVERLAP_RESIM).  `tune` times a short forward+backward
 of the caller's own simulator for each candidate, one knob at a time (coordinate descent
 from the defaults), keeps the fastest, and caches the result in a JSON file keyed by the
 workload's shape class and the device name.  Results never change numerics beyond FP32
@@ -22,12 +25,14 @@ SPACE = {
     "tile_capacity": [1024, 2048],
     "grid_blocks": [0, 32, 64, 128],
     "persistent": [0, 1],
+    "grid_recompute": [0, 1],
+    "overlap_resim": [1, 0],
 }
 DEFAULTS = {"gather_capacity": 512, "smem_tile": 0, "tile_capacity": 1024, "grid_blocks": 0,
-            "persistent": 0}
+            "persistent": 0, "grid_recompute": 0, "overlap_resim": 1}
 
 _OPTION_IDS = {"gather_capacity": 5, "smem_tile": 2, "tile_capacity": 3, "grid_blocks": 6,
-               "persistent": 8}
+               "persistent": 8, "grid_recompute": 12, "overlap_resim": 13}
 
 
 def default_cache_path() -> str:

@@ -39,7 +39,9 @@ __device__ __forceinline__ double warp_tile_sum(const double* a, int t0, int t1,
 // part[tile][slot][value] (FP64), value = x_0..x_{d-1}, v_0..v_{d-1}, count.
 __global__ void ctrl_sense_kernel(int dim, int G, int64_t N, const int4* tiles, const float* st,
                                   const int* group, double* part) {
-  __shared__ double vals[kSenseVals][kSenseThreads];
+  // rows padded by one: the threads summing different values of the same particle then
+  // read different banks
+  __shared__ double vals[kSenseVals][kSenseThreads + 1];
   __shared__ int slot[kSenseThreads];
   const int4 tile = tiles[blockIdx.x];
   const int i = threadIdx.x;

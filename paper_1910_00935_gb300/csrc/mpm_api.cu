@@ -113,7 +113,7 @@ bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
       d->material != MPM_LIQUID && d->material != MPM_MIXED)
     return fail("unknown material");
   if (!(d->rho > 0.0f)) return fail("rho must be > 0");
-  if (d->ckpt_every < 1) return fail("ckpt_every must be >= 1");
+  if (d->ckpt_every < 0) return fail("ckpt_every must be >= 0 (0: ceil(sqrt(max_steps)))");
   if (d->n_groups < 0 || d->n_groups > kMaxGroups) return fail("n_groups must be in [0, 8]");
   if (d->n_basis < 0 || d->n_basis > kMaxBasis) return fail("n_basis must be in [0, 8]");
   if (d->ctrl_hidden < 0 || d->ctrl_hidden > kCtrlMaxHidden)
@@ -136,7 +136,11 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
   m.D = d->dim;
   m.Q = 2 * m.D + 2 * m.D * m.D;
   m.S = d->n_scenes;
-  m.K = d->ckpt_every < max_steps ? d->ckpt_every : max_steps;
+  // 0: the interval that minimises the stored states, T/k checkpoints + k segment states
+  // (Appendix D's O(sqrt(T)) memory)
+  int k = d->ckpt_every;
+  if (k == 0) k = (int)std::ceil(std::sqrt((double)max_steps));
+  m.K = k < max_steps ? k : max_steps;
   m.n_ckpt = (max_steps - 1) / m.K + 1;  // states 0, K, 2K, ... < max_steps
   m.n_grid = d->n_grid;
   m.polar_cache = d->dim == 3 && (d->material == MPM_FIXED_COROTATED || d->material == MPM_MIXED);
@@ -1459,6 +1463,7 @@ int mpm_get_info(mpm_handle* h, int32_t key, int64_t* value) {
     case MPM_INFO_STEPS_RECORDED: *value = h->T_recorded; return MPM_OK;
     case MPM_INFO_KEEPS_SEGMENT_GRIDS: *value = h->m.store_grids && !h->grid_recompute; return MPM_OK;
     case MPM_INFO_ACT_PARAMS: *value = h->m.n_act; return MPM_OK;
+    case MPM_INFO_CKPT_EVERY: *value = h->m.K; return MPM_OK;
   }
   return fail(h, MPM_ERR_ARG, "unknown info key");
 }

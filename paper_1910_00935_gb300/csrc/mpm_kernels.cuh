@@ -908,10 +908,12 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
   }
   stage_commit();
 
-  // adjoint of state s+1: xb, vb, Cb, Fb (Fb = dL/dE = dL/dF); C1 = C of state s+1.  After
-  // a P2G-adjoint the carried xb, Fb and the rows of state s+1 needed again (C, E, mu, la)
-  // are read after its gather -- fresh loads, as the gather's barriers order them -- so
-  // that none of them holds a register across the gather
+  // adjoint of state s+1: xb, vb, Cb, Fb (Fb = dL/dE = dL/dF); C1 = C of state s+1.  In 3D,
+  // after a P2G-adjoint the carried xb, Fb and the rows of state s+1 needed again (C, E,
+  // mu, la, the polar factor) are read after its gather -- fresh loads, as the gather's
+  // barriers order them -- so that none of them holds a register across the gather (in 2D
+  // they fit: loaded once, before it)
+  constexpr bool kLate = D == 3;
   float xb[D], vb[D], Cb[D][D], Fb[D][D];
   float C1[D][D];
   auto load_carried = [&]() {
@@ -926,8 +928,8 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
       }
   };
 
+  if (MODE == kAdjG2P || !kLate) load_carried();
   if (MODE == kAdjG2P) {
-    load_carried();
 #pragma unroll
     for (int a = 0; a < D; ++a) vb[a] = A.adj[(R::V + a) * N + p];
 #pragma unroll
@@ -960,7 +962,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
       mv[i] = P.p_mass * v[i];
 #pragma unroll
       for (int j = 0; j < D; ++j)
-        Am[i][j] = P.kappa * tau[i][j] + P.p_mass * A.st1[(R::C + i * D + j) * N + p];
+        Am[i][j] = P.kappa * tau[i][j] + P.p_mass * (kLate ? A.st1[(R::C + i * D + j) * N + p] : C1[i][j]);
     }
     float Ab[D][D], xg[D], sw[D];
 #pragma unroll
@@ -1033,7 +1035,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
         }
       }
     });
-    load_carried();
+    if (kLate) load_carried();
     // x += inv_dx sum Wbar gradW - A^T sum W dpbar
 #pragma unroll
     for (int b = 0; b < D; ++b) {
@@ -1052,8 +1054,8 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
         tb[i][j] = P.kappa * Ab[i][j];
       }
     float mub = 0.0f, lab = 0.0f, abar = 0.0f;
-    load_E<D>(A.st1, N, p, P.f_diag, E);
-    if (MAT == kFixedCorotated || MAT == kMixed) {
+    if (kLate) load_E<D>(A.st1, N, p, P.f_diag, E);
+    if (kLate && (MAT == kFixedCorotated || MAT == kMixed)) {
       // the polar factor again (from the cache, or recomputed where the state has no cached
       // factor: one adjoint pass per segment), so that it holds no registers across the
       // gather; the stress itself is not needed again

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -53,7 +54,7 @@ def test_host_side_validation_without_gpu(libpath):
     b1 = mpm.mpm_workspace_bytes(d, 64)
     b2 = mpm.mpm_workspace_bytes(d, 256)
     assert b2 > b1 > 0
-    for bad in (dict(dim=4), dict(n_grid=4), dict(dt=0.0), dict(ckpt_every=0),
+    for bad in (dict(dim=4), dict(n_grid=4), dict(dt=0.0), dict(ckpt_every=-1),
                 dict(n_particles=[0]), dict(wall_cells=40), dict(material=7),
                 dict(n_groups=9), dict(n_groups=2, n_basis=0), dict(deterministic_p2g=2)):
         with pytest.raises(mpm.MPMError) as e:
@@ -66,6 +67,12 @@ def test_host_side_validation_without_gpu(libpath):
     bd = mpm.mpm_workspace_bytes(mpm.make_desc({**good, "deterministic_p2g": 1}), 64)
     grids = 10 * 2 * 64 ** 3 * 16  # ten (m, p) and ubar buffers, two scenes, float4 nodes
     assert bd - b1 >= grids
+    # ckpt_every = 0: the interval that minimises the stored states, ceil(sqrt(max_steps))
+    # (T/k checkpoints + k segment states); its workspace matches an explicit k of that size
+    for T_max in (64, 1000, 1024):
+        k = int(np.ceil(np.sqrt(T_max)))
+        assert (mpm.mpm_workspace_bytes(mpm.make_desc({**good, "ckpt_every": 0}), T_max)
+                == mpm.mpm_workspace_bytes(mpm.make_desc({**good, "ckpt_every": k}), T_max))
     # the closed-loop controller: limits, and its per-step tables in the workspace
     ctrl = dict(good, n_groups=8, n_basis=4, ctrl_hidden=32, ctrl_scale=50.0)
     for bad in (dict(ctrl_hidden=65), dict(ctrl_hidden=-1), dict(n_groups=0),

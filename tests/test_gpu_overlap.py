@@ -69,3 +69,18 @@ def test_overlap_backward_twice_and_oracle(mpm):
     # resident): FP32 atomics in a different order, so agreement to rounding, not bitwise
     for key in KEYS:
         assert rel_l2(g2[key], g1[key]) <= 1e-4, key
+
+
+def test_automatic_checkpoint_interval(mpm):
+    """ckpt_every = 0 takes k = ceil(sqrt(max_steps)) (T/k checkpoints + k segment states,
+    Appendix D's O(sqrt(T)) memory); the gradients still meet the oracle bars."""
+    scene = scenes.make("robots3d", n_scenes=2, dims=(12, 8, 8))
+    scene["desc"]["ckpt_every"] = 0
+    T = 40
+    sim = mpm.from_scene(scene, max_steps=T)
+    assert sim.info(mpm.MPM_INFO_CKPT_EVERY) == 7
+    sim.close()
+    seeds = _random_seeds(scene, np.random.default_rng(53))
+    g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    o = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
+    _compare_grads(g["grad"], o, KEYS + ["gw"])
