@@ -9,10 +9,10 @@
 //   h = tanh(W1 u + b1) (H units), a_g = scale tanh(W2 h + b2)_g
 //   theta per scene = [W1 (H x n_in, row-major) | b1 (H) | W2 (G x H, row-major) | b2 (G)]
 //
-// Weights arrive in FP32; sensor sums and the MLP run in FP64 (a few thousand operations
-// per scene and step).  Every sum runs in a fixed order (a tile's particles in order, a
-// scene's tiles in order), so the controller adds nothing order-dependent to a
-// deterministic run.
+// Weights arrive in FP32; a tile's sensor sums are FP32, the sums over tiles and the MLP FP64
+// (a few thousand operations per scene and step).  Every sum runs in a fixed order (a
+// tile's particles in order, a scene's tiles in order), so the controller adds nothing
+// order-dependent to a deterministic run.
 #include "mpm_internal.h"
 
 namespace mpm {
@@ -21,27 +21,59 @@ namespace {
 
 constexpr int kSenseThreads = kTile;  // one CTA per particle tile
 static_assert(kTile <= 512, "the sensing CTA stages a tile's values in static shared memory");
-constexpr int kCtrlThreads = 128;     // one CTA per scene for the MLP passes
+constexpr int kCtrlThreads = 1024;    // one CTA per scene for the MLP passes
 constexpr int kSenseVals = 7;       // x (d), v (d), count: at most 7
 constexpr int kSenseSlots = kMaxGroups + 1;  // slot 0: particles in no group
 
-// sum over t in [t0, t1) of a[t * stride + j], for one warp: lanes stride over t, then a
-// butterfly; the order depends only on (t0, t1), so the result is reproducible
-__device__ __forceinline__ double warp_tile_sum(const double* a, int t0, int t1, int stride, int j) {
+// out[j] = sum over t in [t0, t1) of a[t * stride + j] for j < nv, by the whole CTA: thread
+// (j, r) sums rows t0 + r, t0 + r + R, ... (R = blockDim / nv) with four independent
+// accumulators (loads in flight together), then each out[j] adds its R partials in order.
+// The order depends only on (t0, t1), so the sums are reproducible.  clear: zero every
+// element read (the per-tile actuation adjoints are consumed).  scratch: blockDim doubles;
+// out: shared, nv doubles.  Ends with a barrier.
+template <typename T>
+__device__ void block_tile_sums(T* a, int t0, int t1, int stride, int nv, bool clear,
+                                double* scratch, double* out) {
+  const int R = blockDim.x / nv;
+  const int j = threadIdx.x % nv, r = threadIdx.x / nv;
   double acc = 0.0;
-  for (int t = t0 + (int)(threadIdx.x & 31); t < t1; t += 32) acc += a[(int64_t)t * stride + j];
+  if (r < R) {
+    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    int t = t0 + r;
+    for (; t + 3 * R < t1; t += 4 * R) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  return acc;
+      for (int u = 0; u < 4; ++u) {
+        T* e = a + (int64_t)(t + u * R) * stride + j;
+        q[u] += (double)*e;
+        if (clear) *e = T(0);
+      }
+    }
+    for (; t < t1; t += R) {
+      T* e = a + (int64_t)t * stride + j;
+      q[0] += (double)*e;
+      if (clear) *e = T(0);
+    }
+    acc = (q[0] + q[1]) + (q[2] + q[3]);
+  }
+  scratch[threadIdx.x] = acc;
+  __syncthreads();
+  if ((int)threadIdx.x < nv) {
+    double v = 0.0;
+    for (int k = 0; k < R; ++k) v += scratch[k * nv + threadIdx.x];
+    out[threadIdx.x] = v;
+  }
+  __syncthreads();
 }
 
 // Per-tile sums of x, v and the particle count by group slot, in particle order:
-// part[tile][slot][value] (FP64), value = x_0..x_{d-1}, v_0..v_{d-1}, count.
+// part[tile][slot][value], value = x_0..x_{d-1}, v_0..v_{d-1}, count.  A tile's at most 128
+// terms are summed in FP32 (FP64 adds run at 1/64 of the FP32 rate and made this the
+// controller's slowest step); the sums over a scene's tiles are FP64.
 __global__ void ctrl_sense_kernel(int dim, int G, int64_t N, const int4* tiles, const float* st,
                                   const int* group, double* part) {
   // rows padded by one: the threads summing different values of the same particle then
   // read different banks
-  __shared__ double vals[kSenseVals][kSenseThreads + 1];
+  __shared__ float vals[kSenseVals][kSenseThreads + 1];
   __shared__ int slot[kSenseThreads];
   const int4 tile = tiles[blockIdx.x];
   const int i = threadIdx.x;
@@ -51,25 +83,25 @@ __global__ void ctrl_sense_kernel(int dim, int G, int64_t N, const int4* tiles, 
     const int g = group[p];
     slot[i] = (g >= 0 && g < G) ? g + 1 : 0;
     for (int a = 0; a < dim; ++a) {
-      vals[a][i] = (double)st[(int64_t)a * N + p];
-      vals[dim + a][i] = (double)st[(int64_t)(dim + a) * N + p];
+      vals[a][i] = st[(int64_t)a * N + p];
+      vals[dim + a][i] = st[(int64_t)(dim + a) * N + p];
     }
-    vals[2 * dim][i] = 1.0;
+    vals[2 * dim][i] = 1.0f;
   }
   __syncthreads();
   for (int j = i; j < ns * nv; j += blockDim.x) {
     const int sl = j / nv, c = j % nv;
-    double acc = 0.0;
+    float acc = 0.0f;
     for (int q = 0; q < tile.z; ++q)
       if (slot[q] == sl) acc += vals[c][q];
-    part[(int64_t)blockIdx.x * ns * nv + j] = acc;
+    part[(int64_t)blockIdx.x * ns * nv + j] = (double)acc;
   }
 }
 
 // One CTA per scene: reduce the scene's tile sums in order, form the inputs, run the MLP
 // and store u, h, y = tanh(W2 h + b2) (kept for the reverse pass), the actuation
 // a = scale y, and the group sizes.
-__global__ void ctrl_forward_kernel(CtrlStep cs, const int* tile_off, const double* part,
+__global__ void __launch_bounds__(kCtrlThreads) ctrl_forward_kernel(CtrlStep cs, const int* tile_off, const double* part,
                                     const float* theta, double* u_out, double* h_out,
                                     double* y_out, float* act_out, double* cnt_out) {
   __shared__ double sums[kSenseSlots * kSenseVals];
@@ -81,12 +113,9 @@ __global__ void ctrl_forward_kernel(CtrlStep cs, const int* tile_off, const doub
   const int n_in = K + 2 * dim * G;
   const int n_par = H * n_in + H + G * H + G;
   const float* th = theta + (int64_t)s * n_par;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-  for (int j = warp; j < ns * nv; j += n_warps) {
-    const double acc = warp_tile_sum(part, tile_off[s], tile_off[s + 1], ns * nv, j);
-    if (lane == 0) sums[j] = acc;
-  }
-  __syncthreads();
+  __shared__ double scratch[kCtrlThreads];
+  block_tile_sums(const_cast<double*>(part), tile_off[s], tile_off[s + 1], ns * nv, ns * nv, false,
+                  scratch, sums);
   // inputs: the time basis, then per group (centre offset, mean velocity)
   for (int i = threadIdx.x; i < n_in; i += blockDim.x) {
     double val;
@@ -138,7 +167,7 @@ __global__ void ctrl_forward_kernel(CtrlStep cs, const int* tile_off, const doub
 // actuation adjoints summed in tile order (and the tile slots cleared for the next step);
 // dL/dtheta accumulates in FP64 (thbar); the sensor adjoint becomes per-slot additions to
 // the state adjoint: add[scene][slot][0..d) to xbar, [d..2d) to vbar.
-__global__ void ctrl_backward_kernel(CtrlStep cs, const int* tile_off, float* abar_tile,
+__global__ void __launch_bounds__(kCtrlThreads) ctrl_backward_kernel(CtrlStep cs, const int* tile_off, float* abar_tile,
                                      const float* theta, const double* u_in, const double* h_in,
                                      const double* y_in, const double* cnt, double* thbar,
                                      float* add) {
@@ -160,22 +189,16 @@ __global__ void ctrl_backward_kernel(CtrlStep cs, const int* tile_off, float* ab
   double* b2b = W2b + G * H;
   const double* u = u_in + (int64_t)s * n_in;
   const double* h = h_in + (int64_t)s * H;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-  for (int g = warp; g < G; g += n_warps) {
-    // the scene's per-tile actuation adjoints, read and cleared for the next step
-    double ab = 0.0;
-    for (int t = tile_off[s] + lane; t < tile_off[s + 1]; t += 32) {
-      ab += (double)abar_tile[(int64_t)t * G + g];
-      abar_tile[(int64_t)t * G + g] = 0.0f;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, o);
-    if (lane == 0) {
-      const double y = y_in[(int64_t)s * G + g];
-      const double zb = ab * (double)cs.scale * (1.0 - y * y);
-      z2b[g] = zb;
-      b2b[g] += zb;
-    }
+  // the scene's per-tile actuation adjoints, summed and cleared for the next step
+  __shared__ double scratch[kCtrlThreads];
+  __shared__ double abar[kMaxGroups];
+  block_tile_sums(abar_tile, tile_off[s], tile_off[s + 1], G, G, true, scratch, abar);
+  if ((int)threadIdx.x < G) {
+    const int g = threadIdx.x;
+    const double y = y_in[(int64_t)s * G + g];
+    const double zb = abar[g] * (double)cs.scale * (1.0 - y * y);
+    z2b[g] = zb;
+    b2b[g] += zb;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < H; j += blockDim.x) {
