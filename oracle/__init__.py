@@ -112,6 +112,9 @@ def lib():
                                          d, d, d, d, d, d, d, d, d, d, d]),
                 "orc_grad": (I, [P, I64, I, d, d, i32, d, d, d, d, d, d]),
                 "orc_com_loss": (I, [I, I64, I, d, d, d, d, d, d]),
+                "orc_ms_forward": (I, [I, I, I, i32, i32, d, D, D, D, D, I, d, d]),
+                "orc_ms_backward": (I, [I, I, I, i32, i32, d, D, D, D, D, I, d, d, d, d]),
+                "orc_ms_area_loss": (I, [I, d, D, d, d]),
                 "orc_ctrl_n_inputs": (I, [P]),
                 "orc_ctrl_n_params": (I64, [P]),
                 "orc_controller": (I, [P, d, I64, I, d, d, i32, d, d]),
@@ -474,3 +477,49 @@ def loss_and_grad(scene, T):
         del states
     return dict(loss=float(sum(losses)), losses=losses, finals=finals, gE=gE, gnu=gnu, gw=gw,
                 **g)
+
+
+# ----------------------------------------------------------------------------
+# mass-spring system (Section 2's example, Section 3's tape demonstration)
+# ----------------------------------------------------------------------------
+
+def ms_forward(x0, v0, springs, l0, k, alpha, dt, m, steps):
+    """States 0..steps-1 of one system: (x, v) each [steps, n, dim].  springs: (a, b) pairs."""
+    x0, v0 = _f64(x0), _f64(v0)
+    n, dim = x0.shape
+    sp = np.ascontiguousarray(springs, dtype=np.int32).reshape(-1, 2)
+    sa, sb = np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(sp[:, 1])
+    x = np.zeros((steps, n, dim))
+    v = np.zeros((steps, n, dim))
+    x[0], v[0] = x0, v0
+    _check(lib().orc_ms_forward(dim, n, len(sa), _i(sa), _i(sb), _d(_f64(l0)), float(k),
+                                float(alpha), float(dt), float(m), int(steps), _d(x), _d(v)),
+           "ms_forward")
+    return x, v
+
+
+def ms_backward(x, springs, l0, k, alpha, dt, m, xb_T, vb_T):
+    """Reverse of ms_forward over the recorded positions x [steps, n, dim]: returns
+    (dL/dx0, dL/dv0, dL/dl0) given dL/dx, dL/dv of the last state."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    steps, n, dim = x.shape
+    sp = np.ascontiguousarray(springs, dtype=np.int32).reshape(-1, 2)
+    sa, sb = np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(sp[:, 1])
+    xb = _f64(xb_T).copy()
+    vb = _f64(vb_T).copy()
+    l0b = np.zeros(len(sa))
+    _check(lib().orc_ms_backward(dim, n, len(sa), _i(sa), _i(sb), _d(_f64(l0)), float(k),
+                                 float(alpha), float(dt), float(m), int(steps), _d(x), _d(xb),
+                                 _d(vb), _d(l0b)), "ms_backward")
+    return xb, vb, l0b
+
+
+def ms_area_loss(x, target=0.2):
+    """(L, dL/dx) of the example's triangle-area loss on masses 0, 1, 2 (dim 2)."""
+    x = _f64(x)
+    loss = ctypes.c_double()
+    xb = np.zeros_like(x)
+    _check(lib().orc_ms_area_loss(x.shape[0], _d(x), float(target),
+                                  ctypes.cast(ctypes.byref(loss), ctypes.POINTER(ctypes.c_double)),
+                                  _d(xb)), "ms_area_loss")
+    return loss.value, xb

@@ -1275,3 +1275,114 @@ int orc_com_loss(int dim, int64_t np, int kind, const double* xT, const double* 
   }
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* mass-spring system (the paper's introductory example, Section 2 and */
+/* the tape demonstration of Section 3): Hooke's springs, semi-        */
+/* implicit Euler with damping, and its hand-derived adjoint          */
+/* ------------------------------------------------------------------ */
+
+/* One system: n masses of mass m in dim dimensions, springs (a_j, b_j) with rest length
+   l0_j and stiffness k.  States 0 .. steps-1; step t (1 <= t < steps) from state t-1:
+     d_j = x_a - x_b,  len_j = |d_j| + 1e-4 (the example's guard against a zero length),
+     F_j = k (len_j - l0_j) d_j / len_j,   f_a -= F_j,  f_b += F_j,
+     v_t = exp(-dt alpha) v_{t-1} + dt f / m,   x_t = x_{t-1} + dt v_t.
+   x, v: [steps][n][dim] (row t holds state t; row 0 is read as the initial state). */
+#define ORC_MS_EPS 1e-4
+
+int orc_ms_forward(int dim, int n, int n_springs, const int32_t* sa, const int32_t* sb,
+                   const double* l0, double k, double alpha, double dt, double m, int steps,
+                   double* x, double* v) {
+  if (dim < 1 || dim > 3 || n < 1 || steps < 1) return ORC_ERR_ARG;
+  double* f = (double*)calloc((size_t)n * dim, sizeof(double));
+  if (!f) return ORC_ERR_MEM;
+  const double s = exp(-dt * alpha);
+  for (int t = 1; t < steps; t++) {
+    const double* x0 = x + (size_t)(t - 1) * n * dim;
+    const double* v0 = v + (size_t)(t - 1) * n * dim;
+    double* x1 = x + (size_t)t * n * dim;
+    double* v1 = v + (size_t)t * n * dim;
+    for (int i = 0; i < n * dim; i++) f[i] = 0.0;
+    for (int j = 0; j < n_springs; j++) {
+      const int a = sa[j], b = sb[j];
+      double d[3] = {0, 0, 0}, nrm = 0.0;
+      for (int c = 0; c < dim; c++) {
+        d[c] = x0[a * dim + c] - x0[b * dim + c];
+        nrm += d[c] * d[c];
+      }
+      const double len = sqrt(nrm) + ORC_MS_EPS;
+      for (int c = 0; c < dim; c++) {
+        const double F = k * (len - l0[j]) * d[c] / len;
+        f[a * dim + c] -= F;
+        f[b * dim + c] += F;
+      }
+    }
+    for (int i = 0; i < n * dim; i++) {
+      v1[i] = s * v0[i] + dt * f[i] / m;
+      x1[i] = x0[i] + dt * v1[i];
+    }
+  }
+  free(f);
+  return ORC_OK;
+}
+
+/* Reverse of orc_ms_forward over the recorded states x (v is not needed): xb, vb hold
+   dL/d(state steps-1) on entry and dL/d(state 0) on return; l0b accumulates dL/dl0. */
+int orc_ms_backward(int dim, int n, int n_springs, const int32_t* sa, const int32_t* sb,
+                    const double* l0, double k, double alpha, double dt, double m, int steps,
+                    const double* x, double* xb, double* vb, double* l0b) {
+  if (dim < 1 || dim > 3 || n < 1 || steps < 1) return ORC_ERR_ARG;
+  double* fb = (double*)calloc((size_t)n * dim, sizeof(double));
+  if (!fb) return ORC_ERR_MEM;
+  const double s = exp(-dt * alpha);
+  for (int t = steps - 1; t >= 1; t--) {
+    const double* x0 = x + (size_t)(t - 1) * n * dim;
+    /* x_t = x_{t-1} + dt v_t ; v_t = s v_{t-1} + dt f / m */
+    for (int i = 0; i < n * dim; i++) {
+      vb[i] += dt * xb[i];     /* dL/dv_t, complete */
+      fb[i] = dt / m * vb[i];  /* dL/df_t */
+      vb[i] *= s;              /* dL/dv_{t-1} */
+    }
+    /* xb now carries dL/dx_{t-1} through the position update; add the spring forces' */
+    for (int j = 0; j < n_springs; j++) {
+      const int a = sa[j], b = sb[j];
+      double d[3] = {0, 0, 0}, nrm = 0.0, Fb[3] = {0, 0, 0}, dFb = 0.0;
+      for (int c = 0; c < dim; c++) {
+        d[c] = x0[a * dim + c] - x0[b * dim + c];
+        nrm += d[c] * d[c];
+        Fb[c] = fb[b * dim + c] - fb[a * dim + c]; /* f_a -= F, f_b += F */
+        dFb += d[c] * Fb[c];
+      }
+      const double r = sqrt(nrm), len = r + ORC_MS_EPS;
+      /* F = k (1 - l0/len) d ; dlen/dd = d / r */
+      l0b[j] += -k * dFb / len;
+      for (int c = 0; c < dim; c++) {
+        const double db = k * ((1.0 - l0[j] / len) * Fb[c] + (l0[j] / (len * len)) * dFb * d[c] / r);
+        xb[a * dim + c] += db;
+        xb[b * dim + c] -= db;
+      }
+    }
+  }
+  free(fb);
+  return ORC_OK;
+}
+
+/* The example's loss on the triangle of masses 0, 1, 2 (dim 2): L = (|area| - target)^2,
+   area = (x01 x x02) / 2; writes L and dL/dx (n x 2). */
+int orc_ms_area_loss(int n, const double* x, double target, double* loss, double* xb) {
+  if (n < 3) return ORC_ERR_ARG;
+  const double e1[2] = {x[0] - x[2], x[1] - x[3]}, e2[2] = {x[0] - x[4], x[1] - x[5]};
+  const double cr = e1[0] * e2[1] - e1[1] * e2[0];
+  const double area = fabs(0.5 * cr), r = area - target;
+  *loss = r * r;
+  for (int i = 0; i < 2 * n; i++) xb[i] = 0.0;
+  const double g = 2.0 * r * 0.5 * (cr >= 0.0 ? 1.0 : -1.0); /* dL/dcr */
+  /* cr = e1x e2y - e1y e2x, e1 = x0 - x1, e2 = x0 - x2 */
+  xb[0] += g * (e2[1] - e1[1]);
+  xb[1] += g * (e1[0] - e2[0]);
+  xb[2] += -g * e2[1];
+  xb[3] += g * e2[0];
+  xb[4] += g * e1[1];
+  xb[5] += -g * e1[0];
+  return ORC_OK;
+}

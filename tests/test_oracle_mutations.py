@@ -61,10 +61,18 @@ MUTANTS = {
                                "xb[a2 * np + p] -= 0.0 * body[a2] / (double)np;"),
     "ctrl_velocity_mean": ("vb[a2 * np + p] += ub[K + g * 2 * d + d + a2] / cnt[g];",
                            "vb[a2 * np + p] += ub[K + g * 2 * d + d + a2] / (double)np;"),
+    "ms_damping_order": ("v1[i] = s * v0[i] + dt * f[i] / m;", "v1[i] = s * (v0[i] + dt * f[i] / m);"),
+    "ms_force_sign": ("f[a * dim + c] -= F;\n        f[b * dim + c] += F;",
+                      "f[a * dim + c] += F;\n        f[b * dim + c] -= F;"),
+    "ms_adjoint_norm_derivative": ("(l0[j] / (len * len)) * dFb * d[c] / r);",
+                                   "(l0[j] / (len * len)) * dFb * d[c] / len);"),
+    "ms_adjoint_rest_length": ("l0b[j] += -k * dFb / len;", "l0b[j] += k * dFb / len;"),
+    "ms_adjoint_position_carry": ("vb[i] += dt * xb[i];     /* dL/dv_t, complete */",
+                                  "vb[i] += xb[i];     /* dL/dv_t, complete */"),
 }
 
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py",
-             "tests/test_oracle_controller.py"]
+             "tests/test_oracle_controller.py", "tests/test_oracle_mass_spring.py"]
 
 
 @pytest.fixture(scope="module")
