@@ -283,6 +283,27 @@ def cpu_baseline(name, seconds_hint=20.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.workload == "springs":
+        w = springs_workload()
+        T = args.T or w["T"]
+        times, cb = [], None
+        for i in range(args.warmup + args.steps):
+            r = springs_cpu_baseline(w, T, k=1024)
+            if i >= args.warmup:
+                times.append(r["seconds"])
+                cb = r
+        ms_ = 1e3 * sum(times) / len(times)
+        value = cb["units"] / (ms_ / 1e3)
+        print(json.dumps({"impl": "reference", "metric": SPRINGS_METRIC, "value": value,
+                          "unit": SPRINGS_UNIT, "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": ms_, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "the mass-spring triangle batch (a sample of "
+                                                 "1,024 systems per step)", "T": T},
+                          "cpu_baseline": {**cb, "value": value},
+                          "e2e": {"value": value, "unit": SPRINGS_UNIT, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
     import oracle  # noqa: F401
     name = args.workload
     _, N, T, descr = make_workload(name)
@@ -303,6 +324,162 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+SPRINGS_METRIC = "mass-point-steps/s fwd+bwd (batched mass-spring, Section 2 example)"
+SPRINGS_UNIT = "mass-point-steps/s"
+
+
+def springs_workload(seed=0, S=1 << 20, T=256):
+    """1,048,576 copies of the paper's 2D triangle (3 masses, 3 springs; masses at (0,0),
+    (0,0.1), (0.1,0) jittered by U(+-0.005), rest lengths U(0.09, 0.15)), k = 100,
+    alpha = 10, dt = 2e-3, 256 states, loss (area - 0.2)^2 per system."""
+    from paper_1910_00935_gb300.scenes import uniform
+    import numpy as np
+    tri = np.array([[0.0, 0.0], [0.0, 0.1], [0.1, 0.0]])
+    x0 = (tri.reshape(-1)[:, None] + (uniform(seed, 600, 6 * S).reshape(6, S) - 0.5) * 0.01)
+    rest = 0.09 + 0.06 * uniform(seed, 601, 3 * S).reshape(3, S)
+    return dict(S=S, T=T, x0=x0.astype(np.float32), rest=rest.astype(np.float32),
+                springs=[(0, 1), (0, 2), (1, 2)], k=100.0, alpha=10.0, dt=2e-3, m=1.0)
+
+
+def springs_cpu_baseline(w, T, k=4096):
+    """The FP64 oracle, as it stands, on the first k systems: forward, area loss, backward
+    (1 host thread)."""
+    import numpy as np
+    import oracle
+    n = 3
+    t0 = time.perf_counter()
+    x0h = w["x0"][:, :k].astype(np.float64)
+    for sidx in range(k):
+        X, _ = oracle.ms_forward(x0h[:, sidx].reshape(3, 2), np.zeros((3, 2)), w["springs"],
+                                 w["rest"][:, sidx], w["k"], w["alpha"], w["dt"], w["m"], T)
+        _, xb = oracle.ms_area_loss(X[-1], 0.2)
+        oracle.ms_backward(X, w["springs"], w["rest"][:, sidx], w["k"], w["alpha"], w["dt"],
+                           w["m"], xb, np.zeros((3, 2)))
+    dt_cpu = time.perf_counter() - t0
+    return {"value": k * n * (T - 1) / dt_cpu, "unit": SPRINGS_UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} of the systems x {T} states forward+backward", "seconds": round(dt_cpu, 3),
+            "units": k * n * (T - 1)}
+
+
+def run_springs(args, rank, world):
+    """The mass-spring line: forward (records 256 states of 1,048,576 systems), the area
+    loss and its gradient in torch, backward through the tape; inputs resident."""
+    import numpy as np
+    import torch
+    from paper_1910_00935_gb300 import build as mbuild
+    mbuild.build()
+    from paper_1910_00935_gb300 import mass_spring as ms
+    torch.cuda.set_device(0 if world == 1 else _env_int("LOCAL_RANK", 0))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = springs_workload(seed=rank)
+    S, T, n = w["S"], args.T or w["T"], 3
+    sim = ms.MassSprings(2, n, w["springs"], S, w["k"], w["alpha"], w["dt"], w["m"], steps=T,
+                         device=dev)
+    host = {"x0": torch.as_tensor(w["x0"]).pin_memory(),
+            "v0": torch.zeros(6, S).pin_memory(),
+            "rest": torch.as_tensor(w["rest"]).pin_memory()}
+    devin = {k: v.to(dev) for k, v in host.items()}
+    out = {}
+
+    def device_step():
+        sim.forward(devin["x0"], devin["v0"], devin["rest"], T)
+        xT, _ = sim.state()
+        xT.requires_grad_(True)
+        L = ms.triangle_area(xT)
+        (gT,) = torch.autograd.grad(L.sum(), xT)
+        gx, gv, gl = sim.backward(gT, None)
+        out.update(loss=L.detach(), grest=gl, gx0=gx)
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        device_step()
+    sim.sync()
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        flush.fill_(1)
+        e0.record(stream)
+        device_step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_step = sum(e0.elapsed_time(e1) for e0, e1 in evs) / args.steps
+    clk = clocks.stop() if clocks else None
+    units = S * n * (T - 1)
+    value = world * units / (ms_step / 1e3)
+    # each pass alone (one kernel each): forward writes every state, backward reads the positions
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    flush.fill_(1)
+    ev[0].record(stream)
+    sim.forward(devin["x0"], devin["v0"], devin["rest"], T)
+    ev[1].record(stream)
+    gT = torch.ones(6, S, device=dev)
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    ev[1].record(stream)
+    sim.backward(gT, None)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    rows = n * 2
+    fwd_bytes = S * 4 * (2 * rows * T + 2 * rows + 3)      # states written, x0 v0 rest read
+    bwd_bytes = S * 4 * (rows * (T - 1) + 2 * rows + 3)    # positions read, seeds, outputs
+    hbm, peak_src = measured_peaks()
+    dom, dom_ms, dom_bytes = ("ms_backward", b_ms, bwd_bytes) if b_ms >= f_ms else ("ms_forward", f_ms, fwd_bytes)
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "kernel": dom,
+            "alg_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+            else "fallback 6.8 TB/s",
+            "forward_ms": f_ms, "backward_ms": b_ms}
+    # e2e: host arrays in, loss and dL/drest out
+    e2e = None
+    if not args.no_e2e:
+        out_host = {"loss": torch.empty(S).pin_memory(), "grest": torch.empty(3, S).pin_memory()}
+
+        def e2e_step():
+            for k, v in host.items():
+                devin[k].copy_(v, non_blocking=True)
+            device_step()
+            out_host["loss"].copy_(out["loss"], non_blocking=True)
+            out_host["grest"].copy_(out["grest"], non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        times = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            times.append(time.perf_counter() - t0)
+        e_ms = 1e3 * sum(times) / len(times)
+        e2e = {"value": world * units / (e_ms / 1e3), "unit": SPRINGS_UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in host.values())),
+               "d2h_bytes_per_step": int(sum(v.numel() * 4 for v in out_host.values()))}
+    cb = springs_cpu_baseline(w, T) if rank == 0 and not args.no_cpu_baseline else None
+    sim.sync()
+    if rank == 0:
+        line = {"metric": SPRINGS_METRIC, "value": value, "unit": SPRINGS_UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "1,048,576 copies of the paper's 2D mass-spring triangle "
+                                       "(3 masses, 3 springs), k=100, alpha=10, dt=2e-3, 256 states, "
+                                       "area loss", "systems": S, "T": T,
+                           "l2": "flushed between timed iterations (512 MiB write)",
+                           "parallelism": "1 GPU" if world == 1 else f"{world} replicas"},
+                "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roof, "cpu_baseline": cb,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sim.close()
 
 
 def main():
@@ -328,6 +505,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "springs":
+        run_springs(args, rank, world)
         return
 
     import torch

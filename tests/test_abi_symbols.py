@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads without a GPU, exports every entry point
-that include/mpm.h declares, and validates arguments on the host (no compute calls)."""
+that include/mpm.h and include/mass_spring.h declare, and validates arguments on the host
+(no compute calls)."""
 import ctypes
 import os
 import re
@@ -10,11 +11,13 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "mpm.h")
+MS_HEADER = os.path.join(ROOT, "include", "mass_spring.h")
 
 
-def declared():
-    text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(mpm_\w+)\(", text, re.M)))
+def declared(header=HEADER, prefix="mpm"):
+    text = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(" + prefix + r"_\w+)\(",
+                                 text, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -34,8 +37,8 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(libpath):
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r"\bT (mpm_\w+)$", out, re.M))
-    missing = [n for n in declared() if n not in exported]
+    exported = set(re.findall(r"\bT ((?:mpm|ms)_\w+)$", out, re.M))
+    missing = [n for n in declared() + declared(MS_HEADER, "ms") if n not in exported]
     assert not missing, missing
 
 
@@ -100,3 +103,26 @@ def test_host_side_validation_without_gpu(libpath):
     # NULL handle
     assert mpm.lib().mpm_forward(None, 1, None) == mpm.MPM_ERR_ARG
     assert mpm.lib().mpm_sync_status(None) == mpm.MPM_ERR_ARG
+
+
+def test_mass_spring_binding_and_host_validation(libpath):
+    from paper_1910_00935_gb300 import mass_spring as ms, mpm
+    assert sorted(ms.EXPORTED) == declared(MS_HEADER, "ms")
+    tri = [(0, 1), (0, 2), (1, 2)]
+    d = ms.make_desc(2, 3, tri, 1000, 100.0, 10.0, 1e-3)
+    b = ms.ms_workspace_bytes(d, 100)
+    assert b >= 2 * 100 * 6 * 1000 * 4  # positions and velocities of every state
+    for args in ((4, 3, tri), (2, 9, tri), (2, 3, [(0, 0)]), (2, 3, [(0, 3)]),
+                 (2, 3, [(0, 1)] * 33)):
+        with pytest.raises(mpm.MPMError) as e:
+            ms.ms_workspace_bytes(ms.make_desc(*args, 1000, 100.0, 10.0, 1e-3), 100)
+        assert e.value.code == mpm.MPM_ERR_ARG, args
+    for bad in (dict(dt=0.0), dict(mass=-1.0), dict(n_systems=0)):
+        kw = dict(dim=2, n_masses=3, springs=tri, n_systems=10, stiffness=1.0, damping=0.0,
+                  dt=1e-3, mass=1.0)
+        kw.update(bad)
+        with pytest.raises(mpm.MPMError):
+            ms.ms_workspace_bytes(ms.make_desc(**kw), 10)
+    with pytest.raises(mpm.MPMError):
+        ms.ms_workspace_bytes(d, 0)
+    assert ms.lib().ms_forward(None, None, None, None, 1, None) == mpm.MPM_ERR_ARG
