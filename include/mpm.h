@@ -189,6 +189,14 @@ typedef struct mpm_scene_desc {
                                   around the controller, the backward each fused adjoint pass
                                   around its reverse; the persistent form is not used. */
   float ctrl_scale;            /* controller output scale (ctrl_hidden > 0) */
+  int32_t ckpt_coarse;         /* 0 or 1: one level of checkpoints (every k = ckpt_every steps).
+                                  M >= 2: two levels -- the forward keeps the state every k*M
+                                  steps only, and mpm_backward re-simulates each such coarse
+                                  segment once to rebuild its states every k steps before the
+                                  usual per-segment re-simulation: about T/(kM) + M + 2k states
+                                  stored instead of T/k + 2k, for one more forward's worth of
+                                  re-simulation (Appendix D's recursive checkpointing, one level
+                                  deeper).  The re-simulation then runs on the main stream. */
 } mpm_scene_desc;
 
 /* Device bytes the workspace needs for this description and at most max_steps

@@ -59,7 +59,7 @@ struct Layout {
   size_t perm, keys0, keys1, idx0, sort_tmp, sort_tmp_bytes;
   size_t tiles, scene_off, scene_tiles, scene_tile_off;
   size_t mu, la, E, nu, group, matid, wact, wbar_tile, mubar, labar;
-  size_t fin, cur, ckpt, seg, adj;
+  size_t fin, cur, ckpt, fine, seg, adj;
   size_t rcache;  // 2 x (K+1) x [9][N] FP64 polar factors of a segment (3D FCR), by parity
   size_t grids;  // pm_slots + kUBSlots dense grids
   size_t boxes;  // (pm_slots + kUBSlots) x 2 parities x [scene][8]
@@ -73,6 +73,7 @@ struct Layout {
 
 struct Dims {
   int D, Q, S, K, n_ckpt, n_tiles, n_grid;
+  int M;  // coarse checkpoint multiplier: 1 (one level) or >= 2 (states every K*M, then K)
   int64_t N, nnodes;
   bool polar_cache;  // 3D fixed-corotated: FP64 polar factors are cached per segment
   bool store_grids;  // a re-simulated segment's grids stay live for its adjoint passes
@@ -89,7 +90,7 @@ struct Dims {
 // passes of the longest forward (T + 1) and backward (re-simulation T + segments, adjoint
 // T + 1, plus the measuring pass of the deterministic mode) sequences
 int64_t plan_fwd_cap(const Dims& m) { return (int64_t)m.T_max + 1; }
-int64_t plan_bwd_cap(const Dims& m) { return 2 * (int64_t)m.T_max + m.n_ckpt + 2; }
+int64_t plan_bwd_cap(const Dims& m) { return 3 * (int64_t)m.T_max + m.n_ckpt + 2; }
 
 bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
   auto fail = [&](const char* m) {
@@ -114,6 +115,7 @@ bool valid_desc(const mpm_scene_desc* d, int32_t max_steps, std::string* why) {
     return fail("unknown material");
   if (!(d->rho > 0.0f)) return fail("rho must be > 0");
   if (d->ckpt_every < 0) return fail("ckpt_every must be >= 0 (0: ceil(sqrt(max_steps)))");
+  if (d->ckpt_coarse < 0 || d->ckpt_coarse > 4096) return fail("ckpt_coarse must be in [0, 4096]");
   if (d->n_groups < 0 || d->n_groups > kMaxGroups) return fail("n_groups must be in [0, 8]");
   if (d->n_basis < 0 || d->n_basis > kMaxBasis) return fail("n_basis must be in [0, 8]");
   if (d->ctrl_hidden < 0 || d->ctrl_hidden > kCtrlMaxHidden)
@@ -141,7 +143,8 @@ Dims make_dims(const mpm_scene_desc* d, int32_t max_steps) {
   int k = d->ckpt_every;
   if (k == 0) k = (int)std::ceil(std::sqrt((double)max_steps));
   m.K = k < max_steps ? k : max_steps;
-  m.n_ckpt = (max_steps - 1) / m.K + 1;  // states 0, K, 2K, ... < max_steps
+  m.M = d->ckpt_coarse >= 2 ? d->ckpt_coarse : 1;
+  m.n_ckpt = (max_steps - 1) / (m.K * m.M) + 1;  // states 0, KM, 2KM, ... < max_steps
   m.n_grid = d->n_grid;
   m.polar_cache = d->dim == 3 && (d->material == MPM_FIXED_COROTATED || d->material == MPM_MIXED);
   m.T_max = max_steps;
@@ -203,6 +206,7 @@ Layout make_layout(const Dims& m) {
   L.fin = take(Q * N * 4);
   L.cur = take(Q * N * 4);
   L.ckpt = take((size_t)m.n_ckpt * Q * N * 4);
+  L.fine = take(m.M > 1 ? (size_t)m.M * Q * N * 4 : 0);  // states every K of one coarse segment
   L.seg = take((size_t)2 * (m.K + 1) * Q * N * 4);  // two segment buffers (by parity)
   L.adj = take(Q * N * 4);
   L.rcache = m.polar_cache ? take((size_t)2 * (m.K + 1) * 9 * N * 8) : take(0);
@@ -289,6 +293,14 @@ struct mpm_handle {
   }
   float* state(size_t base, int slot) const {
     return at<float>(base) + (size_t)slot * m.Q * m.N;
+  }
+  // the checkpoint of segment j (state j K): a stored checkpoint, or with two levels
+  // (M > 1) a coarse one (j a multiple of M) or one rebuilt for the coarse segment being
+  // processed
+  float* ckpt(int j) const {
+    if (m.M == 1) return state(L.ckpt, j);
+    if (j % m.M == 0) return state(L.ckpt, j / m.M);
+    return state(L.fine, j % m.M);
   }
   // state s0 + i of segment j (s0 = j K) in the segment buffer of j's parity
   float* seg(int j, int i) const {
@@ -803,6 +815,40 @@ struct Launcher {
 // re-simulating it -- with ckpt_every >= T nothing is re-simulated at all
 int last_segment_start(const mpm_handle* h, int T) { return ((T - 1) / h->m.K) * h->m.K; }
 
+// whether the forward stores state t as a checkpoint: every K steps with one level; with two,
+// every K*M steps, and every K steps over the last coarse segment (left for the backward
+// like the last segment's states)
+bool forward_stores_ckpt(const mpm_handle* h, int T, int t) {
+  const int K = h->m.K, KM = h->m.K * h->m.M;
+  if (t % K != 0) return false;
+  return h->m.M == 1 || t % KM == 0 || t >= ((T - 1) / KM) * KM;
+}
+
+// Two levels: rebuild the checkpoints every K steps of coarse segment Jc (states
+// Jc K M + m K, m = 1 .. M-1 below T) by re-simulating it from its coarse checkpoint.
+int issue_coarse_resim(mpm_handle* h, Launcher& Lc, int Jc, int T) {
+  const int K = h->m.K, M = h->m.M;
+  const int s0 = Jc * K * M;
+  const int last = std::min(s0 + (M - 1) * K, ((T - 1) / K) * K);  // last checkpoint to rebuild
+  if (last <= s0) return MPM_OK;
+  const float* src = h->ckpt(s0 / K);
+  float* cur = h->at<float>(h->L.cur);
+  int g = -1;
+  LK(Lc.step(kP2GOnly, s0, src, nullptr, -1, &g));
+  for (int t = s0 + 1; t < last; ++t) {
+    const bool ck = (t - s0) % K == 0;
+    float* dst = ck ? h->ckpt(t / K) : cur;
+    int g_next = -1;
+    LK(Lc.step(ck ? kG2PP2GFull : kG2PP2G, t, src, dst, g, &g_next));
+    ring_release(h->pm, g);
+    g = g_next;
+    src = dst;
+  }
+  LK(Lc.step(kG2POnlyFull, last, src, h->ckpt(last / K), g, nullptr));
+  ring_release(h->pm, g);
+  return MPM_OK;
+}
+
 int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
   const int K = h->m.K;
   const int sL = last_segment_start(h, T);
@@ -815,8 +861,8 @@ int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
   for (int t = 1; t < T; ++t) {
     float* dst;
     int mode;
-    if (t % K == 0) {
-      dst = h->state(h->L.ckpt, t / K);
+    if (forward_stores_ckpt(h, T, t)) {
+      dst = h->ckpt(t / K);
       mode = kG2PP2GFull;
     } else if (t > sL) {
       dst = h->seg(sL / K, t - sL);
@@ -844,7 +890,7 @@ int issue_forward(mpm_handle* h, Launcher& Lc, int T) {
 // segment is kept live too (seg_grids[t - s0] = grid of step t)
 int issue_resim(mpm_handle* h, Launcher& Lc, int s0, int top, int* grid_top_minus_1,
                 int* seg_grids) {
-  const float* ck = h->state(h->L.ckpt, s0 / h->m.K);
+  const float* ck = h->ckpt(s0 / h->m.K);
   int g = -1;
   LK(Lc.step(kP2GOnly, s0, ck, nullptr, -1, &g, h->rslot(s0 / h->m.K, 0)));
   const float* prev = ck;
@@ -888,13 +934,19 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident, bool overl
     LK(Lc.wait(h->ev_fork));
     Lc.use_stream(0);
   }
+  int coarse = resident ? (T - 1) / (K * h->m.M) : -1;  // coarse segment whose checkpoints are built
   for (int s = T - 1; s >= 0; --s) {
     const int j = s / K, s0 = j * K, pj = j & 1;
     const int top = (s0 + K < T) ? s0 + K : T;
     if (overlap) Lc.use_pool(pj);
+    if (h->m.M > 1 && j / h->m.M != coarse) {
+      coarse = j / h->m.M;
+      int rc = issue_coarse_resim(h, Lc, coarse, T);
+      if (rc) return rc;
+    }
     if (s == T - 1 && resident) {
       // the forward left this segment's states in place: only the grid of step T-1
-      const float* st = (s == s0) ? h->state(h->L.ckpt, j) : h->seg(j, s - s0);
+      const float* st = (s == s0) ? h->ckpt(j) : h->seg(j, s - s0);
       LK(Lc.step(kP2GOnly, s, st, nullptr, -1, &pm_s));
       stored = false;
     } else if (s == top - 1) {
@@ -907,11 +959,11 @@ int issue_backward(mpm_handle* h, Launcher& Lc, int T, bool resident, bool overl
         if (rc) return rc;
       }
     }
-    const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->seg(j, s - s0);
+    const float* st_s = (s == s0) ? h->ckpt(j) : h->seg(j, s - s0);
     const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->seg(j, s + 1 - s0);
     // the recomputed P2G of step s-1 runs only when this segment's grids were not kept
     const float* st_sm = (s - 1 >= s0 && !stored)
-                             ? ((s - 1 == s0) ? h->state(h->L.ckpt, j) : h->seg(j, s - 1 - s0))
+                             ? ((s - 1 == s0) ? h->ckpt(j) : h->seg(j, s - 1 - s0))
                              : nullptr;
     int ub_s = -1, pm_sm = -1;
     // cached polar factors: state s+1 only inside this segment (the segment's top state
@@ -977,7 +1029,7 @@ int issue_forward_ctrl(mpm_handle* h, Launcher& Lc, int T) {
   LK(Lc.ctrl_forward(0, src));
   LK(Lc.step(kP2GOnly, 0, src, nullptr, -1, &g, sL == 0 ? h->rslot(sL / K, 0) : nullptr));
   for (int t = 1; t < T; ++t) {
-    float* dst = (t % K == 0) ? h->state(h->L.ckpt, t / K) : (t > sL) ? h->seg(sL / K, t - sL) : cur;
+    float* dst = forward_stores_ckpt(h, T, t) ? h->ckpt(t / K) : (t > sL) ? h->seg(sL / K, t - sL) : cur;
     LK(Lc.step(kG2POnlyFull, t, src, dst, g, nullptr));
     ring_release(h->pm, g);
     LK(Lc.ctrl_forward(t, dst));
@@ -1003,10 +1055,16 @@ int issue_backward_ctrl(mpm_handle* h, Launcher& Lc, int T, bool resident) {
   int pm_s1 = -1, pm_s = -1, ub_s1 = -1;
   std::vector<int> seg_grids(K, -1);
   bool stored = false;
+  int coarse = resident ? (T - 1) / (K * h->m.M) : -1;  // coarse segment whose checkpoints are built
   for (int s = T - 1; s >= 0; --s) {
     const int j = s / K, s0 = j * K;
     const int top = (s0 + K < T) ? s0 + K : T;
-    const float* st_s = (s == s0) ? h->state(h->L.ckpt, j) : h->seg(j, s - s0);
+    if (h->m.M > 1 && j / h->m.M != coarse) {
+      coarse = j / h->m.M;
+      int rc = issue_coarse_resim(h, Lc, coarse, T);
+      if (rc) return rc;
+    }
+    const float* st_s = (s == s0) ? h->ckpt(j) : h->seg(j, s - s0);
     const float* st_s1 = (s + 1 == T) ? h->at<float>(h->L.fin) : h->seg(j, s + 1 - s0);
     const double* R1 = (s + 1 < top) ? h->rslot(j, s + 1 - s0) : nullptr;
     if (s == T - 1 && resident) {
@@ -1353,7 +1411,7 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   // the re-simulation overlaps the adjoint passes when there is a segment to re-simulate,
   // except in the persistent form (one stream of plan passes) and while profiling (each
   // launch timed alone)
-  const bool overlap = h->overlap && !h->persistent && !h->profile && !ctrl &&
+  const bool overlap = h->overlap && !h->persistent && !h->profile && !ctrl && m.M == 1 &&
                        last_segment_start(h, T) > 0;
   const int64_t key = (int64_t)T * 2 + 1 + (resident ? 0 : ((int64_t)1 << 40)) +
                       (overlap ? ((int64_t)1 << 41) : 0);

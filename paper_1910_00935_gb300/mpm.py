@@ -70,6 +70,7 @@ class SceneDesc(ctypes.Structure):
         ("deterministic_p2g", ctypes.c_int32),
         ("ctrl_hidden", ctypes.c_int32),
         ("ctrl_scale", ctypes.c_float),
+        ("ckpt_coarse", ctypes.c_int32),
     ]
 
 
@@ -154,7 +155,8 @@ def make_desc(desc: dict) -> SceneDesc:
                   int(desc.get("ckpt_every", 32)), int(desc.get("n_groups", 0)),
                   int(desc.get("n_basis", 0)), float(desc.get("act_period", 50.0)),
                   float(desc.get("act_phase", 0.0)), int(desc.get("deterministic_p2g", 0)),
-                  int(desc.get("ctrl_hidden", 0)), float(desc.get("ctrl_scale", 1.0)))
+                  int(desc.get("ctrl_hidden", 0)), float(desc.get("ctrl_scale", 1.0)),
+                  int(desc.get("ckpt_coarse", 0)))
     d._keep = arr  # keep the particle-count array alive with the struct
     return d
 

@@ -93,7 +93,7 @@ def test_triangle_rest_length_optimisation(ms):
         xT, vT = ms.MassSpringRun.apply(sim, T, x0, v0, r)
         L = ms.triangle_area(xT).sum()
         L.backward()
-        losses.append(float(L) / S)
+        losses.append(float(L.detach()) / S)
         rest = (rest - lr * r.grad).detach().contiguous()
     sim.close()
     l0 = np.array([0.1, 0.1, 0.14])

@@ -1,8 +1,10 @@
-"""The backward's re-simulation of segment j-1 on a second stream, overlapped with the
-adjoint passes of segment j (MPM_OPT_OVERLAP_RESIM, on by default).  It changes when work
-runs, not what it computes: in the deterministic mode the gradients and states are bitwise
-those of the single-stream backward (kept and recomputed grids, resident or re-simulated
-last segment, fixed-corotated polar caches), and the default mode meets the oracle bars."""
+"""Checkpoint schedules and the launch form of the re-simulation: the backward's
+re-simulation of segment j-1 on a second stream, overlapped with the adjoint passes of
+segment j (MPM_OPT_OVERLAP_RESIM, on by default); the automatic O(sqrt T) interval; two
+levels of checkpoints (ckpt_coarse).  None of them changes what is computed: in the
+deterministic mode the gradients are bitwise those of the single-stream, one-level backward
+(kept and recomputed grids, resident or re-simulated last segment, fixed-corotated polar
+caches), and the default mode meets the oracle bars."""
 import numpy as np
 import pytest
 
@@ -84,3 +86,42 @@ def test_automatic_checkpoint_interval(mpm):
     g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
     o = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
     _compare_grads(g["grad"], o, KEYS + ["gw"])
+
+
+@pytest.mark.parametrize("name,kw,T,k,M", [
+    ("cube3d", dict(n_side=16, n_grid=64), 40, 4, 3),    # coarse segments of 12, ragged end
+    ("robots3d", dict(n_scenes=2, dims=(12, 8, 8)), 29, 3, 4),  # polar caches, actuation
+    ("robots_nn", dict(n_scenes=2, dims=(12, 8, 8), hidden=8), 21, 4, 2),  # controller
+])
+def test_two_level_checkpoints_bitwise_equal_one_level(mpm, name, kw, T, k, M):
+    """ckpt_coarse = M: the forward keeps the state every k*M steps and the backward rebuilds
+    each coarse segment's checkpoints before its segments' re-simulation; in the
+    deterministic mode the gradients are bitwise those of one level at interval k (the
+    rebuilt checkpoints equal the forward's), for the first and a second backward."""
+    scene = scenes.make(name, **kw)
+    scene["desc"]["ckpt_every"] = k
+    scene["desc"]["deterministic_p2g"] = 1
+    seeds = _random_seeds(scene, np.random.default_rng(54))
+    keys = KEYS + (["gw"] if scene["desc"].get("n_groups", 0) else [])
+    one = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    scene["desc"]["ckpt_coarse"] = M
+    sim = mpm.from_scene(scene, max_steps=T)
+    sim.forward(T)
+    tseeds = {kk: torch.as_tensor(v) for kk, v in seeds.items()}
+    for _ in range(2):
+        g = {kk: v.cpu().numpy() for kk, v in sim.backward(**tseeds).items()}
+        for key in keys:
+            assert np.array_equal(g[key], one["grad"][key]), key
+    assert mpm.mpm_sync_status(sim.h) == mpm.MPM_OK
+    sim.close()
+
+
+def test_two_level_checkpoints_store_fewer_states(mpm):
+    scene = scenes.make("cube3d", n_side=16, n_grid=64)
+    d1 = dict(scene["desc"], ckpt_every=4)
+    d2 = dict(d1, ckpt_coarse=8)
+    b1 = mpm.mpm_workspace_bytes(mpm.make_desc(d1), 1024)
+    b2 = mpm.mpm_workspace_bytes(mpm.make_desc(d2), 1024)
+    state = 24 * 4 * sum(scene["desc"]["n_particles"])
+    # 256 checkpoints -> 32 coarse ones + 8 rebuilt ones
+    assert b1 - b2 >= (256 - 32 - 8) * state
