@@ -8,7 +8,18 @@ scenes from a scene dict of `paper_1910_00935_gb300.scenes`.
 """
 from __future__ import annotations
 
+import pickle
+from datetime import timedelta
+
 import numpy as np
+
+
+class RankFailure(RuntimeError):
+    """Ranks that did not report their shard before the deadline."""
+
+    def __init__(self, missing):
+        super().__init__(f"ranks {sorted(missing)} did not report their shards")
+        self.missing = sorted(missing)
 
 
 def shard_scenes(n_particles, world_size: int, rank: int):
@@ -40,3 +51,23 @@ def subset(scene, idx):
     desc["n_particles"] = [int(desc["n_particles"][i]) for i in idx]
     desc["n_scenes"] = len(idx)
     return {"desc": desc, "arrays": arr}
+
+
+def collect_shards(store, rank: int, world_size: int, payload, timeout_s: float = 60.0,
+                   tag: str = "shard"):
+    """Every rank publishes its shard's result in the rendezvous store; rank 0 waits for all
+    of them for at most timeout_s and returns {rank: payload}, or raises RankFailure naming
+    the ranks that never reported (a rank that crashed, hung or left).  Other ranks return
+    None.  No collective runs, so a missing rank cannot hang the others."""
+    store.set(f"{tag}/{rank}", pickle.dumps(payload))
+    if rank != 0:
+        return None
+    keys = [f"{tag}/{r}" for r in range(world_size)]
+    try:
+        store.wait(keys, timedelta(seconds=timeout_s))
+    except Exception:
+        missing = [r for r, k in enumerate(keys) if not store.check([k])]
+        if missing:
+            raise RankFailure(missing) from None
+        raise
+    return {r: pickle.loads(store.get(k)) for r, k in enumerate(keys)}

@@ -1,6 +1,8 @@
 """Multi-rank host logic on CPU (world size 2, gloo): scenes sharded across ranks with no
-data-path collective give exactly the single-process results, and the benchmark's
-max-over-ranks timing reduction works.  The per-rank work is the FP64 oracle (no GPU)."""
+data-path collective give exactly the single-process results, the benchmark's
+max-over-ranks timing reduction works, and a rank that fails before reporting its shard is
+detected by the others through the rendezvous store within a deadline (no collective hangs).
+The per-rank work is the FP64 oracle (no GPU)."""
 import os
 import socket
 
@@ -12,7 +14,7 @@ import torch.multiprocessing as mp
 
 import oracle
 from paper_1910_00935_gb300 import scenes
-from paper_1910_00935_gb300.sharding import shard_scenes, subset
+from paper_1910_00935_gb300.sharding import RankFailure, collect_shards, shard_scenes, subset
 
 
 def test_shards_partition_and_balance():
@@ -71,3 +73,39 @@ def test_two_rank_sharded_run_equals_single_process():
     assert sorted(merged) == list(range(5))
     for i in range(5):
         np.testing.assert_array_equal(merged[i], single[i])  # bitwise
+
+
+def _failing_worker(rank, world, port, q):
+    store = dist.TCPStore("127.0.0.1", port, world, is_master=(rank == 0),
+                          timeout=__import__("datetime").timedelta(seconds=30))
+    if rank == 1:
+        raise RuntimeError("simulated rank failure before its shard is reported")
+    base = scenes.make("rects2d", n_scenes=3, n_min=200, n_max=400)
+    mine = shard_scenes(base["desc"]["n_particles"], world, rank)
+    res = oracle.simulate(scenes.oracle_view(subset(base, mine)), 2)
+    try:
+        collect_shards(store, rank, world, {i: r for i, r in zip(mine, res)}, timeout_s=5.0)
+        q.put(("no failure detected", None))
+    except RankFailure as e:
+        q.put(("detected", e.missing))
+
+
+def test_failed_rank_is_detected_without_a_hang():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    status, missing = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert status == "detected" and missing == [1]
+    assert procs[0].exitcode == 0 and procs[1].exitcode != 0
+
+
+def test_collect_shards_returns_every_rank():
+    store = dist.HashStore()
+    assert collect_shards(store, 1, 2, {"b": 2}) is None
+    got = collect_shards(store, 0, 2, {"a": 1}, timeout_s=5.0)
+    assert got == {0: {"a": 1}, 1: {"b": 2}}
