@@ -3,7 +3,8 @@
 // demonstration of Section 3, for many independent systems at once.
 //
 // One thread owns one system for the whole run: its positions, velocities and forces live
-// in shared memory (rows indexed by the springs' anchors), its rest lengths in registers,
+// in shared memory (rows indexed by the springs' anchors; in registers for systems of at
+// most 4 masses and 4 springs), its rest lengths in registers,
 // and every step streams the new state to the tape in HBM (coalesced across systems); the
 // backward thread walks the tape in reverse.  The tape is the only memory traffic, so the
 // passes are bound by HBM bandwidth: 2 * n * dim floats written per system-step forward,
@@ -188,6 +189,185 @@ __global__ void __launch_bounds__(kMsBwdThreads)
       if (j < P.ns) grest[j * S + sys] = gl[j];
 }
 
+// Small systems (at most 4 masses and 4 springs, the paper's triangle among them): the whole
+// state of a thread's system in registers.  A spring's anchors are runtime values, so its
+// end points are picked from the register rows by compares (mass i of row i is a
+// compile-time index in every unrolled access) instead of indexing shared memory, which
+// keeps each step free of shared-memory round trips.
+constexpr int kMsSmallMasses = 4;
+
+template <int D>
+__device__ __forceinline__ float ms_pick(const float (&x)[kMsSmallMasses][D], int a, int c) {
+  float r = x[0][c];
+#pragma unroll
+  for (int i = 1; i < kMsSmallMasses; ++i)
+    if (a == i) r = x[i][c];
+  return r;
+}
+template <int D>
+__device__ __forceinline__ void ms_add(float (&x)[kMsSmallMasses][D], int a, int c, float v) {
+#pragma unroll
+  for (int i = 0; i < kMsSmallMasses; ++i)
+    if (a == i) x[i][c] += v;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kMsThreads)
+    ms_forward_small(const __grid_constant__ MsParams P, const float* x0, const float* v0,
+                     const float* rest, float* X, float* V, int steps) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= P.S) return;
+  const int n = P.n;
+  const int64_t S = P.S, RS = (int64_t)n * D * S;
+  float x[kMsSmallMasses][D], v[kMsSmallMasses][D], l0[4];
+#pragma unroll
+  for (int i = 0; i < kMsSmallMasses; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const bool on = i < n;
+      x[i][c] = on ? x0[(i * D + c) * S + sys] : 0.0f;
+      v[i][c] = on ? v0[(i * D + c) * S + sys] : 0.0f;
+      if (on) {
+        X[(i * D + c) * S + sys] = x[i][c];
+        V[(i * D + c) * S + sys] = v[i][c];
+      }
+    }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) l0[j] = j < P.ns ? rest[j * S + sys] : 0.0f;
+  for (int t = 1; t < steps; ++t) {
+    float f[kMsSmallMasses][D];
+#pragma unroll
+    for (int i = 0; i < kMsSmallMasses; ++i)
+#pragma unroll
+      for (int c = 0; c < D; ++c) f[i][c] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j >= P.ns) break;
+      const int a = P.a[j], b = P.b[j];
+      float d[D], nrm = 0.0f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        d[c] = ms_pick<D>(x, a, c) - ms_pick<D>(x, b, c);
+        nrm += d[c] * d[c];
+      }
+      const float len = sqrtf(nrm) + kMsEps;
+      const float coef = P.k * (len - l0[j]) / len;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        ms_add<D>(f, a, c, -coef * d[c]);
+        ms_add<D>(f, b, c, coef * d[c]);
+      }
+    }
+    float* Xt = X + t * RS;
+    float* Vt = V + t * RS;
+#pragma unroll
+    for (int i = 0; i < kMsSmallMasses; ++i)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        v[i][c] = P.s * v[i][c] + P.dt * f[i][c] * P.inv_m;
+        x[i][c] = x[i][c] + P.dt * v[i][c];
+        if (i < n) {
+          Xt[(i * D + c) * S + sys] = x[i][c];
+          Vt[(i * D + c) * S + sys] = v[i][c];
+        }
+      }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kMsBwdThreads)
+    ms_backward_small(const __grid_constant__ MsParams P, const float* rest, const float* X,
+                      const float* xbT, const float* vbT, float* gx0, float* gv0, float* grest,
+                      int steps) {
+  extern __shared__ float ms_sm[];  // the prefetch ring: (kMsAhead + 1) x R rows
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= P.S) return;  // no barrier below: each thread works alone
+  const int tid = threadIdx.x, B = blockDim.x;
+  const int n = P.n, R = n * D;
+  const int64_t S = P.S;
+  auto ring = [&](int q, int r) -> float& { return ms_sm[(q * R + r) * B + tid]; };
+  auto fetch = [&](int u) {
+    if (u < 0) return;
+    const float* Xu = X + (int64_t)u * R * S;
+    const int q = u % (kMsAhead + 1);
+    for (int r = 0; r < R; ++r) ms_copy_async(&ring(q, r), Xu + r * S + sys);
+  };
+#pragma unroll
+  for (int q = 0; q < kMsAhead; ++q) {
+    fetch(steps - 2 - q);
+    ms_commit();
+  }
+  float xb[kMsSmallMasses][D], vb[kMsSmallMasses][D], l0[4], gl[4];
+#pragma unroll
+  for (int i = 0; i < kMsSmallMasses; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const bool on = i < n;
+      xb[i][c] = on && xbT ? xbT[(i * D + c) * S + sys] : 0.0f;
+      vb[i][c] = on && vbT ? vbT[(i * D + c) * S + sys] : 0.0f;
+    }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    l0[j] = j < P.ns ? rest[j * S + sys] : 0.0f;
+    gl[j] = 0.0f;
+  }
+  const float fscale = P.dt * P.inv_m;
+  for (int t = steps - 1; t >= 1; --t) {
+    fetch(t - 1 - kMsAhead);
+    ms_commit();
+    ms_wait<kMsAhead>();  // the copy of state t-1, issued kMsAhead steps ago, has landed
+    const int q = (t - 1) % (kMsAhead + 1);
+    float xp[kMsSmallMasses][D];
+#pragma unroll
+    for (int i = 0; i < kMsSmallMasses; ++i)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        xp[i][c] = i < n ? ring(q, i * D + c) : 0.0f;
+        vb[i][c] += P.dt * xb[i][c];  // dL/dv_t, complete
+      }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j >= P.ns) break;
+      const int a = P.a[j], b = P.b[j];
+      float d[D], Fb[D], nrm = 0.0f, dFb = 0.0f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        d[c] = ms_pick<D>(xp, a, c) - ms_pick<D>(xp, b, c);
+        nrm += d[c] * d[c];
+        Fb[c] = fscale * (ms_pick<D>(vb, b, c) - ms_pick<D>(vb, a, c));  // f_a -= F, f_b += F
+        dFb += d[c] * Fb[c];
+      }
+      const float r = sqrtf(nrm), len = r + kMsEps;
+      gl[j] -= P.k * dFb / len;  // F = k (1 - l0/len) d, dlen/dd = d / r
+      const float c1 = P.k * (1.0f - l0[j] / len);
+      const float c2 = r > 0.0f ? P.k * l0[j] / (len * len) * dFb / r : 0.0f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const float db = c1 * Fb[c] + c2 * d[c];
+        ms_add<D>(xb, a, c, db);
+        ms_add<D>(xb, b, c, -db);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kMsSmallMasses; ++i)
+#pragma unroll
+      for (int c = 0; c < D; ++c) vb[i][c] *= P.s;  // dL/dv_{t-1}
+  }
+  ms_wait<0>();
+#pragma unroll
+  for (int i = 0; i < kMsSmallMasses; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      if (i < n) {
+        if (gx0) gx0[(i * D + c) * S + sys] = xb[i][c];
+        if (gv0) gv0[(i * D + c) * S + sys] = vb[i][c];
+      }
+  if (grest)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < P.ns) grest[j * S + sys] = gl[j];
+}
+
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct MsLayout {
@@ -279,14 +459,29 @@ cudaError_t ms_bwd(const MsParams& P, const float* R, const float* X, const floa
   ms_backward_kernel<D, MAXS><<<blocks_for(P.S, kMsBwdThreads), kMsBwdThreads, smem, s>>>(P, R, X, xb, vb, gx, gv, gl, steps);
   return cudaGetLastError();
 }
+bool ms_small(const MsParams& P) { return P.n <= kMsSmallMasses && P.ns <= 4; }
+
 cudaError_t ms_launch_forward(int dim, const MsParams& P, const float* x0, const float* v0,
                               const float* R, float* X, float* V, int steps, cudaStream_t s) {
+  if (ms_small(P)) {
+    if (dim == 2) ms_forward_small<2><<<blocks_for(P.S, kMsThreads), kMsThreads, 0, s>>>(P, x0, v0, R, X, V, steps);
+    else ms_forward_small<3><<<blocks_for(P.S, kMsThreads), kMsThreads, 0, s>>>(P, x0, v0, R, X, V, steps);
+    return cudaGetLastError();
+  }
   if (dim == 2) return P.ns <= 4 ? ms_fwd<2, 4>(P, x0, v0, R, X, V, steps, s) : ms_fwd<2, MS_MAX_SPRINGS>(P, x0, v0, R, X, V, steps, s);
   return P.ns <= 4 ? ms_fwd<3, 4>(P, x0, v0, R, X, V, steps, s) : ms_fwd<3, MS_MAX_SPRINGS>(P, x0, v0, R, X, V, steps, s);
 }
 cudaError_t ms_launch_backward(int dim, const MsParams& P, const float* R, const float* X,
                                const float* xb, const float* vb, float* gx, float* gv, float* gl,
                                int steps, cudaStream_t s) {
+  if (ms_small(P)) {
+    const size_t smem = (size_t)(kMsAhead + 1) * P.n * dim * kMsBwdThreads * sizeof(float);
+    if (dim == 2)
+      ms_backward_small<2><<<blocks_for(P.S, kMsBwdThreads), kMsBwdThreads, smem, s>>>(P, R, X, xb, vb, gx, gv, gl, steps);
+    else
+      ms_backward_small<3><<<blocks_for(P.S, kMsBwdThreads), kMsBwdThreads, smem, s>>>(P, R, X, xb, vb, gx, gv, gl, steps);
+    return cudaGetLastError();
+  }
   if (dim == 2) return P.ns <= 4 ? ms_bwd<2, 4>(P, R, X, xb, vb, gx, gv, gl, steps, s) : ms_bwd<2, MS_MAX_SPRINGS>(P, R, X, xb, vb, gx, gv, gl, steps, s);
   return P.ns <= 4 ? ms_bwd<3, 4>(P, R, X, xb, vb, gx, gv, gl, steps, s) : ms_bwd<3, MS_MAX_SPRINGS>(P, R, X, xb, vb, gx, gv, gl, steps, s);
 }

@@ -42,11 +42,12 @@ def _unrows(t, n, dim):
     return a.T.reshape(-1, n, dim)
 
 
-@pytest.mark.parametrize("dim,alpha", [(2, 5.0), (3, 0.0)])
-def test_states_and_gradients_match_oracle(ms, dim, alpha):
+@pytest.mark.parametrize("dim,alpha,n", [(2, 5.0, 5), (3, 0.0, 5),   # shared-memory rows
+                                         (2, 5.0, 4), (3, 1.0, 4)])  # register rows (<= 4 masses, springs)
+def test_states_and_gradients_match_oracle(ms, dim, alpha, n):
     import oracle
-    rng = np.random.default_rng(7 + dim)
-    S, n, T = 300, 5, 160
+    rng = np.random.default_rng(7 + dim + n)
+    S, T = 300, 160
     k, dt, m = 40.0, 2e-3, 1.5
     springs, x0, v0, l0 = _batch(S, n, dim, rng)
     sim = ms.MassSprings(dim, n, springs, S, k, alpha, dt, m, steps=T)
