@@ -343,6 +343,39 @@ def springs_workload(seed=0, S=1 << 20, T=256):
                 springs=[(0, 1), (0, 2), (1, 2)], k=100.0, alpha=10.0, dt=2e-3, m=1.0)
 
 
+def springs_digest():
+    """Digest of the mass-spring kernels' source (csrc/mass_spring.cu)."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_1910_00935_gb300", "csrc", "mass_spring.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def springs_traffic(kernel, T):
+    """DRAM bytes per launch of `kernel` from profiles/ncu_springs.md when it was captured on
+    these kernels, scaled from the captured run's states to T (the tape traffic grows with
+    the states; the capture runs a shorter tape of the same systems); else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_springs.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    if f"source digest: {springs_digest()}" not in text:
+        return None
+    import re
+    m = re.search(r"captured states: (\d+)", text)
+    sec = text.split(f"## {kernel}")
+    if not m or len(sec) < 2:
+        return None
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    total = 0.0
+    for metric in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        row = [ln for ln in sec[1].splitlines() if ln.startswith(f"| `{metric}` |")]
+        if not row:
+            return None
+        cells = [c.strip() for c in row[0].strip("|").split("|")]
+        total += statistics.mean(float(c) for c in cells[1:-1]) * scale.get(cells[-1], float("nan"))
+    return total * (T - 1) / (int(m.group(1)) - 1)
+
+
 def springs_cpu_baseline(w, T, k=4096):
     """The FP64 oracle, as it stands, on the first k systems: forward, area loss, backward
     (1 host thread)."""
@@ -434,7 +467,7 @@ def run_springs(args, rank, world):
     dom, dom_ms, dom_bytes = ("ms_backward", b_ms, bwd_bytes) if b_ms >= f_ms else ("ms_forward", f_ms, fwd_bytes)
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "kernel": dom,
+            "frac": achieved / hbm, "traffic": springs_traffic(dom, T), "kernel": dom,
             "alg_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
             else "fallback 6.8 TB/s",
@@ -471,8 +504,8 @@ def run_springs(args, rank, world):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": "1,048,576 copies of the paper's 2D mass-spring triangle "
-                                       "(3 masses, 3 springs), k=100, alpha=10, dt=2e-3, 256 states, "
+                "config": {"workload": f"1,048,576 copies of the paper's 2D mass-spring triangle "
+                                       f"(3 masses, 3 springs), k=100, alpha=10, dt=2e-3, {T} states, "
                                        "area loss", "systems": S, "T": T,
                            "l2": "flushed between timed iterations (512 MiB write)",
                            "parallelism": "1 GPU" if world == 1 else f"{world} replicas"},
