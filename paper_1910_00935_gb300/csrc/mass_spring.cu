@@ -164,11 +164,13 @@ __global__ void __launch_bounds__(kMsBwdThreads)
         Fb[c] = fscale * (svb(b + c) - svb(a + c));  // f_a -= F, f_b += F
         dFb += d[c] * Fb[c];
       }
-      const float r = sqrtf(nrm), len = r + kMsEps;
-      // F = k (1 - l0/len) d, dlen/dd = d / r
-      gl[j] -= P.k * dFb / len;
-      const float c1 = P.k * (1.0f - l0[j] / len);
-      const float c2 = r > 0.0f ? P.k * l0[j] / (len * len) * dFb / r : 0.0f;
+      // F = k (1 - l0/len) d, dlen/dd = d / r: one reciprocal square root and one division
+      // (the reverse pass needs no bit-exact match with the forward's rounding)
+      const float rinv = nrm > 0.0f ? rsqrtf(nrm) : 0.0f;
+      const float r = nrm * rinv, inv = 1.0f / (r + kMsEps);
+      gl[j] -= P.k * dFb * inv;
+      const float c1 = P.k * (1.0f - l0[j] * inv);
+      const float c2 = P.k * l0[j] * inv * inv * dFb * rinv;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         const float db = c1 * Fb[c] + c2 * d[c];
@@ -337,10 +339,12 @@ __global__ void __launch_bounds__(kMsBwdThreads)
         Fb[c] = fscale * (ms_pick<D>(vb, b, c) - ms_pick<D>(vb, a, c));  // f_a -= F, f_b += F
         dFb += d[c] * Fb[c];
       }
-      const float r = sqrtf(nrm), len = r + kMsEps;
-      gl[j] -= P.k * dFb / len;  // F = k (1 - l0/len) d, dlen/dd = d / r
-      const float c1 = P.k * (1.0f - l0[j] / len);
-      const float c2 = r > 0.0f ? P.k * l0[j] / (len * len) * dFb / r : 0.0f;
+      // F = k (1 - l0/len) d, dlen/dd = d / r: one reciprocal square root and one division
+      const float rinv = nrm > 0.0f ? rsqrtf(nrm) : 0.0f;
+      const float r = nrm * rinv, inv = 1.0f / (r + kMsEps);
+      gl[j] -= P.k * dFb * inv;
+      const float c1 = P.k * (1.0f - l0[j] * inv);
+      const float c2 = P.k * l0[j] * inv * inv * dFb * rinv;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         const float db = c1 * Fb[c] + c2 * d[c];
