@@ -271,6 +271,13 @@ int mpm_get_info(mpm_handle* h, int32_t key, int64_t* value);
  * recorded events.  launches, total_ms: host. */
 int mpm_get_profile(mpm_handle* h, int32_t kind, int64_t* launches, double* total_ms);
 
+/* Diagnostics (sub-stage tests): the (m, p) grid that P2G scatters from the initial state
+ * (the first pass of a forward), copied densely to grid: device float [n_scenes][n_grid^dim]
+ * [4] = (m, p_0, .., p_{dim-1}, 0 ...), node (i0, i1[, i2]) at (i0 n + i1)[n + i2].  Needs
+ * mpm_set_initial; leaves any recorded forward intact.  MPM_ERR_ARG in the deterministic mode
+ * (its grids are fixed point) or with a controller. */
+int mpm_initial_p2g_grid(mpm_handle* h, float* grid, void* stream);
+
 /* Message of the last failure on this handle (static storage if h is NULL). */
 const char* mpm_last_error(mpm_handle* h);
 

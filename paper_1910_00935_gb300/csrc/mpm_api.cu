@@ -1446,6 +1446,29 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   return MPM_OK;
 }
 
+int mpm_initial_p2g_grid(mpm_handle* h, float* grid, void* stream) {
+  if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  if (!grid) return fail(h, MPM_ERR_ARG, "grid is NULL");
+  if (!h->initialized) return fail(h, MPM_ERR_STATE, "mpm_set_initial has not been called");
+  if (h->m.words != 1 || h->m.ctrl_H > 0)
+    return fail(h, MPM_ERR_ARG, "not available in the deterministic mode or with a controller");
+  if (h->desc.material == MPM_MIXED && !h->materials_set)
+    return fail(h, MPM_ERR_STATE, "MPM_MIXED: mpm_set_particle_materials has not been called");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  Launcher Lc{h, s};
+  ring_reset(h->pm);
+  ring_reset(h->ub);
+  int g = -1;
+  LK(Lc.step(kP2GOnly, 0, h->ckpt(0), nullptr, -1, &g));
+  CK(cudaMemcpyAsync(grid, ring_grid(h, h->pm, g), (size_t)h->m.S * h->m.nnodes * sizeof(float4),
+                     cudaMemcpyDeviceToDevice, s));
+  ring_release(h->pm, g);
+  LK(Lc.finish());
+  h->launches += Lc.count;
+  return MPM_OK;
+}
+
 int mpm_sync_status(mpm_handle* h) {
   if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
   cudaError_t e = cudaStreamSynchronize(h->last_stream);

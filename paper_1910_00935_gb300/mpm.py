@@ -42,7 +42,7 @@ MPM_INFO_KEEPS_SEGMENT_GRIDS, MPM_INFO_ACT_PARAMS, MPM_INFO_CKPT_EVERY = 4, 5, 6
 EXPORTED = ["mpm_workspace_bytes", "mpm_create", "mpm_set_initial", "mpm_forward",
             "mpm_get_state", "mpm_loss", "mpm_backward", "mpm_sync_status", "mpm_set_option",
             "mpm_get_info", "mpm_get_profile", "mpm_last_error", "mpm_destroy",
-            "mpm_step_noalloc", "mpm_set_particle_materials"]
+            "mpm_step_noalloc", "mpm_set_particle_materials", "mpm_initial_p2g_grid"]
 
 
 class MPMError(RuntimeError):
@@ -109,6 +109,7 @@ def lib(load_only: bool = False):
             "mpm_destroy": (None, [vp]),
             "mpm_step_noalloc": (ctypes.c_int, [D, vp, vp, vp, vp, vp, vp]),
             "mpm_set_particle_materials": (ctypes.c_int, [vp, vp, vp]),
+            "mpm_initial_p2g_grid": (ctypes.c_int, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -215,6 +216,10 @@ def mpm_get_info(h, key: int) -> int:
     out = ctypes.c_int64()
     _check(lib().mpm_get_info(h, key, ctypes.byref(out)), h)
     return out.value
+
+
+def mpm_initial_p2g_grid(h, grid, stream=None):
+    _check(lib().mpm_initial_p2g_grid(h, _ptr(grid), _stream(stream)), h)
 
 
 def mpm_get_profile(h, kind: int):

@@ -121,6 +121,43 @@ def test_one_step_matches_oracle(mpm, name, kw):
     _compare_states(g["state"], _oracle_states(scene, 1), scene, STEP_TOL)
 
 
+@pytest.mark.parametrize("name,kw", [("cube3d", dict(n_side=24, n_grid=64)),
+                                     ("rects2d", dict(n_scenes=3, n_min=300, n_max=900)),
+                                     ("robots3d", dict(n_scenes=2, dims=(12, 8, 8)))])
+def test_p2g_grid_matches_oracle(mpm, name, kw):
+    """Sub-stage: the (m, p) grid one P2G pass scatters from the initial state (stress,
+    actuation and the APIC affine term included) against the oracle's P2G, per scene."""
+    scene = scenes.make(name, **kw)
+    sim = mpm.from_scene(scene, max_steps=2)
+    d, n, S = scene["desc"]["dim"], scene["desc"]["n_grid"], len(scene["desc"]["n_particles"])
+    grid = torch.empty(S, n ** d, 4, device="cuda")
+    mpm.mpm_initial_p2g_grid(sim.h, grid)
+    assert mpm.mpm_sync_status(sim.h) == mpm.MPM_OK
+    sim.close()
+    g = grid.cpu().numpy().astype(np.float64)
+    a = scene["arrays"]
+    for si in range(S):
+        sl = scene_slice(scene, si)
+        mu, la = oracle.lame(a["E"][sl], a["nu"][sl])
+        grp = a["group"][sl] if scene["desc"]["n_groups"] else None
+        w = a["w"][si] if scene["desc"]["n_groups"] else None
+        gm, gp = oracle.p2g(oracle.scene_params(scene, sl), 0, a["x0"][:, sl], a["v0"][:, sl],
+                            a["C0"][:, sl], a["F0"][:, sl], mu, la, grp, w)
+        assert rel_l2(g[si, :, 0], gm) <= 1e-6, (si, "m")
+        assert rel_l2(g[si, :, 1:1 + d], gp) <= 1e-6, (si, "p")
+
+
+def test_one_step_adjoint_matches_oracle(mpm):
+    """Sub-stage: the adjoint of a single step (the G2P-adjoint pass from the seeds and the
+    last P2G-adjoint pass) against the oracle's step adjoint, given the same seeds."""
+    scene = scenes.make("robots3d", n_scenes=2, dims=(12, 8, 8))
+    seeds = _random_seeds(scene, np.random.default_rng(11))
+    g = _run_gpu(mpm, scene, 1, seeds=seeds, loss=False)
+    o = _oracle_grad_linear(scene, 1, {kk: v.astype(np.float64) for kk, v in seeds.items()})
+    for key in ("gx0", "gv0", "gC0", "gF0", "gE", "gnu", "gw"):
+        assert rel_l2(g["grad"][key], o[key]) <= 1e-5, key
+
+
 # ---------------------------------------------------------------------------
 # the workloads' forward passes
 # ---------------------------------------------------------------------------
