@@ -179,6 +179,31 @@ def test_ragged_tiles_and_uneven_batch(mpm):
     _compare_states(g["state"], _oracle_states(scene, T), scene, POS_TOL)
 
 
+@pytest.mark.parametrize("n_min,n_max", [(1, 3), (1, 300)])
+def test_degenerate_and_tiny_scenes(mpm, n_min, n_max):
+    """Scenes of one to three particles (a lone particle keeps C = 0 and F = I, so its
+    material gradients vanish) and a batch spanning 4 to 210 particles (partial tiles,
+    scenes smaller than a warp) in one batch: states and the gradients of a random
+    functional against the oracle."""
+    scene = scenes.make("rects2d", n_scenes=8, n_min=n_min, n_max=n_max)
+    T = 16
+    seeds = _random_seeds(scene, np.random.default_rng(5))
+    g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    d, dx = 2, 1.0 / scene["desc"]["n_grid"]
+    # C of a lone particle is 0 in exact arithmetic (its 9 weighted node terms cancel); in
+    # FP32 each term is about (4/dx) |v|, so C is compared on that absolute scale
+    c_bar = 16 * np.finfo(np.float32).eps * (4 / dx) * np.abs(scene["arrays"]["v0"]).max()
+    for si, blk in enumerate(_oracle_states(scene, T)):
+        sl = scene_slice(scene, si)
+        ox, ov, oC, oF = oracle.unpack_state(blk, d, sl.stop - sl.start)
+        gx, gv, gC, gF = [a[:, sl] for a in g["state"]]
+        assert rel_l2(gx, ox) <= POS_TOL and rel_l2(gF, oF) <= POS_TOL, si
+        assert rel_l2(gv, ov) <= 10 * POS_TOL, si
+        assert np.abs(gC - oC).max() <= c_bar, (si, np.abs(gC - oC).max(), c_bar)
+    o = _oracle_grad_linear(scene, T, {k: v.astype(np.float64) for k, v in seeds.items()})
+    _compare_grads(g["grad"], o, ("gx0", "gv0", "gC0", "gF0", "gE", "gnu"))
+
+
 def test_rects2d_batch_forward(mpm):
     scene = scenes.make("rects2d")  # 64 scenes, log-uniform sizes
     T = 32
