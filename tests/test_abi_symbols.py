@@ -103,6 +103,7 @@ def test_host_side_validation_without_gpu(libpath):
     # NULL handle
     assert mpm.lib().mpm_forward(None, 1, None) == mpm.MPM_ERR_ARG
     assert mpm.lib().mpm_sync_status(None) == mpm.MPM_ERR_ARG
+    assert mpm.lib().mpm_initial_p2g_grid(None, None, None) == mpm.MPM_ERR_ARG
 
 
 def test_mass_spring_binding_and_host_validation(libpath):

@@ -451,6 +451,17 @@ def test_state_errors(mpm):
     with pytest.raises(mpm.MPMError) as e:
         sim.forward(4)  # before set_initial
     assert e.value.code == mpm.MPM_ERR_STATE
+    grid = torch.empty(128 * 128, 4, device="cuda")
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.mpm_initial_p2g_grid(sim.h, grid)
+    assert e.value.code == mpm.MPM_ERR_STATE
+    sim.close()
+    det = scenes.make("square2d", n_side=8)
+    det["desc"]["deterministic_p2g"] = 1
+    sim = mpm.from_scene(det, max_steps=8)
+    with pytest.raises(mpm.MPMError) as e:  # its grids are fixed point
+        mpm.mpm_initial_p2g_grid(sim.h, grid)
+    assert e.value.code == mpm.MPM_ERR_ARG
     sim.close()
     sim = mpm.from_scene(scene, max_steps=8)
     with pytest.raises(mpm.MPMError) as e:
