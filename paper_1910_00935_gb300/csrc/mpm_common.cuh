@@ -492,7 +492,8 @@ __device__ __forceinline__ void polar_to_cache(double* Rc, int64_t N, int64_t p,
 // W S + S W = R^T dF - dF^T R; the adjoint is Fbar += 2 R Y where Y is the
 // antisymmetric solution of Y S + S Y = skew(R^T Rbar).  In 3D that equation is
 // (tr(S) I - S) y = b on axial vectors (eigenvalues sigma_i + sigma_j > 0), in 2D
-// y = b / tr(S); no singular-value differences appear.
+// y = b / tr(S); no singular-value differences appear.  The products and the solve run in
+// FP64; in 3D the final rotation of the solution (2 R Y) runs in FP32.
 template <int D>
 __device__ __forceinline__ void polar_adjoint_f64(const float E[D][D], const Polar<D>& p,
                                                   const float Rbar[D][D], float Fbar[D][D]) {
@@ -531,21 +532,29 @@ __device__ __forceinline__ void polar_adjoint_f64(const float E[D][D], const Pol
     double g12 = -0.5 * (S[1][2] + S[2][1]);
     double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
     double c11 = g00 * g22 - g02 * g02, c12 = g01 * g02 - g00 * g12, c22 = g00 * g11 - g01 * g01;
-    double det = g00 * c00 + g01 * c01 + g02 * c02;
-    double id = 1.0 / fmax(det, 1e-18);
-    double y0 = (c00 * b0 + c01 * b1 + c02 * b2) * id;
-    double y1 = (c01 * b0 + c11 * b1 + c12 * b2) * id;
-    double y2 = (c02 * b0 + c12 * b1 + c22 * b2) * id;
-    const double Y[3][3] = {{0.0, -y2, y1}, {y2, 0.0, -y0}, {-y1, y0, 0.0}};
+    const double det = fmax(g00 * c00 + g01 * c01 + g02 * c02, 1e-18);
+    // 1/det: FP32 reciprocal, two FP64 Newton steps (relative error ~1e-28 -> FP64 ulps);
+    // a plain division beyond the FP32 seed's range
+    double id;
+    if (det < 1e30) {
+      id = (double)__frcp_rn((float)det);
+      id = id * (2.0 - det * id);
+      id = id * (2.0 - det * id);
+    } else {
+      id = 1.0 / det;
+    }
+    // 2y, rounded once: the rotation 2 R Y below is well conditioned (|2 R Y| = 2|y|), so it
+    // runs in FP32 on R rounded to FP32, with the error of the FP32 accumulation into Fbar
+    const float y0 = (float)(2.0 * (c00 * b0 + c01 * b1 + c02 * b2) * id);
+    const float y1 = (float)(2.0 * (c01 * b0 + c11 * b1 + c12 * b2) * id);
+    const float y2 = (float)(2.0 * (c02 * b0 + c12 * b1 + c22 * b2) * id);
+    // (R Y)[i][j] with Y = [[0, -y2, y1], [y2, 0, -y0], [-y1, y0, 0]]
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) s += p.R[i][k] * Y[k][j];
-        Fbar[i][j] += (float)(2.0 * s);
-      }
+    for (int i = 0; i < 3; ++i) {
+      Fbar[i][0] += p.Rf[i][1] * y2 - p.Rf[i][2] * y1;
+      Fbar[i][1] += p.Rf[i][2] * y0 - p.Rf[i][0] * y2;
+      Fbar[i][2] += p.Rf[i][0] * y1 - p.Rf[i][1] * y0;
+    }
   }
 }
 
