@@ -252,6 +252,13 @@ def make_workload(name, seed=0):
         "robots_nn": "4 batched 3D robots x 27,648 particles, 64^3 grids, fixed-corotated, "
                      "8 groups driven by a closed-loop MLP controller (52 inputs, 32 tanh "
                      "units), T=512, ckpt 64",
+        "liquid2d": "2D dam break: 6,144 weakly compressible liquid particles (Tait, E=500 "
+                    "nu=0.3), 128^2 grid, dt=1e-4, T=256, ckpt 32, COM loss",
+        "liquid3d": "3D dam break: 49,152 weakly compressible liquid particles (Tait, E=500 "
+                    "nu=0.3), 64^3 grid, dt=1e-4, T=256, ckpt 32, COM loss",
+        "robot_in_liquid": "3D actuated fixed-corotated robot (8,192 particles, 8 groups x 4 "
+                           "sine terms) in a liquid pool (55,296 particles), per-particle "
+                           "materials in one 64^3 grid, T=256, ckpt 32, x-displacement loss",
     }.get(name, name)
     return scene, N, d["steps"], descr
 
