@@ -37,6 +37,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mpm_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
+_LIB_OMP = os.path.join(_LIBDIR, "liboracle_omp.so")
 
 OK, ERR_ARG, ERR_MEM, ERR_OOB, ERR_DOMAIN = 0, 1, 2, 3, 4
 FIXED_COROTATED, NEO_HOOKEAN, NO_ELASTICITY, LIQUID, MIXED = 0, 1, 2, 3, 4
@@ -69,26 +70,31 @@ class Params(ctypes.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile mpm_oracle.c into _build/liboracle.so (plain C, -O3, no -march)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile mpm_oracle.c into _build/liboracle.so (plain C, -O3, no -march), or with
+    openmp=True into _build/liboracle_omp.so: the same source with -fopenmp, whose particle
+    loops run on all host cores (per-thread private grids summed in thread order)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O3", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+            ["gcc", "-O3", "-std=c99", "-fPIC", "-shared"] + (["-fopenmp"] if openmp else [])
+            + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 def lib():
     """Load the oracle library (ORACLE_LIB overrides the path; the mutation tests use
-    it to load deliberately broken copies of the oracle)."""
+    it to load deliberately broken copies of the oracle).  ORACLE_OPENMP=1 loads the
+    OpenMP build instead of the serial one (a process uses one of the two)."""
     global _lib
     with _lock:
         if _lib is None:
             path = os.environ.get("ORACLE_LIB")
             if not path:
-                path = build()
+                path = build(openmp=os.environ.get("ORACLE_OPENMP", "0") == "1")
             L = ctypes.CDLL(path)
             P = ctypes.POINTER(Params)
             d = ctypes.POINTER(ctypes.c_double)
@@ -118,6 +124,7 @@ def lib():
                 "orc_ctrl_n_inputs": (I, [P]),
                 "orc_ctrl_n_params": (I64, [P]),
                 "orc_controller": (I, [P, d, I64, I, d, d, i32, d, d]),
+                "orc_threads": (I, [I]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -167,6 +174,11 @@ def make_params(dim, n_grid, dt, gravity=(0.0, -9.8, 0.0), wall_cells=3,
     p.ctrl_hidden = int(ctrl_hidden)
     p.ctrl_scale = float(ctrl_scale)
     return p
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the oracle's particle loops (1 for the serial build); n > 0 sets it."""
+    return int(lib().orc_threads(int(n)))
 
 
 def n_act_params(params) -> int:

@@ -834,6 +834,172 @@ static double particle_act(const orc_params* P, const int32_t* grp, const double
   return gact[g];
 }
 
+/* constants of one step shared by the per-particle helpers */
+typedef struct {
+  double dx, inv_dx2, vol, m, kappa;
+  int nst;
+} step_consts;
+
+static step_consts consts_of(const orc_params* P) {
+  step_consts k;
+  int n = P->n_grid;
+  k.dx = 1.0 / n;
+  k.inv_dx2 = 1.0 / (k.dx * k.dx);
+  k.vol = particle_volume(P);
+  k.m = P->rho * k.vol;
+  k.kappa = -P->dt * k.vol * 4.0 / (k.dx * k.dx);
+  k.nst = (int)ipow(3, P->dim);
+  return k;
+}
+
+/* P2G of particle p: its stress, the affine matrix A = kappa tau + m C, and the scatter of
+   mass and momentum into (gm, gp) */
+static int p2g_particle(const orc_params* P, const step_consts* K, int64_t np, int64_t p,
+                        const double* x, const double* v, const double* C, const double* F,
+                        const double* mu, const double* la, const int32_t* grp,
+                        const double* gact, double* gm, double* gp) {
+  int d = P->dim, n = P->n_grid;
+  double m = K->m, kappa = K->kappa;
+  double xp[3] = {0, 0, 0};
+  for (int a = 0; a < d; a++) xp[a] = x[a * np + p];
+  stencil s;
+  int rc = make_stencil(P, xp, &s);
+  if (rc) return rc;
+  mat3 Fp, Cp, tau, A;
+  load_mat(d, F, np, p, Fp);
+  load_mat(d, C, np, p, Cp);
+  int axis;
+  double act = particle_act(P, grp, gact, p, &axis);
+  rc = kirchhoff_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tau);
+  if (rc) return rc;
+  mzero(A);
+  for (int i = 0; i < d; i++)
+    for (int j = 0; j < d; j++) A[i][j] = kappa * tau[i][j] + m * Cp[i][j];
+  for (int o = 0; o < K->nst; o++) {
+    int off[3], idx[3];
+    double W, gW[3], dpos[3];
+    offset_of(d, o, off);
+    stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
+    int64_t ni = node_index(d, n, idx);
+    gm[ni] += W * m;
+    for (int a = 0; a < d; a++) {
+      double Ad = 0.0;
+      for (int b = 0; b < d; b++) Ad += A[a][b] * dpos[b];
+      gp[ni * d + a] += W * (m * v[a * np + p] + Ad);
+    }
+  }
+  return ORC_OK;
+}
+
+#ifdef _OPENMP
+/* ------------------------------------------------------------------ */
+/* OpenMP build (liboracle_omp.so, the all-cores CPU baseline): the same per-particle      */
+/* helpers run over the particles in parallel; a scatter goes into a private grid per     */
+/* thread, and the private grids are summed node by node in thread order over the box    */
+/* the stencils touch.  The serial build (no -fopenmp) never compiles this section.       */
+/* ------------------------------------------------------------------ */
+#include <omp.h>
+
+/* node box [lo, hi] covering every particle's 3^d stencil (clipped to the grid) */
+static int64_t stencil_box(const orc_params* P, int64_t np, const double* x, int lo[3],
+                           int hi[3]) {
+  int d = P->dim, n = P->n_grid;
+  int64_t vol = 1;
+  for (int a = 0; a < 3; a++) lo[a] = hi[a] = 0;
+  for (int a = 0; a < d; a++) {
+    double bmin = (double)n, bmax = -1.0;
+    for (int64_t p = 0; p < np; p++) {
+      double b = floor(x[a * np + p] * (double)n - 0.5);
+      if (b < bmin) bmin = b;
+      if (b > bmax) bmax = b;
+    }
+    lo[a] = bmin < 0.0 ? 0 : (bmin > n - 1 ? n - 1 : (int)bmin);
+    hi[a] = bmax + 2.0 > n - 1 ? n - 1 : (bmax + 2.0 < 0.0 ? 0 : (int)bmax + 2);
+    if (hi[a] < lo[a]) return 0;
+    vol *= hi[a] - lo[a] + 1;
+  }
+  return vol;
+}
+
+static void box_node(int d, const int lo[3], const int hi[3], int64_t l, int idx[3]) {
+  idx[0] = idx[1] = idx[2] = 0;
+  for (int a = d - 1; a >= 0; a--) {
+    int64_t e = hi[a] - lo[a] + 1;
+    idx[a] = lo[a] + (int)(l % e);
+    l /= e;
+  }
+}
+
+/* out[node * w + c] = sum over threads (in thread order) of priv[tid][node * w + c], over
+   the box's nodes; out is zero elsewhere */
+static void reduce_private(const orc_params* P, int nth, const double* priv, int64_t stride,
+                           int w, const int lo[3], const int hi[3], int64_t bvol, double* out) {
+  int d = P->dim, n = P->n_grid;
+#pragma omp parallel for schedule(static)
+  for (int64_t l = 0; l < bvol; l++) {
+    int idx[3];
+    box_node(d, lo, hi, l, idx);
+    int64_t ni = node_index(d, n, idx);
+    for (int c = 0; c < w; c++) {
+      double s = 0.0;
+      for (int t = 0; t < nth; t++) s += priv[(int64_t)t * stride + ni * w + c];
+      out[ni * w + c] = s;
+    }
+  }
+}
+
+static int p2g_omp(const orc_params* P, int64_t np, const double* x, const double* v,
+                   const double* C, const double* F, const double* mu, const double* la,
+                   const int32_t* grp, const double* gact, double* gm, double* gp) {
+  int d = P->dim;
+  int64_t nn = ipow(P->n_grid, d);
+  step_consts K = consts_of(P);
+  int nth = omp_get_max_threads();
+  int lo[3], hi[3];
+  int64_t bvol = stencil_box(P, np, x, lo, hi);
+  double* pm = (double*)calloc((size_t)nth * nn, sizeof(double));
+  double* pp = (double*)calloc((size_t)nth * nn * d, sizeof(double));
+  if (!pm || !pp) {
+    free(pm);
+    free(pp);
+    return ORC_ERR_MEM;
+  }
+  int err = ORC_OK;
+#pragma omp parallel num_threads(nth)
+  {
+    int tid = omp_get_thread_num();
+#pragma omp for schedule(static)
+    for (int64_t p = 0; p < np; p++) {
+      int rc = p2g_particle(P, &K, np, p, x, v, C, F, mu, la, grp, gact, pm + (int64_t)tid * nn,
+                            pp + (int64_t)tid * nn * d);
+      if (rc) {
+#pragma omp atomic write
+        err = rc;
+      }
+    }
+  }
+  if (!err) {
+    reduce_private(P, nth, pm, nn, 1, lo, hi, bvol, gm);
+    reduce_private(P, nth, pp, nn * d, d, lo, hi, bvol, gp);
+  }
+  free(pm);
+  free(pp);
+  return err;
+}
+#endif
+
+/* threads the particle loops use: 1 in the serial build; in the OpenMP build n > 0 sets
+   the count, and the current count is returned */
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* P2G (Appendix D "p2g"): scatter mass and APIC/MLS momentum.  gm[n^d] and
    gp[n^d * d] are overwritten (cleared first, "clear_grid"). */
 int orc_p2g(const orc_params* P, int64_t np, int t, const double* x, const double* v,
@@ -843,41 +1009,16 @@ int orc_p2g(const orc_params* P, int64_t np, int t, const double* x, const doubl
   int64_t nn = ipow(n, d);
   memset(gm, 0, sizeof(double) * nn);
   memset(gp, 0, sizeof(double) * nn * d);
-  double dx = 1.0 / n, vol = particle_volume(P), m = P->rho * vol;
-  double kappa = -P->dt * vol * 4.0 / (dx * dx);
-  int nst = (int)ipow(3, d);
   double gact[ORC_CTRL_MAX_GROUPS];
   int rca = group_actuation(P, np, t, x, v, grp, wact, gact);
   if (rca) return rca;
+#ifdef _OPENMP
+  if (omp_get_max_threads() > 1) return p2g_omp(P, np, x, v, C, F, mu, la, grp, gact, gm, gp);
+#endif
+  step_consts K = consts_of(P);
   for (int64_t p = 0; p < np; p++) {
-    double xp[3] = {0, 0, 0};
-    for (int a = 0; a < d; a++) xp[a] = x[a * np + p];
-    stencil s;
-    int rc = make_stencil(P, xp, &s);
+    int rc = p2g_particle(P, &K, np, p, x, v, C, F, mu, la, grp, gact, gm, gp);
     if (rc) return rc;
-    mat3 Fp, Cp, tau, A;
-    load_mat(d, F, np, p, Fp);
-    load_mat(d, C, np, p, Cp);
-    int axis;
-    double act = particle_act(P, grp, gact, p, &axis);
-    rc = kirchhoff_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tau);
-    if (rc) return rc;
-    mzero(A);
-    for (int i = 0; i < d; i++)
-      for (int j = 0; j < d; j++) A[i][j] = kappa * tau[i][j] + m * Cp[i][j];
-    for (int o = 0; o < nst; o++) {
-      int off[3], idx[3];
-      double W, gW[3], dpos[3];
-      offset_of(d, o, off);
-      stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
-      int64_t ni = node_index(d, n, idx);
-      gm[ni] += W * m;
-      for (int a = 0; a < d; a++) {
-        double Ad = 0.0;
-        for (int b = 0; b < d; b++) Ad += A[a][b] * dpos[b];
-        gp[ni * d + a] += W * (m * v[a * np + p] + Ad);
-      }
-    }
   }
   return ORC_OK;
 }
@@ -886,6 +1027,7 @@ int orc_p2g(const orc_params* P, int64_t np, int t, const double* x, const doubl
 void orc_grid_update(const orc_params* P, const double* gm, const double* gp, double* gu) {
   int d = P->dim, n = P->n_grid;
   int64_t nn = ipow(n, d);
+#pragma omp parallel for schedule(static)
   for (int64_t ni = 0; ni < nn; ni++) {
     int idx[3] = {0, 0, 0};
     int64_t r = ni;
@@ -899,50 +1041,64 @@ void orc_grid_update(const orc_params* P, const double* gm, const double* gp, do
   }
 }
 
-/* G2P (Appendix D "g2p"): gather velocity and affine matrix, advect, update F. */
-int orc_g2p(const orc_params* P, int64_t np, const double* x, const double* F, const double* gu,
-            double* x1, double* v1, double* C1, double* F1) {
+/* G2P of particle p (Appendix D "g2p"): gather velocity and affine matrix, advect, update F */
+static int g2p_particle(const orc_params* P, int64_t np, int64_t p, const double* x,
+                        const double* F, const double* gu, double* x1, double* v1, double* C1,
+                        double* F1) {
   int d = P->dim, n = P->n_grid;
   double dx = 1.0 / n;
   int nst = (int)ipow(3, d);
-  for (int64_t p = 0; p < np; p++) {
-    double xp[3] = {0, 0, 0};
-    for (int a = 0; a < d; a++) xp[a] = x[a * np + p];
-    stencil s;
-    int rc = make_stencil(P, xp, &s);
-    if (rc) return rc;
-    double vn[3] = {0, 0, 0};
-    mat3 B;
-    mzero(B);
-    for (int o = 0; o < nst; o++) {
-      int off[3], idx[3];
-      double W, gW[3], dpos[3];
-      offset_of(d, o, off);
-      stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
-      int64_t ni = node_index(d, n, idx);
-      for (int a = 0; a < d; a++) {
-        double ui = gu[ni * d + a];
-        vn[a] += W * ui;
-        for (int b = 0; b < d; b++) B[a][b] += W * ui * dpos[b];
-      }
-    }
-    mat3 Cn, Fp, G, Fn;
-    mzero(Cn);
-    for (int a = 0; a < d; a++)
-      for (int b = 0; b < d; b++) Cn[a][b] = 4.0 / (dx * dx) * B[a][b];
-    load_mat(d, F, np, p, Fp);
-    meye(d, G);
-    for (int a = 0; a < d; a++)
-      for (int b = 0; b < d; b++) G[a][b] += P->dt * Cn[a][b];
-    mmul(d, G, Fp, Fn);
+  double xp[3] = {0, 0, 0};
+  for (int a = 0; a < d; a++) xp[a] = x[a * np + p];
+  stencil s;
+  int rc = make_stencil(P, xp, &s);
+  if (rc) return rc;
+  double vn[3] = {0, 0, 0};
+  mat3 B;
+  mzero(B);
+  for (int o = 0; o < nst; o++) {
+    int off[3], idx[3];
+    double W, gW[3], dpos[3];
+    offset_of(d, o, off);
+    stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
+    int64_t ni = node_index(d, n, idx);
     for (int a = 0; a < d; a++) {
-      x1[a * np + p] = xp[a] + P->dt * vn[a];
-      v1[a * np + p] = vn[a];
+      double ui = gu[ni * d + a];
+      vn[a] += W * ui;
+      for (int b = 0; b < d; b++) B[a][b] += W * ui * dpos[b];
     }
-    store_mat(d, C1, np, p, Cn);
-    store_mat(d, F1, np, p, Fn);
   }
+  mat3 Cn, Fp, G, Fn;
+  mzero(Cn);
+  for (int a = 0; a < d; a++)
+    for (int b = 0; b < d; b++) Cn[a][b] = 4.0 / (dx * dx) * B[a][b];
+  load_mat(d, F, np, p, Fp);
+  meye(d, G);
+  for (int a = 0; a < d; a++)
+    for (int b = 0; b < d; b++) G[a][b] += P->dt * Cn[a][b];
+  mmul(d, G, Fp, Fn);
+  for (int a = 0; a < d; a++) {
+    x1[a * np + p] = xp[a] + P->dt * vn[a];
+    v1[a * np + p] = vn[a];
+  }
+  store_mat(d, C1, np, p, Cn);
+  store_mat(d, F1, np, p, Fn);
   return ORC_OK;
+}
+
+/* G2P (Appendix D "g2p") of every particle (independent: parallel in the OpenMP build) */
+int orc_g2p(const orc_params* P, int64_t np, const double* x, const double* F, const double* gu,
+            double* x1, double* v1, double* C1, double* F1) {
+  int err = ORC_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < np; p++) {
+    int rc = g2p_particle(P, np, p, x, F, gu, x1, v1, C1, F1);
+    if (rc) {
+#pragma omp atomic write
+      err = rc;
+    }
+  }
+  return err;
 }
 
 typedef struct {
@@ -999,6 +1155,264 @@ int orc_run(const orc_params* P, int64_t np, int T, const double* mu, const doub
 /* adjoint of one step (Appendix D.1 "advance_grad")                    */
 /* ------------------------------------------------------------------ */
 
+/* g2p.grad of particle p: the adjoint of x' = x + dt v' and F' = (I + dt C') F given the
+   adjoint of state s+1, with v' and C' gathered from the grid velocity gu.  Writes xb, Fb of
+   particle p and scatters the grid-velocity adjoint into gub. */
+static int g2p_grad_particle(const orc_params* P, const step_consts* K, int64_t np, int64_t p,
+                             const double* x, const double* F, const double* gu,
+                             const double* xb1, const double* vb1, const double* Cb1,
+                             const double* Fb1, double* gub, double* xb, double* Fb) {
+  int d = P->dim, n = P->n_grid, nst = K->nst;
+  double inv_dx2 = K->inv_dx2;
+  double xp[3] = {0, 0, 0};
+  for (int a = 0; a < d; a++) xp[a] = x[a * np + p];
+  stencil s;
+  int rc = make_stencil(P, xp, &s);
+  if (rc) return rc;
+  /* recompute C' of this particle */
+  mat3 B;
+  mzero(B);
+  for (int o = 0; o < nst; o++) {
+    int off[3], idx[3];
+    double W, gW[3], dpos[3];
+    offset_of(d, o, off);
+    stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
+    int64_t ni = node_index(d, n, idx);
+    for (int a = 0; a < d; a++)
+      for (int b = 0; b < d; b++) B[a][b] += W * gu[ni * d + a] * dpos[b];
+  }
+  mat3 Cn, Fp, Fb1p, Cb1p, G, Gt, Fbp, Ct, Fpt, FbFt;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) Cn[a][b] = 4.0 * inv_dx2 * B[a][b];
+  load_mat(d, F, np, p, Fp);
+  load_mat(d, Fb1, np, p, Fb1p);
+  load_mat(d, Cb1, np, p, Cb1p);
+  /* x' = x + dt v'  ->  xbar += xbar', vtilde = vbar' + dt xbar' */
+  double xbp[3] = {0, 0, 0}, vt[3] = {0, 0, 0};
+  for (int a = 0; a < d; a++) {
+    xbp[a] = xb1[a * np + p];
+    vt[a] = vb1[a * np + p] + P->dt * xb1[a * np + p];
+  }
+  /* F' = (I + dt C') F  ->  Fbar = (I + dt C')^T Fbar', Ctilde = Cbar' + dt Fbar' F^T */
+  meye(d, G);
+  for (int a = 0; a < d; a++)
+    for (int b = 0; b < d; b++) G[a][b] += P->dt * Cn[a][b];
+  mtrans(d, G, Gt);
+  mmul(d, Gt, Fb1p, Fbp);
+  mtrans(d, Fp, Fpt);
+  mmul(d, Fb1p, Fpt, FbFt);
+  mzero(Ct);
+  for (int a = 0; a < d; a++)
+    for (int b = 0; b < d; b++) Ct[a][b] = Cb1p[a][b] + P->dt * FbFt[a][b];
+  /* v' = sum W u_i ; C' = (4/dx^2) sum W u_i dpos^T */
+  for (int o = 0; o < nst; o++) {
+    int off[3], idx[3];
+    double W, gW[3], dpos[3];
+    offset_of(d, o, off);
+    stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
+    int64_t ni = node_index(d, n, idx);
+    const double* u = gu + ni * d;
+    double Wbar = 0.0;
+    for (int a = 0; a < d; a++) {
+      double Cd = 0.0;
+      for (int b = 0; b < d; b++) Cd += Ct[a][b] * dpos[b];
+      gub[ni * d + a] += W * vt[a] + 4.0 * inv_dx2 * W * Cd;
+      Wbar += vt[a] * u[a] + 4.0 * inv_dx2 * u[a] * Cd;
+    }
+    for (int b = 0; b < d; b++) {
+      double CtU = 0.0; /* (Ctilde^T u)_b */
+      for (int a = 0; a < d; a++) CtU += Ct[a][b] * u[a];
+      xbp[b] += Wbar * gW[b] - 4.0 * inv_dx2 * W * CtU;
+    }
+  }
+  for (int a = 0; a < d; a++) xb[a * np + p] = xbp[a];
+  store_mat(d, Fb, np, p, Fbp);
+  return ORC_OK;
+}
+
+/* p2g.grad of particle p and its stress / actuation adjoint, given the momentum and mass
+   adjoints (gpb, gmb) of the grid.  Adds to xb, Fb, mubar, labar of particle p, writes vb, Cb,
+   and accumulates the actuation adjoint into wbar (open loop) or gabar (closed loop). */
+static int p2g_grad_particle(const orc_params* P, const step_consts* K, int64_t np, int t,
+                             int64_t p, const double* x, const double* v, const double* C,
+                             const double* F, const double* mu, const double* la,
+                             const int32_t* grp, const double* wact, const double* gact,
+                             const double* gpb, const double* gmb, double* xb, double* vb,
+                             double* Cb, double* Fb, double* mubar, double* labar, double* wbar,
+                             double* gabar) {
+  int d = P->dim, n = P->n_grid, nst = K->nst;
+  double m = K->m, kappa = K->kappa;
+  double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0};
+  for (int a = 0; a < d; a++) {
+    xp[a] = x[a * np + p];
+    vp[a] = v[a * np + p];
+  }
+  stencil s;
+  int rc = make_stencil(P, xp, &s);
+  if (rc) return rc;
+  mat3 Fp, Cp, tau, A, Abar, Fbp;
+  load_mat(d, F, np, p, Fp);
+  load_mat(d, C, np, p, Cp);
+  int axis;
+  double act = particle_act(P, grp, gact, p, &axis);
+  rc = kirchhoff_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tau);
+  if (rc) return rc;
+  mzero(A);
+  for (int i = 0; i < d; i++)
+    for (int j = 0; j < d; j++) A[i][j] = kappa * tau[i][j] + m * Cp[i][j];
+  mzero(Abar);
+  double vbp[3] = {0, 0, 0}, xbp[3] = {0, 0, 0};
+  for (int o = 0; o < nst; o++) {
+    int off[3], idx[3];
+    double W, gW[3], dpos[3];
+    offset_of(d, o, off);
+    stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
+    int64_t ni = node_index(d, n, idx);
+    const double* pb = gpb + ni * d;
+    /* p_i += W (m v + A dpos) ; m_i += W m */
+    double Wbar = m * gmb[ni];
+    for (int a = 0; a < d; a++) {
+      double Ad = 0.0;
+      for (int b = 0; b < d; b++) Ad += A[a][b] * dpos[b];
+      Wbar += pb[a] * (m * vp[a] + Ad);
+      vbp[a] += W * m * pb[a];
+      for (int b = 0; b < d; b++) Abar[a][b] += W * pb[a] * dpos[b];
+    }
+    for (int b = 0; b < d; b++) {
+      double AtP = 0.0; /* (A^T pbar)_b */
+      for (int a = 0; a < d; a++) AtP += A[a][b] * pb[a];
+      xbp[b] += Wbar * gW[b] - W * AtP;
+    }
+  }
+  /* A = kappa tau + m C */
+  mat3 tb, Cbp;
+  mzero(tb);
+  mzero(Cbp);
+  for (int i = 0; i < d; i++)
+    for (int j = 0; j < d; j++) {
+      tb[i][j] = kappa * Abar[i][j];
+      Cbp[i][j] = m * Abar[i][j];
+    }
+  load_mat(d, Fb, np, p, Fbp);
+  double abar = 0.0;
+  rc = kirchhoff_adjoint_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tb, Fbp, &mubar[p],
+                           &labar[p], &abar);
+  if (rc) return rc;
+  if (P->n_groups > 0 && grp && wact && wbar) {
+    int gi = grp[p];
+    if (gi >= 0 && gi < P->n_groups) {
+      if (P->ctrl_hidden > 0)
+        gabar[gi] += abar;
+      else
+        for (int k = 1; k <= P->n_basis; k++)
+          wbar[gi * P->n_basis + (k - 1)] += abar * act_basis(P, k, t);
+    }
+  }
+  for (int a = 0; a < d; a++) {
+    xb[a * np + p] += xbp[a];
+    vb[a * np + p] = vbp[a];
+  }
+  store_mat(d, Cb, np, p, Cbp);
+  store_mat(d, Fb, np, p, Fbp);
+  return ORC_OK;
+}
+
+/* grid_op.grad of every node (node-local) */
+static void grid_update_adjoint(const orc_params* P, const double* gm, const double* gp,
+                                const double* gub, double* gpb, double* gmb) {
+  int d = P->dim, n = P->n_grid;
+  int64_t nn = ipow(n, d);
+#pragma omp parallel for schedule(static)
+  for (int64_t ni = 0; ni < nn; ni++) {
+    int idx[3] = {0, 0, 0};
+    int64_t r = ni;
+    for (int a = d - 1; a >= 0; a--) {
+      idx[a] = (int)(r % n);
+      r /= n;
+    }
+    if (gm[ni] > 0.0 && !is_wall(P, idx)) {
+      double mb = 0.0;
+      for (int a = 0; a < d; a++) {
+        gpb[ni * d + a] = gub[ni * d + a] / gm[ni];
+        mb -= gub[ni * d + a] * gp[ni * d + a] / (gm[ni] * gm[ni]);
+      }
+      gmb[ni] = mb;
+    }
+  }
+}
+
+#ifdef _OPENMP
+/* g2p.grad over the particles in parallel: private grid-velocity adjoints summed in
+   thread order */
+static int g2p_grad_omp(const orc_params* P, const step_consts* K, int64_t np, const double* x,
+                        const double* F, const double* gu, const double* xb1, const double* vb1,
+                        const double* Cb1, const double* Fb1, double* gub, double* xb,
+                        double* Fb) {
+  int d = P->dim;
+  int64_t nn = ipow(P->n_grid, d);
+  int nth = omp_get_max_threads();
+  int lo[3], hi[3];
+  int64_t bvol = stencil_box(P, np, x, lo, hi);
+  double* pu = (double*)calloc((size_t)nth * nn * d, sizeof(double));
+  if (!pu) return ORC_ERR_MEM;
+  int err = ORC_OK;
+#pragma omp parallel num_threads(nth)
+  {
+    int tid = omp_get_thread_num();
+#pragma omp for schedule(static)
+    for (int64_t p = 0; p < np; p++) {
+      int rc = g2p_grad_particle(P, K, np, p, x, F, gu, xb1, vb1, Cb1, Fb1,
+                                 pu + (int64_t)tid * nn * d, xb, Fb);
+      if (rc) {
+#pragma omp atomic write
+        err = rc;
+      }
+    }
+  }
+  if (!err) reduce_private(P, nth, pu, nn * d, d, lo, hi, bvol, gub);
+  free(pu);
+  return err;
+}
+
+/* p2g.grad over the particles in parallel: per-thread actuation-adjoint partial sums,
+   added in thread order */
+static int p2g_grad_omp(const orc_params* P, const step_consts* K, int64_t np, int t,
+                        const double* x, const double* v, const double* C, const double* F,
+                        const double* mu, const double* la, const int32_t* grp,
+                        const double* wact, const double* gact, const double* gpb,
+                        const double* gmb, double* xb, double* vb, double* Cb, double* Fb,
+                        double* mubar, double* labar, double* wbar, double* gabar) {
+  int nth = omp_get_max_threads();
+  int nw = (P->n_groups > 0 && P->ctrl_hidden <= 0) ? P->n_groups * P->n_basis : 0;
+  int slot = nw + ORC_CTRL_MAX_GROUPS;
+  double* part = (double*)calloc((size_t)nth * slot, sizeof(double));
+  if (!part) return ORC_ERR_MEM;
+  int err = ORC_OK;
+#pragma omp parallel num_threads(nth)
+  {
+    int tid = omp_get_thread_num();
+    double* tw = part + (int64_t)tid * slot;
+#pragma omp for schedule(static)
+    for (int64_t p = 0; p < np; p++) {
+      int rc = p2g_grad_particle(P, K, np, t, p, x, v, C, F, mu, la, grp, wact, gact, gpb, gmb,
+                                 xb, vb, Cb, Fb, mubar, labar, wbar ? tw : NULL, tw + nw);
+      if (rc) {
+#pragma omp atomic write
+        err = rc;
+      }
+    }
+  }
+  for (int th = 0; th < nth && !err; th++) {
+    const double* tw = part + (int64_t)th * slot;
+    if (wbar)
+      for (int i = 0; i < nw; i++) wbar[i] += tw[i];
+    for (int g = 0; g < ORC_CTRL_MAX_GROUPS; g++) gabar[g] += tw[nw + g];
+  }
+  free(part);
+  return err;
+}
+#endif
+
 /* Given state_s and the adjoint of state_{s+1} (xb1, vb1, Cb1, Fb1), write the
    adjoint of state_s into (xb, vb, Cb, Fb) and accumulate mubar, labar (per
    particle) and wbar (the actuation parameters: w[g * K + k] open-loop, the controller's
@@ -1011,9 +1425,13 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
                      double* wbar) {
   int d = P->dim, n = P->n_grid;
   int64_t nn = ipow(n, d);
-  double dx = 1.0 / n, inv_dx2 = 1.0 / (dx * dx), vol = particle_volume(P), m = P->rho * vol;
-  double kappa = -P->dt * vol * 4.0 * inv_dx2;
-  int nst = (int)ipow(3, d);
+  step_consts K;
+  K.dx = 1.0 / n;
+  K.inv_dx2 = 1.0 / (K.dx * K.dx);
+  K.vol = particle_volume(P);
+  K.m = P->rho * K.vol;
+  K.kappa = -P->dt * K.vol * 4.0 * K.inv_dx2;
+  K.nst = (int)ipow(3, d);
   int rc;
 
   /* recompute the grid of this step: clear_grid, p2g, grid_op */
@@ -1026,6 +1444,7 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
   double* gub = (double*)calloc(nn * d, sizeof(double)); /* adjoint of grid velocity */
   double* gpb = (double*)calloc(nn * d, sizeof(double)); /* adjoint of grid momentum */
   double* gmb = (double*)calloc(nn, sizeof(double));     /* adjoint of grid mass */
+  double gact[ORC_CTRL_MAX_GROUPS], gabar[ORC_CTRL_MAX_GROUPS];
   if (!gub || !gpb || !gmb) {
     rc = ORC_ERR_MEM;
     goto done;
@@ -1035,168 +1454,39 @@ int orc_step_adjoint(const orc_params* P, int64_t np, int t, const double* x, co
   orc_grid_update(P, g.gm, g.gp, g.gu);
 
   /* g2p.grad */
-  for (int64_t p = 0; p < np; p++) {
-    double xp[3] = {0, 0, 0};
-    for (int a = 0; a < d; a++) xp[a] = x[a * np + p];
-    stencil s;
-    rc = make_stencil(P, xp, &s);
+#ifdef _OPENMP
+  if (omp_get_max_threads() > 1) {
+    rc = g2p_grad_omp(P, &K, np, x, F, g.gu, xb1, vb1, Cb1, Fb1, gub, xb, Fb);
     if (rc) goto done;
-    /* recompute C' of this particle */
-    mat3 B;
-    mzero(B);
-    for (int o = 0; o < nst; o++) {
-      int off[3], idx[3];
-      double W, gW[3], dpos[3];
-      offset_of(d, o, off);
-      stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
-      int64_t ni = node_index(d, n, idx);
-      for (int a = 0; a < d; a++)
-        for (int b = 0; b < d; b++) B[a][b] += W * g.gu[ni * d + a] * dpos[b];
+  } else
+#endif
+  {
+    for (int64_t p = 0; p < np; p++) {
+      rc = g2p_grad_particle(P, &K, np, p, x, F, g.gu, xb1, vb1, Cb1, Fb1, gub, xb, Fb);
+      if (rc) goto done;
     }
-    mat3 Cn, Fp, Fb1p, Cb1p, G, Gt, Fbp, Ct, Fpt, FbFt;
-    for (int a = 0; a < 3; a++)
-      for (int b = 0; b < 3; b++) Cn[a][b] = 4.0 * inv_dx2 * B[a][b];
-    load_mat(d, F, np, p, Fp);
-    load_mat(d, Fb1, np, p, Fb1p);
-    load_mat(d, Cb1, np, p, Cb1p);
-    /* x' = x + dt v'  ->  xbar += xbar', vtilde = vbar' + dt xbar' */
-    double xbp[3] = {0, 0, 0}, vt[3] = {0, 0, 0};
-    for (int a = 0; a < d; a++) {
-      xbp[a] = xb1[a * np + p];
-      vt[a] = vb1[a * np + p] + P->dt * xb1[a * np + p];
-    }
-    /* F' = (I + dt C') F  ->  Fbar = (I + dt C')^T Fbar', Ctilde = Cbar' + dt Fbar' F^T */
-    meye(d, G);
-    for (int a = 0; a < d; a++)
-      for (int b = 0; b < d; b++) G[a][b] += P->dt * Cn[a][b];
-    mtrans(d, G, Gt);
-    mmul(d, Gt, Fb1p, Fbp);
-    mtrans(d, Fp, Fpt);
-    mmul(d, Fb1p, Fpt, FbFt);
-    mzero(Ct);
-    for (int a = 0; a < d; a++)
-      for (int b = 0; b < d; b++) Ct[a][b] = Cb1p[a][b] + P->dt * FbFt[a][b];
-    /* v' = sum W u_i ; C' = (4/dx^2) sum W u_i dpos^T */
-    for (int o = 0; o < nst; o++) {
-      int off[3], idx[3];
-      double W, gW[3], dpos[3];
-      offset_of(d, o, off);
-      stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
-      int64_t ni = node_index(d, n, idx);
-      const double* u = g.gu + ni * d;
-      double Wbar = 0.0;
-      for (int a = 0; a < d; a++) {
-        double Cd = 0.0;
-        for (int b = 0; b < d; b++) Cd += Ct[a][b] * dpos[b];
-        gub[ni * d + a] += W * vt[a] + 4.0 * inv_dx2 * W * Cd;
-        Wbar += vt[a] * u[a] + 4.0 * inv_dx2 * u[a] * Cd;
-      }
-      for (int b = 0; b < d; b++) {
-        double CtU = 0.0; /* (Ctilde^T u)_b */
-        for (int a = 0; a < d; a++) CtU += Ct[a][b] * u[a];
-        xbp[b] += Wbar * gW[b] - 4.0 * inv_dx2 * W * CtU;
-      }
-    }
-    for (int a = 0; a < d; a++) xb[a * np + p] = xbp[a];
-    store_mat(d, Fb, np, p, Fbp);
   }
 
   /* grid_op.grad */
-  for (int64_t ni = 0; ni < nn; ni++) {
-    int idx[3] = {0, 0, 0};
-    int64_t r = ni;
-    for (int a = d - 1; a >= 0; a--) {
-      idx[a] = (int)(r % n);
-      r /= n;
-    }
-    if (g.gm[ni] > 0.0 && !is_wall(P, idx)) {
-      double mb = 0.0;
-      for (int a = 0; a < d; a++) {
-        gpb[ni * d + a] = gub[ni * d + a] / g.gm[ni];
-        mb -= gub[ni * d + a] * g.gp[ni * d + a] / (g.gm[ni] * g.gm[ni]);
-      }
-      gmb[ni] = mb;
-    }
-  }
+  grid_update_adjoint(P, g.gm, g.gp, gub, gpb, gmb);
 
   /* p2g.grad and the stress / actuation adjoint */
-  double gact[ORC_CTRL_MAX_GROUPS], gabar[ORC_CTRL_MAX_GROUPS];
   rc = group_actuation(P, np, t, x, v, grp, wact, gact);
   if (rc) goto done;
-  for (int g = 0; g < ORC_CTRL_MAX_GROUPS; g++) gabar[g] = 0.0;
-  for (int64_t p = 0; p < np; p++) {
-    double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0};
-    for (int a = 0; a < d; a++) {
-      xp[a] = x[a * np + p];
-      vp[a] = v[a * np + p];
-    }
-    stencil s;
-    rc = make_stencil(P, xp, &s);
+  for (int gi = 0; gi < ORC_CTRL_MAX_GROUPS; gi++) gabar[gi] = 0.0;
+#ifdef _OPENMP
+  if (omp_get_max_threads() > 1) {
+    rc = p2g_grad_omp(P, &K, np, t, x, v, C, F, mu, la, grp, wact, gact, gpb, gmb, xb, vb, Cb,
+                      Fb, mubar, labar, wbar, gabar);
     if (rc) goto done;
-    mat3 Fp, Cp, tau, A, Abar, Fbp;
-    load_mat(d, F, np, p, Fp);
-    load_mat(d, C, np, p, Cp);
-    int axis;
-    double act = particle_act(P, grp, gact, p, &axis);
-    rc = kirchhoff_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tau);
-    if (rc) goto done;
-    mzero(A);
-    for (int i = 0; i < d; i++)
-      for (int j = 0; j < d; j++) A[i][j] = kappa * tau[i][j] + m * Cp[i][j];
-    mzero(Abar);
-    double vbp[3] = {0, 0, 0}, xbp[3] = {0, 0, 0};
-    for (int o = 0; o < nst; o++) {
-      int off[3], idx[3];
-      double W, gW[3], dpos[3];
-      offset_of(d, o, off);
-      stencil_eval(d, n, &s, off, &W, gW, dpos, idx);
-      int64_t ni = node_index(d, n, idx);
-      const double* pb = gpb + ni * d;
-      /* p_i += W (m v + A dpos) ; m_i += W m */
-      double Wbar = m * gmb[ni];
-      for (int a = 0; a < d; a++) {
-        double Ad = 0.0;
-        for (int b = 0; b < d; b++) Ad += A[a][b] * dpos[b];
-        Wbar += pb[a] * (m * vp[a] + Ad);
-        vbp[a] += W * m * pb[a];
-        for (int b = 0; b < d; b++) Abar[a][b] += W * pb[a] * dpos[b];
-      }
-      for (int b = 0; b < d; b++) {
-        double AtP = 0.0; /* (A^T pbar)_b */
-        for (int a = 0; a < d; a++) AtP += A[a][b] * pb[a];
-        xbp[b] += Wbar * gW[b] - W * AtP;
-      }
+  } else
+#endif
+  {
+    for (int64_t p = 0; p < np; p++) {
+      rc = p2g_grad_particle(P, &K, np, t, p, x, v, C, F, mu, la, grp, wact, gact, gpb, gmb, xb,
+                             vb, Cb, Fb, mubar, labar, wbar, gabar);
+      if (rc) goto done;
     }
-    /* A = kappa tau + m C */
-    mat3 tb, Cbp;
-    mzero(tb);
-    mzero(Cbp);
-    for (int i = 0; i < d; i++)
-      for (int j = 0; j < d; j++) {
-        tb[i][j] = kappa * Abar[i][j];
-        Cbp[i][j] = m * Abar[i][j];
-      }
-    load_mat(d, Fb, np, p, Fbp);
-    double abar = 0.0;
-    rc = kirchhoff_adjoint_m(P, material_of(P, p), Fp, mu[p], la[p], act, axis, tb, Fbp, &mubar[p],
-                             &labar[p], &abar);
-    if (rc) goto done;
-    if (P->n_groups > 0 && grp && wact && wbar) {
-      int gi = grp[p];
-      if (gi >= 0 && gi < P->n_groups) {
-        if (P->ctrl_hidden > 0)
-          gabar[gi] += abar;
-        else
-          for (int k = 1; k <= P->n_basis; k++)
-            wbar[gi * P->n_basis + (k - 1)] += abar * act_basis(P, k, t);
-      }
-    }
-    for (int a = 0; a < d; a++) {
-      xb[a * np + p] += xbp[a];
-      vb[a * np + p] = vbp[a];
-    }
-    store_mat(d, Cb, np, p, Cbp);
-    store_mat(d, Fb, np, p, Fbp);
   }
   /* the controller read this state: its adjoint reaches the weights and, through the
      sensors, the positions and velocities */
