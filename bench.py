@@ -11,8 +11,11 @@ bench step).  `value` is measured with the inputs already on the device; `e2e` t
 the same step through the public API from pinned host buffers, the host<->device copies
 inside the timed region.  Prints one JSON line (rank 0).
 
-Multi-GPU (torchrun): every rank runs its own replica of the workload (independent
-scenes; no collective on the data path) -- weak scaling.
+Multi-GPU (torchrun): the scenes of a batch are independent, so no collective runs on the
+data path.  By default every rank owns one seeded batch of the workload (the job's batch is
+the union, partitioned by rank: weak scaling); with --shard the one batch's scenes are split
+across the ranks by shard_scenes, balanced by particle count (strong scaling).  The ranks'
+losses are gathered after the timed region.
 """
 from __future__ import annotations
 
@@ -237,6 +240,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def precision_label(desc):
+    """What the workload's passes compute in: FP32 throughout, FP64 only for the polar
+    factor of fixed-corotated particles."""
+    mat = desc.get("material", 0)
+    fcr = "FP32 state, grid and stress; FP64 polar decomposition and its adjoint"
+    nh = "FP32 throughout (neo-Hookean: J - 1 and ln J in FP32; no polar factor)"
+    liq = "FP32 throughout (Tait liquid: J - 1, log1p/expm1 in FP32; no polar factor)"
+    return {0: fcr, 1: nh, 3: liq,
+            4: "per-particle materials: " + fcr + " for the solid, FP32 for the liquid"}.get(mat, fcr)
+
+
 def make_workload(name, seed=0):
     from paper_1910_00935_gb300 import scenes
     scene = scenes.make(name, seed=seed)
@@ -263,28 +277,49 @@ def make_workload(name, seed=0):
     return scene, N, d["steps"], descr
 
 
-def cpu_baseline(name, seconds_hint=20.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: the full
-    particle set for a few steps of forward + reverse (1 host thread)."""
-    import oracle
-    from paper_1910_00935_gb300 import scenes
-    scene, N, T, _ = make_workload(name)
-    sample_T = {"cube3d": 2, "robots3d": 1, "rects2d": 4, "square2d_grad": 32,
-                "robots_nn": 4}.get(name, 2)
-    if name == "robots3d":  # one of the 16 independent scenes
-        from paper_1910_00935_gb300.scenes import actuated_robots_3d
-        scene = actuated_robots_3d(n_scenes=1)
-        N = sum(scene["desc"]["n_particles"])
-    if name == "robots_nn":  # one of the 4 independent scenes
-        from paper_1910_00935_gb300.scenes import controlled_robots_3d
-        scene = controlled_robots_3d(n_scenes=1)
-        N = sum(scene["desc"]["n_particles"])
-    t0 = time.perf_counter()
-    oracle.loss_and_grad(scenes.oracle_view(scene), sample_T)
-    dt = time.perf_counter() - t0
-    return {"value": N * sample_T / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{N} particles x {sample_T} steps forward+backward of {name}",
-            "seconds": round(dt, 3), "units": N * sample_T}
+# bounded oracle samples: steps of the all-cores run and of the single-thread run
+CPU_WINDOWS = {"cube3d": (64, 2), "robots3d": (64, 4), "rects2d": (16, 4),
+               "square2d_grad": (64, 32), "robots_nn": (16, 4)}
+
+
+def host_cores():
+    """Cores available to this process, and the host CPU's model name (lscpu)."""
+    cores = len(os.sched_getaffinity(0))
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def oracle_timing(name, steps, threads):
+    """One timing of the FP64 oracle (oracle/baseline.py) in a child process: its OpenMP
+    runtime never shares a process with the GPU path's libraries."""
+    cmd = [sys.executable, "-m", "oracle.baseline", "--workload", name, "--steps", str(steps),
+           "--threads", str(threads)]
+    r = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle baseline failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(name, single_thread=True):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload, on all cores
+    available to the process (the OpenMP build of the same source) and on one thread."""
+    cores, model = host_cores()
+    w_all, w_one = CPU_WINDOWS.get(name, (8, 2))
+    one = oracle_timing(name, w_one, 1) if single_thread or cores == 1 else None
+    res = oracle_timing(name, w_all, cores) if cores > 1 else dict(one)
+    res["cpu_model"] = model
+    res["cores_available"] = cores
+    if one is not None:
+        res["single_thread"] = {k: one[k] for k in ("value", "sample", "seconds", "units")}
+    return res
 
 
 def run_reference(args, rank, world):
@@ -317,7 +352,7 @@ def run_reference(args, rank, world):
     times = []
     cb = None
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(name)
+        r = cpu_baseline(name, single_thread=False)
         if i >= args.warmup:
             times.append(r["seconds"])
             cb = r
@@ -537,6 +572,10 @@ def main():
                     help="also time the same batch one scene per launch sequence")
     ap.add_argument("--persistent", type=int, default=0,
                     help="1: run each run of same-kind passes as one persistent launch")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: split the one batch's scenes across the ranks, "
+                         "balanced by particle count (strong scaling; default: every rank "
+                         "owns its own seeded batch, weak scaling)")
     args = ap.parse_args()
 
     world = _env_int("WORLD_SIZE", 1)
@@ -565,8 +604,22 @@ def main():
     from paper_1910_00935_gb300 import mpm
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    # every rank simulates its own independent replica of the workload (seeded by rank)
-    scene, N, T, descr = make_workload(args.workload, seed=rank)
+    shard = bool(args.shard and world > 1)
+    if shard:
+        # one batch, its scenes partitioned across the ranks by particle count; no data
+        # crosses between ranks (the scenes are independent)
+        from paper_1910_00935_gb300.sharding import shard_scenes, subset
+        full, N_total, T, descr = make_workload(args.workload, seed=0)
+        mine = shard_scenes(full["desc"]["n_particles"], world, rank)
+        if not mine:
+            raise RuntimeError(f"rank {rank} of {world} got no scene of {args.workload}")
+        scene = subset(full, mine)
+        N = int(sum(scene["desc"]["n_particles"]))
+    else:
+        # every rank simulates its own seeded batch: the job's batch is the union of the
+        # ranks' batches, partitioned by rank (weak scaling)
+        scene, N, T, descr = make_workload(args.workload, seed=rank)
+        N_total = world * N
     if args.T:
         T = args.T
     if args.ckpt_every:
@@ -638,7 +691,7 @@ def main():
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * N * T / (ms / 1e3)
+    value = N_total * T / (ms / 1e3)
 
     # ---- forward-only throughput (same inputs, same stream) ----
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -683,7 +736,7 @@ def main():
             t = torch.tensor([e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e_ms = float(t.item())
-        e2e = {"value": world * N * T / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+        e2e = {"value": N_total * T / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # ---- live per-kernel timing: CUDA events around every launch on its stream ----
@@ -746,6 +799,13 @@ def main():
         for si in sims:
             si.close()
 
+    # the job's loss: every rank's per-scene losses, gathered after the timed region (a
+    # report, not part of the simulated path)
+    losses = bufs["loss"].cpu().tolist()
+    if world > 1:
+        every = [None] * world
+        dist.all_gather_object(every, losses)
+        losses = [v for r in every for v in r]
     if rank != 0:
         return
     cb = None
@@ -756,15 +816,21 @@ def main():
             cb = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": str(e)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": descr, "particles": N, "scenes": S, "T": T,
+        "config": {"workload": descr, "particles": N_total, "scenes": S if not shard else
+                   len(full["desc"]["n_particles"]), "T": T,
                    "ckpt_every": desc["ckpt_every"], "grid": f"{desc['n_grid']}^{desc['dim']}",
                    "l2": "flushed between timed iterations (512 MiB write)",
-                   "precision": "FP32 state/grid, FP64 polar decomposition",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "precision": precision_label(desc),
+                   "parallelism": ("1 GPU" if world == 1 else
+                                   f"dp{world}: the batch's scenes sharded by particle count"
+                                   if shard else f"dp{world}: one seeded batch per rank"),
                    "launch_form": "persistent" if args.persistent else "one launch per pass"},
-        "forward": {"value": N * T / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms},
+        "forward": {"value": N * T / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms,
+                    "scope": "rank 0's scenes"},
+        "loss": {"sum": float(sum(losses)), "scenes": len(losses)},
         "one_scene_per_launch": per_scene,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -1,8 +1,9 @@
 """Multi-rank host logic on CPU (world size 2, gloo): scenes sharded across ranks with no
-data-path collective give exactly the single-process results, the benchmark's
-max-over-ranks timing reduction works, and a rank that fails before reporting its shard is
-detected by the others through the rendezvous store within a deadline (no collective hangs).
-The per-rank work is the FP64 oracle (no GPU)."""
+data-path collective give exactly the single-process results -- final states, and the
+losses and gradients of a forward+backward run gathered through the rendezvous store --
+the benchmark's max-over-ranks timing reduction works, and a rank that fails before
+reporting its shard is detected by the others through the rendezvous store within a
+deadline (no collective hangs).  The per-rank work is the FP64 oracle (no GPU)."""
 import os
 import socket
 
@@ -109,3 +110,52 @@ def test_collect_shards_returns_every_rank():
     assert collect_shards(store, 1, 2, {"b": 2}) is None
     got = collect_shards(store, 0, 2, {"a": 1}, timeout_s=5.0)
     assert got == {0: {"a": 1}, 1: {"b": 2}}
+
+
+def _grad_worker(rank, world, port, T, q):
+    """The benchmark's --shard split of one batch: each rank runs forward, loss and backward
+    on its scenes and publishes losses and gradients through the store."""
+    store = dist.TCPStore("127.0.0.1", port, world, is_master=(rank == 0),
+                          timeout=__import__("datetime").timedelta(seconds=60))
+    base = scenes.make("robots3d", n_scenes=3, dims=(8, 6, 6), n_grid=32)
+    mine = shard_scenes(base["desc"]["n_particles"], world, rank)
+    r = oracle.loss_and_grad(scenes.oracle_view(subset(base, mine)), T)
+    off = np.concatenate([[0], np.cumsum(subset(base, mine)["desc"]["n_particles"])])
+    per = {}
+    for j, i in enumerate(mine):
+        sl = slice(int(off[j]), int(off[j + 1]))
+        per[i] = dict(loss=r["losses"][j], gx0=r["gx0"][:, sl], gv0=r["gv0"][:, sl],
+                      gE=r["gE"][sl], gw=r["gw"][j])
+    got = collect_shards(store, rank, world, per, timeout_s=120.0, tag="grad")
+    if rank == 0:
+        merged = {}
+        for v in got.values():
+            merged.update(v)
+        q.put(merged)
+
+
+def test_two_rank_sharded_gradients_equal_single_process():
+    T = 5
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, 2, port, T, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    merged = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    base = scenes.make("robots3d", n_scenes=3, dims=(8, 6, 6), n_grid=32)
+    assert sorted(merged) == [0, 1, 2]
+    assert sorted(shard_scenes(base["desc"]["n_particles"], 2, 0) +
+                  shard_scenes(base["desc"]["n_particles"], 2, 1)) == [0, 1, 2]
+    single = oracle.loss_and_grad(scenes.oracle_view(base), T)
+    off = np.concatenate([[0], np.cumsum(base["desc"]["n_particles"])])
+    for i in range(3):
+        sl = slice(int(off[i]), int(off[i + 1]))
+        assert merged[i]["loss"] == single["losses"][i]  # bitwise
+        for k in ("gx0", "gv0"):
+            np.testing.assert_array_equal(merged[i][k], single[k][:, sl])
+        np.testing.assert_array_equal(merged[i]["gE"], single["gE"][sl])
+        np.testing.assert_array_equal(merged[i]["gw"], single["gw"][i])
