@@ -99,6 +99,24 @@ def _noise(seed, stream, shape, half_width=0.05):
     return (uniform(seed, stream, n).reshape(shape) * 2.0 - 1.0) * half_width
 
 
+def linear_functional(dim: int, n: int, seed: int = 0, c_scale: float = 1e-3):
+    """Seeds of a fixed random linear functional L = <a, state_T> of the final state:
+    U(-1, 1) weights on x, v and F and c_scale * U(-1, 1) on C (C is O(1/dt) larger).
+    Returned as FP32 component-major arrays dL_dx[d, n], dL_dv, dL_dC[d^2, n], dL_dF."""
+    f = lambda stream, rows, s=1.0: _f32((uniform(seed, stream, rows * n).reshape(rows, n)
+                                          * 2.0 - 1.0) * s)
+    return dict(dL_dx=f(900, dim), dL_dv=f(901, dim), dL_dC=f(902, dim * dim, c_scale),
+                dL_dF=f(903, dim * dim))
+
+
+def sample_indices(n: int, m: int, seed: int = 0) -> np.ndarray:
+    """m distinct particle indices of [0, n), sorted, drawn with the splitmix64 stream
+    (seed, 950): the particles a full-length comparison samples."""
+    if m >= n:
+        return np.arange(n, dtype=np.int64)
+    return np.sort(np.argsort(uniform(seed, 950, n), kind="stable")[:m]).astype(np.int64)
+
+
 def elastic_square_2d(seed=0, steps=128, n_side=64, ckpt_every=32):
     """2D square of n_side^2 particles (2 per cell per axis), side n_side/256,
     centred at (0.3, 0.5); fixed-corotated E=1e3, nu=0.2; v0 = (1, 0) + U(+-0.05)."""

@@ -1,0 +1,109 @@
+"""The CUDA path at each workload's full size and full step count, against the FP64 oracle.
+
+Expected values come from tests/golden/full_<name>.npz, written by
+tests/golden/make_full_length.py, which calls only the oracle (the tape of Section 3.2 with
+Appendix D.2's checkpoints and Appendix D.1's step adjoints, in FP64).  The GPU runs the
+launch configuration the benchmark times: the workload's own checkpoint interval k, kept
+segment grids and the re-simulation overlapped on a second stream (the defaults).
+
+Compared, element by element:
+* x_T of every particle within 1e-4 relative L2 (per compared scene); v_T, C_T, F_T on a
+  seeded sample of particles at 10x, 100x and 1x that bar (v and C are differences of
+  positions, as in tests/test_gpu_parity.py);
+* the workload's loss (per scene) within 1e-4 relative;
+* the gradients of the workload's loss -- dL/dx0 (with the loss's direct x0 term), dL/dv0,
+  and dL/dw for the actuated robots -- and every gradient block (x0, v0, C0, F0, E, nu, w)
+  of a fixed random linear functional of the final state, each within 1e-3 relative L2 on
+  the sampled particles (dL/dw in full).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from mpm_testlib import rel_l2, to_np
+from paper_1910_00935_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+POS_TOL, GRAD_TOL = 1e-4, 1e-3
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden")
+WORKLOADS = ["cube3d", "rects2d", "robots3d"]
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    from paper_1910_00935_gb300 import build, mpm as m
+    build.build()
+    return m
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, f"full_{name}.npz")
+    if not os.path.exists(path):
+        pytest.fail(f"missing {path}: run tests/golden/make_full_length.py {name}")
+    return dict(np.load(path))
+
+
+def _rows(d):
+    return {"x": d, "v": d, "C": d * d, "F": d * d}
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_full_length_matches_oracle(mpm, name):
+    g = _golden(name)
+    scene = scenes.make(name)
+    desc = scene["desc"]
+    d, T, N = desc["dim"], int(desc["steps"]), int(sum(desc["n_particles"]))
+    assert int(g["T"]) == T and int(g["ckpt_every"]) == desc["ckpt_every"]
+    assert list(g["n_particles"]) == list(desc["n_particles"])
+    off = np.concatenate([[0], np.cumsum(desc["n_particles"])])
+    compared = [int(i) for i in g["compared_scenes"]]
+    idx = g["sample_index"]
+    cols = np.concatenate([np.arange(off[i], off[i + 1]) for i in compared])
+
+    sim = mpm.from_scene(scene, max_steps=T)
+    sim.forward(T)
+    x, v, C, F = [to_np(t) for t in sim.state()]
+    L, gT, g0 = sim.loss(desc["loss_kind"], torch.as_tensor(scene["arrays"]["target"]))
+    grad_loss = {k: to_np(t) for k, t in sim.backward(dL_dx=gT).items()}
+    grad_loss["gx0"] = grad_loss["gx0"] + to_np(g0)
+    lin = scenes.linear_functional(d, N, int(g["functional_seed"]))
+    grad_lin = {k: to_np(t) for k, t in sim.backward(**{k: torch.as_tensor(a)
+                                                          for k, a in lin.items()}).items()}
+    assert mpm.mpm_sync_status(sim.h) == mpm.MPM_OK, mpm.mpm_last_error(sim.h)
+    sim.close()
+
+    report = {}
+    # final state
+    xs = x[:, cols]
+    for j, si in enumerate(compared):
+        n = int(off[si + 1] - off[si])
+        o = int(sum(desc["n_particles"][k] for k in compared[:j]))
+        report[f"x_T[{si}]"] = rel_l2(xs[:, o:o + n], g["xT"][:, o:o + n])
+    for key, arr, tol in (("vT", v, 10 * POS_TOL), ("CT", C, 100 * POS_TOL), ("FT", F, POS_TOL)):
+        report[key] = (rel_l2(arr[:, idx], g[key]), tol)
+    Lg = to_np(L)
+    for si, Lo in zip(compared, g["loss"]):
+        report[f"loss[{si}]"] = (abs(Lg[si] - Lo) / abs(Lo), POS_TOL)
+    # gradients
+    pick = lambda a: (a if a.ndim == 2 else a[None, :])[:, idx]
+    for k in ("gx0", "gv0"):
+        report[f"loss {k}"] = (rel_l2(pick(grad_loss[k]), g[f"loss_{k}"]), GRAD_TOL)
+    if desc["n_groups"]:
+        report["loss gw"] = (rel_l2(grad_loss["gw"][compared], g["loss_gw"]), GRAD_TOL)
+    for k in ("gx0", "gv0", "gC0", "gF0", "gE", "gnu"):
+        report[f"lin {k}"] = (rel_l2(pick(grad_lin[k]), g[f"lin_{k}"]), GRAD_TOL)
+    if desc["n_groups"]:
+        report["lin gw"] = (rel_l2(grad_lin["gw"][compared], g["lin_gw"]), GRAD_TOL)
+
+    print(f"\n{name} (T={T}, k={desc['ckpt_every']}): " +
+          ", ".join(f"{k} {v[0] if isinstance(v, tuple) else v:.2e}" for k, v in report.items()))
+    bad = {}
+    for k, v in report.items():
+        val, tol = v if isinstance(v, tuple) else (v, POS_TOL)
+        if not val <= tol:
+            bad[k] = (val, tol)
+    assert not bad, bad
