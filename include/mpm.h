@@ -111,6 +111,13 @@ extern "C" {
 #define MPM_OPT_PERSISTENT_CHUNK 11 /* persistent form: at most this many passes per launch
                                      (0 = a whole run of same-kind passes) [0]; bounds the
                                      duration of any one launch */
+#define MPM_OPT_BUCKET_SCATTER 14  /* 1: a particle pass groups its tile's particles by stencil
+                                     base and scatters each group with one warp, one float4
+                                     reduction per (base, node) summed in registers, instead of
+                                     one per (particle, node) [0: on GB300 the extra shared-
+                                     memory traffic of the group loop outweighed the saved
+                                     reductions].  FP32 sums only (ignored in the deterministic
+                                     mode and with MPM_OPT_SMEM_TILE). */
 #define MPM_OPT_BARRIER_TEST_EXTRA 10 /* test hook, 0..1024 [0]: arrivals every grid barrier
                                      waits for beyond the launch's own CTAs.  Nonzero values
                                      can never be met, so each persistent launch ends through
@@ -308,15 +315,26 @@ void mpm_destroy(mpm_handle* h);
  * E, nu: device float [N].  device_err: device uint32 or NULL; when given, the
  *   step ORs its device error bits into it (1 = a stencil left the grid, 2 =
  *   non-finite value or det F <= 0); when NULL those bits go to the fixed array
- *   and are not reported.
- * Results equal mpm_forward with T = 1 up to FP32 atomic-order rounding.
+ *   and are not reported.  A particle whose stencil leaves the grid is skipped by
+ *   the kernels' own bounds check (no access outside the grid) and sets bit 1.
+ * Results equal mpm_forward with T = 1 up to FP32 atomic-order rounding, and one more
+ *   rounding: the rows hold F itself, and each call forms F - I in FP32 and adds I back,
+ *   so a caller that chains calls rounds the small strain to FP32's spacing near 1 on
+ *   every step (the workspace path keeps F - I between steps and does not).
  *
- * The first call on each device performs a one-time set-up (it looks up the device
- * address of the fixed array, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array and each
- * call clears what must start at zero; calls that overlap on the GPU (two streams,
- * or two threads) race on it and must be serialised by the caller.
- * Returns MPM_OK, MPM_ERR_ARG, MPM_ERR_TOO_LARGE or MPM_ERR_CUDA. */
+ * Set-up and memory: CUDA loads modules lazily, so the device memory of the fixed array
+ * and the modules of the step kernels are committed on first use.  A call with
+ * n_particles[0] == 0 (the pointers may then be any non-NULL values; nothing is read or
+ * written) does only that set-up for desc's dim and material and returns MPM_OK: make
+ * it at start-up, before the caller's memory budget is spent and before any stream
+ * capture, once per device and per (dim, material) to be used.  Without it the first
+ * real call on a device does the set-up.  The device address of the array is looked up
+ * (cudaGetSymbolAddress, no allocation) on every call, with the calling thread's
+ * current device and context.  Every call on a device shares the one array and each
+ * call clears what must start at zero; calls that overlap on the GPU (two streams, or
+ * two threads) race on it and must be serialised by the caller.
+ * Returns MPM_OK, MPM_ERR_ARG, MPM_ERR_TOO_LARGE or MPM_ERR_CUDA; on failure
+ * mpm_last_error(NULL) names the check or the CUDA call that failed (this host thread). */
 #define MPM_NOALLOC_MAX_NODES (1 << 18)     /* 64^3 in 3D, 512^2 in 2D */
 #define MPM_NOALLOC_MAX_PARTICLES (1 << 18) /* 262,144 */
 int mpm_step_noalloc(const mpm_scene_desc* desc, const float* state_in, const float* E,

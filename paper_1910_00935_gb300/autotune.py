@@ -2,7 +2,8 @@
 
 The knobs are the library's runtime options: the capacity of the shared gather box
 (MPM_OPT_GATHER_CAPACITY), the scatter path (MPM_OPT_SMEM_TILE: shared node box vs. float4
-reductions straight to the grid), the shared box capacity (MPM_OPT_TILE_CAPACITY), the
+reductions straight to the grid; MPM_OPT_BUCKET_SCATTER: one reduction per stencil base and
+node, summed by a warp, vs. one per particle and node), the shared box capacity (MPM_OPT_TILE_CAPACITY), the
 CTA count of the end-of-sequence grid clear (MPM_OPT_GRID_BLOCKS), the launch form
 (MPM_OPT_PERSISTENT: one launch per pass, or persistent launches over the pass plan), and two
 memory-vs-recompute choices of the backward: a re-simulated segment's grids kept or recomputed
@@ -22,16 +23,19 @@ import os
 SPACE = {
     "gather_capacity": [512, 0, 1024, 2048],
     "smem_tile": [0, 1],
+    "bucket_scatter": [0, 1],
     "tile_capacity": [1024, 2048],
     "grid_blocks": [0, 32, 64, 128],
     "persistent": [0, 1],
     "grid_recompute": [0, 1],
     "overlap_resim": [1, 0],
 }
-DEFAULTS = {"gather_capacity": 512, "smem_tile": 0, "tile_capacity": 1024, "grid_blocks": 0,
+DEFAULTS = {"gather_capacity": 512, "smem_tile": 0, "bucket_scatter": 0, "tile_capacity": 1024,
+            "grid_blocks": 0,
             "persistent": 0, "grid_recompute": 0, "overlap_resim": 1}
 
-_OPTION_IDS = {"gather_capacity": 5, "smem_tile": 2, "tile_capacity": 3, "grid_blocks": 6,
+_OPTION_IDS = {"gather_capacity": 5, "smem_tile": 2, "bucket_scatter": 14, "tile_capacity": 3,
+               "grid_blocks": 6,
                "persistent": 8, "grid_recompute": 12, "overlap_resim": 13}
 
 

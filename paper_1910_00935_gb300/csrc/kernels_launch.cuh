@@ -23,6 +23,10 @@ cudaError_t step_one(const SimParams& P, const StepArgs& A, int n_tiles, cudaStr
   auto k = step_kernel<D, MAT, MODE, DET>;
   cudaError_t e = allow_smem(k, smem);
   if (e != cudaSuccess) return e;
+  if (n_tiles <= 0) {  // no tiles: only make sure the kernel's module is loaded
+    cudaFuncAttributes attr;
+    return cudaFuncGetAttributes(&attr, k);
+  }
   k<<<n_tiles, kTile, smem, s>>>(P, A);
   return cudaGetLastError();
 }
@@ -33,6 +37,10 @@ cudaError_t adj_one(const SimParams& P, const AdjArgs& A, int n_tiles, cudaStrea
   auto k = adjoint_kernel<D, MAT, MODE, DET>;
   cudaError_t e = allow_smem(k, smem);
   if (e != cudaSuccess) return e;
+  if (n_tiles <= 0) {  // no tiles: only make sure the kernel's module is loaded
+    cudaFuncAttributes attr;
+    return cudaFuncGetAttributes(&attr, k);
+  }
   k<<<n_tiles, kTile, smem, s>>>(P, A);
   return cudaGetLastError();
 }

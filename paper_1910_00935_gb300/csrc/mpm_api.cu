@@ -254,6 +254,7 @@ struct mpm_handle {
   // options
   bool use_graphs = true;
   bool smem_tile = false;  // measured on GB300: global float4 reductions beat shared FP32 atomics
+  bool bucket_scatter = false;  // one reduction per (base, node) of a tile (measured slower: off)
   int tile_capacity = 1024;
   int gather_capacity = 512;  // nodes; a 128-particle tile's stencil box is ~150-300
   int grid_blocks = 0;  // CTAs per scene of the end-of-sequence grid clear (0 = automatic)
@@ -323,6 +324,12 @@ int fail(mpm_handle* h, int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
+
+void mpm::set_static_error(const char* msg) { g_static_error = msg ? msg : ""; }
+
+namespace {
+
 int cuda_fail(mpm_handle* h, cudaError_t e, const char* where) {
   return fail(h, MPM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
@@ -364,6 +371,8 @@ SimParams params_for(const mpm_handle* h, int t) {
   // the shared scatter box sums in FP32 in arbitrary order: not in the deterministic mode
   P.tile_capacity = h->smem_tile && !d.deterministic_p2g ? h->tile_capacity : 0;
   P.gather_capacity = h->gather_capacity;
+  // the bucketed scatter sums a base's particles in FP32 registers: not in the deterministic mode
+  P.bucket = h->bucket_scatter && !d.deterministic_p2g ? 1 : 0;
   P.f_diag = 0.0f;  // the workspace holds E = F - I
   P.det = d.deterministic_p2g;
   P.node_words = h->m.words;
@@ -1497,6 +1506,7 @@ int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
   switch (key) {
     case MPM_OPT_USE_GRAPHS: h->use_graphs = value != 0; break;
     case MPM_OPT_SMEM_TILE: h->smem_tile = value != 0; break;
+    case MPM_OPT_BUCKET_SCATTER: h->bucket_scatter = value != 0; break;
     case MPM_OPT_GATHER_CAPACITY:
       if (value != 0 && (value < 27 || value > 12288))
         return fail(h, MPM_ERR_ARG, "gather capacity must be 0 or in [27, 12288]");

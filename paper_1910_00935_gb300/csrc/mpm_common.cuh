@@ -81,6 +81,8 @@ struct SimParams {
   float basis2[kMaxBasis]; // same at the step of an adjoint pass's recomputed P2G
   int tile_capacity;       // max nodes of a CTA's shared scatter box (0 = global reductions)
   int gather_capacity;     // max nodes of a CTA's shared gather box (0 = gathers through L1)
+  int bucket;              // 1: FP32 scatters go through the per-base bucket table (one
+                           // reduction per base and node); 0: one per particle and node
   float f_diag;            // the F rows of the state hold F - f_diag I (0: E = F - I, 1: F)
   // deterministic accumulation: grids hold 64-bit fixed-point sums (node_words = 2 float4
   // slots per node), channel c of a contribution v enters as round(v * fix_c); mass uses

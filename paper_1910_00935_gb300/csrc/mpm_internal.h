@@ -31,6 +31,9 @@ template <int D>
 cudaError_t launch_clear(const Clears& C, int nnodes, int n_grid, int n_scenes, int blocks_per_scene,
                          cudaStream_t s);
 
+// the message mpm_last_error(NULL) returns (per host thread)
+void set_static_error(const char* msg);
+
 // dispatch on the runtime material and accumulation mode (P.det)
 #define MPM_DISPATCH_MATERIAL(FN, ...)                                                   \
   switch (material) {                                                                   \

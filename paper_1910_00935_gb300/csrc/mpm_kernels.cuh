@@ -542,6 +542,211 @@ __device__ __forceinline__ void scatter_records(const float* xr, int count, cons
   }
 }
 
+// ---------------------------------------------------------------------------
+// Bucketed scatter (FP32 sums).  A scattered float4 reduction costs the SM's L1/L2 path far
+// more than the arithmetic that produces it (measured on GB300: ~1.5 SM cycles per lane,
+// the equivalent of ~6 warp-wide FMA instructions), and a 128-particle tile sends ~3,500
+// of them into a box of ~200 nodes.  Particles that share a stencil base touch the same
+// 3^D nodes, so the tile's particles are grouped by base in a shared table, and one warp
+// takes a whole group: lane o < 3^D owns node base + o, sums the group's contributions in
+// registers and issues one reduction.  In 3D a tile holds ~45-64 bases of ~2-8 particles,
+// so the reductions drop 2-3x for ~30 extra FMA-class instructions per particle.  Bases
+// whose group overflows the table's slots, and tiles whose base box exceeds its keys, go
+// through the per-particle path.  Not used in the deterministic mode (its sums are
+// fixed point and order-free already).
+// ---------------------------------------------------------------------------
+constexpr int kBucketKeys = 256;  // bases of one tile's base box the table can hold
+constexpr int kBucketSlots = 8;   // particles per base held in the table
+static_assert(kTile <= 256, "bucket entries hold tile-local indices in one byte");
+struct Buckets {
+  int count[kBucketKeys];                           // particles per base (kept zero between uses)
+  unsigned char order[kBucketKeys * kBucketSlots];  // their tile-local indices
+};
+__device__ __forceinline__ void buckets_zero(Buckets& b) {
+  for (int i = threadIdx.x; i < kBucketKeys; i += blockDim.x) b.count[i] = 0;
+}
+
+// array-of-structures scatter record of one particle: f[D], a[D], B[D][D], padded to float4s
+template <int D>
+struct Aos {
+  static constexpr int kFloats = D == 3 ? 16 : 8;
+};
+static_assert(Aos<3>::kFloats * kTile <= Xch<3>::kWidth * Xch<3>::kStride, "record area");
+static_assert(Aos<2>::kFloats * kTile <= Xch<2>::kWidth * Xch<2>::kStride, "record area");
+
+template <int D>
+__device__ __forceinline__ void put_record_aos(float* xr, const float f[D], const float a[D],
+                                               const float B[D][D]) {
+  float r[Aos<D>::kFloats];
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) r[c++] = f[i];
+#pragma unroll
+  for (int i = 0; i < D; ++i) r[c++] = a[i];
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) r[c++] = B[i / D][i % D];
+#pragma unroll
+  for (; c < Aos<D>::kFloats; ++c) r[c] = 0.0f;
+  float4* dst = reinterpret_cast<float4*>(xr) + threadIdx.x * (Aos<D>::kFloats / 4);
+#pragma unroll
+  for (int i = 0; i < Aos<D>::kFloats / 4; ++i)
+    dst[i] = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+}
+
+// keys of the tile's base box: the stencil box bx less its 2-node margin
+template <int D>
+__device__ __forceinline__ int bucket_keys(const BoxInfo<D>& bx) {
+  if (bx.vol <= 0) return 0;
+  int K = 1;
+#pragma unroll
+  for (int a = 0; a < D; ++a) K *= bx.dim[a] - 2;
+  return K;
+}
+template <int D>
+__device__ __forceinline__ int bucket_key(const BoxInfo<D>& bx, const int base[D]) {
+  int k = base[0] - bx.lo[0];
+#pragma unroll
+  for (int a = 1; a < D; ++a) k = k * (bx.dim[a] - 2) + (base[a] - bx.lo[a]);
+  return k;
+}
+
+// Enter this thread's particle in the table (valid particles only); returns true when its
+// base's slots were full and the particle must scatter on its own.
+template <int D>
+__device__ __forceinline__ bool bucket_fill(Buckets& bk, const BoxInfo<D>& bx, bool valid,
+                                            const int base[D]) {
+  if (!valid) return false;
+  const int key = bucket_key<D>(bx, base);
+  const int slot = atomicAdd(&bk.count[key], 1);
+  if (slot < kBucketSlots) {
+    bk.order[key * kBucketSlots + slot] = (unsigned char)threadIdx.x;
+    return false;
+  }
+  return true;
+}
+
+// One particle's 3^D reductions (mass W * mass_c when WITH_MASS, vector W (a + B dpos)) into
+// grid g from its own registers (the per-particle path)
+template <int D, bool WITH_MASS>
+__device__ __forceinline__ void scatter_one(float4* g, int n, const Axes<D>& s, const float a[D],
+                                            const float B[D][D], float mass_c) {
+  float4* gb = g + node_flat<D>(s.base, n);
+  for_nodes<D>(s.w, [&](int i, int jj, int k, float W) {
+    float q[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      q[c] = a[c] + B[c][0] * s.dp[0][i] + B[c][1] * s.dp[1][jj];
+      if (D == 3) q[c] += B[c][D - 1] * s.dp[D - 1][k];
+    }
+    float4 v = WITH_MASS ? make_float4(W * mass_c, W * q[0], W * q[1], D == 3 ? W * q[2] : 0.0f)
+                         : make_float4(W * q[0], W * q[1], D == 3 ? W * q[2] : 0.0f, 0.0f);
+    atomicAdd(gb + stencil_off<D>(i, jj, k, n), v);
+  });
+}
+
+// Every warp takes groups of the table in turn (3D: one group per warp step, lanes 0..26;
+// 2D: three groups, lanes 0..26 in threes of nine), sums each group's records into its
+// lane's node and issues one reduction per node; a group's count is reset to zero once
+// read, so the table is empty again for its next use.  The caller synchronised the CTA
+// after filling the table and writing the records.
+template <int D, bool WITH_MASS>
+__device__ __forceinline__ void scatter_buckets(Buckets& bk, int K, const BoxInfo<D>& bx,
+                                                const float* xr, float4* g, int n, const SimParams& P,
+                                                float mass_c) {
+  constexpr int L = D == 3 ? 27 : 9;  // nodes of a stencil = lanes per group
+  constexpr int PER = 32 / L;         // groups per warp step
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int sub = lane / L, o = lane - sub * L;
+  const bool lane_on = sub < PER;
+  int off[3];
+  off[0] = D == 3 ? o / 9 : o / 3;
+  off[1] = D == 3 ? (o / 3) % 3 : o % 3;
+  off[2] = D == 3 ? o % 3 : 0;
+  // the quadratic B-spline weight of stencil offset off_a as alpha (f - beta)^2 + gamma
+  float alpha[D], beta[D], gamma[D], odx[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    alpha[a] = off[a] == 1 ? -1.0f : 0.5f;
+    beta[a] = off[a] == 0 ? 1.5f : (off[a] == 1 ? 1.0f : 0.5f);
+    gamma[a] = off[a] == 1 ? 0.75f : 0.0f;
+    odx[a] = (float)off[a];
+  }
+  int kd[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) kd[a] = bx.dim[a] - 2;
+  for (int k0 = warp * PER; k0 < K; k0 += nwarps * PER) {
+    const int key = k0 + sub;
+    const bool on = lane_on && key < K;
+    int cnt = on ? bk.count[key] : 0;
+    if (!__any_sync(0xffffffffu, cnt > 0)) continue;
+    const int m = cnt < kBucketSlots ? cnt : kBucketSlots;
+    float am = 0.0f, aq[3] = {0.0f, 0.0f, 0.0f};
+    for (int s = 0; s < m; ++s) {
+      const int q = bk.order[key * kBucketSlots + s];
+      const float4* r4 = reinterpret_cast<const float4*>(xr) + q * (Aos<D>::kFloats / 4);
+      float r[Aos<D>::kFloats];
+#pragma unroll
+      for (int i = 0; i < Aos<D>::kFloats / 4; ++i) {
+        const float4 v = r4[i];
+        r[4 * i] = v.x;
+        r[4 * i + 1] = v.y;
+        r[4 * i + 2] = v.z;
+        r[4 * i + 3] = v.w;
+      }
+      float W = 1.0f, dp[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const float f = r[a];
+        const float t = f - beta[a];
+        W *= fmaf(alpha[a] * t, t, gamma[a]);
+        dp[a] = (odx[a] - f) * P.dx;
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float qc = r[D + c];
+#pragma unroll
+        for (int b = 0; b < D; ++b) qc = fmaf(r[2 * D + c * D + b], dp[b], qc);
+        aq[c] = fmaf(W, qc, aq[c]);
+      }
+      am += W;
+    }
+    if (on && cnt > 0) {
+      int base[D], r = key;
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+        base[a] = bx.lo[a] + r % kd[a] + off[a];
+        r /= kd[a];
+      }
+      const float4 v = WITH_MASS ? make_float4(am * mass_c, aq[0], aq[1], D == 3 ? aq[2] : 0.0f)
+                                 : make_float4(aq[0], aq[1], D == 3 ? aq[2] : 0.0f, 0.0f);
+      atomicAdd(g + node_flat<D>(base, n), v);
+    }
+    __syncwarp();
+    if (on && o == 0 && cnt > 0) bk.count[key] = 0;
+  }
+}
+
+// The bucketed form of one tile's scatter, from the CTA's stencil box bx (every thread
+// calls it; bx came from box_extent, whose barrier separates this from the table's
+// previous use).  Writes the records, fills the table, synchronises, scatters by group and
+// lets overflowing particles scatter on their own.  Returns false (nothing done, no
+// barrier) when the tile's base box exceeds the table; the caller then takes the
+// per-particle path.
+template <int D, bool WITH_MASS>
+__device__ __forceinline__ bool bucket_scatter_tile(Buckets& bk, const BoxInfo<D>& bx, bool valid,
+                                                    const Axes<D>& s, const float a[D],
+                                                    const float B[D][D], float* xr, float4* g,
+                                                    int n, const SimParams& P, float mass_c) {
+  const int K = bucket_keys<D>(bx);
+  if (K > kBucketKeys) return false;
+  if (valid) put_record_aos<D>(xr, s.f, a, B);
+  const bool over = bucket_fill<D>(bk, bx, valid, s.base);
+  __syncthreads();
+  scatter_buckets<D, WITH_MASS>(bk, K, bx, xr, g, n, P, mass_c);
+  if (over) scatter_one<D, WITH_MASS>(g, n, s, a, B, mass_c);
+  return true;
+}
+
 __device__ __forceinline__ float particle_act(const SimParams& P, const float* basis, const int* group,
                                               const float* wact, int scene, int64_t p, int dim,
                                               int& axis) {
@@ -664,7 +869,7 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
                                          const float C[D][D], const float E[D][D], float mu_p,
                                          float la_p, int mat_p, const int* group, const float* wact,
                                          float4* g, int* box_scene, float* sm, float* xr,
-                                         int* s_box, int* s_bbox, unsigned& err,
+                                         int* s_box, int* s_bbox, Buckets& bk, unsigned& err,
                                          const double* R_in, double* R_out, int64_t N) {
   Axes<D> s;
   bool ok = make_axes<D>(x, P, s) && active;
@@ -695,6 +900,19 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
     }
   }
   __syncthreads();  // the record area may still be read by an earlier scatter
+  if (!DET && P.bucket && P.tile_capacity == 0) {
+    const BoxInfo<D> bx = box_extent<D>(ok, s.base, INT_MAX, s_box + 16);
+    if (bucket_scatter_tile<D, true>(bk, bx, ok, s, mv, Am, xr, g, P.n_grid, P, P.p_mass)) {
+      if (threadIdx.x == 0 && bx.vol > 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          atomicMin(&box_scene[a], bx.lo[a]);
+          atomicMax(&box_scene[4 + a], bx.lo[a] + bx.dim[a] - 1);
+        }
+      }
+      return;
+    }
+  }
   put_record<D>(xr, ok, s.base, s.f, mv, Am);
   if (P.tile_capacity > 0) {
     const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box + 16);
@@ -727,7 +945,7 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
 // synchronise between them.
 template <int D, int MAT, int MODE, bool NC, bool DET>
 __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A, int tile_index,
-                                          float* sm, int* s_box, int* s_bbox) {
+                                          float* sm, int* s_box, int* s_bbox, Buckets& bk) {
   using R = Rows<D>;
   cta_bbox_reset(s_bbox);
   reset_box_slots(s_box);
@@ -840,7 +1058,7 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
     p2g_pass<D, MAT, DET>(P, P.basis, active, scene, p, tile.z, x, v, C, E, staged(stage, 0),
                           staged(stage, 1), MAT == kMixed ? A.matid[p] : MAT, A.group, A.wact,
                      scene_grid(A.PMw, scene, P), A.box_w + scene * 8, sm, xr, s_box, s_bbox,
-                     err, nullptr, A.Rw, N);
+                     bk, err, nullptr, A.Rw, N);
   }
   if (err) atomicOr(A.err, err);
 }
@@ -859,7 +1077,9 @@ __global__ void __launch_bounds__(kTile, step_ctas_per_sm<D, MAT>())
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_box[8 * kBoxSlots];
   __shared__ int s_bbox[8];
-  step_tile<D, MAT, MODE, true, DET>(P, A, blockIdx.x, sm, s_box, s_bbox);
+  __shared__ Buckets s_bk;
+  buckets_zero(s_bk);  // ordered before its first use by the tile's first barrier
+  step_tile<D, MAT, MODE, true, DET>(P, A, blockIdx.x, sm, s_box, s_bbox, s_bk);
 }
 
 // ---------------------------------------------------------------------------
@@ -870,7 +1090,7 @@ __global__ void __launch_bounds__(kTile, step_ctas_per_sm<D, MAT>())
 template <int D, int MAT, int MODE, bool NC, bool DET>
 __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& A, int tile_index,
                                              float* sm, int* s_box, int* s_bbox_ub, int* s_bbox_pm,
-                                             float* s_wbar) {
+                                             float* s_wbar, Buckets& bk) {
   using R = Rows<D>;
   cta_bbox_reset(s_bbox_ub);
   cta_bbox_reset(s_bbox_pm);
@@ -1242,8 +1462,17 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     float4* UBs = scene_grid(A.UB0, scene, P);
     float fix_u = 1.0f, unfix_u = 1.0f;
     if (DET) ub_scales(A.ub_m0, fix_u, unfix_u);
-    put_record<D>(xr, ok, s.base, s.f, vt, Bs);
-    if (P.tile_capacity > 0) {
+    if (!DET && P.bucket && P.tile_capacity == 0 && cap_box > 0 &&
+        bucket_scatter_tile<D, false>(bk, bx, ok, s, vt, Bs, xr, UBs, n, P, 0.0f)) {
+      if (threadIdx.x == 0 && bx.vol > 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          atomicMin(&A.box_ub[scene * 8 + a], bx.lo[a]);
+          atomicMax(&A.box_ub[scene * 8 + 4 + a], bx.lo[a] + bx.dim[a] - 1);
+        }
+      }
+    } else if (P.tile_capacity > 0) {
+      put_record<D>(xr, ok, s.base, s.f, vt, Bs);
       BoxInfo<D> sbx = bx;
       sbx.use_tile = bx.use_tile && bx.vol <= P.tile_capacity;
       box_zero<D>(sbx, sm, P.tile_capacity);  // same extent as the gather box
@@ -1257,6 +1486,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
         }
       }
     } else {
+      put_record<D>(xr, ok, s.base, s.f, vt, Bs);
       warp_bbox<D>(ok, s.base, s_bbox_ub);
       __syncthreads();
       cta_bbox_flush<D>(s_bbox_ub, A.box_ub + scene * 8);
@@ -1286,7 +1516,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
                           staged(stage, b + R::Q + 1), MAT == kMixed ? A.matid[p] : MAT, A.group,
                           A.wact,
                      scene_grid(A.PMm, scene, P), A.box_m + scene * 8, sm, xr, s_box, s_bbox_pm,
-                     err, A.Rm, nullptr, N);
+                     bk, err, A.Rm, nullptr, N);
   }
   if (err) atomicOr(A.err, err);
 }
@@ -1299,7 +1529,10 @@ __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
   __shared__ int s_bbox_ub[8];
   __shared__ int s_bbox_pm[8];
   __shared__ float s_wbar[kWbarSlots];
-  adjoint_tile<D, MAT, MODE, true, DET>(P, A, blockIdx.x, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+  __shared__ Buckets s_bk;
+  buckets_zero(s_bk);  // ordered before its first use by the tile's first barrier
+  adjoint_tile<D, MAT, MODE, true, DET>(P, A, blockIdx.x, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar,
+                                        s_bk);
 }
 
 // ---------------------------------------------------------------------------
@@ -1412,16 +1645,18 @@ __global__ void __launch_bounds__(kTile, step_ctas_per_sm<D, MAT>())
   __shared__ int s_bbox[8];
   __shared__ int s_go, s_tile;
   __shared__ PassEntry e;
+  __shared__ Buckets s_bk;
+  buckets_zero(s_bk);  // ordered before its first use by the barriers that follow
   for (int i = 0; i < n_pass; ++i) {
     if (i > 0 && !grid_barrier(ctl, (unsigned)i * gridDim.x + ctl.extra, &s_go)) return;
     __syncthreads();
     cta_copy(&e, plan + i);
     for (int t; (t = next_tile(ctl, i, &s_tile)) < n_tiles;) {
       switch (e.mode) {
-        case kP2GOnly: step_tile<D, MAT, kP2GOnly, false, DET>(e.P, e.S, t, sm, s_box, s_bbox); break;
-        case kG2PP2G: step_tile<D, MAT, kG2PP2G, false, DET>(e.P, e.S, t, sm, s_box, s_bbox); break;
-        case kG2PP2GFull: step_tile<D, MAT, kG2PP2GFull, false, DET>(e.P, e.S, t, sm, s_box, s_bbox); break;
-        default: step_tile<D, MAT, kG2POnlyFull, false, DET>(e.P, e.S, t, sm, s_box, s_bbox); break;
+        case kP2GOnly: step_tile<D, MAT, kP2GOnly, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk); break;
+        case kG2PP2G: step_tile<D, MAT, kG2PP2G, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk); break;
+        case kG2PP2GFull: step_tile<D, MAT, kG2PP2GFull, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk); break;
+        default: step_tile<D, MAT, kG2POnlyFull, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk); break;
       }
       __syncthreads();
     }
@@ -1439,6 +1674,8 @@ __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
   __shared__ float s_wbar[kWbarSlots];
   __shared__ int s_go, s_tile;
   __shared__ PassEntry e;
+  __shared__ Buckets s_bk;
+  buckets_zero(s_bk);  // ordered before its first use by the barriers that follow
   for (int i = 0; i < n_pass; ++i) {
     if (i > 0 && !grid_barrier(ctl, (unsigned)i * gridDim.x + ctl.extra, &s_go)) return;
     __syncthreads();
@@ -1446,13 +1683,13 @@ __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
     for (int t; (t = next_tile(ctl, i, &s_tile)) < n_tiles;) {
       switch (e.mode) {
         case kAdjG2P:
-          adjoint_tile<D, MAT, kAdjG2P, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          adjoint_tile<D, MAT, kAdjG2P, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar, s_bk);
           break;
         case kAdjFused:
-          adjoint_tile<D, MAT, kAdjFused, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          adjoint_tile<D, MAT, kAdjFused, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar, s_bk);
           break;
         default:
-          adjoint_tile<D, MAT, kAdjP2G, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar);
+          adjoint_tile<D, MAT, kAdjP2G, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar, s_bk);
           break;
       }
       __syncthreads();

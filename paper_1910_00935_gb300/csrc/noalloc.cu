@@ -11,10 +11,16 @@
 // The step runs the library's own kernels (P2G from the full input state, then G2P
 // writing the full output state, grid_op applied as it gathers) with pointers into that
 // array, so its results equal those of mpm_forward with T = 1 up to FP32 atomic-order
-// rounding.
+// rounding and the rounding of F - I noted in mpm.h.
+//
+// Device memory for the array, and the kernels' modules, are committed when they are first
+// used (CUDA loads modules lazily): a call with n_particles[0] == 0 does only that set-up,
+// so a caller can make it at start-up, before its memory budget is spent and before any
+// stream capture.
 #include <climits>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "../../include/mpm.h"
 #include "mpm_internal.h"
@@ -40,7 +46,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
+bool g_setup_done[kMaxDevices] = {};
 
 __global__ void noalloc_prepare_kernel(int64_t N, const float* E, const float* nu, float* mu,
                                        float* la, int4* tiles, int* n_tiles, int* box) {
@@ -60,8 +66,18 @@ __global__ void noalloc_prepare_kernel(int64_t N, const float* E, const float* n
   }
 }
 
-// every rejection is reported by its status code alone (documented in mpm.h)
-int reject(int code, const char* /*why*/) { return code; }
+// a rejection's message goes where mpm_last_error(NULL) reads it (this host thread)
+int reject(int code, const char* why) {
+  set_static_error(why);
+  return code;
+}
+
+// message of a failed CUDA call
+int reject_cuda(const char* where, cudaError_t e) {
+  std::string m = std::string("mpm_step_noalloc: ") + where + ": " + cudaGetErrorString(e);
+  set_static_error(m.c_str());
+  return MPM_ERR_CUDA;
+}
 
 }  // namespace
 
@@ -85,34 +101,54 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
   int64_t nnodes = 1;
   for (int a = 0; a < d->dim; ++a) nnodes *= d->n_grid;
   const int64_t N = d->n_particles[0];
-  if (N < 1) return reject(MPM_ERR_ARG, "mpm_step_noalloc: no particles");
+  if (N < 0) return reject(MPM_ERR_ARG, "mpm_step_noalloc: negative particle count");
   if (nnodes > kMaxNodes)
     return reject(MPM_ERR_TOO_LARGE, "mpm_step_noalloc: n_grid^dim exceeds MPM_NOALLOC_MAX_NODES");
   if (N > kMaxParticles)
     return reject(MPM_ERR_TOO_LARGE, "mpm_step_noalloc: more than MPM_NOALLOC_MAX_PARTICLES");
 
-  // one-time set-up per device: the device address of the scratch array
+  // the device address of the scratch array, looked up on every call (cheap, allocates
+  // nothing) so that it is always that of the current context; the first lookup on a
+  // device also commits the array's memory and loads this file's module
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return reject(MPM_ERR_CUDA, "mpm_step_noalloc: no current CUDA device");
   }
-  char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        return reject(MPM_ERR_CUDA, "mpm_step_noalloc: cudaGetSymbolAddress failed");
-      }
-      g_scratch_ptr[dev] = p;
-    }
-    base = static_cast<char*>(g_scratch_ptr[dev]);
+  void* scratch = nullptr;
+  e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
+  if (e != cudaSuccess || !scratch) {
+    cudaGetLastError();
+    return reject_cuda("cudaGetSymbolAddress", e);
   }
+  char* base = static_cast<char*>(scratch);
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    // set-up: once per device, load the modules of the two step kernels this problem
+    // launches (a zero-tile launch only loads); a call with no particles stops here
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_setup_done[dev] || N == 0) {
+      SimParams Q;
+      memset(&Q, 0, sizeof(Q));
+      Q.tile_capacity = 1024;
+      StepArgs Z;
+      memset(&Z, 0, sizeof(Z));
+      e = d->dim == 2 ? launch_step<2>(d->material, kP2GOnly, Q, Z, 0, s)
+                      : launch_step<3>(d->material, kP2GOnly, Q, Z, 0, s);
+      if (e == cudaSuccess)
+        e = d->dim == 2 ? launch_step<2>(d->material, kG2POnlyFull, Q, Z, 0, s)
+                        : launch_step<3>(d->material, kG2POnlyFull, Q, Z, 0, s);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return reject_cuda("loading the step kernels", e);
+      }
+      g_setup_done[dev] = true;
+    }
+  }
+  if (N == 0) return MPM_OK;
+
   float4* PM = reinterpret_cast<float4*>(base + kOffPM);
   float* mu = reinterpret_cast<float*>(base + kOffMu);
   float* la = reinterpret_cast<float*>(base + kOffLa);
@@ -124,14 +160,14 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
 
   // the array keeps the previous call's contents: clear what must start at zero (the
   // mass/momentum grid; the prepare kernel rewrites the box, tiles and Lame parameters)
-  cudaError_t e = cudaMemsetAsync(PM, 0, (size_t)nnodes * sizeof(float4), s);
+  e = cudaMemsetAsync(PM, 0, (size_t)nnodes * sizeof(float4), s);
   if (e == cudaSuccess && !device_err) e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) {
     int blocks = (int)((N + 255) / 256);
     noalloc_prepare_kernel<<<blocks, 256, 0, s>>>(N, E, nu, mu, la, tiles, n_tiles_dev, box);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess) return reject(MPM_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return reject_cuda("clearing the grid", e);
 
   SimParams P;
   memset(&P, 0, sizeof(P));
@@ -174,6 +210,7 @@ extern "C" int mpm_step_noalloc(const mpm_scene_desc* d, const float* state_in, 
     e = launch_step<3>(d->material, kP2GOnly, P, A, n_tiles, s);
     if (e == cudaSuccess) e = launch_step<3>(d->material, kG2POnlyFull, P, G, n_tiles, s);
   }
-  if (e != cudaSuccess) return reject(MPM_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return reject_cuda("launching the step", e);
+  set_static_error("");
   return MPM_OK;
 }

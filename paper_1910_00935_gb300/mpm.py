@@ -33,6 +33,7 @@ MPM_OPT_USE_GRAPHS, MPM_OPT_SMEM_TILE, MPM_OPT_TILE_CAPACITY, MPM_OPT_PROFILE = 
 MPM_OPT_GATHER_CAPACITY, MPM_OPT_GRID_BLOCKS, MPM_OPT_POLAR_CACHE = 5, 6, 7
 MPM_OPT_PERSISTENT, MPM_OPT_BARRIER_TIMEOUT_US, MPM_OPT_BARRIER_TEST_EXTRA = 8, 9, 10
 MPM_OPT_PERSISTENT_CHUNK, MPM_OPT_GRID_RECOMPUTE, MPM_OPT_OVERLAP_RESIM = 11, 12, 13
+MPM_OPT_BUCKET_SCATTER = 14
 KERNEL_CATEGORIES = {1: "p2g", 2: "g2p_p2g", 3: "g2p_p2g_full", 4: "g2p", 5: "grid_clear",
                      6: "adj_g2p", 7: "adj_fused", 8: "adj_p2g", 9: "persistent_step",
                      10: "persistent_adj", 11: "controller"}

@@ -63,6 +63,9 @@ def _compare(out, ref, dim):
 
 @pytest.mark.gpu
 def test_noalloc_step_matches_workspace_path_calls_in_a_row(mpm):
+    # the documented start-up call: no particles, only the set-up (nothing read or written)
+    warm = dict(scenes.make("cube3d", n_side=24, n_grid=64)["desc"], n_particles=[0])
+    assert mpm.mpm_step_noalloc(mpm.make_desc(warm), 256, 256, 256, 512, None) == mpm.MPM_OK
     device_err = torch.zeros(1, dtype=torch.int32, device="cuda")
     cube = scenes.make("cube3d", n_side=24, n_grid=64)   # 13,824 particles, 64^3 nodes (the limit)
     square = scenes.make("square2d")                     # 4,096 particles, 128^2 nodes
@@ -81,16 +84,42 @@ def test_noalloc_step_matches_workspace_path_calls_in_a_row(mpm):
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(mpm):
-    """Size checks run on the host before any CUDA call (no GPU needed)."""
+    """Size checks run on the host before any CUDA call (no GPU needed); each rejection
+    leaves its reason where mpm_last_error(NULL) reads it."""
     big_grid = dict(scenes.make("cube3d", n_side=8, n_grid=128)["desc"])  # 128^3 > 2^18 nodes
     assert mpm.mpm_step_noalloc(mpm.make_desc(big_grid), 256, 256, 256, 512, None, 0) == \
         mpm.MPM_ERR_TOO_LARGE
+    assert "MPM_NOALLOC_MAX_NODES" in mpm.mpm_last_error(None)
     many = dict(big_grid, n_grid=64, n_particles=[mpm.MPM_NOALLOC_MAX_PARTICLES + 1])
     assert mpm.mpm_step_noalloc(mpm.make_desc(many), 256, 256, 256, 512, None, 0) == \
         mpm.MPM_ERR_TOO_LARGE
     two = dict(big_grid, n_grid=64, n_particles=[100, 100])
     assert mpm.mpm_step_noalloc(mpm.make_desc(two), 256, 256, 256, 512, None, 0) == mpm.MPM_ERR_ARG
+    assert "one scene" in mpm.mpm_last_error(None)
     act = dict(big_grid, n_grid=64, n_groups=2, n_basis=1)
     assert mpm.mpm_step_noalloc(mpm.make_desc(act), 256, 256, 256, 512, None, 0) == mpm.MPM_ERR_ARG
     det = dict(big_grid, n_grid=64, deterministic_p2g=1)
     assert mpm.mpm_step_noalloc(mpm.make_desc(det), 256, 256, 256, 512, None, 0) == mpm.MPM_ERR_ARG
+
+
+@pytest.mark.gpu
+def test_noalloc_liquid_and_error_word(mpm):
+    """The liquid material through the entry point, a call whose error bits go to the fixed
+    array (device_err NULL), and a particle placed where its stencil leaves the grid: the
+    kernels' own bounds check skips it and sets bit 1 of the caller's error word."""
+    liquid = scenes.make("liquid3d", cols=(16, 20, 16), n_grid=64)
+    ref = _workspace_step(mpm, liquid)
+    rc, out = _noalloc_step(mpm, liquid, None)
+    assert rc == mpm.MPM_OK
+    _compare(out, ref, 3)
+
+    square = scenes.make("square2d")
+    bad = {"desc": square["desc"], "arrays": dict(square["arrays"])}
+    x0 = bad["arrays"]["x0"].copy()
+    x0[0, 5] = 0.2 / square["desc"]["n_grid"]  # x/dx = 0.2: stencil base -1, off the grid
+    bad["arrays"]["x0"] = x0
+    device_err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc, out = _noalloc_step(mpm, bad, device_err)
+    assert rc == mpm.MPM_OK
+    assert int(device_err.item()) & 1
+    assert np.isfinite(out).all()
