@@ -572,6 +572,8 @@ def main():
                     help="also time the same batch one scene per launch sequence")
     ap.add_argument("--persistent", type=int, default=0,
                     help="1: run each run of same-kind passes as one persistent launch")
+    ap.add_argument("--opt", action="append", default=[], metavar="MPM_OPT_NAME=VALUE",
+                    help="set a library option (include/mpm.h) for the run; repeatable")
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: split the one batch's scenes across the ranks, "
                          "balanced by particle count (strong scaling; default: every rank "
@@ -629,6 +631,11 @@ def main():
     G = desc.get("n_groups", 0)
     sim = mpm.Simulator(desc, T, device=dev)
     sim.set_option(mpm.MPM_OPT_PERSISTENT, args.persistent)
+    options = {}
+    for o in args.opt:
+        k, v = o.split("=")
+        sim.set_option(getattr(mpm, k), int(v))
+        options[k] = int(v)
     names = ["x0", "v0", "C0", "F0", "E", "nu"]
     host = {k: torch.as_tensor(a[k]).pin_memory() for k in names + ["target"]}
     if G:
@@ -827,7 +834,8 @@ def main():
                    "parallelism": ("1 GPU" if world == 1 else
                                    f"dp{world}: the batch's scenes sharded by particle count"
                                    if shard else f"dp{world}: one seeded batch per rank"),
-                   "launch_form": "persistent" if args.persistent else "one launch per pass"},
+                   "launch_form": "persistent" if args.persistent else "one launch per pass",
+                   "options": options or "library defaults"},
         "forward": {"value": N * T / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms,
                     "scope": "rank 0's scenes"},
         "loss": {"sum": float(sum(losses)), "scenes": len(losses)},

@@ -118,6 +118,20 @@ extern "C" {
                                      memory traffic of the group loop outweighed the saved
                                      reductions].  FP32 sums only (ignored in the deterministic
                                      mode and with MPM_OPT_SMEM_TILE). */
+#define MPM_OPT_PAIR_SCATTER 15    /* bit mask, 0..3: float4 reductions straight to the grid
+                                     merge the two contributions of a pair of particles
+                                     (consecutive in the set-up's base order) that share a
+                                     stencil base, one reduction per pair and node -- bit 0 in
+                                     the forward and re-simulation passes, bit 1 in the adjoint
+                                     passes [0; pairs share a base only in MPM_OPT_SORT_ORDER 1].
+                                     FP32 sums only. */
+#define MPM_OPT_SORT_ORDER 16      /* particle order chosen by mpm_set_initial (takes effect at
+                                     the next mpm_set_initial), by a grid coordinate per axis
+                                     in runs of 8 along the last axis: 0 the cell; 1 the
+                                     stencil base; 2 the cell, but the base on the last axis,
+                                     so that consecutive pairs of particles share their base
+                                     (what MPM_OPT_PAIR_SCATTER merges) [0: the adjoint passes'
+                                     gathers run fastest over the cell order's tiles] */
 #define MPM_OPT_BARRIER_TEST_EXTRA 10 /* test hook, 0..1024 [0]: arrivals every grid barrier
                                      waits for beyond the launch's own CTAs.  Nonzero values
                                      can never be met, so each persistent launch ends through
@@ -284,6 +298,32 @@ int mpm_get_profile(mpm_handle* h, int32_t kind, int64_t* launches, double* tota
  * mpm_set_initial; leaves any recorded forward intact.  MPM_ERR_ARG in the deterministic mode
  * (its grids are fixed point) or with a controller. */
 int mpm_initial_p2g_grid(mpm_handle* h, float* grid, void* stream);
+
+/* Checkpoint schedule for a workspace budget (the memory/recompute trade of Appendix D.2,
+ * generalised to two levels): among intervals k (every k up to 4096, powers of two, and
+ * max_steps itself, which re-simulates nothing) and second-level multipliers M (1, i.e. one
+ * level, or 2..1024), the schedule whose mpm_workspace_bytes fits budget_bytes with the
+ * fewest particle passes per forward + backward: 2T, plus the steps before the last
+ * segment's start (re-simulated once), plus those before the last coarse segment's start
+ * for a second level, plus T/2 when a segment's grids cannot be kept (every adjoint
+ * pass then recomputes a P2G pass); ties go to the smaller workspace.  desc: host (its
+ * ckpt_every and ckpt_coarse are ignored); outputs: host, the values to put in
+ * desc->ckpt_every and desc->ckpt_coarse and the resulting workspace bytes (ws_bytes may be
+ * NULL).  Host-only arithmetic, no GPU needed.  Returns MPM_OK, MPM_ERR_ARG, or
+ * MPM_ERR_WORKSPACE when no schedule fits. */
+int mpm_plan_checkpoints(const mpm_scene_desc* desc, int32_t max_steps, size_t budget_bytes,
+                         int32_t* ckpt_every, int32_t* ckpt_coarse, size_t* ws_bytes);
+
+/* Arithmetic peak of the current GPU, measured with the library's own kernel (8
+ * independent fused multiply-add chains per thread, 8 CTAs of 256 threads per SM; an FMA
+ * counts 2 FLOP; best of three timed launches after a warm-up, CUDA events on `stream`).
+ * It is the denominator of the ALU rooflines: the FP64 polar factor and its adjoint bound
+ * the fixed-corotated passes.  kind: MPM_PEAK_FP64_FMA or MPM_PEAK_FP32_FMA;
+ * flops_per_s: host.  Blocks until the launches finish (a diagnostic, ~0.1 s).  Returns
+ * MPM_OK, MPM_ERR_ARG or MPM_ERR_CUDA (message in mpm_last_error(NULL)). */
+#define MPM_PEAK_FP64_FMA 0
+#define MPM_PEAK_FP32_FMA 1
+int mpm_measure_peak(int32_t kind, double* flops_per_s, void* stream);
 
 /* Message of the last failure on this handle (static storage if h is NULL). */
 const char* mpm_last_error(mpm_handle* h);

@@ -24,17 +24,21 @@ SPACE = {
     "gather_capacity": [512, 0, 1024, 2048],
     "smem_tile": [0, 1],
     "bucket_scatter": [0, 1],
+    "pair_scatter": [0, 1, 3],
+    "sort_order": [0, 1, 2],
     "tile_capacity": [1024, 2048],
     "grid_blocks": [0, 32, 64, 128],
     "persistent": [0, 1],
     "grid_recompute": [0, 1],
     "overlap_resim": [1, 0],
 }
-DEFAULTS = {"gather_capacity": 512, "smem_tile": 0, "bucket_scatter": 0, "tile_capacity": 1024,
+DEFAULTS = {"gather_capacity": 512, "smem_tile": 0, "bucket_scatter": 0, "pair_scatter": 0, "sort_order": 0,
+            "tile_capacity": 1024,
             "grid_blocks": 0,
             "persistent": 0, "grid_recompute": 0, "overlap_resim": 1}
 
-_OPTION_IDS = {"gather_capacity": 5, "smem_tile": 2, "bucket_scatter": 14, "tile_capacity": 3,
+_OPTION_IDS = {"gather_capacity": 5, "smem_tile": 2, "bucket_scatter": 14, "pair_scatter": 15, "sort_order": 16,
+               "tile_capacity": 3,
                "grid_blocks": 6,
                "persistent": 8, "grid_recompute": 12, "overlap_resim": 13}
 
@@ -95,9 +99,12 @@ def coordinate_descent(measure, space=SPACE, start=DEFAULTS, rounds: int = 1):
 
 
 def apply(sim, config: dict) -> None:
-    """Set the knobs of `config` on a Simulator."""
+    """Set the knobs of `config` on a Simulator (the particle order takes effect through a
+    new set-up from the simulator's inputs)."""
     for knob, value in config.items():
         sim.set_option(_OPTION_IDS[knob], int(value))
+    if "sort_order" in config and getattr(sim, "_inputs", None) is not None:
+        sim.reload()
 
 
 def tune(sim, T: int = 32, repeats: int = 2, cache_path: str | None = None, force: bool = False):

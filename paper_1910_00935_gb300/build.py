@@ -21,7 +21,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["kernels_3d_fcr.cu", "kernels_3d_fcr_det.cu", "kernels_3d_nh.cu", "kernels_3d_nh_det.cu",
            "kernels_3d_liq.cu", "kernels_3d_liq_det.cu", "kernels_3d_mixed.cu",
            "kernels_3d_mixed_det.cu", "kernels_2d.cu", "setup.cu", "controller.cu",
-           "mass_spring.cu", "mpm_api.cu", "noalloc.cu"]
+           "mass_spring.cu", "mpm_api.cu", "noalloc.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE]

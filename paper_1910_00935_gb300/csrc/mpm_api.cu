@@ -255,6 +255,13 @@ struct mpm_handle {
   bool use_graphs = true;
   bool smem_tile = false;  // measured on GB300: global float4 reductions beat shared FP32 atomics
   bool bucket_scatter = false;  // one reduction per (base, node) of a tile (measured slower: off)
+  // one reduction per (pair sharing a base, node): bit 0 forward passes, bit 1 adjoint passes.
+  // Off by default: it needs the base order (sort_order 1), whose tiles make the adjoint
+  // passes' gathers slower than the cell order's (measured on GB300, cube3d: forward pass
+  // 43.6 vs 46.3 us, adjoint 88.9 vs 77.1 us)
+  int pair_scatter = 0;
+  int sort_order = 0;  // particle order of mpm_set_initial: 0 cells, 1 stencil bases, 2 cells
+                       // with the base on the last axis
   int tile_capacity = 1024;
   int gather_capacity = 512;  // nodes; a 128-particle tile's stencil box is ~150-300
   int grid_blocks = 0;  // CTAs per scene of the end-of-sequence grid clear (0 = automatic)
@@ -373,6 +380,7 @@ SimParams params_for(const mpm_handle* h, int t) {
   P.gather_capacity = h->gather_capacity;
   // the bucketed scatter sums a base's particles in FP32 registers: not in the deterministic mode
   P.bucket = h->bucket_scatter && !d.deterministic_p2g ? 1 : 0;
+  P.pair = d.deterministic_p2g ? 0 : h->pair_scatter;
   P.f_diag = 0.0f;  // the workspace holds E = F - I
   P.det = d.deterministic_p2g;
   P.node_words = h->m.words;
@@ -1209,6 +1217,55 @@ int mpm_workspace_bytes(const mpm_scene_desc* desc, int32_t max_steps, size_t* o
   return MPM_OK;
 }
 
+int mpm_plan_checkpoints(const mpm_scene_desc* desc, int32_t max_steps, size_t budget_bytes,
+                         int32_t* ckpt_every, int32_t* ckpt_coarse, size_t* ws_bytes) {
+  std::string why;
+  if (!ckpt_every || !ckpt_coarse) return fail(nullptr, MPM_ERR_ARG, "NULL output");
+  if (!valid_desc(desc, max_steps, &why)) return fail(nullptr, MPM_ERR_ARG, why);
+  const int64_t T = max_steps;
+  // candidate intervals: every k up to 4096, then powers of two, and T itself (no re-simulation)
+  std::vector<int64_t> ks;
+  for (int64_t k = 1; k <= std::min<int64_t>(T, 4096); ++k) ks.push_back(k);
+  for (int64_t k = 8192; k < T; k *= 2) ks.push_back(k);
+  if (T > 4096) ks.push_back(T);
+  const int coarse[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024};
+  mpm_scene_desc d = *desc;
+  double best_cost = 0.0;
+  size_t best_bytes = 0;
+  int64_t best_k = -1, best_M = 0;
+  for (int M : coarse) {
+    for (int64_t k : ks) {
+      if (M > 1 && k * M >= T) break;  // a second level needs more than one coarse segment
+      d.ckpt_every = (int32_t)k;
+      d.ckpt_coarse = M > 1 ? M : 0;
+      const Dims m = make_dims(&d, max_steps);
+      const size_t bytes = make_layout(m).total;
+      if (bytes > budget_bytes) continue;
+      // cost in particle passes of one forward + backward: T forward, T adjoint, every
+      // segment but the last re-simulated once (the steps before the last segment's start),
+      // a second level re-simulates every coarse segment but the last once more, and an
+      // adjoint pass that cannot keep its segment's grids recomputes one P2G pass (about
+      // half an adjoint pass)
+      const int64_t K = m.K;
+      double cost = 2.0 * (double)T + (double)(((T - 1) / K) * K);
+      if (M > 1) cost += (double)(((T - 1) / (K * M)) * (K * M));
+      if (!m.store_grids) cost += 0.5 * (double)T;
+      if (best_k < 0 || cost < best_cost || (cost == best_cost && bytes < best_bytes)) {
+        best_cost = cost;
+        best_bytes = bytes;
+        best_k = K;
+        best_M = M;
+      }
+    }
+  }
+  if (best_k < 0)
+    return fail(nullptr, MPM_ERR_WORKSPACE, "no checkpoint schedule fits the workspace budget");
+  *ckpt_every = (int32_t)best_k;
+  *ckpt_coarse = best_M > 1 ? (int32_t)best_M : 0;
+  if (ws_bytes) *ws_bytes = best_bytes;
+  return MPM_OK;
+}
+
 int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_bytes,
                int32_t max_steps, mpm_handle** out) {
   std::string why;
@@ -1289,9 +1346,9 @@ int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float
   h->last_stream = s;
   const Dims& m = h->m;
   const Layout& L = h->L;
-  int end_bit = 32;
-  while ((1ll << (end_bit - 32)) < m.S) ++end_bit;
-  CK(launch_sort_keys(m.D, m.n_grid, m.S, h->at<int64_t>(L.scene_off), m.N, x0,
+  int end_bit = 36;  // scene id above 36 bits of base Morton code and half-cell bits
+  while ((1ll << (end_bit - 36)) < m.S) ++end_bit;
+  CK(launch_sort_keys(m.D, m.n_grid, m.S, h->at<int64_t>(L.scene_off), m.N, x0, h->sort_order,
                       h->at<uint64_t>(L.keys0), h->at<int>(L.idx0), s));
   CK(launch_sort(h->at<void>(L.sort_tmp), L.sort_tmp_bytes, h->at<uint64_t>(L.keys0),
                  h->at<uint64_t>(L.keys1), h->at<int>(L.idx0), h->at<int>(L.perm), m.N, end_bit, s));
@@ -1507,6 +1564,14 @@ int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
     case MPM_OPT_USE_GRAPHS: h->use_graphs = value != 0; break;
     case MPM_OPT_SMEM_TILE: h->smem_tile = value != 0; break;
     case MPM_OPT_BUCKET_SCATTER: h->bucket_scatter = value != 0; break;
+    case MPM_OPT_SORT_ORDER:
+      if (value < 0 || value > 2) return fail(h, MPM_ERR_ARG, "sort order must be 0, 1 or 2");
+      h->sort_order = (int)value;
+      break;
+    case MPM_OPT_PAIR_SCATTER:
+      if (value < 0 || value > 3) return fail(h, MPM_ERR_ARG, "pair scatter must be in [0, 3]");
+      h->pair_scatter = (int)value;
+      break;
     case MPM_OPT_GATHER_CAPACITY:
       if (value != 0 && (value < 27 || value > 12288))
         return fail(h, MPM_ERR_ARG, "gather capacity must be 0 or in [27, 12288]");

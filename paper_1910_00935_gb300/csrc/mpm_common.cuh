@@ -83,6 +83,9 @@ struct SimParams {
   int gather_capacity;     // max nodes of a CTA's shared gather box (0 = gathers through L1)
   int bucket;              // 1: FP32 scatters go through the per-base bucket table (one
                            // reduction per base and node); 0: one per particle and node
+  int pair;                // FP32 reductions straight to the grid merge pairs of particles
+                           // that share a stencil base (one per pair and node): bit 0 in
+                           // the forward passes, bit 1 in the adjoint passes
   float f_diag;            // the F rows of the state hold F - f_diag I (0: E = F - I, 1: F)
   // deterministic accumulation: grids hold 64-bit fixed-point sums (node_words = 2 float4
   // slots per node), channel c of a contribution v enters as round(v * fix_c); mass uses

@@ -70,7 +70,7 @@ inline cudaError_t launch_persistent(int kind, int material, const SimParams& P,
 // setup.cu
 size_t sort_temp_bytes(int64_t n);
 cudaError_t launch_sort_keys(int dim, int n_grid, int n_scenes, const int64_t* scene_off, int64_t N,
-                             const float* x0, uint64_t* keys, int* idx, cudaStream_t s);
+                             const float* x0, int order, uint64_t* keys, int* idx, cudaStream_t s);
 cudaError_t launch_sort(void* tmp, size_t tmp_bytes, const uint64_t* keys_in, uint64_t* keys_out,
                         const int* idx_in, int* idx_out, int64_t N, int end_bit, cudaStream_t s);
 cudaError_t launch_gather_initial(int dim, int64_t N, const int* perm, const float* x0,

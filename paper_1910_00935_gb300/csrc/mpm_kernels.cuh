@@ -437,6 +437,147 @@ __device__ __forceinline__ void put_record(float* xr, bool valid, const int base
   for (int c = 0; c < D * D; ++c) xr[(1 + 2 * D + c) * S + i] = B[c / D][c % D];
 }
 
+// quadratic B-spline weight of stencil offset o (compile-time after unrolling) at f = x/dx - base
+__device__ __forceinline__ float bspline_w(int o, float f) {
+  if (o == 0) {
+    const float r = 1.5f - f;
+    return 0.5f * r * r;
+  }
+  if (o == 1) {
+    const float r = f - 1.0f;
+    return 0.75f - r * r;
+  }
+  const float r = f - 0.5f;
+  return 0.5f * r * r;
+}
+
+// Reversed stencil walk.  Particles sorted by stencil base put ~8 particles (3D) of a base in
+// one tile, so two lanes of a reduction instruction often share a base; if both walk the 27
+// nodes in the same order they reduce into the same node in the same instruction, which the
+// L2 serialises.  A lane with rev walks them in reverse: by the B-spline symmetry
+// w_o(f) = w_(2-o)(2 - f) and dpos_o(f) = -dpos_(2-o)(2 - f), the contribution for the loop's
+// offset o, computed from f' = 2 - f and -B, belongs to node base + 2 - o.  This rewrites f
+// and B in place and returns the grid pointer of node base + 2 rev and the offset sign.
+template <int D>
+__device__ __forceinline__ float4* reversed_stencil(bool rev, float4* g, int n, const int base[D],
+                                                    float f[D], float B[D][D], int& sgn) {
+  int b[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    f[a] = rev ? 2.0f - f[a] : f[a];
+    b[a] = base[a] + (rev ? 2 : 0);
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) B[i][j] = rev ? -B[i][j] : B[i][j];
+  sgn = rev ? -1 : 1;
+  return g + node_flat<D>(b, n);
+}
+
+// Pair-merged scatter (FP32 sums, reductions straight to the grid).  On GB300 a pass's
+// time grows with its count of scattered float4 reductions (measured on the fused forward
+// pass of a 262,144-particle cube: 51 us with 27 per particle, 26 us with none and the
+// arithmetic kept).  Particles are sorted by stencil base with the last axis's half-cell
+// varying fastest, so particles 2j and 2j+1 of a tile usually share their base: two
+// threads take such a pair, each one half of the 3^D nodes, and sum the pair's two
+// contributions to a node before one reduction -- half the reductions for the same
+// arithmetic.  A pair whose bases differ scatters each particle's contributions on their
+// own.  The node half is uniform per warp (no divergence); each thread reads two records.
+template <int D, bool WITH_MASS>
+__device__ __forceinline__ void scatter_pairs(const float* xr, int count, float4* g, int n,
+                                              const SimParams& P, float mass_c) {
+  static_assert(kTile % 64 == 0, "pairs: two node halves of whole warps");
+  constexpr int S = Xch<D>::kStride;
+  constexpr int NN = D == 3 ? 27 : 9;
+  constexpr int SPLIT = D == 3 ? 15 : 5;   // nodes of the first half (whole columns in 3D)
+  constexpr int HW = kTile / 64;           // warps per node half
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = warp >= HW ? 1 : 0;
+  // lanes of a warp take every second pair, so fewer of them share a base (and nodes)
+  const int j = lane * HW + (warp - h * HW);  // 0 .. kTile/2 - 1
+  const int ia = 2 * j, ib = 2 * j + 1;
+  const int pa = ia < count ? __float_as_int(xr[xidx(ia)]) : -1;
+  const int pb = ib < count ? __float_as_int(xr[xidx(ib)]) : -1;
+  const bool va = pa >= 0, vb = pb >= 0;
+  if (!va && !vb) return;
+  const bool merged = va && vb && pa == pb;
+  float fa[D], fb[D], aa[D], ab[D], Ba[D][D], Bb[D][D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    fa[c] = va ? xr[(1 + c) * S + xidx(ia)] : 1.0f;
+    aa[c] = va ? xr[(1 + D + c) * S + xidx(ia)] : 0.0f;
+    fb[c] = vb ? xr[(1 + c) * S + xidx(ib)] : 1.0f;
+    ab[c] = vb ? xr[(1 + D + c) * S + xidx(ib)] : 0.0f;
+  }
+#pragma unroll
+  for (int c = 0; c < D * D; ++c) {
+    Ba[c / D][c % D] = va ? xr[(1 + 2 * D + c) * S + xidx(ia)] : 0.0f;
+    Bb[c / D][c % D] = vb ? xr[(1 + 2 * D + c) * S + xidx(ib)] : 0.0f;
+  }
+  int base_a[D], base_b[D];
+  unpack_base<D>(va ? pa : 0, base_a);
+  unpack_base<D>(vb ? pb : 0, base_b);
+  // odd lanes walk their pair's stencils in reverse (reversed_stencil)
+  const bool rev = (lane & 1) != 0;
+  int sgn;
+  float4* ga = reversed_stencil<D>(rev, g, n, base_a, fa, Ba, sgn);
+  float4* gb = reversed_stencil<D>(rev, g, n, base_b, fb, Bb, sgn);
+  // weights and dpos are formed where they are used (few registers: the pair's records
+  // already hold 2 (2D + D^2) values)
+#pragma unroll
+  for (int col = 0; col < (D == 3 ? 9 : 3); ++col) {
+    // column: (i, jj) in 3D (nodes k = 0..2), i in 2D (nodes jj = 0..2)
+    const int i = D == 3 ? col / 3 : col;
+    const int jj = D == 3 ? col % 3 : 0;
+    const int o0 = D == 3 ? col * 3 : col * 3;  // first node of the column
+    // the column's nodes all lie in one half (3D: 15 = 5 columns; 2D: split inside col 1)
+    if (D == 3 && ((o0 < SPLIT) != (h == 0))) continue;
+    float wca = bspline_w(i, fa[0]), wcb = bspline_w(i, fb[0]);
+    float qca[D], qcb[D];
+    const float dia = ((float)i - fa[0]) * P.dx, dib = ((float)i - fb[0]) * P.dx;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      qca[c] = aa[c] + Ba[c][0] * dia;
+      qcb[c] = ab[c] + Bb[c][0] * dib;
+    }
+    if (D == 3) {
+      const float dja = ((float)jj - fa[1]) * P.dx, djb = ((float)jj - fb[1]) * P.dx;
+      wca *= bspline_w(jj, fa[1]);
+      wcb *= bspline_w(jj, fb[1]);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        qca[c] += Ba[c][1] * dja;
+        qcb[c] += Bb[c][1] * djb;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int o = o0 + k;
+      if (D == 2 && ((o < SPLIT) != (h == 0))) continue;
+      const float Wa = wca * bspline_w(k, fa[D - 1]), Wb = wcb * bspline_w(k, fb[D - 1]);
+      const float dza = ((float)k - fa[D - 1]) * P.dx, dzb = ((float)k - fb[D - 1]) * P.dx;
+      float q_a[3] = {0.0f, 0.0f, 0.0f}, q_b[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        q_a[c] = qca[c] + Ba[c][D - 1] * dza;
+        q_b[c] = qcb[c] + Bb[c][D - 1] * dzb;
+      }
+      const float4 ca = WITH_MASS ? make_float4(Wa * mass_c, Wa * q_a[0], Wa * q_a[1], D == 3 ? Wa * q_a[2] : 0.0f)
+                                  : make_float4(Wa * q_a[0], Wa * q_a[1], D == 3 ? Wa * q_a[2] : 0.0f, 0.0f);
+      const float4 cb = WITH_MASS ? make_float4(Wb * mass_c, Wb * q_b[0], Wb * q_b[1], D == 3 ? Wb * q_b[2] : 0.0f)
+                                  : make_float4(Wb * q_b[0], Wb * q_b[1], D == 3 ? Wb * q_b[2] : 0.0f, 0.0f);
+      const int off = sgn * (D == 3 ? stencil_off<D>(i, jj, k, n) : stencil_off<D>(i, k, 0, n));
+      if (merged) {
+        atomicAdd(ga + off, make_float4(ca.x + cb.x, ca.y + cb.y, ca.z + cb.z, ca.w + cb.w));
+      } else {
+        if (va) atomicAdd(ga + off, ca);
+        if (vb) atomicAdd(gb + off, cb);
+      }
+    }
+  }
+}
+
 // Interleaved scatter of the records: node (i, j, k) receives
 //   mass  W * mass_c                      (when WITH_MASS)
 //   vec   W * (a + B dpos)
@@ -445,8 +586,12 @@ template <int D, bool WITH_MASS, bool DET>
 __device__ __forceinline__ void scatter_records(const float* xr, int count, const BoxInfo<D>& bx,
                                                 float* sm, int cap, float4* g, int n,
                                                 const SimParams& P, float mass_c, float fix0,
-                                                float fix1, unsigned& err) {
+                                                float fix1, unsigned& err, bool pair) {
   constexpr int S = Xch<D>::kStride;
+  if (!DET && !bx.use_tile && pair) {
+    scatter_pairs<D, WITH_MASS>(xr, count, g, n, P, mass_c);
+    return;
+  }
   const int j = scatter_slot(threadIdx.x);
   if (j >= count) return;
   const int xi = xidx(j);
@@ -463,7 +608,7 @@ __device__ __forceinline__ void scatter_records(const float* xr, int count, cons
 #pragma unroll
   for (int c = 0; c < D * D; ++c) B[c / D][c % D] = xr[(1 + 2 * D + c) * S + xi];
   float w[D][3], dp[D][3];
-  axes_from_f<D>(f, P, w, dp);
+  if (bx.use_tile || DET) axes_from_f<D>(f, P, w, dp);
   if (bx.use_tile) {
     int lb = base[0] - bx.lo[0];
 #pragma unroll
@@ -527,17 +672,23 @@ __device__ __forceinline__ void scatter_records(const float* xr, int count, cons
       fix_red(g, nb + stencil_off<D>(i, jj, k, n), v, fix0, fix1, WITH_MASS ? D + 1 : D, err);
     });
   } else {
-    float4* gb = g + node_flat<D>(base, n);
-    for_nodes<D>(w, [&](int i, int jj, int k, float W) {
+    // odd lanes walk the stencil in reverse (see reversed_stencil), so two lanes that share
+    // a base hit different nodes in each reduction instruction
+    const bool rev = (threadIdx.x & 1) != 0;
+    int sgn;
+    float4* gb = reversed_stencil<D>(rev, g, n, base, f, B, sgn);
+    float wr[D][3], dpr[D][3];
+    axes_from_f<D>(f, P, wr, dpr);
+    for_nodes<D>(wr, [&](int i, int jj, int k, float W) {
       float q[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        q[c] = a[c] + B[c][0] * dp[0][i] + B[c][1] * dp[1][jj];
-        if (D == 3) q[c] += B[c][D - 1] * dp[D - 1][k];
+        q[c] = a[c] + B[c][0] * dpr[0][i] + B[c][1] * dpr[1][jj];
+        if (D == 3) q[c] += B[c][D - 1] * dpr[D - 1][k];
       }
       float4 v = WITH_MASS ? make_float4(W * mass_c, W * q[0], W * q[1], D == 3 ? W * q[2] : 0.0f)
                            : make_float4(W * q[0], W * q[1], D == 3 ? W * q[2] : 0.0f, 0.0f);
-      atomicAdd(gb + stencil_off<D>(i, jj, k, n), v);
+      atomicAdd(gb + sgn * stencil_off<D>(i, jj, k, n), v);
     });
   }
 }
@@ -549,11 +700,15 @@ __device__ __forceinline__ void scatter_records(const float* xr, int count, cons
 // of them into a box of ~200 nodes.  Particles that share a stencil base touch the same
 // 3^D nodes, so the tile's particles are grouped by base in a shared table, and one warp
 // takes a whole group: lane o < 3^D owns node base + o, sums the group's contributions in
-// registers and issues one reduction.  In 3D a tile holds ~45-64 bases of ~2-8 particles,
+// registers and issues one reduction.  In 3D a tile holds ~16-64 bases of ~2-8 particles,
 // so the reductions drop 2-3x for ~30 extra FMA-class instructions per particle.  Bases
 // whose group overflows the table's slots, and tiles whose base box exceeds its keys, go
 // through the per-particle path.  Not used in the deterministic mode (its sums are
-// fixed point and order-free already).
+// fixed point and order-free already).  Measured on GB300 it is slower than the per-particle
+// reductions (cube3d fused forward 53.2 vs 50.8 us): each group step is a chain of
+// dependent shared-memory reads (slot, then record) and the pass was already limited by
+// its shared-memory instruction queue as much as by the reductions; the pair-merged
+// scatter (scatter_pairs) halves the reductions without that cost.  It stays an option.
 // ---------------------------------------------------------------------------
 constexpr int kBucketKeys = 256;  // bases of one tile's base box the table can hold
 constexpr int kBucketSlots = 8;   // particles per base held in the table
@@ -870,7 +1025,7 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
                                          float la_p, int mat_p, const int* group, const float* wact,
                                          float4* g, int* box_scene, float* sm, float* xr,
                                          int* s_box, int* s_bbox, Buckets& bk, unsigned& err,
-                                         const double* R_in, double* R_out, int64_t N) {
+                                         const double* R_in, double* R_out, int64_t N, bool pair) {
   Axes<D> s;
   bool ok = make_axes<D>(x, P, s) && active;
   if (active && !ok) err |= kErrOOB;
@@ -918,7 +1073,7 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
     const BoxInfo<D> bx = box_extent<D>(ok, s.base, P.tile_capacity, s_box + 16);
     box_zero<D>(bx, sm, P.tile_capacity);
     scatter_records<D, true, DET>(xr, count, bx, sm, P.tile_capacity, g, P.n_grid, P, P.p_mass, P.fix_m,
-                             P.fix_p, err);
+                             P.fix_p, err, pair);
     box_flush<D>(bx, sm, P.tile_capacity, g, P.n_grid);
     if (threadIdx.x == 0 && bx.vol > 0) {
 #pragma unroll
@@ -933,7 +1088,8 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
     cta_bbox_flush<D>(s_bbox, box_scene);
     BoxInfo<D> none;
     none.use_tile = false;
-    scatter_records<D, true, DET>(xr, count, none, sm, 0, g, P.n_grid, P, P.p_mass, P.fix_m, P.fix_p, err);
+    scatter_records<D, true, DET>(xr, count, none, sm, 0, g, P.n_grid, P, P.p_mass, P.fix_m, P.fix_p, err,
+                                  pair);
   }
 }
 
@@ -1058,7 +1214,7 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
     p2g_pass<D, MAT, DET>(P, P.basis, active, scene, p, tile.z, x, v, C, E, staged(stage, 0),
                           staged(stage, 1), MAT == kMixed ? A.matid[p] : MAT, A.group, A.wact,
                      scene_grid(A.PMw, scene, P), A.box_w + scene * 8, sm, xr, s_box, s_bbox,
-                     bk, err, nullptr, A.Rw, N);
+                     bk, err, nullptr, A.Rw, N, (P.pair & 1) != 0);
   }
   if (err) atomicOr(A.err, err);
 }
@@ -1476,7 +1632,8 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
       BoxInfo<D> sbx = bx;
       sbx.use_tile = bx.use_tile && bx.vol <= P.tile_capacity;
       box_zero<D>(sbx, sm, P.tile_capacity);  // same extent as the gather box
-      scatter_records<D, false, DET>(xr, tile.z, sbx, sm, P.tile_capacity, UBs, n, P, 0.0f, fix_u, fix_u, err);
+      scatter_records<D, false, DET>(xr, tile.z, sbx, sm, P.tile_capacity, UBs, n, P, 0.0f, fix_u, fix_u, err,
+                                     false);
       box_flush<D>(sbx, sm, P.tile_capacity, UBs, n);
       if (threadIdx.x == 0 && sbx.vol > 0) {
 #pragma unroll
@@ -1492,7 +1649,8 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
       cta_bbox_flush<D>(s_bbox_ub, A.box_ub + scene * 8);
       BoxInfo<D> none;
       none.use_tile = false;
-      scatter_records<D, false, DET>(xr, tile.z, none, sm, 0, UBs, n, P, 0.0f, fix_u, fix_u, err);
+      scatter_records<D, false, DET>(xr, tile.z, none, sm, 0, UBs, n, P, 0.0f, fix_u, fix_u, err,
+                                     (P.pair & 2) != 0);
     }
   }
 
@@ -1516,7 +1674,7 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
                           staged(stage, b + R::Q + 1), MAT == kMixed ? A.matid[p] : MAT, A.group,
                           A.wact,
                      scene_grid(A.PMm, scene, P), A.box_m + scene * 8, sm, xr, s_box, s_bbox_pm,
-                     bk, err, A.Rm, nullptr, N);
+                     bk, err, A.Rm, nullptr, N, (P.pair & 2) != 0);
   }
   if (err) atomicOr(A.err, err);
 }

@@ -1,0 +1,89 @@
+// peaks.cu -- mpm_measure_peak: arithmetic peaks of this GPU measured with the library's
+// own kernel, the denominators of the ALU rooflines (the FP64 polar factor and its adjoint
+// bound the fixed-corotated passes; their FP64 FLOP/s is compared with this peak).
+//
+// The kernel runs 8 independent fused multiply-add chains per thread (enough to hide the
+// pipe's latency), on 8 CTAs of 256 threads per SM, for a fixed number of iterations; a
+// multiply-add counts as 2 FLOP.  The first launch warms up, the next ones are timed with
+// CUDA events on the caller's stream and the best is returned.
+#include <cuda_runtime.h>
+
+#include "../../include/mpm.h"
+#include "mpm_internal.h"
+
+namespace {
+
+__device__ double g_peak_sink;  // written only when the chains reach an impossible value
+
+constexpr int kChains = 8;
+constexpr int kThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) fma_chains_kernel(int iters, T seed) {
+  T a[kChains];
+  const T b = seed * (T)0.999999, c = seed * (T)1e-7;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) a[k] = seed + (T)(threadIdx.x + k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int k = 0; k < kChains; ++k) a[k] = a[k] * b + c;  // contracted to one FMA
+  }
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += a[k];
+  if (s == (T)-1.2345e-30) g_peak_sink = (double)s;
+}
+
+template <typename T>
+int measure(double* out, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mpm::set_static_error("mpm_measure_peak: no CUDA device");
+    return MPM_ERR_CUDA;
+  }
+  const int blocks = sms * 8;
+  const int iters = sizeof(T) == 8 ? 256 : 4096;  // ~10-30 ms a launch
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    mpm::set_static_error("mpm_measure_peak: cudaEventCreate failed");
+    return MPM_ERR_CUDA;
+  }
+  double best = 0.0;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, st);
+    fma_chains_kernel<T><<<blocks, kThreads, 0, st>>>(iters, (T)1.0000001);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    const double flops = 2.0 * kChains * 16.0 * iters * (double)blocks * kThreads;
+    if (e == cudaSuccess && rep > 0 && ms > 0.0f && flops / (ms * 1e-3) > best)
+      best = flops / (ms * 1e-3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mpm::set_static_error(cudaGetErrorString(e));
+    return MPM_ERR_CUDA;
+  }
+  *out = best;
+  return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" int mpm_measure_peak(int32_t kind, double* flops_per_s, void* stream) {
+  if (!flops_per_s || (kind != MPM_PEAK_FP64_FMA && kind != MPM_PEAK_FP32_FMA)) {
+    mpm::set_static_error("mpm_measure_peak: bad kind or NULL output");
+    return MPM_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return kind == MPM_PEAK_FP64_FMA ? measure<double>(flops_per_s, s) : measure<float>(flops_per_s, s);
+}

@@ -33,7 +33,7 @@ MPM_OPT_USE_GRAPHS, MPM_OPT_SMEM_TILE, MPM_OPT_TILE_CAPACITY, MPM_OPT_PROFILE = 
 MPM_OPT_GATHER_CAPACITY, MPM_OPT_GRID_BLOCKS, MPM_OPT_POLAR_CACHE = 5, 6, 7
 MPM_OPT_PERSISTENT, MPM_OPT_BARRIER_TIMEOUT_US, MPM_OPT_BARRIER_TEST_EXTRA = 8, 9, 10
 MPM_OPT_PERSISTENT_CHUNK, MPM_OPT_GRID_RECOMPUTE, MPM_OPT_OVERLAP_RESIM = 11, 12, 13
-MPM_OPT_BUCKET_SCATTER = 14
+MPM_OPT_BUCKET_SCATTER, MPM_OPT_PAIR_SCATTER, MPM_OPT_SORT_ORDER = 14, 15, 16
 KERNEL_CATEGORIES = {1: "p2g", 2: "g2p_p2g", 3: "g2p_p2g_full", 4: "g2p", 5: "grid_clear",
                      6: "adj_g2p", 7: "adj_fused", 8: "adj_p2g", 9: "persistent_step",
                      10: "persistent_adj", 11: "controller"}
@@ -43,7 +43,8 @@ MPM_INFO_KEEPS_SEGMENT_GRIDS, MPM_INFO_ACT_PARAMS, MPM_INFO_CKPT_EVERY = 4, 5, 6
 EXPORTED = ["mpm_workspace_bytes", "mpm_create", "mpm_set_initial", "mpm_forward",
             "mpm_get_state", "mpm_loss", "mpm_backward", "mpm_sync_status", "mpm_set_option",
             "mpm_get_info", "mpm_get_profile", "mpm_last_error", "mpm_destroy",
-            "mpm_step_noalloc", "mpm_set_particle_materials", "mpm_initial_p2g_grid"]
+            "mpm_step_noalloc", "mpm_set_particle_materials", "mpm_initial_p2g_grid",
+            "mpm_measure_peak", "mpm_plan_checkpoints"]
 
 
 class MPMError(RuntimeError):
@@ -111,6 +112,9 @@ def lib(load_only: bool = False):
             "mpm_step_noalloc": (ctypes.c_int, [D, vp, vp, vp, vp, vp, vp]),
             "mpm_set_particle_materials": (ctypes.c_int, [vp, vp, vp]),
             "mpm_initial_p2g_grid": (ctypes.c_int, [vp, vp, vp]),
+            "mpm_measure_peak": (ctypes.c_int, [i32, ctypes.POINTER(ctypes.c_double), vp]),
+            "mpm_plan_checkpoints": (ctypes.c_int, [D, i32, sz, ctypes.POINTER(i32),
+                                                    ctypes.POINTER(i32), ctypes.POINTER(sz)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -169,6 +173,14 @@ def mpm_workspace_bytes(desc: SceneDesc, max_steps: int) -> int:
     return out.value
 
 
+def mpm_plan_checkpoints(desc: SceneDesc, max_steps: int, budget_bytes: int):
+    """(ckpt_every, ckpt_coarse, workspace bytes) of the fastest schedule within the budget."""
+    k, M, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    _check(lib().mpm_plan_checkpoints(ctypes.byref(desc), max_steps, budget_bytes, ctypes.byref(k),
+                                      ctypes.byref(M), ctypes.byref(b)))
+    return k.value, M.value, b.value
+
+
 def mpm_create(desc: SceneDesc, workspace, workspace_bytes: int, max_steps: int):
     h = ctypes.c_void_p()
     _check(lib().mpm_create(ctypes.byref(desc), _ptr(workspace), workspace_bytes, max_steps,
@@ -223,6 +235,16 @@ def mpm_initial_p2g_grid(h, grid, stream=None):
     _check(lib().mpm_initial_p2g_grid(h, _ptr(grid), _stream(stream)), h)
 
 
+MPM_PEAK_FP64_FMA, MPM_PEAK_FP32_FMA = 0, 1
+
+
+def mpm_measure_peak(kind: int, stream=None) -> float:
+    """Measured FMA peak (FLOP/s) of the current GPU: MPM_PEAK_FP64_FMA or MPM_PEAK_FP32_FMA."""
+    out = ctypes.c_double()
+    _check(lib().mpm_measure_peak(int(kind), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
 def mpm_get_profile(h, kind: int):
     """(launches, total_ms) of one kernel category while MPM_OPT_PROFILE is on."""
     n, ms = ctypes.c_int64(), ctypes.c_double()
@@ -254,7 +276,13 @@ class Simulator:
     """One handle plus its workspace (a torch tensor).  `desc` is a dict with the fields
     of mpm_scene_desc (see include/mpm.h); `max_steps` bounds T."""
 
-    def __init__(self, desc: dict, max_steps: int, device="cuda"):
+    def __init__(self, desc: dict, max_steps: int, device="cuda", workspace_budget=None):
+        """workspace_budget (bytes): if given, ckpt_every and ckpt_coarse are chosen by
+        mpm_plan_checkpoints for that budget instead of taken from desc."""
+        desc = dict(desc)
+        if workspace_budget is not None:
+            k, M, _ = mpm_plan_checkpoints(make_desc(desc), max_steps, int(workspace_budget))
+            desc["ckpt_every"], desc["ckpt_coarse"] = k, M
         self.desc = dict(desc)
         self.dim = int(desc["dim"])
         self.n_scenes = len(desc["n_particles"])
@@ -304,6 +332,13 @@ class Simulator:
         if material is not None:
             self._material = material.to(self.device, torch.int32).contiguous()
         if self.desc.get("material") == MPM_MIXED:  # every set-up re-sorts the particles
+            mpm_set_particle_materials(self.h, self._material)
+
+    def reload(self):
+        """Run the set-up again from the last set_initial inputs (after an option that the
+        set-up applies, such as MPM_OPT_SORT_ORDER)."""
+        mpm_set_initial(self.h, *self._inputs)
+        if self.desc.get("material") == MPM_MIXED:
             mpm_set_particle_materials(self.h, self._material)
 
     def forward(self, T):

@@ -104,6 +104,7 @@ def test_host_side_validation_without_gpu(libpath):
     assert mpm.lib().mpm_forward(None, 1, None) == mpm.MPM_ERR_ARG
     assert mpm.lib().mpm_sync_status(None) == mpm.MPM_ERR_ARG
     assert mpm.lib().mpm_initial_p2g_grid(None, None, None) == mpm.MPM_ERR_ARG
+    assert mpm.lib().mpm_measure_peak(7, None, None) == mpm.MPM_ERR_ARG
 
 
 def test_mass_spring_binding_and_host_validation(libpath):
@@ -127,3 +128,38 @@ def test_mass_spring_binding_and_host_validation(libpath):
     with pytest.raises(mpm.MPMError):
         ms.ms_workspace_bytes(d, 0)
     assert ms.lib().ms_forward(None, None, None, None, 1, None) == mpm.MPM_ERR_ARG
+
+
+@pytest.mark.gpu
+def test_measured_peaks_are_sane(libpath):
+    """The FMA peaks the ALU rooflines divide by: positive, FP32 well above FP64 (this
+    part's FP64 rate is a small fraction of FP32), both below the chip's nominal ceilings
+    (FP32: 152 SMs x 128 lanes x 2 FLOP x ~2.1 GHz = 82 TFLOP/s)."""
+    from paper_1910_00935_gb300 import mpm
+    f64 = mpm.mpm_measure_peak(mpm.MPM_PEAK_FP64_FMA)
+    f32 = mpm.mpm_measure_peak(mpm.MPM_PEAK_FP32_FMA)
+    assert 1e11 < f64 < 2e13, f64
+    assert 1e13 < f32 < 1e14, f32
+    assert f32 > 4 * f64
+
+
+def test_planned_schedule_fits_budget_and_prefers_fewer_passes(libpath):
+    """mpm_plan_checkpoints (host only): within a budget it returns the schedule with the
+    fewest re-simulated steps; a huge budget keeps every state (nothing re-simulated), the
+    smallest one-level workspace keeps one level, one byte less needs two levels, and a
+    budget below any schedule is refused."""
+    from paper_1910_00935_gb300 import mpm, scenes
+    desc = dict(scenes.make("cube3d", n_side=24, n_grid=32)["desc"], ckpt_every=16)
+    T = 512
+    ws = lambda k, M=0: mpm.mpm_workspace_bytes(mpm.make_desc(dict(desc, ckpt_every=k,
+                                                                   ckpt_coarse=M)), T)
+    k, M, b = mpm.mpm_plan_checkpoints(mpm.make_desc(desc), T, 1 << 50)
+    assert (k, M) == (T, 0) and b == ws(T)
+    one_min = min(ws(k) for k in range(1, T + 1))
+    k, M, b = mpm.mpm_plan_checkpoints(mpm.make_desc(desc), T, one_min)
+    assert M == 0 and b == one_min == ws(k)
+    k, M, b = mpm.mpm_plan_checkpoints(mpm.make_desc(desc), T, one_min - 1)
+    assert M >= 2 and b < one_min and b == ws(k, M)
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.mpm_plan_checkpoints(mpm.make_desc(desc), T, one_min // 2)
+    assert e.value.code == mpm.MPM_ERR_WORKSPACE

@@ -8,7 +8,8 @@ torch = pytest.importorskip("torch")
 
 
 def test_coordinate_descent_finds_separable_minimum():
-    target = {"gather_capacity": 1024, "smem_tile": 1, "bucket_scatter": 1, "tile_capacity": 2048,
+    target = {"gather_capacity": 1024, "smem_tile": 1, "bucket_scatter": 1, "pair_scatter": 3, "sort_order": 1,
+              "tile_capacity": 2048,
               "grid_blocks": 64, "persistent": 1, "grid_recompute": 1, "overlap_resim": 0}
     cost = lambda c: sum((0 if c[k] == target[k] else 1.0 + i) for i, k in enumerate(c))
     best, t, log = autotune.coordinate_descent(cost, rounds=3)

@@ -125,3 +125,32 @@ def test_two_level_checkpoints_store_fewer_states(mpm):
     state = 24 * 4 * sum(scene["desc"]["n_particles"])
     # 256 checkpoints -> 32 coarse ones + 8 rebuilt ones
     assert b1 - b2 >= (256 - 32 - 8) * state
+
+
+def test_budget_chosen_schedule_bitwise_equal_one_level(mpm):
+    """A two-level schedule chosen by mpm_plan_checkpoints for a budget just below the
+    smallest one-level workspace gives, in the deterministic mode, bitwise the gradients of
+    the one-level schedule at the same interval (Appendix D.2's segment invariance, carried
+    to two levels), through the Simulator's workspace_budget argument."""
+    scene = scenes.make("cube3d", n_side=24, n_grid=32)
+    scene["desc"]["deterministic_p2g"] = 1
+    T = 512
+    desc = scene["desc"]
+    one_min = min(mpm.mpm_workspace_bytes(mpm.make_desc(dict(desc, ckpt_every=k)), T)
+                  for k in range(1, T + 1))
+    sim = mpm.Simulator(desc, T, workspace_budget=one_min - 1)
+    k, M = sim.desc["ckpt_every"], sim.desc["ckpt_coarse"]
+    assert M >= 2 and sim.ws_bytes < one_min, (k, M, sim.ws_bytes, one_min)
+    seeds = _random_seeds(scene, np.random.default_rng(61))
+    a = scene["arrays"]
+    t = lambda key: torch.as_tensor(a[key])
+    sim.set_initial(t("x0"), t("v0"), t("C0"), t("F0"), t("E"), t("nu"))
+    sim.forward(T)
+    g = {kk: v.cpu().numpy() for kk, v in sim.backward(**{kk: torch.as_tensor(v)
+                                                         for kk, v in seeds.items()}).items()}
+    assert mpm.mpm_sync_status(sim.h) == mpm.MPM_OK
+    sim.close()
+    scene["desc"]["ckpt_every"], scene["desc"]["ckpt_coarse"] = k, 0
+    one = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    for key in KEYS:
+        assert np.array_equal(g[key], one["grad"][key]), key

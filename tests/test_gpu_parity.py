@@ -497,12 +497,18 @@ def _random_cloud():
     return scene
 
 
+SCATTER_FORMS = {"pairs": {}, "pairs_forward_only": {"MPM_OPT_PAIR_SCATTER": 1},
+                 "per_particle": {"MPM_OPT_PAIR_SCATTER": 0},
+                 "bucket": {"MPM_OPT_PAIR_SCATTER": 0, "MPM_OPT_BUCKET_SCATTER": 1}}
+
+
 @pytest.mark.parametrize("case", ["dense", "cloud", "rects2d", "robots3d"])
-@pytest.mark.parametrize("bucket", [1, 0])
-def test_scatter_forms_match_oracle(mpm, case, bucket):
-    """States and random-functional gradients with the bucketed scatter on and off, on
-    scenes that exercise its overflow (dense cube), its fall-back (random cloud), 2D groups
-    (three per warp step) and actuated robots."""
+@pytest.mark.parametrize("form", list(SCATTER_FORMS))
+def test_scatter_forms_match_oracle(mpm, case, form):
+    """States and random-functional gradients for each scatter form (pair-merged reductions,
+    the default; one reduction per particle and node; the per-base bucket table) on scenes
+    that exercise pairs whose bases differ and the bucket table's overflow (dense cube), its
+    fall-back (random cloud), 2D (three bucket groups per warp step) and actuated robots."""
     scene = {"dense": _dense_cube, "cloud": _random_cloud,
              "rects2d": lambda: scenes.make("rects2d", n_scenes=4, n_min=500, n_max=3000),
              "robots3d": lambda: scenes.make("robots3d", n_scenes=2, dims=(12, 8, 8))}[case]()
@@ -510,7 +516,7 @@ def test_scatter_forms_match_oracle(mpm, case, bucket):
     scene["desc"]["ckpt_every"] = 3
     seeds = _random_seeds(scene, np.random.default_rng(21))
     g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False,
-                 options={mpm.MPM_OPT_BUCKET_SCATTER: bucket})
+                 options={getattr(mpm, k): v for k, v in SCATTER_FORMS[form].items()})
     _compare_states(g["state"], _oracle_states(scene, T), scene, POS_TOL)
     o = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
     keys = ["gx0", "gv0", "gC0", "gF0", "gE", "gnu"] + (["gw"] if scene["desc"]["n_groups"] else [])

@@ -18,10 +18,10 @@ MUTANTS = {
                   "s->w[a][2] = 0.5 * (f - 0.5) * (f - 0.4);"),
     "gravity_sign": ("gp[ni * d + a] / gm[ni] + P->dt * P->gravity[a]",
                      "gp[ni * d + a] / gm[ni] - P->dt * P->gravity[a]"),
-    "stress_kappa_sign": ("double kappa = -P->dt * vol * 4.0 / (dx * dx);",
-                          "double kappa = P->dt * vol * 4.0 / (dx * dx);"),
-    "apic_C_dropped": ("A[i][j] = kappa * tau[i][j] + m * Cp[i][j];\n    for (int o = 0; o < nst; o++) {\n      int off[3], idx[3];\n      double W, gW[3], dpos[3];\n      offset_of(d, o, off);\n      stencil_eval(d, n, &s, off, &W, gW, dpos, idx);\n      int64_t ni = node_index(d, n, idx);\n      gm[ni]",
-                       "A[i][j] = kappa * tau[i][j];\n    for (int o = 0; o < nst; o++) {\n      int off[3], idx[3];\n      double W, gW[3], dpos[3];\n      offset_of(d, o, off);\n      stencil_eval(d, n, &s, off, &W, gW, dpos, idx);\n      int64_t ni = node_index(d, n, idx);\n      gm[ni]"),
+    "stress_kappa_sign": ("k.kappa = -P->dt * k.vol * 4.0 / (k.dx * k.dx);",
+                          "k.kappa = P->dt * k.vol * 4.0 / (k.dx * k.dx);"),
+    "apic_C_dropped": ("A[i][j] = kappa * tau[i][j] + m * Cp[i][j];\n  for (int o = 0; o < K->nst; o++) {",
+                       "A[i][j] = kappa * tau[i][j];\n  for (int o = 0; o < K->nst; o++) {"),
     "C_scale": ("Cn[a][b] = 4.0 / (dx * dx) * B[a][b];",
                 "Cn[a][b] = 3.0 / (dx * dx) * B[a][b];"),
     "F_update_order": ("mmul(d, G, Fp, Fn);", "mmul(d, Fp, G, Fn);"),
@@ -34,11 +34,11 @@ MUTANTS = {
     "nh_log": ("for (int i = 0; i < d; i++) tau[i][i] += la * log(J);",
                "for (int i = 0; i < d; i++) tau[i][i] += la * (J - 1.0);"),
     "polar_adjoint_factor": ("Fbar[i][j] += 2.0 * RY[i][j];", "Fbar[i][j] += RY[i][j];"),
-    "g2p_adj_transpose": ("mtrans(d, G, Gt);\n    mmul(d, Gt, Fb1p, Fbp);",
-                          "mtrans(d, G, Gt);\n    mmul(d, G, Fb1p, Fbp);"),
+    "g2p_adj_transpose": ("mtrans(d, G, Gt);\n  mmul(d, Gt, Fb1p, Fbp);",
+                          "mtrans(d, G, Gt);\n  mmul(d, G, Fb1p, Fbp);"),
     "p2g_adj_mass_term": ("double Wbar = m * gmb[ni];", "double Wbar = 0.0;"),
-    "grid_adj_mass_sign": ("mb -= gub[ni * d + a] * g.gp[ni * d + a]",
-                           "mb += gub[ni * d + a] * g.gp[ni * d + a]"),
+    "grid_adj_mass_sign": ("mb -= gub[ni * d + a] * gp[ni * d + a]",
+                           "mb += gub[ni * d + a] * gp[ni * d + a]"),
     "actuation_index": ("a += wact[g * P->n_basis + (k - 1)] * act_basis(P, k, t);",
                         "a += wact[g * P->n_basis + (k - 1)] * act_basis(P, k - 1, t);"),
     "actuation_adjoint_transpose": ("Fbar[i][axis] += act * s;", "Fbar[axis][i] += act * s;"),
