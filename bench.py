@@ -40,9 +40,9 @@ UNIT = "particle-steps/s"
 def alg_bytes(d):
     """Algorithmic bytes per particle of each pass category (FP32 state rows; the minimum
     each pass must move).  S: full state x, v, C, F; XF: x and F rows; M: mu, la;
-    MB: mu-bar, la-bar read and written."""
+    MB: mu-bar, la-bar (FP64 sums over the steps) read and written."""
     S, XF, X, C = 4 * (2 * d + 2 * d * d), 4 * (d + d * d), 4 * d, 4 * d * d
-    M, MB = 8, 16
+    M, MB = 8, 32
     return {
         "p2g": S + M,                       # read x, v, C, F, mu, la
         "g2p_p2g": XF + M + XF,             # read x, F, mu, la; write x, F
@@ -106,7 +106,7 @@ def pass_bytes_ctrl(N, T, K, dim=3, kept=True):
     the x and v rows of the adjoint."""
     a = alg_bytes(dim)
     S = 4 * (2 * dim + 2 * dim * dim)
-    XF, M, MB = 4 * (dim + dim * dim), 8, 16
+    XF, M, MB = 4 * (dim + dim * dim), 8, 32
     sense, sense_adj = 4 * 2 * dim + 4, 4 + 2 * 4 * 2 * dim
     by = {k: 0 for k in ("p2g", "g2p_p2g", "g2p_p2g_full", "g2p", "adj_g2p", "adj_fused",
                          "adj_p2g", "controller")}
@@ -557,6 +557,149 @@ def run_springs(args, rank, world):
     sim.close()
 
 
+def fp64_flop_per_particle(workload, category):
+    """FP64 FLOP per particle of one launch of `category` (2 per fused multiply-add, 1 per add
+    or multiply), from profiles/fp64_<category>_<workload>.md when that summary was taken
+    on these kernels (same source digest); else None."""
+    path = os.path.join(ROOT, "profiles", f"fp64_{category}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    if f"source digest: {source_digest()}" not in text:
+        return None
+    import re
+    m = re.search(r"FP64 FLOP per particle: ([0-9.eE+-]+)", text)
+    return float(m.group(1)) if m else None
+
+
+def fp64_roofline(mpm, workload, category, n_launch, cat_ms, particles_per_launch):
+    """Achieved FP64 FLOP/s of a kernel category against the GPU's FP64 FMA peak measured
+    live with the library's own kernel (mpm_measure_peak)."""
+    per = fp64_flop_per_particle(workload, category)
+    peak = mpm.mpm_measure_peak(mpm.MPM_PEAK_FP64_FMA)
+    out = {"bound": "fp64", "peak": peak / 1e12, "unit": "TFLOP/s", "kernel": category,
+           "peak_source": "measured live: mpm_measure_peak (FP64 FMA chains, CUDA events)"}
+    if per is None or not n_launch:
+        out.update(achieved=None, frac=None,
+                   note="no FP64 FLOP count captured on these kernels (profiles/fp64_*.md)")
+        return out
+    avg_ms = cat_ms / n_launch
+    achieved = per * particles_per_launch / (avg_ms / 1e3) / 1e12
+    out.update(achieved=achieved, frac=achieved / out["peak"], flop_per_particle=per,
+               avg_launch_ms=avg_ms)
+    return out
+
+
+def batched_line(name, dev, flush, steps=2, warmup=1, autotune_probe=True):
+    """One batched configuration measured compactly for the headline's JSON line: forward and
+    forward+backward particle-steps/s with inputs resident (L2 flushed between timed steps),
+    the dominant kernel's roofline (HBM, and FP64 for the fixed-corotated passes), the same
+    batch as one scene per launch sequence, the persistent launch form, and the autotuned
+    knobs."""
+    import torch
+    from paper_1910_00935_gb300 import autotune, mpm
+    from paper_1910_00935_gb300.sharding import subset
+    scene, N, T, descr = make_workload(name)
+    desc, a = scene["desc"], scene["arrays"]
+    G = desc.get("n_groups", 0)
+    S = len(desc["n_particles"])
+    t = lambda k: torch.as_tensor(a[k]).to(dev)
+    target = t("target")
+
+    def run(sim):
+        sim.forward(T)
+        _, gT, _ = sim.loss(desc["loss_kind"], target)
+        sim.backward(dL_dx=gT)
+
+    def timed(fn, n):
+        ms = []
+        for _ in range(n):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sum(ms) / len(ms)
+
+    sim = mpm.from_scene(scene, max_steps=T, device=dev)
+    for _ in range(warmup):
+        run(sim)
+    torch.cuda.synchronize()
+    sim.check()
+    ms = timed(lambda: run(sim), steps)
+    fwd_ms = timed(lambda: sim.forward(T), 1)
+    # per-kernel timing pass (CUDA events around every launch on its stream)
+    sim.set_option(mpm.MPM_OPT_PROFILE, 1)
+    flush.fill_(1)
+    run(sim)
+    torch.cuda.synchronize()
+    prof = sim.profile()
+    sim.set_option(mpm.MPM_OPT_PROFILE, 0)
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_launch, dom_ms = prof[dom]
+    step_bytes = pass_bytes(N, T, desc["ckpt_every"], desc["dim"],
+                            kept=bool(sim.info(mpm.MPM_INFO_KEEPS_SEGMENT_GRIDS)))
+    hbm, peak_src = measured_peaks()
+    roof = None
+    if dom in step_bytes and n_launch:
+        avg = dom_ms / n_launch
+        ach = step_bytes[dom] / n_launch / (avg / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": profiled_traffic(name, dom), "kernel": dom,
+                "alg_bytes_per_launch": step_bytes[dom] / n_launch, "avg_launch_ms": avg,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    roof64 = None
+    if desc["material"] in (mpm.MPM_FIXED_COROTATED, mpm.MPM_MIXED) and desc["dim"] == 3:
+        roof64 = fp64_roofline(mpm, name, dom, n_launch, dom_ms, N)
+    line = {"workload": descr, "particles": N, "scenes": S, "T": T,
+            "value": N * T / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "forward": {"value": N * T / (fwd_ms / 1e3), "ms": fwd_ms},
+            "roofline": roof, "roofline_fp64": roof64,
+            "kernel_times_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
+            "precision": precision_label(desc)}
+    # the same batch through persistent launches (each run of same-kind passes one launch)
+    sim.set_option(mpm.MPM_OPT_PERSISTENT, 1)
+    run(sim)
+    torch.cuda.synchronize()
+    pms = timed(lambda: run(sim), steps)
+    sim.set_option(mpm.MPM_OPT_PERSISTENT, 0)
+    line["persistent"] = {"value": N * T / (pms / 1e3), "ms_per_step": pms}
+    # autotuned knobs (coordinate descent over the library's options, short probes)
+    if autotune_probe:
+        cfg = autotune.tune(sim, T=min(T, 64), repeats=1, force=True)
+        run(sim)
+        torch.cuda.synchronize()
+        ams = timed(lambda: run(sim), steps)
+        line["autotuned"] = {"value": N * T / (ams / 1e3), "ms_per_step": ams, "config": cfg}
+    sim.check()
+    sim.close()
+    # one scene per launch sequence, scenes back to back
+    sims = []
+    for i in range(S):
+        sub = subset(scene, [i])
+        si = mpm.from_scene(sub, max_steps=T, device=dev)
+        si._tgt = torch.as_tensor(sub["arrays"]["target"]).to(dev)
+        sims.append(si)
+
+    def per_scene():
+        for si in sims:
+            si.forward(T)
+            _, gT, _ = si.loss(desc["loss_kind"], si._tgt)
+            si.backward(dL_dx=gT)
+
+    per_scene()
+    torch.cuda.synchronize()
+    sms = timed(per_scene, 1)
+    for si in sims:
+        si.check()
+        si.close()
+    line["one_scene_per_launch"] = {"value": N * T / (sms / 1e3), "ms_per_step": sms,
+                                    "form": "one scene per launch sequence, back to back"}
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -574,6 +717,9 @@ def main():
                     help="1: run each run of same-kind passes as one persistent launch")
     ap.add_argument("--opt", action="append", default=[], metavar="MPM_OPT_NAME=VALUE",
                     help="set a library option (include/mpm.h) for the run; repeatable")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched configurations (rects2d, robots3d) that the default "
+                         "cube3d line carries under 'batched'")
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: split the one batch's scenes across the ranks, "
                          "balanced by particle count (strong scaling; default: every rank "
@@ -813,6 +959,11 @@ def main():
         every = [None] * world
         dist.all_gather_object(every, losses)
         losses = [v for r in every for v in r]
+    # the batched configurations of the same workload family (one GPU, default line only)
+    batched = None
+    if world == 1 and args.workload == "cube3d" and not args.no_batched and not args.T:
+        sim.close()
+        batched = {w: batched_line(w, dev, flush) for w in ("rects2d", "robots3d")}
     if rank != 0:
         return
     cb = None
@@ -840,6 +991,7 @@ def main():
                     "scope": "rank 0's scenes"},
         "loss": {"sum": float(sum(losses)), "scenes": len(losses)},
         "one_scene_per_launch": per_scene,
+        "batched": batched,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roof,

@@ -83,7 +83,7 @@ __global__ void ctrl_sense_kernel(int dim, int G, int64_t N, const int4* tiles, 
     const int g = group[p];
     slot[i] = (g >= 0 && g < G) ? g + 1 : 0;
     for (int a = 0; a < dim; ++a) {
-      vals[a][i] = st[(int64_t)a * N + p];
+      vals[a][i] = (float)pos_from_fix(st[(int64_t)a * N + p]);  // fixed-point position rows
       vals[dim + a][i] = st[(int64_t)(dim + a) * N + p];
     }
     vals[2 * dim][i] = 1.0f;

@@ -201,8 +201,8 @@ Layout make_layout(const Dims& m) {
   L.matid = take(N * 4);
   L.wact = take(S * (size_t)std::max<int64_t>(kMaxGroups * kMaxBasis, m.n_act) * 4);
   L.wbar_tile = take((size_t)m.n_tiles * kMaxGroups * kMaxBasis * 4);
-  L.mubar = take(N * 4);
-  L.labar = take(N * 4);
+  L.mubar = take(N * 8);  // FP64 sums over the steps (see AdjArgs::mubar)
+  L.labar = take(N * 8);
   L.fin = take(Q * N * 4);
   L.cur = take(Q * N * 4);
   L.ckpt = take((size_t)m.n_ckpt * Q * N * 4);
@@ -382,6 +382,7 @@ SimParams params_for(const mpm_handle* h, int t) {
   P.bucket = h->bucket_scatter && !d.deterministic_p2g ? 1 : 0;
   P.pair = d.deterministic_p2g ? 0 : h->pair_scatter;
   P.f_diag = 0.0f;  // the workspace holds E = F - I
+  P.xfix = 1;       // and positions in 32-bit fixed point
   P.det = d.deterministic_p2g;
   P.node_words = h->m.words;
   if (P.det) {
@@ -710,8 +711,8 @@ struct Launcher {
     A.adj = h->at<float>(h->L.adj);
     A.mu = h->at<float>(h->L.mu);
     A.la = h->at<float>(h->L.la);
-    A.mubar = h->at<float>(h->L.mubar);
-    A.labar = h->at<float>(h->L.labar);
+    A.mubar = h->at<double>(h->L.mubar);
+    A.labar = h->at<double>(h->L.labar);
     A.group = h->at<int>(h->L.group);
     A.matid = h->at<int>(h->L.matid);
     A.wact = act_ptr(h, s_step + 1);
@@ -1415,7 +1416,8 @@ int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* s
   for (int k = 0; k < 4; ++k) {
     if (outs[k]) {
       // the workspace holds E = F - I; the caller gets F
-      CK(launch_scatter_rows(rows[k], m.N, perm, fin + (size_t)r0 * m.N, outs[k], k == 3 ? D : 0, s));
+      CK(launch_scatter_rows(rows[k], m.N, perm, fin + (size_t)r0 * m.N, outs[k], k == 3 ? D : 0,
+                             k == 0 ? D : 0, s));
       ++h->launches;
     }
     r0 += rows[k];
@@ -1462,8 +1464,8 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
     CK(launch_gather_rows(rows[k], m.N, perm, seeds[k], adj + (size_t)r0 * m.N, s));
     r0 += rows[k];
   }
-  CK(cudaMemsetAsync(h->at<float>(L.mubar), 0, (size_t)m.N * 4, s));
-  CK(cudaMemsetAsync(h->at<float>(L.labar), 0, (size_t)m.N * 4, s));
+  CK(cudaMemsetAsync(h->at<double>(L.mubar), 0, (size_t)m.N * 8, s));
+  CK(cudaMemsetAsync(h->at<double>(L.labar), 0, (size_t)m.N * 8, s));
   const bool ctrl = m.ctrl_H > 0;
   // per-tile sums of the actuation adjoint: times the sine basis (open loop), or per step
   // and group for the controller (cleared again by each controller reverse)
@@ -1492,14 +1494,14 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
   r0 = 0;
   for (int k = 0; k < 4; ++k) {
     if (outs[k]) {
-      CK(launch_scatter_rows(rows[k], m.N, perm, adj + (size_t)r0 * m.N, outs[k], 0, s));
+      CK(launch_scatter_rows(rows[k], m.N, perm, adj + (size_t)r0 * m.N, outs[k], 0, 0, s));
       ++h->launches;
     }
     r0 += rows[k];
   }
   if (gE || gnu) {
-    CK(launch_material_grad(m.N, perm, h->at<float>(L.E), h->at<float>(L.nu), h->at<float>(L.mubar),
-                            h->at<float>(L.labar), gE, gnu, s));
+    CK(launch_material_grad(m.N, perm, h->at<float>(L.E), h->at<float>(L.nu), h->at<double>(L.mubar),
+                            h->at<double>(L.labar), gE, gnu, s));
     ++h->launches;
   }
   if (gw && ctrl) {

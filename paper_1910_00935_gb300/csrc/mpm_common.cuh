@@ -83,6 +83,8 @@ struct SimParams {
   int gather_capacity;     // max nodes of a CTA's shared gather box (0 = gathers through L1)
   int bucket;              // 1: FP32 scatters go through the per-base bucket table (one
                            // reduction per base and node); 0: one per particle and node
+  int xfix;                // 1: the state's x rows hold positions in 32-bit fixed point
+                           // (the float bits are the int32 x * 2^31), 0: FP32 positions
   int pair;                // FP32 reductions straight to the grid merge pairs of particles
                            // that share a stencil base (one per pair and node): bit 0 in
                            // the forward passes, bit 1 in the adjoint passes
@@ -151,6 +153,36 @@ __device__ __forceinline__ void fix_scales_from(float m0, float& fix, float& unf
 }
 
 // ---------------------------------------------------------------------------
+// Fixed-point positions.  An FP32 position in [0, 1) carries ~6e-8 of absolute precision,
+// and rounding it at every step is what bounds the accuracy of long runs: emulated in the
+// FP64 oracle on a 4,096-particle cube over 1,024 steps, rounding x alone to FP32 after each
+// step moves dL/dmu by 7.4e-4 and dL/dF0 by 1.5e-4 (relative L2), while 32-bit fixed point
+// (resolution 2^-31 = 4.7e-10) moves them by 1.6e-5 and 5e-7 -- at the same 4 bytes.  The
+// state's x rows therefore hold int32(x * 2^31) in their float bits; the stencil base and
+// fraction are formed exactly from the integer, and the step's advance x += dt v adds the
+// rounded increment in integer arithmetic.  A particle that leaves [-1, 1) saturates (it left
+// the grid long before, and its stencil check reports it).
+// ---------------------------------------------------------------------------
+constexpr float kFixPos = 2147483648.0f;              // 2^31
+constexpr double kFixPosInv = 4.656612873077392578e-10;  // 2^-31
+
+__device__ __forceinline__ int fix_saturate(long long v) {
+  return v > 2147483647LL ? 2147483647 : (v < -2147483648LL ? (int)(-2147483647 - 1) : (int)v);
+}
+// FP32 position -> fixed-point bits
+__device__ __forceinline__ float pos_to_fix(float x) {
+  return __int_as_float(fix_saturate(__float2ll_rn(x * kFixPos)));
+}
+// fixed-point bits -> position (FP64 is exact; FP32 rounds to the nearest float)
+__device__ __forceinline__ double pos_from_fix(float raw) {
+  return (double)__float_as_int(raw) * kFixPosInv;
+}
+// x + delta on fixed-point bits (delta rounded once to the 2^-31 grid)
+__device__ __forceinline__ float pos_advance(float raw, float delta) {
+  return __int_as_float(fix_saturate((long long)__float_as_int(raw) + __float2ll_rn(delta * kFixPos)));
+}
+
+// ---------------------------------------------------------------------------
 // quadratic B-spline stencil (MLS-MPM, Hu et al. 2018), kept per axis: the weight of
 // node base + (i, j, k) is w[0][i] w[1][j] w[2][k] and dpos = (dp[0][i], dp[1][j], dp[2][k])
 // ---------------------------------------------------------------------------
@@ -170,12 +202,24 @@ __device__ __forceinline__ bool make_axes(const float* x, const SimParams& P, Ax
   bool ok = true;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    float X = x[a] * P.inv_dx;
-    float b = floorf(X - 0.5f);
-    bool good = (X == X) && b >= 0.0f && b <= (float)(P.n_grid - 3);
+    float b, f;
+    bool good;
+    if (P.xfix) {
+      // X = x / dx with 31 fractional bits, exact in 64-bit integers
+      const long long X = (long long)__float_as_int(x[a]) * (long long)P.n_grid;
+      const long long bi = (X - (1LL << 30)) >> 31;  // floor(X - 0.5)
+      good = bi >= 0 && bi <= (long long)(P.n_grid - 3);
+      b = good ? (float)bi : 0.0f;
+      // the fraction X - base in [0.5, 1.5): below 2^32 in units of 2^-31 (FP32 rounds it once)
+      f = good ? __uint2float_rn((unsigned)(X - (bi << 31))) * (1.0f / kFixPos) : 1.0f;
+    } else {
+      const float Xf = x[a] * P.inv_dx;
+      b = floorf(Xf - 0.5f);
+      good = (Xf == Xf) && b >= 0.0f && b <= (float)(P.n_grid - 3);
+      b = good ? b : 0.0f;
+      f = good ? Xf - b : 1.0f;
+    }
     ok = ok && good;
-    b = good ? b : 0.0f;
-    float f = good ? X - b : 1.0f;
     s.base[a] = (int)b;
     s.f[a] = f;
     float r0 = 1.5f - f, r1 = f - 1.0f, r2 = f - 0.5f;
@@ -695,7 +739,9 @@ __device__ __forceinline__ float kirchhoff_adjoint(const float E[D][D], float mu
         }
         Fbar[i][j] += 2.0f * mu * (tF + tD);
         Rbar[i][j] = -2.0f * mu * tF;
-        mub += tb[i][j] * DFt;
+        // <tb, (F - R) F^T>: (F - R) F^T = F F^T - R S R^T is symmetric; symmetrise tb first
+        // (its antisymmetric part then cancels exactly)
+        if (j >= i) mub += (i == j ? tb[i][j] : tb[i][j] + tb[j][i]) * DFt;
       }
     polar_adjoint_f64<D>(E, sc.pol, Rbar, Fbar);
     float c = la * (2.0f * sc.J - 1.0f) * trtb;
@@ -732,10 +778,13 @@ __device__ __forceinline__ float kirchhoff_adjoint(const float E[D][D], float mu
 #pragma unroll
         for (int k = 0; k < D; ++k) s += (tb[i][k] + tb[k][i]) * E[k][j];
         Fbar[i][j] += mu * s + c * cof[i][j];
+        if (j < i) continue;
+        // <tb, F F^T - I> over the symmetric g = E + E^T + E E^T, pairing tb_ij + tb_ji
+        // first: a large antisymmetric part of tb then cancels exactly instead of in the sum
         float g = E[i][j] + E[j][i];
 #pragma unroll
         for (int k = 0; k < D; ++k) g += E[i][k] * E[j][k];
-        mub += tb[i][j] * g;
+        mub += (i == j ? tb[i][j] : tb[i][j] + tb[j][i]) * g;
       }
     mubar += mub;
     labar += trtb * log1pf(sc.Jm1);

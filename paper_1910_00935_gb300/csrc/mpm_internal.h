@@ -84,13 +84,15 @@ cudaError_t launch_gather_rows(int rows, int64_t N, const int* perm, const float
 // dst[i] = src[perm[i]] for int32 rows (per-particle material ids)
 cudaError_t launch_gather_int(int64_t N, const int* perm, const int* src_caller, int* dst_internal,
                               cudaStream_t s);
-// identity_dim > 0: rows are a dim x dim matrix per particle and I is added on the way out
+// identity_dim > 0: rows are a dim x dim matrix per particle and I is added on the way out;
+// the first fix_rows rows hold fixed-point positions, converted to FP32 on the way out
 cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const float* src_internal,
-                                float* dst_caller, int identity_dim, cudaStream_t s);
+                                float* dst_caller, int identity_dim, int fix_rows, cudaStream_t s);
 cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, const float* nu,
-                                 const float* mubar, const float* labar, float* gE, float* gnu,
+                                 const double* mubar, const double* labar, float* gE, float* gnu,
                                  cudaStream_t s);
-// per-scene sums of x_T and x_0 into com[scene][6]; part: com_scratch_doubles(n_scenes)
+// per-scene sums of x_T and x_0 (state rows, fixed-point positions) into com[scene][6];
+// part: com_scratch_doubles(n_scenes)
 size_t com_scratch_doubles(int n_scenes);
 cudaError_t launch_com(int dim, int64_t N, int n_scenes, const int64_t* scene_off, const int* perm,
                        const float* xT, const float* x0, double* part, double* com, cudaStream_t s);

@@ -88,8 +88,8 @@ struct AdjArgs {
   float* adj;         // adjoint rows x, v, C, F
   const float* mu;
   const float* la;
-  float* mubar;
-  float* labar;
+  double* mubar;      // dL/dmu, dL/dlambda per particle, summed over the steps in FP64: the
+  double* labar;      // per-step terms oscillate in sign over a long run and mostly cancel
   const int* group;
   const int* matid;   // per-particle material (kMixed scenes) or null
   const float* wact;
@@ -485,8 +485,8 @@ __device__ __forceinline__ float4* reversed_stencil(bool rev, float4* g, int n, 
 // arithmetic.  A pair whose bases differ scatters each particle's contributions on their
 // own.  The node half is uniform per warp (no divergence); each thread reads two records.
 template <int D, bool WITH_MASS>
-__device__ __forceinline__ void scatter_pairs(const float* xr, int count, float4* g, int n,
-                                              const SimParams& P, float mass_c) {
+__device__ __noinline__ void scatter_pairs(const float* xr, int count, float4* g, int n,
+                                           const SimParams& P, float mass_c) {
   static_assert(kTile % 64 == 0, "pairs: two node halves of whole warps");
   constexpr int S = Xch<D>::kStride;
   constexpr int NN = D == 3 ? 27 : 9;
@@ -1184,7 +1184,7 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
 #pragma unroll
       for (int b = 0; b < D; ++b) C[a][b] = c4 * B[a][b];
 #pragma unroll
-    for (int a = 0; a < D; ++a) x[a] = xo[a] + P.dt * v[a];
+    for (int a = 0; a < D; ++a) x[a] = P.xfix ? pos_advance(xo[a], P.dt * v[a]) : xo[a] + P.dt * v[a];
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -1440,8 +1440,8 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     }
     if (ok) abar = kirchhoff_adjoint<D, MAT>(E, A.mu[p], A.la[p], act, axis, sc, tb, Fb, mub, lab, mat_p);
     if (active) {
-      A.mubar[p] += mub;
-      A.labar[p] += lab;
+      A.mubar[p] += (double)mub;
+      A.labar[p] += (double)lab;
     }
     if (P.n_groups > 0) {
       // dL/dw_gk += basis_k * sum of abar over this tile's particles of group g, reduced in

@@ -90,7 +90,7 @@ __global__ void gather_initial_kernel(int dim, int64_t N, const int* perm, const
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = perm[i];
     for (int a = 0; a < dim; ++a) {
-      st[a * N + i] = x0[a * N + e];
+      st[a * N + i] = pos_to_fix(x0[a * N + e]);  // positions in fixed point (mpm_common.cuh)
       st[(dim + a) * N + i] = v0[a * N + e];
     }
     for (int k = 0; k < dd; ++k) {
@@ -131,29 +131,34 @@ __global__ void gather_rows_kernel(int rows, int64_t N, const int* perm, const f
 }
 
 __global__ void scatter_rows_kernel(int rows, int64_t N, const int* perm, const float* src,
-                                    float* dst, int identity_dim) {
+                                    float* dst, int identity_dim, int fix_rows) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = perm[i];
     for (int r = 0; r < rows; ++r) {
+      if (r < fix_rows) {
+        dst[r * N + e] = (float)pos_from_fix(src[r * N + i]);
+        continue;
+      }
       float add = (identity_dim > 0 && r / identity_dim == r % identity_dim) ? 1.0f : 0.0f;
       dst[r * N + e] = src[r * N + i] + add;
     }
   }
 }
 
-// chain rule of the Lame parameters: (mubar, labar) -> (Ebar, nubar)
+// chain rule of the Lame parameters: (mubar, labar) -> (Ebar, nubar), in FP64 (the two
+// terms of dL/dnu have opposite signs and nearly cancel)
 __global__ void material_grad_kernel(int64_t N, const int* perm, const float* E, const float* nu,
-                                     const float* mubar, const float* labar, float* gE,
+                                     const double* mubar, const double* labar, float* gE,
                                      float* gnu) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = perm[i];
-    float Ee = E[i], v = nu[i];
-    float q = (1.0f + v) * (1.0f - 2.0f * v);
-    float mb = mubar[i], lb = labar[i];
-    if (gE) gE[e] = mb / (2.0f * (1.0f + v)) + lb * v / q;
-    if (gnu) gnu[e] = -mb * Ee / (2.0f * (1.0f + v) * (1.0f + v)) + lb * Ee * (1.0f + 2.0f * v * v) / (q * q);
+    const double Ee = E[i], v = nu[i];
+    const double q = (1.0 + v) * (1.0 - 2.0 * v);
+    const double mb = mubar[i], lb = labar[i];
+    if (gE) gE[e] = (float)(mb / (2.0 * (1.0 + v)) + lb * v / q);
+    if (gnu) gnu[e] = (float)(-mb * Ee / (2.0 * (1.0 + v) * (1.0 + v)) + lb * Ee * (1.0 + 2.0 * v * v) / (q * q));
   }
 }
 
@@ -169,9 +174,9 @@ __global__ void com_kernel(int dim, int n_scenes, const int64_t* off, int64_t N,
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t i = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e;
        i += (int64_t)gridDim.x * blockDim.x)
-    for (int a = 0; a < dim; ++a) {
-      acc[a] += (double)xT[a * N + i];
-      acc[3 + a] += (double)x0[a * N + i];
+    for (int a = 0; a < dim; ++a) {  // the state rows hold fixed-point positions
+      acc[a] += pos_from_fix(xT[a * N + i]);
+      acc[3 + a] += pos_from_fix(x0[a * N + i]);
     }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c = 0; c < 6; ++c) {
@@ -295,14 +300,14 @@ cudaError_t launch_gather_int(int64_t N, const int* perm, const int* src_caller,
 }
 
 cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const float* src_internal,
-                                float* dst_caller, int identity_dim, cudaStream_t s) {
+                                float* dst_caller, int identity_dim, int fix_rows, cudaStream_t s) {
   scatter_rows_kernel<<<grid_for(N), 256, 0, s>>>(rows, N, perm, src_internal, dst_caller,
-                                                  identity_dim);
+                                                  identity_dim, fix_rows);
   return cudaGetLastError();
 }
 
 cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, const float* nu,
-                                 const float* mubar, const float* labar, float* gE, float* gnu,
+                                 const double* mubar, const double* labar, float* gE, float* gnu,
                                  cudaStream_t s) {
   material_grad_kernel<<<grid_for(N), 256, 0, s>>>(N, perm, E, nu, mubar, labar, gE, gnu);
   return cudaGetLastError();
