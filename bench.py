@@ -672,7 +672,8 @@ def batched_line(name, dev, flush, steps=2, warmup=1, autotune_probe=True):
         run(sim)
         torch.cuda.synchronize()
         ams = timed(lambda: run(sim), steps)
-        line["autotuned"] = {"value": N * T / (ams / 1e3), "ms_per_step": ams, "config": cfg}
+        line["autotuned"] = {"value": N * T / (ams / 1e3), "ms_per_step": ams, "config": cfg,
+                             "refused": getattr(sim, "autotune_failed", [])}
     sim.check()
     sim.close()
     # one scene per launch sequence, scenes back to back

@@ -78,7 +78,10 @@ extern "C" {
 #define MPM_OPT_SMEM_TILE 2       /* 1: scatters accumulate in a shared-memory node box and
                                      flush once per node; 0: float4 reductions straight to
                                      the L2-resident grid [0, faster on GB300] */
-#define MPM_OPT_TILE_CAPACITY 3   /* max nodes of one CTA's shared tile [1024] */
+#define MPM_OPT_TILE_CAPACITY 3   /* max nodes of one CTA's shared tile [1024]; this and
+                                     MPM_OPT_GATHER_CAPACITY / MPM_OPT_SMEM_TILE return
+                                     MPM_ERR_ARG (option unchanged) when the node boxes would
+                                     not fit the device's shared memory per CTA */
 #define MPM_OPT_PROFILE 4         /* 1: time every kernel launch with CUDA events on its
                                      stream (launches go unbatched, no graphs) [0];
                                      setting it clears the collected timings */

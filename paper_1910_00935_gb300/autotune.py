@@ -112,6 +112,8 @@ def tune(sim, T: int = 32, repeats: int = 2, cache_path: str | None = None, forc
     Returns the chosen configuration."""
     import torch
 
+    from .mpm import MPMError
+
     key = shape_key(sim.desc, torch.cuda.get_device_name(sim.device))
     cache = load_cache(cache_path)
     if not force and key in cache:
@@ -120,24 +122,35 @@ def tune(sim, T: int = 32, repeats: int = 2, cache_path: str | None = None, forc
     T = min(T, sim.max_steps)
     target = torch.zeros(sim.n_scenes, sim.dim, device=sim.device)
 
+    failed = []
+
     def measure(config):
-        apply(sim, config)
-        best = float("inf")
-        for _ in range(repeats + 1):  # the first run captures the graphs
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            sim.forward(T)
-            _, gT, _ = sim.loss(0, target)
-            sim.backward(dL_dx=gT)
-            e1.record()
-            torch.cuda.synchronize()
-            best = min(best, e0.elapsed_time(e1) / 1e3)
-        sim.check()
-        return best
+        # a candidate the library refuses (an error status from any call) is infeasible:
+        # it is recorded and never chosen, and the next candidate starts from a new set-up
+        try:
+            apply(sim, config)
+            best = float("inf")
+            for _ in range(repeats + 1):  # the first run captures the graphs
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                sim.forward(T)
+                _, gT, _ = sim.loss(0, target)
+                sim.backward(dL_dx=gT)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            sim.check()
+            return best
+        except MPMError as e:
+            failed.append([dict(config), str(e)])
+            return float("inf")
 
     config, t, log = coordinate_descent(measure)
+    sim.autotune_failed = failed
     apply(sim, config)
+    if "sort_order" not in config and getattr(sim, "_inputs", None) is not None:
+        sim.reload()
     cache[key] = {"config": config, "seconds_per_probe": t, "T_probe": T,
-                  "evaluated": [[c, s] for c, s in log]}
+                  "evaluated": [[c, s] for c, s in log], "failed": failed}
     save_cache(cache, cache_path)
     return config

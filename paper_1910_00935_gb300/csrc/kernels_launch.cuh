@@ -11,9 +11,12 @@
 namespace mpm {
 
 namespace {
+// Raise a kernel's dynamic shared-memory limit when static + dynamic may pass the default
+// 48 KB: the passes' static shared memory (box slots, bucket table, group sums, the
+// persistent forms' pass entry) stays below 8 KB, so any dynamic size above 32 KB sets it.
 template <typename K>
 cudaError_t allow_smem(K k, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
+  if (smem <= 32 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -22,13 +25,18 @@ cudaError_t step_one(const SimParams& P, const StepArgs& A, int n_tiles, cudaStr
   const size_t smem = step_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
   auto k = step_kernel<D, MAT, MODE, DET>;
   cudaError_t e = allow_smem(k, smem);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    note_launch_failure("step_kernel", D, MAT, MODE, smem, e);
+    return e;
+  }
   if (n_tiles <= 0) {  // no tiles: only make sure the kernel's module is loaded
     cudaFuncAttributes attr;
     return cudaFuncGetAttributes(&attr, k);
   }
   k<<<n_tiles, kTile, smem, s>>>(P, A);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) note_launch_failure("step_kernel", D, MAT, MODE, smem, cudaSuccess);
+  return e;
 }
 
 template <int D, int MAT, int MODE, bool DET>
@@ -36,13 +44,18 @@ cudaError_t adj_one(const SimParams& P, const AdjArgs& A, int n_tiles, cudaStrea
   const size_t smem = adj_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
   auto k = adjoint_kernel<D, MAT, MODE, DET>;
   cudaError_t e = allow_smem(k, smem);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    note_launch_failure("adjoint_kernel", D, MAT, MODE, smem, e);
+    return e;
+  }
   if (n_tiles <= 0) {  // no tiles: only make sure the kernel's module is loaded
     cudaFuncAttributes attr;
     return cudaFuncGetAttributes(&attr, k);
   }
   k<<<n_tiles, kTile, smem, s>>>(P, A);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) note_launch_failure("adjoint_kernel", D, MAT, MODE, smem, cudaSuccess);
+  return e;
 }
 
 // Cooperative launch of a persistent pass interpreter: as many CTAs as can be resident
@@ -96,16 +109,29 @@ cudaError_t adj_variant(int mode, const SimParams& P, const AdjArgs& A, int n_ti
   return cudaErrorInvalidValue;
 }
 
+// kind_mode = PassKind * 8 + the run's pass mode (StepMode or AdjMode)
 template <int D, int MAT, bool DET>
-cudaError_t persistent_variant(int kind, const SimParams& P, const PassEntry* plan, int n_pass,
+cudaError_t persistent_variant(int kind_mode, const SimParams& P, const PassEntry* plan, int n_pass,
                                int n_tiles, const PersistCtl& ctl, cudaStream_t s, int* grid_out) {
-  if (kind == kPassStep)
-    return persistent_one(step_persistent_kernel<D, MAT, DET>,
-                          step_smem_bytes<D>(P.tile_capacity, P.gather_capacity), plan, n_pass, n_tiles,
-                          ctl, s, grid_out);
-  return persistent_one(adjoint_persistent_kernel<D, MAT, DET>,
-                        adj_smem_bytes<D>(P.tile_capacity, P.gather_capacity), plan, n_pass, n_tiles,
-                        ctl, s, grid_out);
+  const size_t ss = step_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
+  const size_t as = adj_smem_bytes<D>(P.tile_capacity, P.gather_capacity);
+  switch (kind_mode) {
+    case kPassStep * 8 + kP2GOnly:
+      return persistent_one(step_persistent_kernel<D, MAT, kP2GOnly, DET>, ss, plan, n_pass, n_tiles, ctl, s, grid_out);
+    case kPassStep * 8 + kG2PP2G:
+      return persistent_one(step_persistent_kernel<D, MAT, kG2PP2G, DET>, ss, plan, n_pass, n_tiles, ctl, s, grid_out);
+    case kPassStep * 8 + kG2PP2GFull:
+      return persistent_one(step_persistent_kernel<D, MAT, kG2PP2GFull, DET>, ss, plan, n_pass, n_tiles, ctl, s, grid_out);
+    case kPassStep * 8 + kG2POnlyFull:
+      return persistent_one(step_persistent_kernel<D, MAT, kG2POnlyFull, DET>, ss, plan, n_pass, n_tiles, ctl, s, grid_out);
+    case kPassAdjoint * 8 + kAdjG2P:
+      return persistent_one(adjoint_persistent_kernel<D, MAT, kAdjG2P, DET>, as, plan, n_pass, n_tiles, ctl, s, grid_out);
+    case kPassAdjoint * 8 + kAdjFused:
+      return persistent_one(adjoint_persistent_kernel<D, MAT, kAdjFused, DET>, as, plan, n_pass, n_tiles, ctl, s, grid_out);
+    case kPassAdjoint * 8 + kAdjP2G:
+      return persistent_one(adjoint_persistent_kernel<D, MAT, kAdjP2G, DET>, as, plan, n_pass, n_tiles, ctl, s, grid_out);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int D>

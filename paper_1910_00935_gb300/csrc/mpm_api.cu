@@ -247,6 +247,7 @@ struct mpm_handle {
   Layout L;
   char* ws = nullptr;
   size_t ws_bytes = 0;
+  int smem_optin = 0;  // the device's per-CTA shared-memory limit (bytes)
   bool initialized = false;
   bool materials_set = false;  // MPM_MIXED: per-particle materials given since the last set-up
   int32_t T_recorded = 0;
@@ -335,10 +336,25 @@ int fail(mpm_handle* h, int code, const std::string& msg) {
 
 void mpm::set_static_error(const char* msg) { g_static_error = msg ? msg : ""; }
 
+static thread_local std::string g_launch_failure;
+void mpm::note_launch_failure(const char* kernel, int dim, int material, int mode, size_t smem,
+                              cudaError_t attr_rc) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), " [%s<dim %d, material %d, mode %d>: %zu B dynamic shared memory%s%s]",
+           kernel, dim, material, mode, smem, attr_rc != cudaSuccess ? ", raising its limit failed: " : "",
+           attr_rc != cudaSuccess ? cudaGetErrorString(attr_rc) : "");
+  g_launch_failure = buf;
+}
+std::string mpm::take_launch_failure() {
+  std::string s;
+  s.swap(g_launch_failure);
+  return s;
+}
+
 namespace {
 
 int cuda_fail(mpm_handle* h, cudaError_t e, const char* where) {
-  return fail(h, MPM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return fail(h, MPM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e) + take_launch_failure());
 }
 
 #define CK(expr)                                   \
@@ -523,6 +539,7 @@ struct Launcher {
   const PassEntry* dplan = nullptr;
   int next = 0;        // passes issued so far (kPersistent)
   int run_kind = -1;   // kind of the pending run of passes
+  int run_mode = -1;   // and its pass mode (a persistent launch runs one kind and mode)
   int run_first = 0;   // its first pass
   // two-stream backward (issue_backward_overlap): the stream passes go to, and the range
   // of (m, p) grid buffers they allocate from
@@ -576,10 +593,11 @@ struct Launcher {
       return cudaSuccess;
     }
     if (mode == kPersistent) {
-      if (run_kind != kind) {
+      if (run_kind != kind || run_mode != pmode) {
         cudaError_t e = flush();
         if (e != cudaSuccess) return e;
         run_kind = kind;
+        run_mode = pmode;
         run_first = next;
       }
       ++next;
@@ -622,12 +640,13 @@ struct Launcher {
     c.extra = h->barrier_extra;
     const SimParams P = params_for(h, 0);  // shared-memory capacities
     const int kind = run_kind;
+    const int kind_mode = run_kind * 8 + run_mode;
     const PassEntry* plan = dplan + run_first;
     const Dims& m = h->m;
     ++count;
     e = timed(kind == kPassStep ? MPM_KERNEL_PERSISTENT_STEP : MPM_KERNEL_PERSISTENT_ADJ, [&] {
-      return m.D == 2 ? launch_persistent<2>(kind, h->desc.material, P, plan, n, m.n_tiles, c, s, nullptr)
-                      : launch_persistent<3>(kind, h->desc.material, P, plan, n, m.n_tiles, c, s, nullptr);
+      return m.D == 2 ? launch_persistent<2>(kind_mode, h->desc.material, P, plan, n, m.n_tiles, c, s, nullptr)
+                      : launch_persistent<3>(kind_mode, h->desc.material, P, plan, n, m.n_tiles, c, s, nullptr);
     });
     run_first += n;
     return e;
@@ -1125,6 +1144,22 @@ void drop_graphs(mpm_handle* h) {
   h->graphs.clear();
 }
 
+// After a failed issue inside a capture: join the side stream back into the capturing
+// stream if a fork left it in the capture, so that ending the capture takes both streams out
+// of capture mode (the event is destroyed by the caller after the capture ends).
+void unjoin_side_stream(mpm_handle* h, cudaEvent_t* join) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (!h->side_stream || cudaStreamIsCapturing(h->side_stream, &st) != cudaSuccess ||
+      st == cudaStreamCaptureStatusNone)
+    return;
+  if (cudaEventCreateWithFlags(join, cudaEventDisableTiming) != cudaSuccess) {
+    *join = nullptr;
+    return;
+  }
+  cudaEventRecord(*join, h->side_stream);
+  cudaStreamWaitEvent(h->cap_stream, *join, 0);
+}
+
 // Run a launch sequence on `stream`, through a cached CUDA graph when enabled.
 template <typename Fn>
 int run_sequence_impl(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
@@ -1173,10 +1208,14 @@ int run_sequence_impl(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issu
     Launcher Lc{h, h->cap_stream};
     configure(Lc);
     int rc = issue(Lc);
+    cudaEvent_t join = nullptr;
+    if (rc) unjoin_side_stream(h, &join);  // a failed issue may leave the side stream forked
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (join) cudaEventDestroy(join);
     if (rc) {
       if (g) cudaGraphDestroy(g);
+      cudaGetLastError();  // the capture's own errors are not the caller's
       return rc;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
@@ -1201,6 +1240,24 @@ int run_sequence(mpm_handle* h, int64_t key, cudaStream_t stream, Fn&& issue) {
     h->T_recorded = 0;
   }
   return rc;
+}
+
+// Dynamic shared memory the particle passes need with the handle's capacities, plus the
+// passes' static shared memory (below 8 KB), against the device's per-CTA limit.
+bool capacities_fit(const mpm_handle* h, std::string* why) {
+  if (h->smem_optin <= 0) return true;
+  const SimParams P = params_for(h, 0);
+  const size_t need = (h->m.D == 2 ? std::max(step_smem_bytes<2>(P.tile_capacity, P.gather_capacity),
+                                              adj_smem_bytes<2>(P.tile_capacity, P.gather_capacity))
+                                   : std::max(step_smem_bytes<3>(P.tile_capacity, P.gather_capacity),
+                                              adj_smem_bytes<3>(P.tile_capacity, P.gather_capacity))) +
+                      8 * 1024;
+  if (need <= (size_t)h->smem_optin) return true;
+  char buf[160];
+  snprintf(buf, sizeof(buf), "the shared node boxes need %zu B of shared memory per CTA, the device allows %d B",
+           need, h->smem_optin);
+  *why = buf;
+  return false;
 }
 
 }  // namespace
@@ -1292,6 +1349,11 @@ int mpm_create(const mpm_scene_desc* desc, void* workspace, size_t workspace_byt
   h->m = m;
   h->L = L;
   h->ws = static_cast<char*>(workspace);
+  h->smem_optin = 0;
+  if (cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, attr.device) != cudaSuccess) {
+    cudaGetLastError();
+    h->smem_optin = 0;  // unknown: capacities are then checked by the launches alone
+  }
   h->pm.n = m.pm_slots;
   h->ub.first = m.pm_slots;
   {
@@ -1562,6 +1624,21 @@ int mpm_sync_status(mpm_handle* h) {
 
 int mpm_set_option(mpm_handle* h, int32_t key, int64_t value) {
   if (!h) return fail(nullptr, MPM_ERR_ARG, "handle is NULL");
+  if (key == MPM_OPT_GATHER_CAPACITY || key == MPM_OPT_TILE_CAPACITY || key == MPM_OPT_SMEM_TILE) {
+    // try the value on a copy of the capacities first: a size the device cannot hold is
+    // refused here rather than by a launch
+    const int g0 = h->gather_capacity, t0 = h->tile_capacity;
+    const bool s0 = h->smem_tile;
+    if (key == MPM_OPT_GATHER_CAPACITY && (value == 0 || (value >= 27 && value <= 12288))) h->gather_capacity = (int)value;
+    if (key == MPM_OPT_TILE_CAPACITY && value >= 27 && value <= 12288) h->tile_capacity = (int)value;
+    if (key == MPM_OPT_SMEM_TILE) h->smem_tile = value != 0;
+    std::string why;
+    const bool ok = capacities_fit(h, &why);
+    h->gather_capacity = g0;
+    h->tile_capacity = t0;
+    h->smem_tile = s0;
+    if (!ok) return fail(h, MPM_ERR_ARG, why);
+  }
   switch (key) {
     case MPM_OPT_USE_GRAPHS: h->use_graphs = value != 0; break;
     case MPM_OPT_SMEM_TILE: h->smem_tile = value != 0; break;

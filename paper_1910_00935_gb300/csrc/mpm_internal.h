@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "mpm_common.cuh"
@@ -33,6 +34,11 @@ cudaError_t launch_clear(const Clears& C, int nnodes, int n_grid, int n_scenes, 
 
 // the message mpm_last_error(NULL) returns (per host thread)
 void set_static_error(const char* msg);
+// detail of the last failed kernel launch on this host thread (which pass, its dynamic
+// shared memory), appended to the next CUDA error message and then cleared
+void note_launch_failure(const char* kernel, int dim, int material, int mode, size_t smem,
+                         cudaError_t attr_rc);
+std::string take_launch_failure();
 
 // dispatch on the runtime material and accumulation mode (P.det)
 #define MPM_DISPATCH_MATERIAL(FN, ...)                                                   \

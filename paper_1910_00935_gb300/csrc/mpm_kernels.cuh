@@ -1794,8 +1794,10 @@ __device__ __forceinline__ int next_tile(const PersistCtl& c, int i, int* s_tile
   return *s_tile;
 }
 
-// Forward-kind passes plan[0..n_pass), tiles handed out by tickets.
-template <int D, int MAT, bool DET>
+// Forward-kind passes plan[0..n_pass), all of pass mode MODE (the launcher splits runs at
+// mode changes, so each interpreter compiles one pass body, as the one-launch-per-pass kernel
+// does), tiles handed out by tickets.
+template <int D, int MAT, int MODE, bool DET>
 __global__ void __launch_bounds__(kTile, step_ctas_per_sm<D, MAT>())
     step_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
   extern __shared__ __align__(16) float sm[];
@@ -1810,19 +1812,14 @@ __global__ void __launch_bounds__(kTile, step_ctas_per_sm<D, MAT>())
     __syncthreads();
     cta_copy(&e, plan + i);
     for (int t; (t = next_tile(ctl, i, &s_tile)) < n_tiles;) {
-      switch (e.mode) {
-        case kP2GOnly: step_tile<D, MAT, kP2GOnly, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk); break;
-        case kG2PP2G: step_tile<D, MAT, kG2PP2G, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk); break;
-        case kG2PP2GFull: step_tile<D, MAT, kG2PP2GFull, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk); break;
-        default: step_tile<D, MAT, kG2POnlyFull, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk); break;
-      }
+      step_tile<D, MAT, MODE, false, DET>(e.P, e.S, t, sm, s_box, s_bbox, s_bk);
       __syncthreads();
     }
   }
 }
 
-// Adjoint-kind passes plan[0..n_pass).
-template <int D, int MAT, bool DET>
+// Adjoint-kind passes plan[0..n_pass), all of mode MODE.
+template <int D, int MAT, int MODE, bool DET>
 __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
     adjoint_persistent_kernel(const PassEntry* plan, int n_pass, int n_tiles, PersistCtl ctl) {
   extern __shared__ __align__(16) float sm[];
@@ -1839,17 +1836,7 @@ __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
     __syncthreads();
     cta_copy(&e, plan + i);
     for (int t; (t = next_tile(ctl, i, &s_tile)) < n_tiles;) {
-      switch (e.mode) {
-        case kAdjG2P:
-          adjoint_tile<D, MAT, kAdjG2P, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar, s_bk);
-          break;
-        case kAdjFused:
-          adjoint_tile<D, MAT, kAdjFused, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar, s_bk);
-          break;
-        default:
-          adjoint_tile<D, MAT, kAdjP2G, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar, s_bk);
-          break;
-      }
+      adjoint_tile<D, MAT, MODE, false, DET>(e.P, e.A, t, sm, s_box, s_bbox_ub, s_bbox_pm, s_wbar, s_bk);
       __syncthreads();
     }
   }

@@ -521,3 +521,35 @@ def test_scatter_forms_match_oracle(mpm, case, form):
     o = _oracle_grad_linear(scene, T, {kk: v.astype(np.float64) for kk, v in seeds.items()})
     keys = ["gx0", "gv0", "gC0", "gF0", "gE", "gnu"] + (["gw"] if scene["desc"]["n_groups"] else [])
     _compare_grads(g["grad"], o, keys)
+
+
+@pytest.mark.parametrize("name,kw", [("square2d", dict(n_side=40)),
+                                     ("cube3d", dict(n_side=16, n_grid=64))])
+@pytest.mark.parametrize("gather", [1536, 2048, 4096])
+def test_gather_capacities_near_the_static_limit(mpm, name, kw, gather):
+    """Gather boxes whose dynamic shared memory lands just under or over 48 KB (where the
+    kernel's static shared memory decides whether the limit must be raised) run and give
+    the default's results; graphs on, re-simulation overlapped."""
+    scene = scenes.make(name, **kw)
+    T = 12
+    scene["desc"]["ckpt_every"] = 5
+    seeds = _random_seeds(scene, np.random.default_rng(3))
+    ref = _run_gpu(mpm, scene, T, seeds=seeds, loss=False)
+    g = _run_gpu(mpm, scene, T, seeds=seeds, loss=False,
+                 options={mpm.MPM_OPT_GATHER_CAPACITY: gather})
+    assert rel_l2(g["state"][0], ref["state"][0]) <= 1e-6
+    for key in ("gx0", "gv0", "gF0"):
+        assert rel_l2(g["grad"][key], ref["grad"][key]) <= 1e-4, key
+
+
+def test_capacity_beyond_shared_memory_is_refused(mpm):
+    """A gather box that cannot fit one CTA's shared memory is refused by the option call
+    (MPM_ERR_ARG, option unchanged), and the handle keeps working."""
+    scene = scenes.make("cube3d", n_side=12, n_grid=32)
+    sim = mpm.from_scene(scene, max_steps=4)
+    with pytest.raises(mpm.MPMError) as ei:
+        sim.set_option(mpm.MPM_OPT_GATHER_CAPACITY, 12288)
+    assert ei.value.code == mpm.MPM_ERR_ARG and "shared memory" in str(ei.value)
+    sim.forward(4)
+    sim.check()
+    sim.close()
