@@ -89,8 +89,9 @@ extern "C" {
 #define MPM_OPT_GATHER_CAPACITY 5 /* max nodes of a CTA's shared gather box; 0 = gathers
                                      read the grid through L1 [512] */
 #define MPM_OPT_POLAR_CACHE 7     /* 3D fixed-corotated: the re-simulation stores each state's
-                                     FP64 polar factor for the two backward passes that need it
-                                     instead of recomputing it [1] */
+                                     polar factor (as an FP32 value + correction pair) for the
+                                     two backward passes that need it instead of recomputing
+                                     it [1] */
 #define MPM_OPT_GRID_BLOCKS 6     /* CTAs per scene of the end-of-sequence grid clear; 0 = automatic [0] */
 #define MPM_OPT_PERSISTENT 8      /* 1: each run of same-kind passes (a whole forward; the
                                      re-simulation and the adjoint passes of each backward
@@ -320,8 +321,8 @@ int mpm_plan_checkpoints(const mpm_scene_desc* desc, int32_t max_steps, size_t b
 /* Arithmetic peak of the current GPU, measured with the library's own kernel (8
  * independent fused multiply-add chains per thread, 8 CTAs of 256 threads per SM; an FMA
  * counts 2 FLOP; best of three timed launches after a warm-up, CUDA events on `stream`).
- * It is the denominator of the ALU rooflines: the FP64 polar factor and its adjoint bound
- * the fixed-corotated passes.  kind: MPM_PEAK_FP64_FMA or MPM_PEAK_FP32_FMA;
+ * It is the denominator of the ALU rooflines of the particle passes.  kind:
+ * MPM_PEAK_FP64_FMA or MPM_PEAK_FP32_FMA;
  * flops_per_s: host.  Blocks until the launches finish (a diagnostic, ~0.1 s).  Returns
  * MPM_OK, MPM_ERR_ARG or MPM_ERR_CUDA (message in mpm_last_error(NULL)). */
 #define MPM_PEAK_FP64_FMA 0

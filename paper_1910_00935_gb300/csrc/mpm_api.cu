@@ -60,7 +60,7 @@ struct Layout {
   size_t tiles, scene_off, scene_tiles, scene_tile_off;
   size_t mu, la, E, nu, group, matid, wact, wbar_tile, mubar, labar;
   size_t fin, cur, ckpt, fine, seg, adj;
-  size_t rcache;  // 2 x (K+1) x [9][N] FP64 polar factors of a segment (3D FCR), by parity
+  size_t rcache;  // 2 x (K+1) x [9][N] polar factors of a segment (3D FCR; R_hi, R_lo as FP32 pairs), by parity
   size_t grids;  // pm_slots + kUBSlots dense grids
   size_t boxes;  // (pm_slots + kUBSlots) x 2 parities x [scene][8]
   size_t err, com, com_part, ub_m0;
@@ -75,7 +75,7 @@ struct Dims {
   int D, Q, S, K, n_ckpt, n_tiles, n_grid;
   int M;  // coarse checkpoint multiplier: 1 (one level) or >= 2 (states every K*M, then K)
   int64_t N, nnodes;
-  bool polar_cache;  // 3D fixed-corotated: FP64 polar factors are cached per segment
+  bool polar_cache;  // 3D fixed-corotated: polar factors are cached per segment
   bool store_grids;  // a re-simulated segment's grids stay live for its adjoint passes
   int pm_slots;      // (m, p) grid buffers: two pools of pm_pool
   int pm_pool;       // kPMSlots, or K + 3 when store_grids
@@ -315,7 +315,7 @@ struct mpm_handle {
   float* seg(int j, int i) const {
     return at<float>(L.seg) + ((size_t)(j & 1) * (m.K + 1) + i) * m.Q * m.N;
   }
-  // the cached FP64 polar factor of that state (3D fixed-corotated), or null
+  // the cached polar factor of that state (3D fixed-corotated), or null
   double* rslot(int j, int i) const {
     return m.polar_cache && use_polar_cache
                ? at<double>(L.rcache) + ((size_t)(j & 1) * (m.K + 1) + i) * 9 * m.N
@@ -848,7 +848,7 @@ struct Launcher {
 
 // forward: states 0..T; full state stored at multiples of K and at T (fin)
 // first step of the last segment of a T-step run: the forward leaves that segment's states
-// (and their FP64 polar factors) in the segment buffer, so the backward starts without
+// (and their polar factors) in the segment buffer, so the backward starts without
 // re-simulating it -- with ckpt_every >= T nothing is re-simulated at all
 int last_segment_start(const mpm_handle* h, int T) { return ((T - 1) / h->m.K) * h->m.K; }
 
@@ -1608,16 +1608,18 @@ int mpm_sync_status(mpm_handle* h) {
   if (e != cudaSuccess) return cuda_fail(h, e, "read error word");
   if (err) {
     cudaMemset(h->at<unsigned>(h->L.err), 0, 4);
-    if (err & kErrOOB) return fail(h, MPM_ERR_OOB, "a particle's stencil left the grid");
-    if (err & kErrNonFinite) return fail(h, MPM_ERR_NONFINITE, "non-finite value or det F <= 0");
-    if (err & kErrRange)
-      return fail(h, MPM_ERR_RANGE, "deterministic mode: a fixed-point grid contribution left its range");
+    // a timeout first: the passes after the barrier that gave up never ran, so whatever else
+    // the word holds may follow from the incomplete state
     if (err & kErrTimeout) {
-      // passes after the barrier that gave up never ran: grid buffers may be dirty
+      // grid buffers may be dirty
       h->initialized = false;
       h->T_recorded = 0;
       return fail(h, MPM_ERR_TIMEOUT, "a bounded device wait gave up (call mpm_set_initial again)");
     }
+    if (err & kErrOOB) return fail(h, MPM_ERR_OOB, "a particle's stencil left the grid");
+    if (err & kErrNonFinite) return fail(h, MPM_ERR_NONFINITE, "non-finite value or det F <= 0");
+    if (err & kErrRange)
+      return fail(h, MPM_ERR_RANGE, "deterministic mode: a fixed-point grid contribution left its range");
   }
   return MPM_OK;
 }

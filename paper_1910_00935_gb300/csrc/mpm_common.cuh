@@ -2,9 +2,9 @@
 //
 // Quadratic B-spline stencil, Kirchhoff stress (fixed-corotated / neo-Hookean,
 // plus the actuation fibre stress of diffmpm's open-loop controller, Section 4.1),
-// the stress adjoint, and the FP64 polar decomposition with its adjoint (the
-// hand-written SVD/polar gradient of Appendix C).  Bulk arithmetic is FP32; the
-// polar factor R, F - R, S = R^T F and the polar adjoint are FP64.
+// the stress adjoint, and the polar decomposition with its adjoint (the hand-written
+// SVD/polar gradient of Appendix C).  Bulk arithmetic is FP32; the polar factor R and F - R
+// are resolved to ~1e-14 (compensated FP32 in 3D, FP64 in 2D); the polar adjoint is FP32.
 //
 // The deformation gradient is carried as E = F - I: an FP32 F close to a rotation-free
 // identity keeps only ~1e-7/|strain| relative precision on the strain, E keeps 1e-7.
@@ -25,7 +25,7 @@ namespace mpm {
 #endif
 // 3D forward passes: 7 CTAs per SM (72 registers, a few spills; 2,048 cube3d tiles then run in
 // 1.9 waves instead of 2.25) measured 3% faster than 6 for neo-Hookean; the fixed-corotated
-// passes (FP64 polar factor) keep 6 (80 registers)
+// passes (polar factor) keep 6 (80 registers)
 #ifndef MPM_STEP_CTAS_PER_SM_3D
 #define MPM_STEP_CTAS_PER_SM_3D (896 / MPM_TILE)
 #endif
@@ -177,9 +177,12 @@ __device__ __forceinline__ float pos_to_fix(float x) {
 __device__ __forceinline__ double pos_from_fix(float raw) {
   return (double)__float_as_int(raw) * kFixPosInv;
 }
-// x + delta on fixed-point bits (delta rounded once to the 2^-31 grid)
+// x + delta on fixed-point bits (delta rounded once to the 2^-31 grid).  A step moves a
+// particle by less than the unit domain, so delta * 2^31 fits 32 bits and converts without
+// the 64-bit conversion (which issues on the FP64 pipe); a larger delta saturates, and that
+// particle has left the grid anyway (the stencil check reports it).
 __device__ __forceinline__ float pos_advance(float raw, float delta) {
-  return __int_as_float(fix_saturate((long long)__float_as_int(raw) + __float2ll_rn(delta * kFixPos)));
+  return __int_as_float(fix_saturate((long long)__float_as_int(raw) + (long long)__float2int_rn(delta * kFixPos)));
 }
 
 // ---------------------------------------------------------------------------
@@ -298,18 +301,18 @@ __device__ __forceinline__ void plus_identity(const float E[D][D], float F[D][D]
 }
 
 // ---------------------------------------------------------------------------
-// FP64 polar decomposition F = R S (R in SO(d), S symmetric positive definite)
+// Polar decomposition F = R S (R in SO(d), S symmetric positive definite)
 // ---------------------------------------------------------------------------
 template <int D>
 struct Polar {
-  double R[D][D];
-  float Rf[D][D];   // R rounded to FP32
-  float Df[D][D];   // F - R computed in FP64, rounded once
+  float Rh[D][D], Rl[D][D];  // R = Rh + Rl to ~1e-14 (the per-segment cache stores both)
+  float Rf[D][D];            // R rounded to FP32
+  float Df[D][D];            // F - R formed from the exact parts, rounded once
 };
 
 // 3x3 cofactor matrix (c[i][j] = cofactor of X[i][j]; X^-T = c / det X)
 template <typename T>
-__device__ __forceinline__ void cofactor3(const T X[3][3], T c[3][3]) {
+__host__ __device__ __forceinline__ void cofactor3(const T X[3][3], T c[3][3]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -323,7 +326,7 @@ __device__ __forceinline__ void cofactor3(const T X[3][3], T c[3][3]) {
 // quadratically to the orthogonal polar factor and keeps det X > 0.  Stops once the
 // squared update norm is below `tol`; false for det <= 0, overflow or no convergence.
 template <typename T>
-__device__ __forceinline__ bool polar_newton3(T X[3][3], T tol, int max_it) {
+__host__ __device__ __forceinline__ bool polar_newton3(T X[3][3], T tol, int max_it) {
   for (int it = 0; it < max_it; ++it) {
     T c[3][3];
     cofactor3<T>(X, c);
@@ -345,57 +348,148 @@ __device__ __forceinline__ bool polar_newton3(T X[3][3], T tol, int max_it) {
   return false;
 }
 
-// One Newton-Schulz step toward the nearest orthogonal matrix, Q <- Q (3I - Q^T Q)/2, in
-// FP64 (quadratic: an orthogonality error e becomes ~e^2)
-__device__ __forceinline__ void orthonormalize_step(double Q[3][3]) {
-  double G[3][3];  // symmetric: six entries
+// Error-free transformations in FP32: a + b = s + e exactly (Knuth's TwoSum) and
+// a * b = p + e exactly (the fused multiply-add gives the product's rounding error).  The
+// _rn intrinsics keep the compiler from fusing or reordering these operations.
+__host__ __device__ __forceinline__ float ef_add(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float ef_mul(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = ef_add(a, b);
+  const float bb = ef_add(s, -a);
+  e = ef_add(ef_add(a, -ef_add(s, -bb)), ef_add(b, -bb));
+}
+__host__ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = ef_mul(a, b);
+  e = fmaf(a, b, -p);
+}
+
+// (delta + e) - (rh + rl) rounded once: delta + e = fh + fl and fh - rh = g + ge exactly
+__host__ __device__ __forceinline__ float f_minus_r(float delta, float e, float rh, float rl) {
+  float fh, fl, g, ge;
+  two_sum(delta, e, fh, fl);
+  two_sum(fh, -rh, g, ge);
+  return g + ((ge + fl) - rl);
+}
+
+// 3D polar factor refined from an FP32 one without FP64 arithmetic (the FP64 pipe runs at
+// 1/64 of the FP32 rate on this part).  Q is Newton's FP32 iterate, orthogonal and equal to R
+// to within FP32 resolution (~1e-7), so every correction below is of that size and needs only
+// FP32 relative precision, provided the quantities it is formed from are exact to ~1e-14:
+//  1. orthonormalise: X = Q (3I - Q^T Q)/2 = Q + Q H, H = (I - Q^T Q)/2, with Q^T Q summed
+//     from exact products and sums (its deviation from I is the small part);
+//  2. M = X^T F = X^T + X^T E, again from exact products and sums, as a value and a
+//     correction (M_hi, M_lo);
+//  3. the small rotation X^T R = exp(W) that makes X^T F symmetric solves
+//     (tr(S) I - S) w = (M32 - M23, M13 - M31, M21 - M12) for the axial vector w of W
+//     (S = sym(M); eigenvalues sigma_i + sigma_j > 0): an FP32 solve, |w| ~ 1e-7;
+//  4. R = X (I + W) = Q + (Q H + Q W) to first order (the dropped terms are ~|w|^2, 1e-14):
+//     kept as R_hi = Q and R_lo = Q (H + W);
+//  5. F - R = (I + E) - (R_hi + R_lo) with exact sums, rounded once.
+// R = R_hi + R_lo agrees with an FP64 polar decomposition to ~1e-14 (checked against an
+// SVD on random F with strains up to 0.6), far below what the FP32 stress resolves.
+// Returns false when the solve of step 3 is singular (then the caller falls back).
+__host__ __device__ __forceinline__ bool polar_refine3(const float E[3][3], const float Q[3][3],
+                                                       float Rh[3][3], float Rl[3][3], float Df[3][3]) {
+  float H[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j) {
-      double g = 0.0;
+      float sh = 0.0f, sl = 0.0f;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) g += Q[k][i] * Q[k][j];
-      G[i][j] = G[j][i] = 0.5 * ((i == j ? 3.0 : 0.0) - g);
+      for (int k = 0; k < 3; ++k) {
+        float pk, ek, t, et;
+        two_prod(Q[k][i], Q[k][j], pk, ek);
+        two_sum(sh, pk, t, et);
+        sh = t;
+        sl += ek + et;
+      }
+      // 1 - sh is exact (sh within 1e-6 of 1), 0 - sh trivially
+      H[i][j] = H[j][i] = 0.5f * (ef_add(i == j ? 1.0f : 0.0f, -sh) - sl);
     }
-  double Qn[3][3];
+  float Xl[3][3];  // X = Q + Xl, Xl = Q H
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Xl[i][j] = Q[i][0] * H[0][j] + Q[i][1] * H[1][j] + Q[i][2] * H[2][j];
+  float Mh[3][3], Ml[3][3];  // M = X^T (I + E)
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      double q = 0.0;
+      float sh = Q[j][i], sl = Xl[j][i];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) q += Q[i][k] * G[k][j];
-      Qn[i][j] = q;
+      for (int k = 0; k < 3; ++k) {
+        float pk, ek, t, et;
+        two_prod(Q[k][i], E[k][j], pk, ek);
+        two_sum(sh, pk, t, et);
+        sh = t;
+        sl += ek + et + Xl[k][i] * E[k][j];
+      }
+      Mh[i][j] = sh;
+      Ml[i][j] = sl;
     }
+  // right-hand side: the skew part of M (the hi differences are exact or carry only a
+  // relative rounding of their own result)
+  const float b0 = ef_add(Mh[2][1], -Mh[1][2]) + (Ml[2][1] - Ml[1][2]);
+  const float b1 = ef_add(Mh[0][2], -Mh[2][0]) + (Ml[0][2] - Ml[2][0]);
+  const float b2 = ef_add(Mh[1][0], -Mh[0][1]) + (Ml[1][0] - Ml[0][1]);
+  const float tr = Mh[0][0] + Mh[1][1] + Mh[2][2];
+  float A[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Q[i][j] = Qn[i][j];
+    for (int j = 0; j < 3; ++j) A[i][j] = (i == j ? tr : 0.0f) - 0.5f * (Mh[i][j] + Mh[j][i]);
+  float c[3][3];
+  cofactor3<float>(A, c);
+  const float det = A[0][0] * c[0][0] + A[0][1] * c[0][1] + A[0][2] * c[0][2];
+  if (!(det > 1e-30f) || !(det < 1e30f)) return false;
+  const float id = 1.0f / det;
+  const float w0 = (c[0][0] * b0 + c[1][0] * b1 + c[2][0] * b2) * id;
+  const float w1 = (c[0][1] * b0 + c[1][1] * b1 + c[2][1] * b2) * id;
+  const float w2 = (c[0][2] * b0 + c[1][2] * b1 + c[2][2] * b2) * id;
+  // H + W, W = [[0, -w2, w1], [w2, 0, -w0], [-w1, w0, 0]]
+  const float K[3][3] = {{H[0][0], H[0][1] - w2, H[0][2] + w1},
+                         {H[1][0] + w2, H[1][1], H[1][2] - w0},
+                         {H[2][0] - w1, H[2][1] + w0, H[2][2]}};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Rh[i][j] = Q[i][j];
+      Rl[i][j] = Q[i][0] * K[0][j] + Q[i][1] * K[1][j] + Q[i][2] * K[2][j];
+      Df[i][j] = f_minus_r(i == j ? 1.0f : 0.0f, E[i][j], Rh[i][j], Rl[i][j]);
+    }
+  return true;
 }
 
 // 2D: R is the rotation by atan2(F10 - F01, F00 + F11), formed without a transcendental
 // as (c, s) / |(c, s)|.
-// 3D: Newton's iteration in FP32 gives an orthogonal Q within FP32 resolution of R; the
-// FP64 refinement is anchored to F itself: orthonormalize Q (one Newton-Schulz step),
-// then rotate it by the small rotation that makes Q^T F symmetric.  With M = Q^T F and
-// S = sym(M), Q^T R = exp(W) solves skew(exp(-W) M) = 0, whose linearisation is
-// (tr(S) I - S) w = (M32 - M23, M13 - M31, M21 - M12) for the axial vector w of W (the
-// same Sylvester form as the polar adjoint: eigenvalues sigma_i + sigma_j > 0), and
-// R = Q (I + W + W^2/2) is within ~1e-14 of the polar factor (against an SVD on 3,000
-// random F with strains up to 0.6: max 2.3e-14, median 2.8e-15; orthogonal to 5e-14), seven
-// orders below what the FP32 stress can resolve, for under half the FP64 work of Newton's
-// iteration in FP64 (the FP64 pipe bounds the fixed-corotated passes).  When the FP32
-// stage fails (near-singular F) Newton's iteration runs in FP64 from F.
+// 3D: Newton's iteration in FP32 gives Q within FP32 resolution of R, refined without FP64
+// arithmetic (polar_refine3) to R = R_hi + R_lo and F - R; R in FP64 is formed from the pair
+// only where a pass needs it (the polar adjoint, the per-segment cache).  When the FP32 stage
+// fails (near-singular F) Newton's iteration runs in FP64 from F.
 // Returns false for det F <= 0 or non-finite input.
 template <int D>
-__device__ __forceinline__ bool polar_f64(const float E[D][D], Polar<D>& p) {
+__device__ __forceinline__ bool polar_factor(const float E[D][D], Polar<D>& p) {
   double Fd[D][D];  // F = I + E, exact in FP64
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) Fd[i][j] = (double)E[i][j] + (i == j ? 1.0 : 0.0);
-  if (D == 2) {
+  if constexpr (D == 2) {
     double c = Fd[0][0] + Fd[1][1];
     double s = Fd[1][0] - Fd[0][1];
     double r = sqrt(c * c + s * s);
@@ -404,97 +498,41 @@ __device__ __forceinline__ bool polar_f64(const float E[D][D], Polar<D>& p) {
       c = 1.0; s = 0.0; r = 1.0;
     }
     double ir = 1.0 / r;
-    p.R[0][0] = c * ir;
-    p.R[0][1] = -s * ir;
-    p.R[1][0] = s * ir;
-    p.R[1][1] = c * ir;
+    const double R[2][2] = {{c * ir, -s * ir}, {s * ir, c * ir}};
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        p.Rf[i][j] = (float)p.R[i][j];
-        p.Df[i][j] = (float)(Fd[i][j] - p.R[i][j]);
+        p.Rh[i][j] = p.Rf[i][j] = (float)R[i][j];
+        p.Rl[i][j] = (float)(R[i][j] - (double)p.Rh[i][j]);
+        p.Df[i][j] = (float)(Fd[i][j] - R[i][j]);
       }
     return det > 0.0 && r > 0.0;
   } else {
-    double X[3][3];
-    bool ok;
-    {
-      float Xf[3][3];
+    float Xf[3][3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) Xf[i][j] = E[i][j] + (i == j ? 1.0f : 0.0f);
-      ok = polar_newton3<float>(Xf, 1e-12f, 20);
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) X[i][j] = (double)Xf[i][j];
-    }
+      for (int j = 0; j < 3; ++j) Xf[i][j] = E[i][j] + (i == j ? 1.0f : 0.0f);
+    bool ok = polar_newton3<float>(Xf, 1e-12f, 20);
     if (ok) {
-      orthonormalize_step(X);
-      double M[3][3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          double m = 0.0;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) m += X[k][i] * Fd[k][j];
-          M[i][j] = m;
-        }
-      const double tr = M[0][0] + M[1][1] + M[2][2];
-      double A[3][3];  // tr(S) I - S, S = sym(M)
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) A[i][j] = (i == j ? tr : 0.0) - 0.5 * (M[i][j] + M[j][i]);
-      const double b[3] = {M[2][1] - M[1][2], M[0][2] - M[2][0], M[1][0] - M[0][1]};
-      double c[3][3];
-      cofactor3<double>(A, c);
-      const double det = A[0][0] * c[0][0] + A[0][1] * c[0][1] + A[0][2] * c[0][2];
-      ok = det > 1e-30 && det < 1e30;
+      ok = polar_refine3(E, Xf, p.Rh, p.Rl, p.Df);
       if (ok) {
-        // 1/det: FP32 reciprocal, two FP64 Newton steps (relative error ~1e-28 -> FP64 ulps)
-        double id = (double)__frcp_rn((float)det);
-        id = id * (2.0 - det * id);
-        id = id * (2.0 - det * id);
-        double w[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) w[i] = (c[0][i] * b[0] + c[1][i] * b[1] + c[2][i] * b[2]) * id;
-        // G = I + W + W^2/2 with W the cross-product matrix of w (W^2 = w w^T - |w|^2 I)
-        const double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        const double Wm[3][3] = {{0.0, -w[2], w[1]}, {w[2], 0.0, -w[0]}, {-w[1], w[0], 0.0}};
-        double G[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int j = 0; j < 3; ++j)
-            G[i][j] = (i == j ? 1.0 - 0.5 * ww : 0.0) + Wm[i][j] + 0.5 * w[i] * w[j];
-        double Rn[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            double r = 0.0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) r += X[i][k] * G[k][j];
-            Rn[i][j] = r;
-          }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) X[i][j] = Rn[i][j];
+          for (int j = 0; j < 3; ++j) p.Rf[i][j] = p.Rh[i][j] + p.Rl[i][j];
+        return true;
       }
     }
-    if (!ok) {  // Newton's iteration in FP64 from F
+    // near-singular F: Newton's iteration in FP64 from F
+    double X[3][3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) X[i][j] = Fd[i][j];
-      // stop when the next update would be below FP64 resolution
-      ok = polar_newton3<double>(X, 1e-20, 24);
-    }
+      for (int j = 0; j < 3; ++j) X[i][j] = Fd[i][j];
+    // stop when the next update would be below FP64 resolution
+    ok = polar_newton3<double>(X, 1e-20, 24);
     if (!ok) {
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -505,98 +543,95 @@ __device__ __forceinline__ bool polar_f64(const float E[D][D], Polar<D>& p) {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        p.R[i][j] = X[i][j];
-        p.Rf[i][j] = (float)X[i][j];
+        p.Rh[i][j] = p.Rf[i][j] = (float)X[i][j];
+        p.Rl[i][j] = (float)(X[i][j] - (double)p.Rh[i][j]);
         p.Df[i][j] = (float)(Fd[i][j] - X[i][j]);
       }
     return ok;
   }
 }
 
-// The polar factor of F = I + E from a cached FP64 R ([9][N] rows, row-major per particle):
-// F - R is formed in FP64 as in polar_f64.
+// The per-segment polar cache holds R_hi and R_lo as FP32 rows [2 D^2][N] (rows i*D + j,
+// then D^2 + i*D + j), in the footprint of [D^2][N] FP64 values; F - R is re-formed from them
+// exactly as the factorisation forms it.
 template <int D>
 __device__ __forceinline__ void polar_from_cache(const double* Rc, int64_t N, int64_t p,
                                                  const float E[D][D], Polar<D>& pol) {
+  const float* r = reinterpret_cast<const float*>(Rc);
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      const double r = Rc[(int64_t)(i * D + j) * N + p];
-      pol.R[i][j] = r;
-      pol.Rf[i][j] = (float)r;
-      pol.Df[i][j] = (float)((double)E[i][j] + (i == j ? 1.0 : 0.0) - r);
+      const float rh = r[(int64_t)(i * D + j) * N + p];
+      const float rl = r[(int64_t)(D * D + i * D + j) * N + p];
+      pol.Rh[i][j] = rh;
+      pol.Rl[i][j] = rl;
+      pol.Rf[i][j] = rh + rl;
+      pol.Df[i][j] = f_minus_r(i == j ? 1.0f : 0.0f, E[i][j], rh, rl);
     }
 }
 
 template <int D>
 __device__ __forceinline__ void polar_to_cache(double* Rc, int64_t N, int64_t p, const Polar<D>& pol) {
-#pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = 0; j < D; ++j) Rc[(int64_t)(i * D + j) * N + p] = pol.R[i][j];
-}
-
-// Fbar += dR/dF^T [Rbar] in FP64.  With F = R S, dR = R W (W antisymmetric) and
-// W S + S W = R^T dF - dF^T R; the adjoint is Fbar += 2 R Y where Y is the
-// antisymmetric solution of Y S + S Y = skew(R^T Rbar).  In 3D that equation is
-// (tr(S) I - S) y = b on axial vectors (eigenvalues sigma_i + sigma_j > 0), in 2D
-// y = b / tr(S); no singular-value differences appear.  The products and the solve run in
-// FP64; in 3D the final rotation of the solution (2 R Y) runs in FP32.
-template <int D>
-__device__ __forceinline__ void polar_adjoint_f64(const float E[D][D], const Polar<D>& p,
-                                                  const float Rbar[D][D], float Fbar[D][D]) {
-  double M[D][D], S[D][D];
+  float* r = reinterpret_cast<float*>(Rc);
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      double m = 0.0, s = 0.0;
+      r[(int64_t)(i * D + j) * N + p] = pol.Rh[i][j];
+      r[(int64_t)(D * D + i * D + j) * N + p] = pol.Rl[i][j];
+    }
+}
+
+// Fbar += dR/dF^T [Rbar].  With F = R S, dR = R W (W antisymmetric) and
+// W S + S W = R^T dF - dF^T R; the adjoint is Fbar += 2 R Y where Y is the
+// antisymmetric solution of Y S + S Y = skew(R^T Rbar).  In 3D that equation is
+// (tr(S) I - S) y = b on axial vectors (eigenvalues sigma_i + sigma_j > 0), in 2D
+// y = b / tr(S); no singular-value differences appear.  It runs in FP32 on R rounded to
+// FP32: Rbar is an FP32 value, so R^T Rbar carries its rounding whatever the precision of
+// the product, and the solve is well conditioned (tr(S) I - S ~ 2 I at small strain).
+template <int D>
+__device__ __forceinline__ void polar_adjoint(const float E[D][D], const Polar<D>& p,
+                                              const float Rbar[D][D], float Fbar[D][D]) {
+  float M[D][D], S[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float m = 0.0f, sv = 0.0f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        m += p.R[k][i] * (double)Rbar[k][j];
-        s += p.R[k][i] * ((double)E[k][j] + (k == j ? 1.0 : 0.0));
+        m += p.Rf[k][i] * Rbar[k][j];
+        sv += p.Rf[k][i] * (E[k][j] + (k == j ? 1.0f : 0.0f));
       }
       M[i][j] = m;
-      S[i][j] = s;
+      S[i][j] = sv;
     }
-  if (D == 2) {
-    double b = 0.5 * (M[1][0] - M[0][1]);
-    double tr = S[0][0] + S[1][1];
-    double y = b / fmax(tr, 1e-6);
+  if constexpr (D == 2) {
+    const float b = 0.5f * (M[1][0] - M[0][1]);
+    const float tr = S[0][0] + S[1][1];
+    const float y2 = 2.0f * b / fmaxf(tr, 1e-6f);
     // 2 R Y, Y = [[0, -y], [y, 0]]
-    Fbar[0][0] += (float)(2.0 * p.R[0][1] * y);
-    Fbar[0][1] += (float)(-2.0 * p.R[0][0] * y);
-    Fbar[1][0] += (float)(2.0 * p.R[1][1] * y);
-    Fbar[1][1] += (float)(-2.0 * p.R[1][0] * y);
+    Fbar[0][0] += p.Rf[0][1] * y2;
+    Fbar[0][1] -= p.Rf[0][0] * y2;
+    Fbar[1][0] += p.Rf[1][1] * y2;
+    Fbar[1][1] -= p.Rf[1][0] * y2;
   } else {
-    double b0 = 0.5 * (M[2][1] - M[1][2]);
-    double b1 = 0.5 * (M[0][2] - M[2][0]);
-    double b2 = 0.5 * (M[1][0] - M[0][1]);
-    double tr = S[0][0] + S[1][1] + S[2][2];
+    const float b0 = 0.5f * (M[2][1] - M[1][2]);
+    const float b1 = 0.5f * (M[0][2] - M[2][0]);
+    const float b2 = 0.5f * (M[1][0] - M[0][1]);
+    const float tr = S[0][0] + S[1][1] + S[2][2];
     // G = tr(S) I - sym(S)
-    double g00 = tr - S[0][0], g11 = tr - S[1][1], g22 = tr - S[2][2];
-    double g01 = -0.5 * (S[0][1] + S[1][0]);
-    double g02 = -0.5 * (S[0][2] + S[2][0]);
-    double g12 = -0.5 * (S[1][2] + S[2][1]);
-    double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
-    double c11 = g00 * g22 - g02 * g02, c12 = g01 * g02 - g00 * g12, c22 = g00 * g11 - g01 * g01;
-    const double det = fmax(g00 * c00 + g01 * c01 + g02 * c02, 1e-18);
-    // 1/det: FP32 reciprocal, two FP64 Newton steps (relative error ~1e-28 -> FP64 ulps);
-    // a plain division beyond the FP32 seed's range
-    double id;
-    if (det < 1e30) {
-      id = (double)__frcp_rn((float)det);
-      id = id * (2.0 - det * id);
-      id = id * (2.0 - det * id);
-    } else {
-      id = 1.0 / det;
-    }
-    // 2y, rounded once: the rotation 2 R Y below is well conditioned (|2 R Y| = 2|y|), so it
-    // runs in FP32 on R rounded to FP32, with the error of the FP32 accumulation into Fbar
-    const float y0 = (float)(2.0 * (c00 * b0 + c01 * b1 + c02 * b2) * id);
-    const float y1 = (float)(2.0 * (c01 * b0 + c11 * b1 + c12 * b2) * id);
-    const float y2 = (float)(2.0 * (c02 * b0 + c12 * b1 + c22 * b2) * id);
+    const float g00 = tr - S[0][0], g11 = tr - S[1][1], g22 = tr - S[2][2];
+    const float g01 = -0.5f * (S[0][1] + S[1][0]);
+    const float g02 = -0.5f * (S[0][2] + S[2][0]);
+    const float g12 = -0.5f * (S[1][2] + S[2][1]);
+    const float c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+    const float c11 = g00 * g22 - g02 * g02, c12 = g01 * g02 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+    const float id = 2.0f / fmaxf(g00 * c00 + g01 * c01 + g02 * c02, 1e-30f);
+    const float y0 = (c00 * b0 + c01 * b1 + c02 * b2) * id;  // 2y
+    const float y1 = (c01 * b0 + c11 * b1 + c12 * b2) * id;
+    const float y2 = (c02 * b0 + c12 * b1 + c22 * b2) * id;
     // (R Y)[i][j] with Y = [[0, -y2, y1], [y2, 0, -y0], [-y1, y0, 0]]
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -632,8 +667,8 @@ __device__ __forceinline__ float column_of(const float row[D], int axis) {
 // tau += act (F e)(F e)^T, e = unit vector of `axis` (actuation fibre)
 // with F = I + E; every product is formed on E (or on F - R) so small strains keep
 // their relative precision.
-// Rc (fixed-corotated only, may be null): the cached FP64 polar factor of this particle
-// ([9][N] rows, particle p), used instead of recomputing it.
+// Rc (fixed-corotated only, may be null): the cached polar factor of this particle (R_hi and
+// R_lo rows, particle p), used instead of recomputing it.
 template <int D, int MAT>
 __device__ __forceinline__ bool kirchhoff(const float E[D][D], float mu, float la, float act, int axis,
                                           float tau[D][D], StressCache<D>& sc,
@@ -653,7 +688,7 @@ __device__ __forceinline__ bool kirchhoff(const float E[D][D], float mu, float l
       polar_from_cache<D>(Rc, N, p, E, sc.pol);
       ok = sc.J > 0.0f;
     } else {
-      ok = polar_f64<D>(E, sc.pol);
+      ok = polar_factor<D>(E, sc.pol);
     }
     // (F - R) F^T = Df + Df E^T
 #pragma unroll
@@ -743,7 +778,7 @@ __device__ __forceinline__ float kirchhoff_adjoint(const float E[D][D], float mu
         // (its antisymmetric part then cancels exactly)
         if (j >= i) mub += (i == j ? tb[i][j] : tb[i][j] + tb[j][i]) * DFt;
       }
-    polar_adjoint_f64<D>(E, sc.pol, Rbar, Fbar);
+    polar_adjoint<D>(E, sc.pol, Rbar, Fbar);
     float c = la * (2.0f * sc.J - 1.0f) * trtb;
 #pragma unroll
     for (int i = 0; i < D; ++i)

@@ -71,7 +71,7 @@ struct StepArgs {
   const float* wact;       // [scene][group][basis]
   const float4* PMr;       // grid (m, p) of step t-1, read by G2P (null: P2G only)
   float4* PMw;             // grid of step t, accumulated by P2G (null: G2P only)
-  double* Rw;              // [9][N] FP64 polar factors of the P2G's states, written (or null)
+  double* Rw;              // [9][N] polar factors (R_hi, R_lo pairs) of the P2G's states, written (or null)
   int* box_w;              // [scene][8] box of PMw for this use
   int* box_reset;          // [scene][8] the other parity box of PMw, reset here (or null)
   Clears clears;
@@ -105,7 +105,7 @@ struct AdjArgs {
                       // the backward's first scatter (FP32 bits; the measuring pass raises it,
                       // every pass derives the fixed-point scale of the ubar grids from it)
   int measure;        // 1: this kAdjG2P pass only measures that bound (no scatter, no writes)
-  const double* R1;   // [9][N] cached FP64 polar factors of state s+1 (or null: recompute)
+  const double* R1;   // [9][N] cached polar factors of state s+1 (or null: recompute)
   const double* Rm;   // same for state s-1
   int* box_m;
   int* box_m_reset;
@@ -1807,6 +1807,9 @@ __global__ void __launch_bounds__(kTile, step_ctas_per_sm<D, MAT>())
   __shared__ PassEntry e;
   __shared__ Buckets s_bk;
   buckets_zero(s_bk);  // ordered before its first use by the barriers that follow
+  // a barrier of an earlier launch of this sequence gave up: its passes never finished, so
+  // this launch would only run on an incomplete state
+  if (*(volatile unsigned*)ctl.err & kErrTimeout) return;
   for (int i = 0; i < n_pass; ++i) {
     if (i > 0 && !grid_barrier(ctl, (unsigned)i * gridDim.x + ctl.extra, &s_go)) return;
     __syncthreads();
@@ -1831,6 +1834,9 @@ __global__ void __launch_bounds__(kTile, MPM_ADJ_CTAS_PER_SM)
   __shared__ PassEntry e;
   __shared__ Buckets s_bk;
   buckets_zero(s_bk);  // ordered before its first use by the barriers that follow
+  // a barrier of an earlier launch of this sequence gave up: its passes never finished, so
+  // this launch would only run on an incomplete state
+  if (*(volatile unsigned*)ctl.err & kErrTimeout) return;
   for (int i = 0; i < n_pass; ++i) {
     if (i > 0 && !grid_barrier(ctl, (unsigned)i * gridDim.x + ctl.extra, &s_go)) return;
     __syncthreads();

@@ -1,6 +1,6 @@
 // peaks.cu -- mpm_measure_peak: arithmetic peaks of this GPU measured with the library's
-// own kernel, the denominators of the ALU rooflines (the FP64 polar factor and its adjoint
-// bound the fixed-corotated passes; their FP64 FLOP/s is compared with this peak).
+// own kernel, the denominators of the ALU rooflines (FP64 and FP32 fused multiply-adds: the
+// ratio of the two is why the polar factor's refinement runs in compensated FP32).
 //
 // The kernel runs 8 independent fused multiply-add chains per thread (enough to hide the
 // pipe's latency), on 8 CTAs of 256 threads per SM, for a fixed number of iterations; a
