@@ -165,6 +165,9 @@ extern "C" {
 #define MPM_INFO_ACT_PARAMS 5      /* actuation parameters per scene: n_groups * n_basis, or
                                       the controller's theta when ctrl_hidden > 0 */
 #define MPM_INFO_CKPT_EVERY 6      /* the checkpoint interval k in use */
+#define MPM_INFO_POLAR_FP64 7      /* 1: this library was built with MPM_POLAR_FP64=1 (the
+                                      fixed-corotated polar refinement and adjoint in FP64);
+                                      0: compensated FP32 refinement, FP32 adjoint */
 
 typedef struct mpm_handle mpm_handle;
 

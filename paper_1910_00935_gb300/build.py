@@ -1,9 +1,11 @@
 """Build libmpm.so (the C-ABI library) for sm_103a with nvcc, in-tree.
 
-    python -m paper_1910_00935_gb300.build [--force]
+    python -m paper_1910_00935_gb300.build [--force] [--polar-fp64]
 
 Each translation unit is compiled in parallel; the objects are linked into
-paper_1910_00935_gb300/_build/libmpm.so.  Only the sm_103a target is built.
+paper_1910_00935_gb300/_build/libmpm.so.  Only the sm_103a target is built.  The variant
+with the fixed-corotated polar factor's refinement and adjoint in FP64 (MPM_POLAR_FP64=1)
+goes to paper_1910_00935_gb300/_build_polar64/libmpm.so; load it with MPM_LIB.
 """
 from __future__ import annotations
 
@@ -17,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpm.so")
+OUT_DIR_POLAR64 = os.path.join(HERE, "_build_polar64")
+LIB_POLAR64 = os.path.join(OUT_DIR_POLAR64, "libmpm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["kernels_3d_fcr.cu", "kernels_3d_fcr_det.cu", "kernels_3d_nh.cu", "kernels_3d_nh_det.cu",
            "kernels_3d_liq.cu", "kernels_3d_liq_det.cu", "kernels_3d_mixed.cu",
@@ -40,22 +44,27 @@ def _deps():
     return files
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(out_dir: str = OUT_DIR) -> bool:
+    lib = os.path.join(out_dir, "libmpm.so")
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
-    objs = [os.path.join(OUT_DIR, src.replace(".cu", ".o")) for src in SOURCES]
+    t = os.path.getmtime(lib)
+    objs = [os.path.join(out_dir, src.replace(".cu", ".o")) for src in SOURCES]
     return any(not os.path.exists(o) for o in objs) or any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), polar_fp64: bool = False) -> str:
+    out_dir = OUT_DIR_POLAR64 if polar_fp64 else OUT_DIR
+    lib = os.path.join(out_dir, "libmpm.so")
+    if polar_fp64:
+        extra_flags = [*extra_flags, "-DMPM_POLAR_FP64=1"]
+    if not force and not needs_build(out_dir):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -66,15 +75,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-          extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [])
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [],
+                polar_fp64="--polar-fp64" in sys.argv))

@@ -1701,6 +1701,7 @@ int mpm_get_info(mpm_handle* h, int32_t key, int64_t* value) {
     case MPM_INFO_KEEPS_SEGMENT_GRIDS: *value = h->m.store_grids && !h->grid_recompute; return MPM_OK;
     case MPM_INFO_ACT_PARAMS: *value = h->m.n_act; return MPM_OK;
     case MPM_INFO_CKPT_EVERY: *value = h->m.K; return MPM_OK;
+    case MPM_INFO_POLAR_FP64: *value = MPM_POLAR_FP64; return MPM_OK;
   }
   return fail(h, MPM_ERR_ARG, "unknown info key");
 }

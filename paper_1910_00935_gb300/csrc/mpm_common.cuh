@@ -24,16 +24,23 @@ namespace mpm {
 #define MPM_TILE 128
 #endif
 // 3D forward passes: 7 CTAs per SM (72 registers, a few spills; 2,048 cube3d tiles then run in
-// 1.9 waves instead of 2.25) measured 3% faster than 6 for neo-Hookean; the fixed-corotated
-// passes (polar factor) keep 6 (80 registers)
+// 1.9 waves instead of 2.25) measured 3% faster than 6 for neo-Hookean, and 2% faster for the
+// fixed-corotated passes once their polar refinement left the FP64 pipe
 #ifndef MPM_STEP_CTAS_PER_SM_3D
 #define MPM_STEP_CTAS_PER_SM_3D (896 / MPM_TILE)
 #endif
 #ifndef MPM_STEP_CTAS_PER_SM_3D_POLAR
-#define MPM_STEP_CTAS_PER_SM_3D_POLAR (768 / MPM_TILE)
+#define MPM_STEP_CTAS_PER_SM_3D_POLAR (896 / MPM_TILE)
 #endif
 #ifndef MPM_STEP_CTAS_PER_SM_2D
 #define MPM_STEP_CTAS_PER_SM_2D (1024 / MPM_TILE)
+#endif
+// Precision of the fixed-corotated polar factor's refinement and adjoint: 0 (default) =
+// compensated FP32 refinement (R to ~1e-14) and an FP32 adjoint; 1 = both in FP64 (a build
+// variant, `build(polar_fp64=True)`, kept to compare against and for users who want the FP64
+// forms; ~3x slower on this part, whose FP64 pipe runs at 1/64 of the FP32 rate)
+#ifndef MPM_POLAR_FP64
+#define MPM_POLAR_FP64 0
 #endif
 #ifndef MPM_ADJ_CTAS_PER_SM
 #define MPM_ADJ_CTAS_PER_SM (640 / MPM_TILE)  // 96 registers: a few spills, 25% more warps
@@ -348,6 +355,37 @@ __host__ __device__ __forceinline__ bool polar_newton3(T X[3][3], T tol, int max
   return false;
 }
 
+#if MPM_POLAR_FP64
+// One Newton-Schulz step toward the nearest orthogonal matrix, Q <- Q (3I - Q^T Q)/2, in
+// FP64 (quadratic: an orthogonality error e becomes ~e^2)
+__device__ __forceinline__ void orthonormalize_step(double Q[3][3]) {
+  double G[3][3];  // symmetric: six entries
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      double g = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) g += Q[k][i] * Q[k][j];
+      G[i][j] = G[j][i] = 0.5 * ((i == j ? 3.0 : 0.0) - g);
+    }
+  double Qn[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double q = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) q += Q[i][k] * G[k][j];
+      Qn[i][j] = q;
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Q[i][j] = Qn[i][j];
+}
+#endif
+
 // Error-free transformations in FP32: a + b = s + e exactly (Knuth's TwoSum) and
 // a * b = p + e exactly (the fused multiply-add gives the product's rounding error).  The
 // _rn intrinsics keep the compiler from fusing or reordering these operations.
@@ -515,6 +553,7 @@ __device__ __forceinline__ bool polar_factor(const float E[D][D], Polar<D>& p) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) Xf[i][j] = E[i][j] + (i == j ? 1.0f : 0.0f);
     bool ok = polar_newton3<float>(Xf, 1e-12f, 20);
+#if !MPM_POLAR_FP64
     if (ok) {
       ok = polar_refine3(E, Xf, p.Rh, p.Rl, p.Df);
       if (ok) {
@@ -525,14 +564,81 @@ __device__ __forceinline__ bool polar_factor(const float E[D][D], Polar<D>& p) {
         return true;
       }
     }
-    // near-singular F: Newton's iteration in FP64 from F
+    double X[3][3];
+#else
+    // FP64 refinement: orthonormalise Q (one Newton-Schulz step), then rotate it by the small
+    // rotation that makes Q^T F symmetric, all in FP64
     double X[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) X[i][j] = Fd[i][j];
-    // stop when the next update would be below FP64 resolution
-    ok = polar_newton3<double>(X, 1e-20, 24);
+      for (int j = 0; j < 3; ++j) X[i][j] = (double)Xf[i][j];
+    if (ok) {
+      orthonormalize_step(X);
+      double M[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          double m = 0.0;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) m += X[k][i] * Fd[k][j];
+          M[i][j] = m;
+        }
+      const double tr = M[0][0] + M[1][1] + M[2][2];
+      double A[3][3];  // tr(S) I - S, S = sym(M)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A[i][j] = (i == j ? tr : 0.0) - 0.5 * (M[i][j] + M[j][i]);
+      const double b[3] = {M[2][1] - M[1][2], M[0][2] - M[2][0], M[1][0] - M[0][1]};
+      double c[3][3];
+      cofactor3<double>(A, c);
+      const double det = A[0][0] * c[0][0] + A[0][1] * c[0][1] + A[0][2] * c[0][2];
+      ok = det > 1e-30 && det < 1e30;
+      if (ok) {
+        // 1/det: FP32 reciprocal, two FP64 Newton steps (relative error ~1e-28 -> FP64 ulps)
+        double id = (double)__frcp_rn((float)det);
+        id = id * (2.0 - det * id);
+        id = id * (2.0 - det * id);
+        double w[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[i] = (c[0][i] * b[0] + c[1][i] * b[1] + c[2][i] * b[2]) * id;
+        // G = I + W + W^2/2 with W the cross-product matrix of w (W^2 = w w^T - |w|^2 I)
+        const double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        const double Wm[3][3] = {{0.0, -w[2], w[1]}, {w[2], 0.0, -w[0]}, {-w[1], w[0], 0.0}};
+        double G[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            G[i][j] = (i == j ? 1.0 - 0.5 * ww : 0.0) + Wm[i][j] + 0.5 * w[i] * w[j];
+        double Rn[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            double r = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) r += X[i][k] * G[k][j];
+            Rn[i][j] = r;
+          }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) X[i][j] = Rn[i][j];
+      }
+    }
+#endif
+    if (!ok) {
+      // near-singular F: Newton's iteration in FP64 from F
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) X[i][j] = Fd[i][j];
+      // stop when the next update would be below FP64 resolution
+      ok = polar_newton3<double>(X, 1e-20, 24);
+    }
     if (!ok) {
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -590,6 +696,7 @@ __device__ __forceinline__ void polar_to_cache(double* Rc, int64_t N, int64_t p,
 // y = b / tr(S); no singular-value differences appear.  It runs in FP32 on R rounded to
 // FP32: Rbar is an FP32 value, so R^T Rbar carries its rounding whatever the precision of
 // the product, and the solve is well conditioned (tr(S) I - S ~ 2 I at small strain).
+#if !MPM_POLAR_FP64
 template <int D>
 __device__ __forceinline__ void polar_adjoint(const float E[D][D], const Polar<D>& p,
                                               const float Rbar[D][D], float Fbar[D][D]) {
@@ -641,6 +748,77 @@ __device__ __forceinline__ void polar_adjoint(const float E[D][D], const Polar<D
     }
   }
 }
+#else
+// FP64 form: the products and the solve in FP64 on R = R_hi + R_lo
+template <int D>
+__device__ __forceinline__ void polar_adjoint(const float E[D][D], const Polar<D>& p,
+                                                  const float Rbar[D][D], float Fbar[D][D]) {
+  double Rd[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) Rd[i][j] = (double)p.Rh[i][j] + (double)p.Rl[i][j];
+  double M[D][D], S[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double m = 0.0, s = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        m += Rd[k][i] * (double)Rbar[k][j];
+        s += Rd[k][i] * ((double)E[k][j] + (k == j ? 1.0 : 0.0));
+      }
+      M[i][j] = m;
+      S[i][j] = s;
+    }
+  if constexpr (D == 2) {
+    double b = 0.5 * (M[1][0] - M[0][1]);
+    double tr = S[0][0] + S[1][1];
+    double y = b / fmax(tr, 1e-6);
+    // 2 R Y, Y = [[0, -y], [y, 0]]
+    Fbar[0][0] += (float)(2.0 * Rd[0][1] * y);
+    Fbar[0][1] += (float)(-2.0 * Rd[0][0] * y);
+    Fbar[1][0] += (float)(2.0 * Rd[1][1] * y);
+    Fbar[1][1] += (float)(-2.0 * Rd[1][0] * y);
+  } else {
+    double b0 = 0.5 * (M[2][1] - M[1][2]);
+    double b1 = 0.5 * (M[0][2] - M[2][0]);
+    double b2 = 0.5 * (M[1][0] - M[0][1]);
+    double tr = S[0][0] + S[1][1] + S[2][2];
+    // G = tr(S) I - sym(S)
+    double g00 = tr - S[0][0], g11 = tr - S[1][1], g22 = tr - S[2][2];
+    double g01 = -0.5 * (S[0][1] + S[1][0]);
+    double g02 = -0.5 * (S[0][2] + S[2][0]);
+    double g12 = -0.5 * (S[1][2] + S[2][1]);
+    double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+    double c11 = g00 * g22 - g02 * g02, c12 = g01 * g02 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+    const double det = fmax(g00 * c00 + g01 * c01 + g02 * c02, 1e-18);
+    // 1/det: FP32 reciprocal, two FP64 Newton steps (relative error ~1e-28 -> FP64 ulps);
+    // a plain division beyond the FP32 seed's range
+    double id;
+    if (det < 1e30) {
+      id = (double)__frcp_rn((float)det);
+      id = id * (2.0 - det * id);
+      id = id * (2.0 - det * id);
+    } else {
+      id = 1.0 / det;
+    }
+    // 2y, rounded once: the rotation 2 R Y below is well conditioned (|2 R Y| = 2|y|), so it
+    // runs in FP32 on R rounded to FP32, with the error of the FP32 accumulation into Fbar
+    const float y0 = (float)(2.0 * (c00 * b0 + c01 * b1 + c02 * b2) * id);
+    const float y1 = (float)(2.0 * (c01 * b0 + c11 * b1 + c12 * b2) * id);
+    const float y2 = (float)(2.0 * (c02 * b0 + c12 * b1 + c22 * b2) * id);
+    // (R Y)[i][j] with Y = [[0, -y2, y1], [y2, 0, -y0], [-y1, y0, 0]]
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Fbar[i][0] += p.Rf[i][1] * y2 - p.Rf[i][2] * y1;
+      Fbar[i][1] += p.Rf[i][2] * y0 - p.Rf[i][0] * y2;
+      Fbar[i][2] += p.Rf[i][0] * y1 - p.Rf[i][1] * y0;
+    }
+  }
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // Kirchhoff stress tau(F) and its adjoint
