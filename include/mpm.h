@@ -165,6 +165,12 @@ extern "C" {
 #define MPM_INFO_ACT_PARAMS 5      /* actuation parameters per scene: n_groups * n_basis, or
                                       the controller's theta when ctrl_hidden > 0 */
 #define MPM_INFO_CKPT_EVERY 6      /* the checkpoint interval k in use */
+#define MPM_INFO_GATHER_BOXES 8    /* forward gathers (one per CTA and G2P pass) since the last
+                                      mpm_set_initial, and of them ... (waits for the handle's
+                                      last stream) */
+#define MPM_INFO_GATHER_BOX_OVERFLOWS 9 /* ... those whose stencil box exceeded the shared gather
+                                      box (MPM_OPT_GATHER_CAPACITY) and read the grid through L1:
+                                      the particle order's decay as a body flows */
 #define MPM_INFO_POLAR_FP64 7      /* 1: this library was built with MPM_POLAR_FP64=1 (the
                                       fixed-corotated polar refinement and adjoint in FP64);
                                       0: compensated FP32 refinement, FP32 adjoint */

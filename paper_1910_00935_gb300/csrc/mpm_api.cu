@@ -63,7 +63,7 @@ struct Layout {
   size_t rcache;  // 2 x (K+1) x [9][N] polar factors of a segment (3D FCR; R_hi, R_lo as FP32 pairs), by parity
   size_t grids;  // pm_slots + kUBSlots dense grids
   size_t boxes;  // (pm_slots + kUBSlots) x 2 parities x [scene][8]
-  size_t err, com, com_part, ub_m0;
+  size_t err, box_stats, com, com_part, ub_m0;
   size_t plan_fwd, plan_bwd, gsync;  // persistent-form pass plans and barrier counters
   // closed-loop controller: per-tile sensor sums, per-step inputs / hidden / outputs /
   // actuation, group sizes, dL/dtheta (FP64) and the per-slot sensor adjoints
@@ -214,6 +214,7 @@ Layout make_layout(const Dims& m) {
   L.grids = take(grid * (m.pm_slots + kUBSlots));
   L.boxes = take((size_t)(m.pm_slots + kUBSlots) * 2 * S * 8 * 4);
   L.err = take(4);
+  L.box_stats = take(16);
   L.ub_m0 = take(4);
   L.com = take(S * 6 * 8);
   L.com_part = take(com_scratch_doubles(m.S) * 8);
@@ -690,6 +691,7 @@ struct Launcher {
     A.matid = h->at<int>(h->L.matid);
     A.wact = act_ptr(h, t);
     A.err = h->at<unsigned>(h->L.err);
+    A.box_stats = h->at<unsigned long long>(h->L.box_stats);
     if (read >= 0) A.PMr = ring_grid(h, h->pm, read);
     A.Rw = R_out;
     if (written) {
@@ -1422,6 +1424,7 @@ int mpm_set_initial(mpm_handle* h, const float* x0, const float* v0, const float
   if (wbytes) CK(cudaMemcpyAsync(h->at<float>(L.wact), w, wbytes, cudaMemcpyDeviceToDevice, s));
   const size_t grid = (size_t)m.S * m.nnodes * sizeof(float4) * m.words;
   CK(cudaMemsetAsync(h->at<char>(L.grids), 0, grid * (m.pm_slots + kUBSlots), s));
+  CK(cudaMemsetAsync(h->at<char>(L.box_stats), 0, 16, s));
   CK(launch_reset_boxes(h->at<int>(L.boxes), (int64_t)(m.pm_slots + kUBSlots) * 2 * m.S, s));
   ring_reset(h->pm);
   ring_reset(h->ub);
@@ -1702,6 +1705,15 @@ int mpm_get_info(mpm_handle* h, int32_t key, int64_t* value) {
     case MPM_INFO_ACT_PARAMS: *value = h->m.n_act; return MPM_OK;
     case MPM_INFO_CKPT_EVERY: *value = h->m.K; return MPM_OK;
     case MPM_INFO_POLAR_FP64: *value = MPM_POLAR_FP64; return MPM_OK;
+    case MPM_INFO_GATHER_BOXES:
+    case MPM_INFO_GATHER_BOX_OVERFLOWS: {
+      unsigned long long st[2] = {0, 0};
+      cudaError_t e = cudaStreamSynchronize(h->last_stream);
+      if (e == cudaSuccess) e = cudaMemcpy(st, h->at<char>(h->L.box_stats), 16, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(h, e, "read gather-box counters");
+      *value = (int64_t)st[key == MPM_INFO_GATHER_BOXES ? 0 : 1];
+      return MPM_OK;
+    }
   }
   return fail(h, MPM_ERR_ARG, "unknown info key");
 }

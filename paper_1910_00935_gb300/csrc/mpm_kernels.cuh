@@ -76,6 +76,8 @@ struct StepArgs {
   int* box_reset;          // [scene][8] the other parity box of PMw, reset here (or null)
   Clears clears;
   unsigned* err;
+  unsigned long long* box_stats;  // [2]: gather boxes staged, of which too large for the shared
+                                  // box (read from the grid instead); null: not counted
 };
 
 struct AdjArgs {
@@ -1156,6 +1158,10 @@ __device__ __forceinline__ void step_tile(const SimParams& P, const StepArgs& A,
     gbx.use_tile = false;
     if (P.gather_capacity > 0) {
       gbx = box_extent<D>(ok, s.base, P.gather_capacity, s_box);  // slot 0
+      if (A.box_stats && threadIdx.x == 0 && gbx.vol > 0) {
+        atomicAdd(A.box_stats, 1ull);
+        if (!gbx.use_tile) atomicAdd(A.box_stats + 1, 1ull);
+      }
       box_load<D>(gbx, reinterpret_cast<float4*>(sm), velocity);
     }
     if (ok) {

@@ -40,6 +40,7 @@ KERNEL_CATEGORIES = {1: "p2g", 2: "g2p_p2g", 3: "g2p_p2g_full", 4: "g2p", 5: "gr
 MPM_INFO_KERNEL_LAUNCHES, MPM_INFO_N_TOTAL, MPM_INFO_STEPS_RECORDED = 1, 2, 3
 MPM_INFO_KEEPS_SEGMENT_GRIDS, MPM_INFO_ACT_PARAMS, MPM_INFO_CKPT_EVERY = 4, 5, 6
 MPM_INFO_POLAR_FP64 = 7
+MPM_INFO_GATHER_BOXES, MPM_INFO_GATHER_BOX_OVERFLOWS = 8, 9
 
 EXPORTED = ["mpm_workspace_bytes", "mpm_create", "mpm_set_initial", "mpm_forward",
             "mpm_get_state", "mpm_loss", "mpm_backward", "mpm_sync_status", "mpm_set_option",

@@ -553,3 +553,24 @@ def test_capacity_beyond_shared_memory_is_refused(mpm):
     sim.forward(4)
     sim.check()
     sim.close()
+
+
+def test_gather_box_counters(mpm):
+    """MPM_INFO_GATHER_BOXES / _OVERFLOWS count the forward's gathers and those whose stencil
+    box did not fit the shared gather box; a set-up resets them."""
+    scene = scenes.make("cube3d", n_side=16, n_grid=64)  # 4,096 particles: 32 tiles of 128
+    sim = mpm.from_scene(scene, max_steps=8)
+    assert sim.info(mpm.MPM_INFO_GATHER_BOXES) == 0
+    sim.forward(8)
+    boxes = sim.info(mpm.MPM_INFO_GATHER_BOXES)
+    # the first step is a P2G from the initial state; then 7 fused G2P+P2G passes and the last
+    # G2P each gather once per tile
+    assert boxes == 8 * 32, boxes
+    assert sim.info(mpm.MPM_INFO_GATHER_BOX_OVERFLOWS) == 0  # a compact tile's box fits 512
+    sim.set_option(mpm.MPM_OPT_GATHER_CAPACITY, 27)  # smaller than any 3D stencil box of a tile
+    sim.reload()
+    assert sim.info(mpm.MPM_INFO_GATHER_BOXES) == 0
+    sim.forward(8)
+    assert sim.info(mpm.MPM_INFO_GATHER_BOX_OVERFLOWS) == sim.info(mpm.MPM_INFO_GATHER_BOXES) == boxes
+    sim.check()
+    sim.close()
