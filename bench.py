@@ -557,10 +557,10 @@ def run_springs(args, rank, world):
     sim.close()
 
 
-def fp64_flop_per_particle(workload, category):
-    """FP64 FLOP per particle of one launch of `category` (2 per fused multiply-add, 1 per add
-    or multiply), from profiles/fp64_<category>_<workload>.md when that summary was taken
-    on these kernels (same source digest); else None."""
+def flop_per_particle(workload, category, precision="FP64"):
+    """FP64 (or FP32) FLOP per particle of one launch of `category` (2 per fused multiply-add,
+    1 per add or multiply), from profiles/fp64_<category>_<workload>.md when that summary was
+    taken on these kernels (same source digest); else None."""
     path = os.path.join(ROOT, "profiles", f"fp64_{category}_{workload}.md")
     if not os.path.exists(path):
         return None
@@ -568,14 +568,16 @@ def fp64_flop_per_particle(workload, category):
     if f"source digest: {source_digest()}" not in text:
         return None
     import re
-    m = re.search(r"FP64 FLOP per particle: ([0-9.eE+-]+)", text)
+    m = re.search(precision + r" FLOP per particle: ([0-9.eE+-]+)", text)
     return float(m.group(1)) if m else None
 
 
 def fp64_roofline(mpm, workload, category, n_launch, cat_ms, particles_per_launch):
     """Achieved FP64 FLOP/s of a kernel category against the GPU's FP64 FMA peak measured
-    live with the library's own kernel (mpm_measure_peak)."""
-    per = fp64_flop_per_particle(workload, category)
+    live with the library's own kernel (mpm_measure_peak), and the same for FP32 (the
+    fixed-corotated passes' polar factor and adjoint left the FP64 pipe; their FP32
+    arithmetic is the ALU share that remains)."""
+    per = flop_per_particle(workload, category, "FP64")
     peak = mpm.mpm_measure_peak(mpm.MPM_PEAK_FP64_FMA)
     out = {"bound": "fp64", "peak": peak / 1e12, "unit": "TFLOP/s", "kernel": category,
            "peak_source": "measured live: mpm_measure_peak (FP64 FMA chains, CUDA events)"}
@@ -587,6 +589,12 @@ def fp64_roofline(mpm, workload, category, n_launch, cat_ms, particles_per_launc
     achieved = per * particles_per_launch / (avg_ms / 1e3) / 1e12
     out.update(achieved=achieved, frac=achieved / out["peak"], flop_per_particle=per,
                avg_launch_ms=avg_ms)
+    per32 = flop_per_particle(workload, category, "FP32")
+    if per32 is not None:
+        peak32 = mpm.mpm_measure_peak(mpm.MPM_PEAK_FP32_FMA) / 1e12
+        a32 = per32 * particles_per_launch / (avg_ms / 1e3) / 1e12
+        out["fp32"] = {"achieved": a32, "peak": peak32, "unit": "TFLOP/s", "frac": a32 / peak32,
+                       "flop_per_particle": per32}
     return out
 
 
