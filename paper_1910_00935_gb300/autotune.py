@@ -13,6 +13,12 @@ of the caller's own simulator for each candidate, one knob at a time (coordinate
 from the defaults), keeps the fastest, and caches the result in a JSON file keyed by the
 workload's shape class and the device name.  Results never change numerics beyond FP32
 atomic-order rounding (the GPU tests check every knob setting against the oracle).
+
+`tune_build` does the same for the build-time shapes: particles (= threads) per CTA,
+`MPM_TILE`, with the CTAs per SM of each pass that follow from it.  Each candidate is a
+library build of its own (`build.build(tag=...)`), timed in a child process (one process
+loads one library) on the caller's scene and checked against the default build's final
+positions; the fastest valid build's path is returned for `MPM_LIB`.
 """
 from __future__ import annotations
 
@@ -154,3 +160,111 @@ def tune(sim, T: int = 32, repeats: int = 2, cache_path: str | None = None, forc
                   "evaluated": [[c, s] for c, s in log], "failed": failed}
     save_cache(cache, cache_path)
     return config
+
+
+# build-time block shapes: variant tag -> extra nvcc flags (the default build is "tile128")
+BUILD_SPACE = {"tile128": [], "tile64": ["-DMPM_TILE=64"], "tile256": ["-DMPM_TILE=256"]}
+
+_CHILD = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+import torch
+from paper_1910_00935_gb300 import mpm
+desc = json.load(open({desc!r}))
+arrays = dict(np.load({npz!r}))
+scene = {{"desc": desc, "arrays": arrays}}
+T = {T}
+sim = mpm.from_scene(scene, max_steps=T)
+S = len(desc["n_particles"])
+tgt = torch.as_tensor(arrays["target"]).cuda() if "target" in arrays else torch.zeros(S, desc["dim"], device="cuda")
+def run():
+    sim.forward(T)
+    _, gT, _ = sim.loss(desc.get("loss_kind", 0), tgt)
+    sim.backward(dL_dx=gT)
+run()
+torch.cuda.synchronize()
+best = float("inf")
+for _ in range({repeats}):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run()
+    e1.record()
+    torch.cuda.synchronize()
+    best = min(best, e0.elapsed_time(e1) / 1e3)
+sim.check()
+sim.forward(T)
+np.save({xout!r}, sim.state()[0].cpu().numpy())
+sim.check()
+print(json.dumps({{"seconds": best}}))
+"""
+
+
+def _jsonable(v):
+    import numpy as np
+    if isinstance(v, np.ndarray):
+        return v.tolist()
+    if isinstance(v, np.generic):
+        return v.item()
+    raise TypeError(type(v))
+
+
+def tune_build(scene: dict, T: int = 32, repeats: int = 2, space: dict = BUILD_SPACE,
+               cache_path: str | None = None, force: bool = False, device_name: str | None = None,
+               timeout: float = 900.0) -> dict:
+    """Pick the build-time block shape for `scene` (a scenes.make dict) by measurement.
+    Returns {"tag", "lib", "seconds": {tag: s}, "refused": {tag: reason}}; the library path
+    is the one to load through MPM_LIB."""
+    import subprocess
+    import sys
+    import tempfile
+
+    import numpy as np
+
+    from . import build as _build
+
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name(0)
+    key = "build|" + shape_key(scene["desc"], device_name)
+    cache = load_cache(cache_path)
+    if not force and key in cache and os.path.exists(cache[key]["lib"]):
+        return cache[key]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    seconds, refused, xs, libs = {}, {}, {}, {}
+    with tempfile.TemporaryDirectory() as tmp:
+        desc_path, npz = os.path.join(tmp, "desc.json"), os.path.join(tmp, "arrays.npz")
+        with open(desc_path, "w") as f:
+            json.dump(scene["desc"], f, default=_jsonable)
+        np.savez(npz, **scene["arrays"])
+        for tag, flags in space.items():
+            try:
+                libs[tag] = _build.build(extra_flags=flags, tag=tag if flags else "")
+            except RuntimeError as e:
+                refused[tag] = f"build failed: {str(e)[:200]}"
+                continue
+            xout = os.path.join(tmp, f"x_{tag}.npy")
+            script = _CHILD.format(root=root, desc=desc_path, npz=npz, T=int(T), repeats=int(repeats),
+                                   xout=xout)
+            r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True,
+                               env=dict(os.environ, MPM_LIB=libs[tag]), timeout=timeout)
+            if r.returncode != 0:
+                refused[tag] = "run failed: " + (r.stderr.strip().splitlines() or [""])[-1][:200]
+                continue
+            seconds[tag] = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+            xs[tag] = np.load(xout)
+        ref = next(iter(space))  # the first entry is the default build: the others must agree
+        if ref in xs:
+            for tag in list(seconds):
+                d = float(np.linalg.norm(xs[tag] - xs[ref]) / max(np.linalg.norm(xs[ref]), 1e-30))
+                if not d <= 1e-5:
+                    refused[tag] = f"final positions differ from {ref} by {d:.2e}"
+                    del seconds[tag]
+    if not seconds:
+        raise RuntimeError(f"no build-time variant ran: {refused}")
+    best = min(seconds, key=seconds.get)
+    res = {"tag": best, "lib": libs[best], "flags": list(space[best]), "seconds": seconds,
+           "refused": refused, "T_probe": int(T)}
+    cache[key] = res
+    save_cache(cache, cache_path)
+    return res

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpm.so")
-OUT_DIR_POLAR64 = os.path.join(HERE, "_build_polar64")
+OUT_DIR_POLAR64 = os.path.join(HERE, "_build_polar64")  # the polar_fp64 variant
 LIB_POLAR64 = os.path.join(OUT_DIR_POLAR64, "libmpm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["kernels_3d_fcr.cu", "kernels_3d_fcr_det.cu", "kernels_3d_nh.cu", "kernels_3d_nh_det.cu",
@@ -53,11 +53,21 @@ def needs_build(out_dir: str = OUT_DIR) -> bool:
     return any(not os.path.exists(o) for o in objs) or any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=(), polar_fp64: bool = False) -> str:
-    out_dir = OUT_DIR_POLAR64 if polar_fp64 else OUT_DIR
-    lib = os.path.join(out_dir, "libmpm.so")
+def variant_dir(tag: str) -> str:
+    """Build folder of a named variant (`_build_<tag>` beside the default `_build`)."""
+    return OUT_DIR if not tag else os.path.join(HERE, f"_build_{tag}")
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=(), polar_fp64: bool = False,
+          tag: str = "") -> str:
+    """Compile and link libmpm.so; returns its path.  `tag` names a variant folder for
+    builds with other `extra_flags` (e.g. another MPM_TILE); polar_fp64 is the variant
+    `polar64` with -DMPM_POLAR_FP64=1."""
     if polar_fp64:
+        tag = tag or "polar64"
         extra_flags = [*extra_flags, "-DMPM_POLAR_FP64=1"]
+    out_dir = variant_dir(tag)
+    lib = os.path.join(out_dir, "libmpm.so")
     if not force and not needs_build(out_dir):
         return lib
     os.makedirs(out_dir, exist_ok=True)

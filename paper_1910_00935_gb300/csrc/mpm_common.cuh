@@ -4,7 +4,7 @@
 // plus the actuation fibre stress of diffmpm's open-loop controller, Section 4.1),
 // the stress adjoint, and the polar decomposition with its adjoint (the hand-written
 // SVD/polar gradient of Appendix C).  Bulk arithmetic is FP32; the polar factor R and F - R
-// are resolved to ~1e-14 (compensated FP32 in 3D, FP64 in 2D); the polar adjoint is FP32.
+// are resolved to ~1e-14 in compensated FP32; the polar adjoint is FP32.
 //
 // The deformation gradient is carried as E = F - I: an FP32 F close to a rotation-free
 // identity keeps only ~1e-7/|strain| relative precision on the strain, E keeps 1e-7.
@@ -421,6 +421,64 @@ __host__ __device__ __forceinline__ float f_minus_r(float delta, float e, float 
   return g + ((ge + fl) - rl);
 }
 
+// 2D polar factor R = [[c, -s], [s, c]] / r, c = F00 + F11, s = F10 - F01, r = |(c, s)|,
+// without FP64 arithmetic: c, s, c^2 + s^2, r and 1/r are carried as value + correction pairs
+// (exact sums and products; one correction of the FP32 square root from its exact residual,
+// and of the FP32 reciprocal from r0 i0 - 1, exact in one fused multiply-add), so cos = c / r
+// and sin = s / r are resolved to ~1e-14 and F - R is formed from the exact parts.  Returns
+// false (R = I) for det F <= 0 or a degenerate (c, s).
+__host__ __device__ __forceinline__ bool polar_refine2(const float E[2][2], float Rh[2][2], float Rl[2][2],
+                                                       float Df[2][2]) {
+  float ch, cl, sh, sl;
+  {
+    float t, e1, e2;
+    two_sum(2.0f, E[0][0], t, e1);
+    two_sum(t, E[1][1], ch, e2);
+    cl = e1 + e2;
+  }
+  two_sum(E[1][0], -E[0][1], sh, sl);
+  float p1, e1, p2, e2, qh, e3;
+  two_prod(ch, ch, p1, e1);
+  two_prod(sh, sh, p2, e2);
+  two_sum(p1, p2, qh, e3);
+  const float ql = e1 + e2 + e3 + 2.0f * (ch * cl + sh * sl);
+  const float det = (1.0f + E[0][0]) * (1.0f + E[1][1]) - E[0][1] * E[1][0];
+  if (!(det > 0.0f) || !(qh > 1e-30f) || !(qh < 1e30f)) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        Rh[i][j] = i == j ? 1.0f : 0.0f;
+        Rl[i][j] = 0.0f;
+        Df[i][j] = E[i][j];
+      }
+    return false;
+  }
+  const float r0 = sqrtf(qh);
+  float pp, ee;
+  two_prod(r0, r0, pp, ee);
+  const float rl = ((ef_add(qh, -pp) - ee) + ql) / (2.0f * r0);  // r = r0 + rl
+  const float i0 = 1.0f / r0;
+  const float ie = fmaf(r0, i0, -1.0f);                           // r0 i0 - 1, exact
+  const float il = -i0 * (ie + rl * i0);                          // 1 / r = i0 + il
+  float ah, al, bh, bl;
+  two_prod(ch, i0, ah, al);
+  al += ch * il + cl * i0;
+  two_prod(sh, i0, bh, bl);
+  bl += sh * il + sl * i0;
+  Rh[0][0] = Rh[1][1] = ah;
+  Rl[0][0] = Rl[1][1] = al;
+  Rh[1][0] = bh;
+  Rl[1][0] = bl;
+  Rh[0][1] = -bh;
+  Rl[0][1] = -bl;
+  Df[0][0] = f_minus_r(1.0f, E[0][0], ah, al);
+  Df[1][1] = f_minus_r(1.0f, E[1][1], ah, al);
+  Df[1][0] = f_minus_r(0.0f, E[1][0], bh, bl);
+  Df[0][1] = f_minus_r(0.0f, E[0][1], -bh, -bl);
+  return true;
+}
+
 // 3D polar factor refined from an FP32 one without FP64 arithmetic (the FP64 pipe runs at
 // 1/64 of the FP32 rate on this part).  Q is Newton's FP32 iterate, orthogonal and equal to R
 // to within FP32 resolution (~1e-7), so every correction below is of that size and needs only
@@ -514,7 +572,7 @@ __host__ __device__ __forceinline__ bool polar_refine3(const float E[3][3], cons
 }
 
 // 2D: R is the rotation by atan2(F10 - F01, F00 + F11), formed without a transcendental
-// as (c, s) / |(c, s)|.
+// as (c, s) / |(c, s)| in compensated FP32 (polar_refine2).
 // 3D: Newton's iteration in FP32 gives Q within FP32 resolution of R, refined without FP64
 // arithmetic (polar_refine3) to R = R_hi + R_lo and F - R; R in FP64 is formed from the pair
 // only where a pass needs it (the polar adjoint, the per-segment cache).  When the FP32 stage
@@ -528,6 +586,14 @@ __device__ __forceinline__ bool polar_factor(const float E[D][D], Polar<D>& p) {
 #pragma unroll
     for (int j = 0; j < D; ++j) Fd[i][j] = (double)E[i][j] + (i == j ? 1.0 : 0.0);
   if constexpr (D == 2) {
+#if !MPM_POLAR_FP64
+    const bool ok = polar_refine2(E, p.Rh, p.Rl, p.Df);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) p.Rf[i][j] = p.Rh[i][j] + p.Rl[i][j];
+    return ok;
+#else
     double c = Fd[0][0] + Fd[1][1];
     double s = Fd[1][0] - Fd[0][1];
     double r = sqrt(c * c + s * s);
@@ -546,6 +612,7 @@ __device__ __forceinline__ bool polar_factor(const float E[D][D], Polar<D>& p) {
         p.Df[i][j] = (float)(Fd[i][j] - R[i][j]);
       }
     return det > 0.0 && r > 0.0;
+#endif
   } else {
     float Xf[3][3];
 #pragma unroll
@@ -862,7 +929,7 @@ __device__ __forceinline__ bool kirchhoff(const float E[D][D], float mu, float l
   sc.Jm1 = det_minus_one<D>(E);
   sc.J = 1.0f + sc.Jm1;
   if (MAT == kFixedCorotated) {
-    if (Rc) {
+    if (D == 3 && Rc) {  // the cache is kept for 3D only
       polar_from_cache<D>(Rc, N, p, E, sc.pol);
       ok = sc.J > 0.0f;
     } else {

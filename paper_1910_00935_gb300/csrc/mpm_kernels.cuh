@@ -1047,7 +1047,8 @@ __device__ __forceinline__ void p2g_pass(const SimParams& P, const float* basis,
       err |= kErrNonFinite;
       ok = false;
     }
-    if ((MAT == kFixedCorotated || (MAT == kMixed && mat_p == kFixedCorotated)) && R_out && active)
+    // the polar cache is a 3D fixed-corotated feature
+    if (D == 3 && (MAT == kFixedCorotated || (MAT == kMixed && mat_p == kFixedCorotated)) && R_out && active)
       polar_to_cache<D>(R_out, N, p, sc.pol);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
