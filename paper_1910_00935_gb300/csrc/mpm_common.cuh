@@ -219,7 +219,9 @@ __device__ __forceinline__ bool make_axes(const float* x, const SimParams& P, Ax
       const long long X = (long long)__float_as_int(x[a]) * (long long)P.n_grid;
       const long long bi = (X - (1LL << 30)) >> 31;  // floor(X - 0.5)
       good = bi >= 0 && bi <= (long long)(P.n_grid - 3);
-      b = good ? (float)bi : 0.0f;
+      // a 32-bit conversion (0 <= bi <= n_grid - 3): the 64-bit one issues on the FP64 pipe
+      // (measured 0.3-0.6% faster passes on cube3d, rects2d and robots3d)
+      b = good ? (float)(int)bi : 0.0f;
       // the fraction X - base in [0.5, 1.5): below 2^32 in units of 2^-31 (FP32 rounds it once)
       f = good ? __uint2float_rn((unsigned)(X - (bi << 31))) * (1.0f / kFixPos) : 1.0f;
     } else {
