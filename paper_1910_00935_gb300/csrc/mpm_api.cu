@@ -201,7 +201,7 @@ Layout make_layout(const Dims& m) {
   L.matid = take(N * 4);
   L.wact = take(S * (size_t)std::max<int64_t>(kMaxGroups * kMaxBasis, m.n_act) * 4);
   L.wbar_tile = take((size_t)m.n_tiles * kMaxGroups * kMaxBasis * 4);
-  L.mubar = take(N * 8);  // FP64 sums over the steps (see AdjArgs::mubar)
+  L.mubar = take(N * 8);  // compensated FP32 sums over the steps (see AdjArgs::mubar)
   L.labar = take(N * 8);
   L.fin = take(Q * N * 4);
   L.cur = take(Q * N * 4);
@@ -732,8 +732,8 @@ struct Launcher {
     A.adj = h->at<float>(h->L.adj);
     A.mu = h->at<float>(h->L.mu);
     A.la = h->at<float>(h->L.la);
-    A.mubar = h->at<double>(h->L.mubar);
-    A.labar = h->at<double>(h->L.labar);
+    A.mubar = h->at<float2>(h->L.mubar);
+    A.labar = h->at<float2>(h->L.labar);
     A.group = h->at<int>(h->L.group);
     A.matid = h->at<int>(h->L.matid);
     A.wact = act_ptr(h, s_step + 1);
@@ -1565,8 +1565,8 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, const fl
     r0 += rows[k];
   }
   if (gE || gnu) {
-    CK(launch_material_grad(m.N, perm, h->at<float>(L.E), h->at<float>(L.nu), h->at<double>(L.mubar),
-                            h->at<double>(L.labar), gE, gnu, s));
+    CK(launch_material_grad(m.N, perm, h->at<float>(L.E), h->at<float>(L.nu), h->at<float2>(L.mubar),
+                            h->at<float2>(L.labar), gE, gnu, s));
     ++h->launches;
   }
   if (gw && ctrl) {

@@ -410,6 +410,14 @@ __host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, flo
   const float bb = ef_add(s, -a);
   e = ef_add(ef_add(a, -ef_add(s, -bb)), ef_add(b, -bb));
 }
+// acc.x + acc.y += v: the rounding error of the sum goes to the correction term (a
+// compensated sum: over n terms its error is ~n ulp^2 of the total, FP64-like for n ~ 1e3)
+__host__ __device__ __forceinline__ void compensated_add(float2& acc, float v) {
+  float s, e;
+  two_sum(acc.x, v, s, e);
+  acc.x = s;
+  acc.y += e;
+}
 __host__ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
   p = ef_mul(a, b);
   e = fmaf(a, b, -p);

@@ -95,7 +95,7 @@ cudaError_t launch_gather_int(int64_t N, const int* perm, const int* src_caller,
 cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const float* src_internal,
                                 float* dst_caller, int identity_dim, int fix_rows, cudaStream_t s);
 cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, const float* nu,
-                                 const double* mubar, const double* labar, float* gE, float* gnu,
+                                 const float2* mubar, const float2* labar, float* gE, float* gnu,
                                  cudaStream_t s);
 // per-scene sums of x_T and x_0 (state rows, fixed-point positions) into com[scene][6];
 // part: com_scratch_doubles(n_scenes)

@@ -90,8 +90,9 @@ struct AdjArgs {
   float* adj;         // adjoint rows x, v, C, F
   const float* mu;
   const float* la;
-  double* mubar;      // dL/dmu, dL/dlambda per particle, summed over the steps in FP64: the
-  double* labar;      // per-step terms oscillate in sign over a long run and mostly cancel
+  float2* mubar;      // dL/dmu, dL/dlambda per particle, summed over the steps as compensated
+  float2* labar;      // FP32 (value, correction) pairs: the per-step terms oscillate in sign
+                      // over a long run and mostly cancel, so the sum needs ~48 bits
   const int* group;
   const int* matid;   // per-particle material (kMixed scenes) or null
   const float* wact;
@@ -1447,8 +1448,11 @@ __device__ __forceinline__ void adjoint_tile(const SimParams& P, const AdjArgs& 
     }
     if (ok) abar = kirchhoff_adjoint<D, MAT>(E, A.mu[p], A.la[p], act, axis, sc, tb, Fb, mub, lab, mat_p);
     if (active) {
-      A.mubar[p] += (double)mub;
-      A.labar[p] += (double)lab;
+      float2 ms = A.mubar[p], ls = A.labar[p];
+      compensated_add(ms, mub);
+      compensated_add(ls, lab);
+      A.mubar[p] = ms;
+      A.labar[p] = ls;
     }
     if (P.n_groups > 0) {
       // dL/dw_gk += basis_k * sum of abar over this tile's particles of group g, reduced in

@@ -147,16 +147,18 @@ __global__ void scatter_rows_kernel(int rows, int64_t N, const int* perm, const 
 }
 
 // chain rule of the Lame parameters: (mubar, labar) -> (Ebar, nubar), in FP64 (the two
-// terms of dL/dnu have opposite signs and nearly cancel)
+// terms of dL/dnu have opposite signs and nearly cancel); the sums arrive as compensated FP32
+// (value, correction) pairs
 __global__ void material_grad_kernel(int64_t N, const int* perm, const float* E, const float* nu,
-                                     const double* mubar, const double* labar, float* gE,
+                                     const float2* mubar, const float2* labar, float* gE,
                                      float* gnu) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = perm[i];
     const double Ee = E[i], v = nu[i];
     const double q = (1.0 + v) * (1.0 - 2.0 * v);
-    const double mb = mubar[i], lb = labar[i];
+    const double mb = (double)mubar[i].x + (double)mubar[i].y;
+    const double lb = (double)labar[i].x + (double)labar[i].y;
     if (gE) gE[e] = (float)(mb / (2.0 * (1.0 + v)) + lb * v / q);
     if (gnu) gnu[e] = (float)(-mb * Ee / (2.0 * (1.0 + v) * (1.0 + v)) + lb * Ee * (1.0 + 2.0 * v * v) / (q * q));
   }
@@ -307,7 +309,7 @@ cudaError_t launch_scatter_rows(int rows, int64_t N, const int* perm, const floa
 }
 
 cudaError_t launch_material_grad(int64_t N, const int* perm, const float* E, const float* nu,
-                                 const double* mubar, const double* labar, float* gE, float* gnu,
+                                 const float2* mubar, const float2* labar, float* gE, float* gnu,
                                  cudaStream_t s) {
   material_grad_kernel<<<grid_for(N), 256, 0, s>>>(N, perm, E, nu, mubar, labar, gE, gnu);
   return cudaGetLastError();
