@@ -12,8 +12,9 @@
  *   the full particle state every ckpt_every steps (Appendix D.2); mpm_backward
  *   re-simulates each segment and replays the step adjoints in reverse order,
  *   recomputing each step's grid (Appendix D.1, "advance_grad").
- *   Materials: fixed-corotated (polar factor and its adjoint in FP64) or
- *   neo-Hookean; optional actuation stress a_g(t) (F e)(F e)^T with
+ *   Materials: fixed-corotated (polar factor resolved to FP64 accuracy with
+ *   compensated FP32 arithmetic, FP32 adjoint; the build variant MPM_POLAR_FP64=1
+ *   forms both in FP64) or neo-Hookean; optional actuation stress a_g(t) (F e)(F e)^T with
  *   a_g(t) = sum_k w_gk sin(2 pi k t / act_period + act_phase), k = 1..n_basis
  *   (open loop), or a_g(t) = the output of a closed-loop controller evaluated on
  *   state t (the neural-network controllers of Section 4.1; see ctrl_hidden).
