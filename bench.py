@@ -241,10 +241,11 @@ class ClockSampler:
 
 
 def precision_label(desc):
-    """What the workload's passes compute in: FP32 throughout, FP64 only for the polar
-    factor of fixed-corotated particles."""
+    """What the workload's passes compute in: FP32 arithmetic, with the polar factor of
+    fixed-corotated particles resolved to FP64 accuracy by compensated FP32 arithmetic."""
     mat = desc.get("material", 0)
-    fcr = "FP32 state, grid and stress; FP64 polar decomposition and its adjoint"
+    fcr = ("FP32 state, grid and stress; polar factor resolved to FP64 accuracy in compensated "
+           "FP32, FP32 polar adjoint")
     nh = "FP32 throughout (neo-Hookean: J - 1 and ln J in FP32; no polar factor)"
     liq = "FP32 throughout (Tait liquid: J - 1, log1p/expm1 in FP32; no polar factor)"
     return {0: fcr, 1: nh, 3: liq,
@@ -260,7 +261,7 @@ def make_workload(name, seed=0):
         "cube3d": "3D elastic cube: 262,144 particles (64^3 lattice, 2/cell/axis), 128^3 grid, "
                   "neo-Hookean E=5e3 nu=0.3, dt=1e-4, T=1024, checkpoint every 64, COM loss",
         "robots3d": "16 batched 3D actuated robots x 65,536 particles, 64^3 grids, "
-                    "fixed-corotated (FP64 polar), 8 groups x 4 sine terms, T=2048, ckpt 64",
+                    "fixed-corotated, 8 groups x 4 sine terms, T=2048, ckpt 64",
         "rects2d": "64 batched 2D rectangles (1k-16k particles), 128^2 grids, T=512",
         "square2d_grad": "2D square 4,096 particles, 128^2 grid, T=512, ckpt 32",
         "robots_nn": "4 batched 3D robots x 27,648 particles, 64^3 grids, fixed-corotated, "
@@ -726,6 +727,8 @@ def main():
                     help="1: run each run of same-kind passes as one persistent launch")
     ap.add_argument("--opt", action="append", default=[], metavar="MPM_OPT_NAME=VALUE",
                     help="set a library option (include/mpm.h) for the run; repeatable")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="bitwise-reproducible fixed-point grid sums (deterministic_p2g = 1)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched configurations (rects2d, robots3d) that the default "
                          "cube3d line carries under 'batched'")
@@ -781,6 +784,8 @@ def main():
         T = args.T
     if args.ckpt_every:
         scene["desc"]["ckpt_every"] = args.ckpt_every
+    if args.deterministic:
+        scene["desc"]["deterministic_p2g"] = 1
     desc = scene["desc"]
     a = scene["arrays"]
     G = desc.get("n_groups", 0)
@@ -995,6 +1000,8 @@ def main():
                                    f"dp{world}: the batch's scenes sharded by particle count"
                                    if shard else f"dp{world}: one seeded batch per rank"),
                    "launch_form": "persistent" if args.persistent else "one launch per pass",
+                   "grid_sums": ("64-bit fixed point (deterministic)" if desc.get("deterministic_p2g")
+                                 else "FP32 atomics"),
                    "options": options or "library defaults"},
         "forward": {"value": N * T / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms,
                     "scope": "rank 0's scenes"},
