@@ -32,7 +32,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "particle-steps/s fwd+bwd (3D MLS-MPM, FP32 bulk, FP64 polar)"
+# the workload's headline metric; `value` is the forward+backward figure, the forward one is in
+# the line's `forward` object and the HBM fraction in `roofline`
+METRIC = ("particle-steps/s fwd and fwd+bwd (3D, FP32, grad err<=1e-3 vs FP64 oracle); "
+          "% HBM roofline")
 UNIT = "particle-steps/s"
 
 # algorithmic bytes per particle of each pass category (3D, FP32 state rows):
