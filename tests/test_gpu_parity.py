@@ -378,7 +378,7 @@ def test_kept_segment_grids_equal_recomputed_grids(mpm):
 
 
 def test_polar_cache_does_not_change_results(mpm):
-    """3D fixed-corotated: backward passes that read the FP64 polar factors cached by the
+    """3D fixed-corotated: backward passes that read the polar factors cached by the
     re-simulation give the gradients of the passes that recompute them (both against the
     oracle, and against each other to FP32 atomic-order rounding)."""
     scene = scenes.make("robots3d", n_scenes=2, dims=(16, 8, 8))
