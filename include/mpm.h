@@ -94,12 +94,15 @@ extern "C" {
                                      two backward passes that need it instead of recomputing
                                      it [1] */
 #define MPM_OPT_GRID_BLOCKS 6     /* CTAs per scene of the end-of-sequence grid clear; 0 = automatic [0] */
-#define MPM_OPT_PERSISTENT 8      /* 1: each run of same-kind passes (a whole forward; the
-                                     re-simulation and the adjoint passes of each backward
-                                     segment) is one cooperative launch of resident CTAs that
-                                     step through a recorded pass plan with a grid-wide
-                                     barrier between passes [0].  Results equal the
-                                     one-launch-per-pass form up to FP32 atomic order. */
+#define MPM_OPT_PERSISTENT 8      /* 1: each run of passes of one kind and one pass mode (the
+                                     fused steps of a forward; the re-simulation and the
+                                     adjoint passes of each backward segment, each split at
+                                     its first and last pass) is one cooperative launch of
+                                     resident CTAs that step through a recorded pass plan
+                                     with a grid-wide barrier between passes [0].  Results
+                                     equal the one-launch-per-pass form up to FP32 atomic
+                                     order; slower than it on this GPU (the interpreter spills
+                                     the parameters the per-pass kernels read as constants). */
 #define MPM_OPT_BARRIER_TIMEOUT_US 9 /* limit of one grid-barrier wait in the persistent form,
                                      microseconds, 1..6e8 [2000000].  A wait that runs out sets
                                      MPM_ERR_TIMEOUT (reported by mpm_sync_status, after which the
