@@ -10,7 +10,9 @@
 // identity keeps only ~1e-7/|strain| relative precision on the strain, E keeps 1e-7.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace mpm {
@@ -113,6 +115,60 @@ struct SimParams {
 // ---------------------------------------------------------------------------
 constexpr float kFixLimit = 36028797018963968.0f;  // 2^55
 
+// bit and conversion primitives of the fixed-point helpers below, with host versions so
+// that those helpers can be checked on the host
+__host__ __device__ __forceinline__ unsigned fx_float_bits(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, 4);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ float fx_bits_float(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+__host__ __device__ __forceinline__ int fx_f2i_rn(float f) {  // |f| < 2^31, ties to even
+#ifdef __CUDA_ARCH__
+  return __float2int_rn(f);
+#else
+  return (int)nearbyintf(f);
+#endif
+}
+__host__ __device__ __forceinline__ float fx_u2f_rn(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint2float_rn(u);
+#else
+  return (float)u;
+#endif
+}
+__host__ __device__ __forceinline__ int fx_clzll(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)u);
+#else
+  return u ? __builtin_clzll(u) : 64;
+#endif
+}
+
+// round(c) as a 64-bit integer for |c| <= 2^55, equal to __float2ll_rn(c) but without the
+// 64-bit conversion, which issues on the FP64 pipe (1/64 of the FP32 rate here): below 2^23
+// the 32-bit conversion rounds; from 2^23 on a float is an integer, its mantissa shifted by
+// its exponent
+__host__ __device__ __forceinline__ long long fix_round(float c) {
+  if (fabsf(c) < 8388608.0f) return (long long)fx_f2i_rn(c);
+  const unsigned b = fx_float_bits(c);
+  const int sh = (int)((b >> 23) & 0xFFu) - 150;  // 0 <= sh <= 32 for 2^23 <= |c| <= 2^55
+  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u) << sh;
+  return (b >> 31) ? -m : m;
+}
+
 // channels 0..nch-1 of v into the fixed-point node `node` of grid g (two float4 slots
 // per node); channel 0 is scaled by f0, the others by f1
 __device__ __forceinline__ void fix_red(float4* g, int64_t node, float4 v, float f0, float f1,
@@ -126,11 +182,29 @@ __device__ __forceinline__ void fix_red(float4* g, int64_t node, float4 v, float
       err |= kErrRange;
       continue;
     }
-    atomicAdd(q + k, (unsigned long long)__float2ll_rn(c[k]));
+    atomicAdd(q + k, (unsigned long long)fix_round(c[k]));
   }
 }
 
-// the fixed-point node as floats: channel 0 times u0, the others times u1
+// a 64-bit integer rounded to the nearest float (ties to even) with 32-bit integer and
+// conversion instructions only (the 64-bit conversion issues on the FP64 pipe)
+__host__ __device__ __forceinline__ float ll_to_float_rn(long long a) {
+  const bool neg = a < 0;
+  const unsigned long long u = neg ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  if (u < (1ull << 24)) {
+    const float f = fx_u2f_rn((unsigned)u);  // exact
+    return neg ? -f : f;
+  }
+  const int sh = 40 - fx_clzll(u);  // bits below a 24-bit mantissa, 1..40
+  unsigned long long m = u >> sh;
+  const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  if (rem > half || (rem == half && (m & 1ull))) ++m;  // may reach 2^24: still exact below
+  const float f = fx_u2f_rn((unsigned)m) * fx_bits_float((unsigned)(127 + sh) << 23);
+  return neg ? -f : f;
+}
+
+// the fixed-point node as floats: channel 0 times u0, the others times u1 (powers of two,
+// so each product is exact and the node value is rounded once, in ll_to_float_rn)
 template <bool NC>
 __device__ __forceinline__ float4 fix_load(const float4* g, int64_t node, float u0, float u1) {
   const longlong2* q = reinterpret_cast<const longlong2*>(g + 2 * node);
@@ -142,8 +216,8 @@ __device__ __forceinline__ float4 fix_load(const float4* g, int64_t node, float 
     a = q[0];
     b = q[1];
   }
-  return make_float4((float)((double)a.x * (double)u0), (float)((double)a.y * (double)u1),
-                     (float)((double)b.x * (double)u1), (float)((double)b.y * (double)u1));
+  return make_float4(ll_to_float_rn(a.x) * u0, ll_to_float_rn(a.y) * u1, ll_to_float_rn(b.x) * u1,
+                     ll_to_float_rn(b.y) * u1);
 }
 
 // scale pair of the velocity-adjoint grids of one backward from the largest contribution

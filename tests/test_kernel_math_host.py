@@ -1,4 +1,5 @@
-"""The compensated FP32 polar factors of the particle passes, run as host code.
+"""Arithmetic helpers of the particle passes run as host code: the compensated FP32 polar
+factors, and the fixed-point conversions of the deterministic grid sums.
 
 `polar_refine2` / `polar_refine3` (csrc/mpm_common.cuh) are host-and-device functions; here
 nvcc compiles them into a host program (tests/host/polar_refine_check.cu) that compares them
@@ -40,3 +41,19 @@ def test_compensated_polar_factors_match_extended_precision(tmp_path):
     assert f3 == 0 and r3 <= 1e-13 and d3 <= 5e-7, res
     n2, f2, r2, d2 = res["2d"]
     assert f2 == 0 and r2 <= 1e-13 and d2 <= 5e-7, res
+
+
+def test_fixed_point_conversions_match_the_c_library(tmp_path):
+    """fix_round (float -> nearest int64) and ll_to_float_rn (int64 -> nearest float) of the
+    deterministic grid sums, built as host code, agree with llrintf and the C cast on random
+    and halfway inputs (they replace conversions that issue on the GPU's FP64 pipe)."""
+    cc = _nvcc()
+    if cc is None:
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path / "fixed_point_check")
+    src = os.path.join(HERE, "host", "fixed_point_check.cu")
+    subprocess.run([cc, "-std=c++17", "-O2", "--expt-relaxed-constexpr", "-o", exe, src],
+                   check=True, capture_output=True, timeout=300)
+    n, bad_round, bad_float = map(int, subprocess.run([exe], check=True, capture_output=True,
+                                                      text=True, timeout=300).stdout.split())
+    assert n > 0 and bad_round == 0 and bad_float == 0, (n, bad_round, bad_float)
