@@ -21,8 +21,8 @@ steps) the random functional's dL/dE and dL/dnu come out 2.3e-2 and 1.3e-1 from 
 (every other block of every workload within its bar; cube3d's worst other block 1.3e-4).  They
 are sums over 1,024 steps of contractions of the stress adjoint with the cube's small strain
 (|J - 1| ~ 3e-6 in free flight), which the FP32 grid transfers do not resolve to 1e-3: summing
-them in FP64, storing positions in fixed point and pairing the stress adjoint's symmetric part
-left them unchanged, and FP32 storage of every stored quantity emulated in the FP64 oracle moves
+them in FP64, storing positions in fixed point, pairing the stress adjoint's symmetric part and
+accumulating the P2G-adjoint moment sum in FP64 left them unchanged, and FP32 storage of every stored quantity emulated in the FP64 oracle moves
 them 10x less than the GPU does, so the remaining error is FP32 arithmetic in the transfers
 (the fixed-point grid sums of the deterministic mode reduce it 2.5x on a 32,768-particle cube).
 """
