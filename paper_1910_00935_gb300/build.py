@@ -19,8 +19,6 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpm.so")
-OUT_DIR_POLAR64 = os.path.join(HERE, "_build_polar64")  # the polar_fp64 variant
-LIB_POLAR64 = os.path.join(OUT_DIR_POLAR64, "libmpm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["kernels_3d_fcr.cu", "kernels_3d_fcr_det.cu", "kernels_3d_nh.cu", "kernels_3d_nh_det.cu",
            "kernels_3d_liq.cu", "kernels_3d_liq_det.cu", "kernels_3d_mixed.cu",
@@ -56,6 +54,10 @@ def needs_build(out_dir: str = OUT_DIR) -> bool:
 def variant_dir(tag: str) -> str:
     """Build folder of a named variant (`_build_<tag>` beside the default `_build`)."""
     return OUT_DIR if not tag else os.path.join(HERE, f"_build_{tag}")
+
+
+# the library of the polar_fp64 variant (build(polar_fp64=True))
+LIB_POLAR64 = os.path.join(variant_dir("polar64"), "libmpm.so")
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=(), polar_fp64: bool = False,
