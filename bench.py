@@ -602,6 +602,28 @@ def fp64_roofline(mpm, workload, category, n_launch, cat_ms, particles_per_launc
     return out
 
 
+def scatter_roofline(mpm, prof, N, dim):
+    """Grid reductions per second of the scattering passes against this GPU's float4
+    reduction rate measured live (mpm_measure_peak): one float4 reduction per particle and
+    stencil node (3^dim), the work that bounds these L2-resident passes rather than bytes.
+    The recomputed P2G of a resident segment's adjoint passes is not counted."""
+    red = mpm.mpm_measure_peak(mpm.MPM_PEAK_RED_F32X4)
+    spread = mpm.mpm_measure_peak(mpm.MPM_PEAK_RED_F32X4_SPREAD)
+    out = {"bound": "l2_reductions", "unit": "float4 reductions/s", "peak": red,
+           "peak_spread": spread,
+           "peak_source": "measured live: mpm_measure_peak (float4 reductions, 32 lanes on 32 "
+                          "consecutive nodes; peak_spread: on 32 cache lines)",
+           "reductions_per_particle": 3 ** dim, "kernels": {}}
+    for cat in ("g2p_p2g", "g2p_p2g_full", "adj_fused"):
+        if cat in prof and prof[cat][0]:
+            n, ms = prof[cat]
+            avg = ms / n
+            ach = 3 ** dim * N / (avg / 1e3)
+            out["kernels"][cat] = {"achieved": ach, "frac": ach / red, "frac_spread": ach / spread,
+                                   "avg_launch_ms": avg}
+    return out
+
+
 def batched_line(name, dev, flush, steps=2, warmup=1, autotune_probe=True):
     """One batched configuration measured compactly for the headline's JSON line: forward and
     forward+backward particle-steps/s with inputs resident (L2 flushed between timed steps),
@@ -669,6 +691,7 @@ def batched_line(name, dev, flush, steps=2, warmup=1, autotune_probe=True):
             "value": N * T / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "forward": {"value": N * T / (fwd_ms / 1e3), "ms": fwd_ms},
             "roofline": roof, "roofline_fp64": roof64,
+            "roofline_scatter": scatter_roofline(mpm, prof, N, desc["dim"]),
             "kernel_times_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
             "precision": precision_label(desc)}
     # the same batch through persistent launches (each run of same-kind passes one launch)
@@ -1014,6 +1037,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roof,
+        "roofline_scatter": scatter_roofline(mpm, prof, N, desc["dim"]),
         "kernel_times_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
         "cpu_baseline": cb,
         "clocks": clk,

@@ -331,15 +331,22 @@ int mpm_initial_p2g_grid(mpm_handle* h, float* grid, void* stream);
 int mpm_plan_checkpoints(const mpm_scene_desc* desc, int32_t max_steps, size_t budget_bytes,
                          int32_t* ckpt_every, int32_t* ckpt_coarse, size_t* ws_bytes);
 
-/* Arithmetic peak of the current GPU, measured with the library's own kernel (8
- * independent fused multiply-add chains per thread, 8 CTAs of 256 threads per SM; an FMA
- * counts 2 FLOP; best of three timed launches after a warm-up, CUDA events on `stream`).
- * It is the denominator of the ALU rooflines of the particle passes.  kind:
- * MPM_PEAK_FP64_FMA or MPM_PEAK_FP32_FMA;
- * flops_per_s: host.  Blocks until the launches finish (a diagnostic, ~0.1 s).  Returns
- * MPM_OK, MPM_ERR_ARG or MPM_ERR_CUDA (message in mpm_last_error(NULL)). */
+/* Peaks of the current GPU, measured with the library's own kernels (best of three timed
+ * launches after a warm-up, CUDA events on `stream`, 8 CTAs of 256 threads per SM), the
+ * denominators of the ALU and scatter rooflines of the particle passes.  kind:
+ *   MPM_PEAK_FP64_FMA / MPM_PEAK_FP32_FMA: FLOP/s of 8 independent fused multiply-add
+ *     chains per thread (an FMA counts 2 FLOP);
+ *   MPM_PEAK_RED_F32X4: float4 reductions per second (atomicAdd(float4*), result unused)
+ *     into an L2-resident array of 2^18 nodes, the 32 lanes of an instruction on 32
+ *     consecutive nodes (4 cache lines: the best case);
+ *   MPM_PEAK_RED_F32X4_SPREAD: the same with the 32 lanes on 32 different cache lines.
+ * flops_per_s (host) receives the rate.  The reduction kernels write a fixed 4 MiB device
+ * array of the library (no allocation).  Blocks until the launches finish (a diagnostic,
+ * ~0.1 s).  Returns MPM_OK, MPM_ERR_ARG or MPM_ERR_CUDA (message in mpm_last_error(NULL)). */
 #define MPM_PEAK_FP64_FMA 0
 #define MPM_PEAK_FP32_FMA 1
+#define MPM_PEAK_RED_F32X4 2
+#define MPM_PEAK_RED_F32X4_SPREAD 3
 int mpm_measure_peak(int32_t kind, double* flops_per_s, void* stream);
 
 /* Message of the last failure on this handle (static storage if h is NULL). */

@@ -36,6 +36,24 @@ __global__ void __launch_bounds__(kThreads) fma_chains_kernel(int iters, T seed)
   if (s == (T)-1.2345e-30) g_peak_sink = (double)s;
 }
 
+// float4 reduction throughput: every thread issues `iters` reductions (results unused, so
+// they compile to RED) into an L2-resident array of nodes; SPREAD puts the 32 lanes of an
+// instruction on 32 different 128-byte lines (the scattered case), else on 32 consecutive
+// nodes (4 lines: the best case)
+constexpr unsigned kRedNodes = 1u << 18;  // 4 MiB of float4 nodes
+__device__ float4 g_red_nodes[kRedNodes];
+
+template <bool SPREAD>
+__global__ void __launch_bounds__(kThreads) red_kernel(int iters) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int it = 0; it < iters; ++it) {
+    const unsigned base = (warp * 1237u + (unsigned)it * 613u) * 32u;
+    const unsigned node = (SPREAD ? base + lane * 8u : base + lane) & (kRedNodes - 1u);
+    atomicAdd(&g_red_nodes[node], make_float4(1.0f, 1.0f, 1.0f, 1.0f));
+  }
+}
+
 template <typename T>
 int measure(double* out, cudaStream_t st) {
   int dev = 0, sms = 0;
@@ -79,11 +97,56 @@ int measure(double* out, cudaStream_t st) {
 
 }  // namespace
 
+template <bool SPREAD>
+int measure_red(double* out, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mpm::set_static_error("mpm_measure_peak: no CUDA device");
+    return MPM_ERR_CUDA;
+  }
+  const int blocks = sms * 8, iters = 256;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    mpm::set_static_error("mpm_measure_peak: cudaEventCreate failed");
+    return MPM_ERR_CUDA;
+  }
+  double best = 0.0;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, st);
+    red_kernel<SPREAD><<<blocks, kThreads, 0, st>>>(iters);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    const double updates = (double)iters * blocks * kThreads;
+    if (e == cudaSuccess && rep > 0 && ms > 0.0f && updates / (ms * 1e-3) > best)
+      best = updates / (ms * 1e-3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mpm::set_static_error(cudaGetErrorString(e));
+    return MPM_ERR_CUDA;
+  }
+  *out = best;
+  return MPM_OK;
+}
+
 extern "C" int mpm_measure_peak(int32_t kind, double* flops_per_s, void* stream) {
-  if (!flops_per_s || (kind != MPM_PEAK_FP64_FMA && kind != MPM_PEAK_FP32_FMA)) {
+  if (!flops_per_s || kind < MPM_PEAK_FP64_FMA || kind > MPM_PEAK_RED_F32X4_SPREAD) {
     mpm::set_static_error("mpm_measure_peak: bad kind or NULL output");
     return MPM_ERR_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return kind == MPM_PEAK_FP64_FMA ? measure<double>(flops_per_s, s) : measure<float>(flops_per_s, s);
+  switch (kind) {
+    case MPM_PEAK_FP64_FMA: return measure<double>(flops_per_s, s);
+    case MPM_PEAK_FP32_FMA: return measure<float>(flops_per_s, s);
+    case MPM_PEAK_RED_F32X4: return measure_red<false>(flops_per_s, s);
+    default: return measure_red<true>(flops_per_s, s);
+  }
 }

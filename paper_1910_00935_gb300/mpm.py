@@ -237,11 +237,12 @@ def mpm_initial_p2g_grid(h, grid, stream=None):
     _check(lib().mpm_initial_p2g_grid(h, _ptr(grid), _stream(stream)), h)
 
 
-MPM_PEAK_FP64_FMA, MPM_PEAK_FP32_FMA = 0, 1
+MPM_PEAK_FP64_FMA, MPM_PEAK_FP32_FMA, MPM_PEAK_RED_F32X4, MPM_PEAK_RED_F32X4_SPREAD = 0, 1, 2, 3
 
 
 def mpm_measure_peak(kind: int, stream=None) -> float:
-    """Measured FMA peak (FLOP/s) of the current GPU: MPM_PEAK_FP64_FMA or MPM_PEAK_FP32_FMA."""
+    """Measured peak of the current GPU: FLOP/s for MPM_PEAK_FP64_FMA / MPM_PEAK_FP32_FMA,
+    float4 reductions per second for MPM_PEAK_RED_F32X4 / MPM_PEAK_RED_F32X4_SPREAD."""
     out = ctypes.c_double()
     _check(lib().mpm_measure_peak(int(kind), ctypes.byref(out), _stream(stream)))
     return out.value

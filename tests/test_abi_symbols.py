@@ -141,6 +141,12 @@ def test_measured_peaks_are_sane(libpath):
     assert 1e11 < f64 < 2e13, f64
     assert 1e13 < f32 < 1e14, f32
     assert f32 > 4 * f64
+    # float4 reductions per second: the scatter roofline's denominators; lanes on 32
+    # consecutive nodes touch 4 cache lines, on 32 spread nodes 32, so the spread rate is
+    # the lower one
+    red = mpm.mpm_measure_peak(mpm.MPM_PEAK_RED_F32X4)
+    spread = mpm.mpm_measure_peak(mpm.MPM_PEAK_RED_F32X4_SPREAD)
+    assert 1e10 < spread <= 1.1 * red < 1e13, (spread, red)
 
 
 def test_planned_schedule_fits_budget_and_prefers_fewer_passes(libpath):
