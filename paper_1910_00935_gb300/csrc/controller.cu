@@ -9,8 +9,9 @@
 //   h = tanh(W1 u + b1) (H units), a_g = scale tanh(W2 h + b2)_g
 //   theta per scene = [W1 (H x n_in, row-major) | b1 (H) | W2 (G x H, row-major) | b2 (G)]
 //
-// Weights arrive in FP32; a tile's sensor sums are FP32, the sums over tiles and the MLP FP64
-// (a few thousand operations per scene and step).  Every sum runs in a fixed order (a
+// Weights arrive in FP32; a tile's sensor sums are FP32, the sums over tiles, the inputs and
+// the MLP's dot products FP64 (a few thousand operations per scene and step, one warp per
+// dot product), the activations tanh in FP32.  Every sum runs in a fixed order (a
 // tile's particles in order, a scene's tiles in order), so the controller adds nothing
 // order-dependent to a deterministic run.
 #include "mpm_internal.h"
@@ -63,6 +64,14 @@ __device__ void block_tile_sums(T* a, int t0, int t1, int stride, int nv, bool c
     out[threadIdx.x] = v;
   }
   __syncthreads();
+}
+
+// sum of v over the 32 lanes of the warp, the same butterfly order on every run (all lanes
+// must call it)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // Per-tile sums of x, v and the particle count by group slot, in particle order:
@@ -146,20 +155,32 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_forward_kernel(CtrlStep cs,
   const float* b1 = th + H * n_in;
   const float* W2 = b1 + H;
   const float* b2 = W2 + G * H;
-  for (int j = threadIdx.x; j < H; j += blockDim.x) {
-    double z = (double)b1[j];
-    for (int i = 0; i < n_in; ++i) z += (double)W1[j * n_in + i] * u[i];
-    const double hj = tanh(z);
-    hs[j] = hj;
-    h_out[(int64_t)s * H + j] = hj;
+  // one warp per hidden unit (then per output): its lanes take the dot product's terms and
+  // a butterfly sums them, instead of one thread running the whole chain while the CTA
+  // waits at the barrier
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n_warps = blockDim.x >> 5;
+  for (int j = warp; j < H; j += n_warps) {
+    double z = 0.0;
+    for (int i = lane; i < n_in; i += 32) z += (double)W1[j * n_in + i] * u[i];
+    z = warp_sum(z);
+    if (lane == 0) {
+      // the activation in FP32: FP64 transcendentals run on the FP64 pipe (1/64 of the FP32
+      // rate here) and made these one-CTA-per-scene kernels latency chains
+      const double hj = (double)tanhf((float)(z + (double)b1[j]));
+      hs[j] = hj;
+      h_out[(int64_t)s * H + j] = hj;
+    }
   }
   __syncthreads();
-  for (int g = threadIdx.x; g < G; g += blockDim.x) {
-    double z = (double)b2[g];
-    for (int j = 0; j < H; ++j) z += (double)W2[g * H + j] * hs[j];
-    const double y = tanh(z);
-    y_out[(int64_t)s * G + g] = y;
-    act_out[(int64_t)s * G + g] = (float)((double)cs.scale * y);
+  for (int g = warp; g < G; g += n_warps) {
+    double z = 0.0;
+    for (int j = lane; j < H; j += 32) z += (double)W2[g * H + j] * hs[j];
+    z = warp_sum(z);
+    if (lane == 0) {
+      const double y = (double)tanhf((float)(z + (double)b2[g]));
+      y_out[(int64_t)s * G + g] = y;
+      act_out[(int64_t)s * G + g] = (float)((double)cs.scale * y);
+    }
   }
 }
 
@@ -213,10 +234,14 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_backward_kernel(CtrlStep cs
   }
   __syncthreads();
   for (int e = threadIdx.x; e < H * n_in; e += blockDim.x) W1b[e] += z1b[e / n_in] * u[e % n_in];
-  for (int i = threadIdx.x; i < n_in; i += blockDim.x) {
-    double acc = 0.0;
-    for (int j = 0; j < H; ++j) acc += (double)W1[j * n_in + i] * z1b[j];
-    ub[i] = acc;
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n_warps = blockDim.x >> 5;
+    for (int i = warp; i < n_in; i += n_warps) {  // one warp per input, as in the forward
+      double acc = 0.0;
+      for (int j = lane; j < H; j += 32) acc += (double)W1[j * n_in + i] * z1b[j];
+      acc = warp_sum(acc);
+      if (lane == 0) ub[i] = acc;
+    }
   }
   __syncthreads();
   // u_xg = mean_{p in g} x_p - mean_p x_p: every particle carries -sum_g ub_xg / N, and
